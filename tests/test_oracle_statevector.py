@@ -1,0 +1,136 @@
+"""Pins of the oracle's statevector functions (Eq. 1, 3, 4, 5, 6)."""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import bruteforce as bf
+from oracle import mapping, pool, statevector as sv
+from oracle.pauli import PauliTable
+from synth import molecular_integrals, random_state, config_integrals
+
+
+def _random_table(n, t, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 1 << n, size=t)
+    z = rng.integers(0, 1 << n, size=t)
+    ph = rng.integers(0, 4, size=t)
+    c = rng.normal(size=t)
+    return PauliTable(n, x.astype(np.int64), z.astype(np.int64), ph.astype(np.int64), c)
+
+
+@pytest.mark.parametrize("n", [1, 3, 6, 9])
+def test_apply_matches_kronecker_matrices(n):
+    t = _random_table(n, 40, seed=n)
+    psi = random_state(n, seed=100 + n)
+    assert np.max(np.abs(sv.apply_terms(t, psi) - bf.table_dense(t) @ psi)) < 1e-12
+    rows = np.arange(0, 1 << n, 3)
+    assert np.max(np.abs(sv.apply_terms_at(t, psi, rows) - (bf.table_dense(t) @ psi)[rows])) < 1e-12
+
+
+@pytest.mark.parametrize("mp", ["jw", "bk"])
+def test_hamiltonian_apply_matches_ladder_matrix(mp):
+    ints = molecular_integrals(4, seed=11, decay=True)
+    t = mapping.hamiltonian_table(ints, mp)
+    perm = bf.permutation_from_gf2(bf.srl_beta(8)) if mp == "bk" else np.eye(256)
+    hd = perm @ bf.hamiltonian_dense(ints) @ perm.T
+    psi = random_state(8, seed=5)
+    assert np.max(np.abs(sv.apply_terms(t, psi) - hd @ psi)) < 1e-12
+    e = sv.energy(t, psi)
+    assert abs(e - np.vdot(psi, hd @ psi).real) < 1e-12
+
+
+def test_taylor_chain_vs_expm_and_truncation_bound():
+    nq, ne = 6, 2
+    tabs = pool.pool_tables(nq, ne, "jw")
+    psi = random_state(nq, seed=1)
+    for t in tabs[:6]:
+        a = bf.table_dense(t)
+        for th in (0.05, -0.2, 0.7):
+            exact = sla.expm(th * a) @ psi
+            got = sv.taylor5(t, th, psi)
+            # per active pair T5 - exp = (c5 - cos) I + (s5 - sin) A, ||A|| = 1
+            bound = abs(th) ** 6 / 720 + abs(th) ** 7 / 5040 + 1e-14
+            assert np.linalg.norm(got - exact) <= bound * 1.0001
+            # closed form of the truncated series on each pair
+            c5 = 1 - th ** 2 / 2 + th ** 4 / 24
+            s5 = th - th ** 3 / 6 + th ** 5 / 120
+            a2 = a @ a
+            closed = psi + s5 * (a @ psi) + (1 - c5) * (a2 @ psi)
+            assert np.max(np.abs(got - closed)) < 1e-14
+
+
+def test_taylor_derivative_is_series_derivative():
+    nq, ne = 6, 2
+    tabs = pool.pool_tables(nq, ne, "jw")
+    psi = random_state(nq, seed=2)
+    h = 1e-6
+    for t in tabs[::4]:
+        for th in (0.1, -0.6):
+            fd = (sv.taylor5(t, th + h, psi) - sv.taylor5(t, th - h, psi)) / (2 * h)
+            assert np.max(np.abs(sv.taylor5_derivative(t, th, psi) - fd)) < 1e-9
+
+
+def test_gradients_equal_commutator_and_append_derivative():
+    ints = molecular_integrals(3, seed=4, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw")
+    tabs = pool.pool_tables(6, 2, "jw")
+    psi = random_state(6, seed=8)
+    g = sv.pool_gradients(h, tabs, psi)
+    hd = bf.table_dense(h)
+    pn = psi / np.linalg.norm(psi)
+    for k, t in enumerate(tabs):
+        a = bf.table_dense(t)
+        comm = np.vdot(pn, (hd @ a - a @ hd) @ pn)
+        assert abs(comm.imag) < 1e-13
+        assert abs(g[k] - comm.real) < 1e-12
+        eps = 1e-5
+        ep = sv.energy(h, sv.taylor5(t, eps, psi))
+        em = sv.energy(h, sv.taylor5(t, -eps, psi))
+        assert abs(g[k] - (ep - em) / (2 * eps)) < 1e-8
+
+
+def test_energy_grad_forward_mode_vs_central_differences():
+    ints = molecular_integrals(3, seed=2, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw")
+    tabs = pool.pool_tables(6, 2, "jw")
+    ref = sv.basis_state(6, mapping.hf_index("jw", 6, 2))
+    rng = np.random.default_rng(3)
+    ops = rng.integers(0, len(tabs), size=6)
+    th = rng.normal(0, 0.3, size=6)
+    e, grad = sv.energy_grad(h, ref, tabs, ops, th)
+    assert abs(e - sv.energy(h, sv.prepare_state(ref, tabs, ops, th))) < 1e-14
+    hstep = 1e-5
+    for j in range(len(ops)):
+        tp, tm = th.copy(), th.copy()
+        tp[j] += hstep
+        tm[j] -= hstep
+        fd = (sv.energy(h, sv.prepare_state(ref, tabs, ops, tp))
+              - sv.energy(h, sv.prepare_state(ref, tabs, ops, tm))) / (2 * hstep)
+        assert abs(fd - grad[j]) < 1e-8
+
+
+def test_rayleigh_quotient_scale_invariant_and_fidelity():
+    ints, c = config_integrals("c1_4q")
+    h = mapping.hamiltonian_table(ints, "jw")
+    psi = random_state(4, seed=0, normalize=False)
+    assert abs(sv.energy(h, psi) - sv.energy(h, 3.7 * psi)) < 1e-13
+    assert abs(sv.fidelity(psi, (0.5 - 2j) * psi) - 1.0) < 1e-14
+    other = random_state(4, seed=1)
+    assert sv.fidelity(psi, other) < 1.0
+
+
+def test_sector_preserved_by_taylor():
+    nq, ne = 8, 4
+    tabs = pool.pool_tables(nq, ne, "jw")
+    ref = sv.basis_state(nq, mapping.hf_index("jw", nq, ne))
+    rng = np.random.default_rng(0)
+    psi = sv.prepare_state(ref, tabs, rng.integers(0, len(tabs), 12), rng.normal(0, 0.3, 12))
+    nn, sz = bf.number_ops(nq)
+    outside = (nn != ne) | (sz != 0)
+    # exact arithmetic keeps the sector; string-by-string float sums leave
+    # only rounding residue outside it
+    assert np.max(np.abs(psi[outside])) < 1e-15
+    assert np.linalg.norm(psi[~outside]) > 0.9
