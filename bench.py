@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""ADAPT-iteration benchmark of the GB300 GOCP ADAPT-VQE hot path.
+
+Workload (one GPU): 24 qubits = 12 spatial orbitals, 8 electrons, seeded
+molecular-shaped integrals with off-diagonal decay, integrals |v| < 1e-3
+dropped, Jordan-Wigner, 1424-operator singles+doubles pool, complex64 state
+(128 MiB), a 100-operator ansatz drawn from the pool with angles N(0, 0.05).
+
+One step = one ADAPT iteration with a one-evaluation re-optimisation budget:
+  1. prepare psi(theta) (100 fused O(5) Taylor steps), H psi, E, all 1424 pool
+     gradients, argmax selection                         (gocp_adapt_step)
+  2. E and dE/dtheta of the grown 101-operator ansatz by the adjoint sweep
+                                                         (gocp_energy_grad)
+`value` times steps with the ansatz, states and outputs resident on the
+device; `e2e` times the same step through the host-array API (ansatz copied
+in from pinned memory, E / gradients / dE copied out every step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gocp|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the path has
+no exchange step): value = iterations of all ranks / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import config_integrals, draw_ansatz  # noqa: E402
+
+WORKLOAD = "c5_24q"
+N_OPS = 100
+N_ELEC = 8
+METRIC = "ADAPT iterations/s (24 qubits, complex64, 1424-op pool, 100-op ansatz + adjoint dE/dtheta)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world, device):
+    import torch
+    import paper_2607_15906_gb300 as gb
+    from paper_2607_15906_gb300 import _lib
+
+    torch.cuda.set_device(device)
+    gb.load()
+    ints, cfg = config_integrals(WORKLOAD)
+    prob = gb.Problem.build(ints, N_ELEC, mapping="jw", precision=args.precision,
+                            int_drop=cfg["int_drop"], term_drop=cfg["term_drop"], device=device)
+    m = prob.pool_size
+    ops, theta = draw_ansatz(m, N_OPS, seed=0)
+    dev = f"cuda:{device}"
+    ops_d = torch.from_numpy(ops).to(dev)
+    th_d = torch.from_numpy(theta).to(dev)
+    ops_g = torch.zeros(N_OPS + 1, dtype=torch.int32, device=dev)
+    ops_g[:N_OPS] = ops_d
+    th_g = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    th_g[:N_OPS] = th_d
+    ws = prob.workspace()
+    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
+    grads = torch.zeros(m, dtype=torch.float64, device=dev)
+    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    e_out = torch.zeros(1, dtype=torch.float64, device=dev)
+    de_out = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+
+    def step_device():
+        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-4, out=(e2, grads, sel))
+        ops_g[N_OPS:].copy_(sel)                       # append the selected operator, theta = 0
+        prob.energy_grad(ops_g, th_g, ws=ws, out_e=e_out, out_de=de_out)
+
+    pin_ops = torch.from_numpy(ops).pin_memory().numpy()
+    pin_th = torch.from_numpy(theta).pin_memory().numpy()
+    pin_og = torch.zeros(N_OPS + 1, dtype=torch.int32).pin_memory().numpy()
+    pin_tg = torch.zeros(N_OPS + 1, dtype=torch.float64).pin_memory().numpy()
+    pin_og[:N_OPS] = ops
+    pin_tg[:N_OPS] = theta
+    h2d = pin_ops.nbytes + pin_th.nbytes + pin_og.nbytes + pin_tg.nbytes
+    d2h = 16 + 8 * m + 4 + 8 + 8 * (N_OPS + 1)
+
+    def step_host():
+        e, nrm, g, s = prob.adapt_step(pin_ops, pin_th, ws=ws, tie_rel=1e-4)
+        pin_og[N_OPS] = s
+        prob.energy_grad(pin_og, pin_tg, ws=ws)
+
+    stream = torch.cuda.current_stream(device)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return a.elapsed_time(b) / 1e3
+
+    # ---- device-resident timed region, with kernel timing and clock sampling
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    _lib.profile_enable(True)
+    for kind in range(4):
+        _lib.profile_read(kind)
+    launches0 = gb.launch_count()
+    with ClockSampler(device) as clk:
+        secs = timed(step_device, args.steps, 0)
+    launches = gb.launch_count() - launches0
+    _lib.profile_enable(False)
+    kern = {name: _lib.profile_read(kind) for kind, name in
+            enumerate(["apply_h", "taylor5", "pool_grad", "adjoint"])}
+    clocks = clk.summary()
+    # ---- end-to-end through the host-array API
+    e2e_secs = timed(step_host, args.steps, 1)
+
+    if world > 1:
+        t = torch.tensor([secs, e2e_secs], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs, e2e_secs = float(t[0]), float(t[1])
+    info = prob.info
+    return dict(prob=prob, secs=secs, e2e_secs=e2e_secs, kern=kern, clocks=clocks, launches=launches,
+                h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]))
+
+
+def roofline(res, peaks, how):
+    """Dominant kernel vs its roof (see the design doc for the per-unit figures)."""
+    info = res["info"]
+    n = info["n_qubits"]
+    dim = 1 << n
+    kern = res["kern"]
+    tot = {k: v[1] for k, v in kern.items()}
+    top = max(tot, key=tot.get)
+    launches, ms = kern[top]
+    per_launch_s = ms / 1e3 / max(launches, 1)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if top == "apply_h":
+        t, g = info["n_terms"], info["n_groups"]
+        # per amplitude: one signed add per term, one complex x real multiply-add per group
+        flops = dim * (t + 4 * g)
+        achieved = flops / per_launch_s / 1e12
+        out = {"kernel": "k_apply_h", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+               "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
+               "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)"}
+    else:
+        state = dim * 8
+        per = {"taylor5": 2 * state, "adjoint": 4 * state, "pool_grad": 2 * state}[top]
+        achieved = per / per_launch_s / 1e9
+        out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+               "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs"}
+    out["traffic"] = None
+    out["launch_ms"] = per_launch_s * 1e3
+    out["launches_per_step"] = launches / max(1, res.get("steps", 1))
+    return out
+
+
+def cpu_baseline_sample(target_s: float = 12.0):
+    """Times the oracle's term-by-term Pauli application on the full 2^24 state
+    and scales by the term applications one oracle ADAPT iteration makes."""
+    from oracle import mapping, pool as opool, statevector as sv
+
+    ints, cfg = config_integrals(WORKLOAD)
+    h = mapping.hamiltonian_table(ints, "jw", cfg["int_drop"], cfg["term_drop"])
+    tabs = opool.pool_tables(24, N_ELEC, "jw")
+    ops, theta = draw_ansatz(len(tabs), N_OPS, seed=0)
+    psi = sv.basis_state(24, mapping.hf_index("jw", 24, N_ELEC)) * (1 + 0j)
+    sub = type(h)(h.n, h.x[:1], h.z[:1], h.phase[:1], h.coeff[:1])
+    t0 = time.perf_counter()
+    applied = 0
+    while time.perf_counter() - t0 < target_s:
+        sv.apply_terms(sub, psi)
+        applied += 1
+    per_term = (time.perf_counter() - t0) / applied
+    strings = [len(tabs[k]) for k in ops]
+    s_op = float(np.mean(strings))
+    p = N_OPS
+    # oracle ADAPT iteration: prepare (5 chained applies per op), pool_gradients
+    # (H psi + every generator), energy_grad (prepare + H psi + P+1 forward-mode
+    # re-preparations of the P+1-op ansatz)
+    prep = 5 * s_op * p
+    pool_g = len(h) + sum(len(t) for t in tabs)
+    eg = (p + 2) * 5 * s_op * (p + 1) + len(h)
+    count = prep + len(h) + pool_g + eg
+    secs = count * per_term
+    return {"value": 1.0 / secs, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{applied} single-term applications of oracle.statevector.apply_terms on the "
+                      f"2^24 state ({per_term:.3f} s each), scaled by the {count:.3g} term applications "
+                      f"of one oracle iteration"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gocp", choices=["gocp", "reference"])
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    config = {"workload": "24q ADAPT iteration: 12 orbitals, 8 electrons, JW, int_drop 1e-3, "
+                          "1424-op pool, 100-op ansatz, theta~N(0,0.05), seed 0",
+              "qubits": 24, "ansatz_ops": N_OPS, "pool": 1424, "mapping": "jw",
+              "l2": "working set 256 MiB (2 states) > 129 MB L2; no flush",
+              "parallelism": f"replicas x{args.gpus}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        warm = max(args.warmup, 0)
+        vals = []
+        for i in range(warm + args.steps):
+            r = cpu_baseline_sample(target_s=4.0)
+            if i >= warm:
+                vals.append(1.0 / r["value"])
+        secs = float(np.mean(vals))
+        value = 1.0 / secs
+        line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": config, "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                                 "sample": r["sample"]},
+                "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    res = run_gpu(args, rank, world, local)
+    res["steps"] = args.steps
+    peaks, how = _peaks()
+    if rank == 0:
+        secs = res["secs"]
+        value = world * args.steps / secs
+        e2e = world * args.steps / res["e2e_secs"]
+        roof = roofline(res, peaks, how)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline_sample()
+        kern = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+                for k, v in res["kern"].items()}
+        line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic", "config": config,
+                "e2e": {"value": e2e, "unit": "iterations/s", "h2d_bytes_per_step": res["h2d"],
+                        "d2h_bytes_per_step": res["d2h"]},
+                "gpu_launches": res["launches"], "roofline": roof, "cpu_baseline": cpu,
+                "clocks": res["clocks"], "kernels": kern, "energy": res["e"], "selected": res["sel"]}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

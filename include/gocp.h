@@ -1,0 +1,278 @@
+/*
+ * gocp.h -- C ABI of the GB300 (sm_103a) GOCP ADAPT-VQE hot path.
+ *
+ * The method (arxiv 2607.15906) evolves a 2^n complex statevector under
+ * qubit-mapped Pauli sums: the Hamiltonian H = sum_p c_p P_p of Eq. (3) and
+ * anti-Hermitian excitation generators A_k from an operator pool.  This
+ * library implements, on one GPU:
+ *   - the host build: integrals -> Eq. (2) -> Jordan-Wigner / Bravyi-Kitaev
+ *     Pauli table (Sec. II.A), the singles+doubles pool (Table II) and the
+ *     Greedy Operator Commutativity Partitioning of the pool (Sec. III.A,
+ *     Algorithm 1);
+ *   - matrix-free H psi and the energy <psi|H|psi>/<psi|psi> (Eq. 1);
+ *   - the chained fifth-order Taylor propagator (Eq. 5, Eq. 6);
+ *   - the pool gradients g_k = <psi|[H, A_k]|psi> = 2 Re <H psi|A_k psi>
+ *     (Eq. 4);
+ *   - dE/dtheta of the whole ansatz by an adjoint sweep of the Taylor chain;
+ *   - a continuous-batching request server for energy+gradient solves.
+ *
+ * Conventions shared by every entry point
+ *   Pauli term (x, z, phase, coeff) = coeff * i^phase * X^x Z^z, with x, z
+ *     uint32 bit masks (bit j = qubit j, so n <= 30 here) and Z applied
+ *     first: it maps |b> to coeff * i^phase * (-1)^popcount(b & z) |b ^ x>.
+ *   Spin-orbital i = 2p + sigma (sigma 0 alpha, 1 beta) sits on qubit i.
+ *   A state is an interleaved complex array of 2^n amplitudes, index bit j =
+ *     qubit j: float2 (re, im) for GOCP_C64, double2 for GOCP_C128.
+ *   The ansatz applies ops[0] first: psi = T(theta[P-1] A_ops[P-1]) ...
+ *     T(theta[0] A_ops[0]) |ref>, T the O(5) Taylor series of exp.
+ *   Every call returns a status code (GOCP_OK or a negative GOCP_E*); the
+ *     message of the calling thread's last failure is in gocp_last_error().
+ *     No call traps the device or throws across the ABI.
+ *   Inputs passed by pointer are read (and copied where kept) during the
+ *     call; the caller keeps ownership.  Objects returned through ** are
+ *     owned by the library until the matching _free / _destroy.
+ *   Device buffers (states, workspaces, GOCP_MEM_DEVICE arrays) are
+ *     caller-owned device memory on the problem's device.  `stream` is a
+ *     cudaStream_t (NULL = legacy default stream); work is enqueued on it.
+ *     Calls with GOCP_MEM_HOST outputs synchronise that stream before they
+ *     return; GOCP_MEM_DEVICE calls return without synchronising.
+ *   Calls that compute on the same problem share the problem's reduction
+ *     scratch, so they must be ordered (one stream, or externally
+ *     serialised).  Different problems are independent.
+ */
+#ifndef GOCP_H
+#define GOCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GOCP_OK = 0,
+  GOCP_EINVAL = -1,     /* bad argument; nothing was enqueued */
+  GOCP_ENOMEM = -2,     /* host or device allocation failed */
+  GOCP_ECUDA = -3,      /* a CUDA runtime call failed */
+  GOCP_EAGAIN = -4,     /* result not ready (poll with zero timeout) */
+  GOCP_ETIMEDOUT = -5,  /* wait ran out */
+  GOCP_ECANCELED = -6,  /* request was cancelled */
+  GOCP_ENODEV = -7      /* no device tables (host-only problem) or no GPU */
+};
+enum { GOCP_JW = 0, GOCP_BK = 1 };          /* qubit mapping, Sec. II.A */
+enum { GOCP_C64 = 0, GOCP_C128 = 1 };       /* amplitude precision */
+enum { GOCP_MEM_HOST = 0, GOCP_MEM_DEVICE = 1 };
+enum { GOCP_BUILD_NO_COLOURING = 1 };       /* gocp_build_args.flags */
+
+typedef struct gocp_problem gocp_problem;
+typedef struct gocp_server gocp_server;
+
+/* ------------------------------------------------------------------ build */
+
+/* Spatial-orbital integrals of Eq. (2) (h_ijkl read as <ij|kl> = (ik|jl)):
+ *   H = e0 + sum_{pq,s} h[p*n+q] a+_{ps} a_{qs}
+ *          + 1/2 sum_{pqrs,s,t} g[((p*n+q)*n+r)*n+s] a+_{ps} a+_{rt} a_{st} a_{qs}
+ * with g in chemist order (pq|rs) and the 8-fold symmetry of real orbitals.
+ * int_drop zeroes integrals with |v| < int_drop before mapping; mapped terms
+ * are summed exactly (one rounding per term) and those with |c| < term_drop
+ * dropped.  Pool: spin-conserving singles then doubles over occupied
+ * spin-orbitals 0..n_elec-1 (Table II counts).  device >= 0 uploads the
+ * tables to that CUDA device; device = -1 builds host tables only (export
+ * works, compute calls return GOCP_ENODEV). */
+typedef struct {
+  int n_orb;            /* spatial orbitals; qubits = 2*n_orb, 1..15 */
+  int n_elec;           /* electrons, 0..2*n_orb */
+  int mapping;          /* GOCP_JW | GOCP_BK */
+  int precision;        /* GOCP_C64 | GOCP_C128 */
+  const double* h;      /* n_orb^2, row-major, symmetric */
+  const double* g;      /* n_orb^4, chemist order */
+  double e0;            /* constant energy */
+  double int_drop;      /* >= 0 */
+  double term_drop;     /* >= 0 */
+  int device;           /* CUDA ordinal, or -1 */
+  int flags;            /* GOCP_BUILD_* bits */
+} gocp_build_args;
+
+/* Build a problem from integrals (Eq. 2 -> Eq. 3, pool, Algorithm 1).
+ * Returns GOCP_EINVAL on bad sizes or pointers, GOCP_ENOMEM / GOCP_ECUDA on
+ * allocation or upload failure; *out is set only on success. */
+int gocp_build(const gocp_build_args* args, gocp_problem** out);
+
+/* Build a problem from caller-supplied Pauli tables (any Hermitian H and
+ * any generators).  Terms need not be sorted or unique: duplicates are
+ * summed exactly.  Generator k is strings [op_offsets[k], op_offsets[k+1])
+ * and must be a single x-mask group with x != 0 (one pair per basis state,
+ * as every fermionic excitation is).  ref_index is the reference basis
+ * state.  GOCP families are computed unless GOCP_BUILD_NO_COLOURING is set
+ * (the commutator test needs generator coefficients that are multiples of
+ * 1/8; otherwise GOCP_EINVAL). */
+typedef struct {
+  int n_qubits;                 /* 1..30 */
+  int precision;
+  int device;
+  int flags;
+  int64_t n_terms;
+  const uint32_t* x;
+  const uint32_t* z;
+  const uint8_t* phase;         /* 0..3 */
+  const double* coeff;
+  int n_ops;
+  const int64_t* op_offsets;    /* n_ops + 1, non-decreasing from 0 */
+  const uint32_t* op_x;
+  const uint32_t* op_z;
+  const uint8_t* op_phase;
+  const double* op_coeff;
+  uint32_t ref_index;
+} gocp_table_args;
+int gocp_build_from_tables(const gocp_table_args* args, gocp_problem** out);
+
+typedef struct {
+  int n_qubits;
+  int n_elec;             /* -1 for table-built problems */
+  int mapping;            /* -1 for table-built problems */
+  int precision;
+  int device;             /* -1: host tables only */
+  int pool_size;          /* M */
+  int n_families;         /* K of Algorithm 1, 0 if not coloured */
+  uint32_t ref_index;     /* reference basis state */
+  int64_t n_terms;        /* T */
+  int64_t n_groups;       /* distinct x masks of H */
+  int64_t n_pool_strings;
+  size_t device_bytes;    /* device memory held by the problem */
+} gocp_info;
+int gocp_problem_info(const gocp_problem* p, gocp_info* out);
+
+/* Copy H's table out, sorted by (x, z) ascending; arrays sized n_terms. */
+int gocp_export_terms(const gocp_problem* p, uint32_t* x, uint32_t* z, uint8_t* phase, double* coeff);
+
+/* Copy the pool out: op_offsets (pool_size+1), strings (n_pool_strings,
+ * each generator's strings sorted by z), family (pool_size; -1 when not
+ * coloured).  Any pointer may be NULL to skip that array. */
+int gocp_export_pool(const gocp_problem* p, int64_t* op_offsets, uint32_t* x, uint32_t* z,
+                     uint8_t* phase, double* coeff, int32_t* family);
+
+void gocp_problem_free(gocp_problem* p);
+
+/* Correctly rounded (round-half-even) value of the exact sum of v[0..n-1],
+ * the summation the builder uses for every Pauli coefficient. */
+int gocp_exact_sum(const double* v, int64_t n, double* out);
+
+/* ---------------------------------------------------------------- compute */
+
+/* Bytes of one state: 2^n * (8 for C64, 16 for C128). */
+size_t gocp_state_bytes(const gocp_problem* p);
+
+/* psi <- |ref>. */
+int gocp_reference_state(const gocp_problem* p, void* psi, void* stream);
+
+/* psi <- T(theta_{P-1} A_{ops[P-1]}) ... T(theta_0 A_{ops[0]}) |ref>, each T
+ * the literal chain of Eq. (6): v_0 = psi, v_m = A v_{m-1},
+ * psi' = sum_{m=0..5} theta^m/m! v_m (Eq. 5).  ops/theta are host or device
+ * arrays per `mem`; ops must lie in [0, pool_size) (GOCP_EINVAL for host
+ * arrays; device arrays are clamped and flagged, see gocp_device_errors).
+ * n_ops may be 0. */
+int gocp_prepare_state(const gocp_problem* p, const int32_t* ops, const double* theta, int n_ops,
+                       int mem, void* psi, void* stream);
+
+/* Apply the Taylor step of pool operator `op` to psi in place. */
+int gocp_taylor_step(const gocp_problem* p, int op, double theta, void* psi, void* stream);
+
+/* hpsi <- H psi (Eq. 3), matrix-free.  psi and hpsi must not overlap. */
+int gocp_apply_h(const gocp_problem* p, const void* psi, void* hpsi, void* stream);
+
+/* hpsi <- H psi, and out[0] = E = Re<psi|H psi>/<psi|psi> (Eq. 1),
+ * out[1] = <psi|psi>, both reduced in FP64.  `out` (2 doubles) is host or
+ * device memory per `mem`. */
+int gocp_energy(const gocp_problem* p, const void* psi, void* hpsi, double* out, int mem,
+                void* stream);
+
+/* grads[k] = 2 Re <H psi|A_k psi> / <psi|psi> for every pool operator k
+ * (Eq. 4 on the normalised state), with hpsi = H psi from gocp_energy or
+ * gocp_apply_h.  Operators are evaluated family by family (GOCP order);
+ * results are stored in pool order.  grads has pool_size doubles. */
+int gocp_pool_gradients(const gocp_problem* p, const void* psi, const void* hpsi, double* grads,
+                        int mem, void* stream);
+
+/* E(theta) and dE/dtheta_j for j < n_ops by an adjoint sweep of the Taylor
+ * chain: forward prepare, H psi, lambda = (H - E) psi / <psi|psi>, then for
+ * j = P-1..0 un-compute psi_j exactly per basis pair, accumulate
+ * 2 Re <lambda|T'_j psi_j> and propagate lambda <- T_j^dagger lambda.
+ * ws: caller device buffer of >= 2 states (2 * gocp_state_bytes).
+ * E (1 double) and dE (n_ops doubles) are host or device per `mem`. */
+int gocp_energy_grad(const gocp_problem* p, const int32_t* ops, const double* theta, int n_ops,
+                     int mem, void* ws, double* E, double* dE, void* stream);
+
+/* One ADAPT selection step (Sec. II.B): prepare psi(theta) in ws[0],
+ * H psi in ws[1], E, all pool gradients and the selected operator
+ * (largest |g_k|; values within relative tie_rel of the largest count as
+ * ties, lowest index wins).  out_e: 2 doubles (E, <psi|psi>); grads:
+ * pool_size doubles; selected: 1 int32.  All per `mem`. */
+int gocp_adapt_step(const gocp_problem* p, const int32_t* ops, const double* theta, int n_ops,
+                    int mem, void* ws, double tie_rel, double* out_e, double* grads,
+                    int32_t* selected, void* stream);
+
+/* Device-side argument errors flagged since the last call (bit 0: op index
+ * out of range in a GOCP_MEM_DEVICE ansatz), and clear them.  Synchronises
+ * `stream`. */
+int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A request server: a worker thread owns one stream and advances every
+ * resident request by one stage per tick with one batched launch per stage
+ * kind (forward Taylor op, H psi + energy, adjoint op), admitting queued
+ * requests as slots and arena memory free up (continuous batching).
+ * hbm_budget_bytes is reserved up front as the state arena (power-of-two
+ * buddy blocks; a request holds 2 states); max_slots bounds residency
+ * (1..256).  Problems must outlive the requests that name them and must be
+ * C64 or C128 problems built on `device`. */
+int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_server** out);
+void gocp_server_destroy(gocp_server* s);
+
+/* Queue an energy+gradient request; ops/theta are host arrays copied here.
+ * GOCP_ENOMEM if one request can never fit the arena. */
+int gocp_submit(gocp_server* s, const gocp_problem* p, const int32_t* ops, const double* theta,
+                int n_ops, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait, <0 = forever) for a request.
+ * GOCP_OK: E and dE (n_ops doubles, host) written, ticket retired.
+ * GOCP_EAGAIN (timeout 0) / GOCP_ETIMEDOUT: not finished yet.
+ * GOCP_ECANCELED: the request was cancelled; ticket retired.
+ * GOCP_EINVAL: unknown or already retired ticket. */
+int gocp_poll(gocp_server* s, uint64_t ticket, double* E, double* dE, int64_t timeout_us);
+
+/* Cancel a queued or running request (it stops at its next stage). */
+int gocp_cancel(gocp_server* s, uint64_t ticket);
+
+typedef struct {
+  uint64_t submitted, completed, cancelled;
+  uint64_t ticks;               /* worker iterations that launched work */
+  uint64_t launches;            /* batched kernel launches */
+  uint64_t max_resident;        /* peak concurrent requests */
+  size_t arena_bytes, arena_in_use, arena_peak;
+  int resident, queued;
+} gocp_server_stats;
+int gocp_server_get_stats(gocp_server* s, gocp_server_stats* out);
+
+/* ---------------------------------------------------------- kernel timing */
+
+/* While enabled, every launch of the kernel kinds below is bracketed by a
+ * CUDA event pair recorded on the launching stream.  gocp_profile_read
+ * waits for the recorded events of one kind, returns their launch count and
+ * summed elapsed milliseconds, and forgets them.  Disabled by default. */
+enum { GOCP_KERNEL_APPLY_H = 0, GOCP_KERNEL_TAYLOR = 1, GOCP_KERNEL_POOL_GRAD = 2,
+       GOCP_KERNEL_ADJOINT = 3, GOCP_KERNEL_KINDS = 4 };
+int gocp_profile_enable(int on);
+int gocp_profile_read(int kind, int64_t* launches, double* total_ms);
+
+/* -------------------------------------------------------------- utilities */
+
+const char* gocp_last_error(void);      /* thread-local, never NULL */
+int64_t gocp_launch_count(void);        /* kernels launched by this library */
+const char* gocp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOCP_H */

@@ -119,3 +119,58 @@ def energy_grad(h: PauliTable, ref: np.ndarray, pool: list[PauliTable], ops, the
                 d = taylor5(pool[k], th, d)
         grads[j] = 2.0 * np.vdot(resid, d).real / nrm
     return e, grads
+
+
+# ---------------------------------------------------------------- sparse states
+#
+# The same per-term formula restricted to the nonzero entries of a state held
+# as (indices, values).  It lets full-size (24-qubit) cases with a sparse
+# input (a basis state evolved by a few operators) be checked exactly.
+
+def apply_terms_sparse(t: PauliTable, idx: np.ndarray, vals: np.ndarray, chunk: int = 512):
+    idx = np.asarray(idx, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.complex128)
+    w = t.weights()
+    outs_i, outs_v = [], []
+    for s in range(0, len(t), chunk):
+        xs, zs, ws = t.x[s:s + chunk, None], t.z[s:s + chunk, None], w[s:s + chunk, None]
+        sign = 1 - 2 * parity(idx[None, :] & zs)
+        outs_i.append((idx[None, :] ^ xs).ravel())
+        outs_v.append((ws * sign * vals[None, :]).ravel())
+    if not outs_i:
+        return np.zeros(0, np.int64), np.zeros(0, np.complex128)
+    ai = np.concatenate(outs_i)
+    av = np.concatenate(outs_v)
+    keys, inv = np.unique(ai, return_inverse=True)
+    acc = np.zeros(keys.shape[0], dtype=np.complex128)
+    np.add.at(acc, inv, av)
+    return keys, acc
+
+
+def _sparse_axpy(ai, av, bi, bv, scale):
+    keys, inv = np.unique(np.concatenate([ai, bi]), return_inverse=True)
+    acc = np.zeros(keys.shape[0], dtype=np.complex128)
+    np.add.at(acc, inv, np.concatenate([av, scale * bv]))
+    return keys, acc
+
+
+def taylor5_sparse(a: PauliTable, theta: float, idx, vals):
+    oi, ov = np.asarray(idx, np.int64), np.asarray(vals, np.complex128)
+    vi, vv = oi, ov
+    for m in range(1, 6):
+        vi, vv = apply_terms_sparse(a, vi, vv)
+        oi, ov = _sparse_axpy(oi, ov, vi, vv, theta ** m / math.factorial(m))
+    return oi, ov
+
+
+def prepare_state_sparse(ref_index: int, pool: list[PauliTable], ops, thetas):
+    idx, vals = np.array([ref_index], np.int64), np.array([1.0 + 0j])
+    for k, th in zip(list(ops), list(thetas)):
+        idx, vals = taylor5_sparse(pool[int(k)], float(th), idx, vals)
+    return idx, vals
+
+
+def sparse_dot(ai, av, bi, bv) -> complex:
+    """<a|b> of two sparse states."""
+    common, ia, ib = np.intersect1d(ai, bi, return_indices=True)
+    return complex(np.sum(np.conj(av[ia]) * bv[ib]))

@@ -1,0 +1,73 @@
+// Device-side types shared by the kernels and their launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gocp {
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <typename R> using C_t = typename Cplx<R>::T;
+
+template <typename R>
+__host__ __device__ __forceinline__ C_t<R> cmake(R re, R im) {
+  C_t<R> v;
+  v.x = re;
+  v.y = im;
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ C_t<R> cadd(C_t<R> a, C_t<R> b) { return cmake<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+__device__ __forceinline__ C_t<R> csub(C_t<R> a, C_t<R> b) { return cmake<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+__device__ __forceinline__ C_t<R> cmul(C_t<R> a, C_t<R> b) {
+  return cmake<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R>
+__device__ __forceinline__ C_t<R> cscale(C_t<R> a, R s) { return cmake<R>(a.x * s, a.y * s); }
+template <typename R>
+__device__ __forceinline__ C_t<R> cconj(C_t<R> a) { return cmake<R>(a.x, -a.y); }
+
+// Device copies of the tables of one problem.
+//
+// Hamiltonian: groups of terms sharing an x mask, ascending x.  Group g owns
+// terms [goff[g], goff[g+1]); terms [goff[g], gmid[g]) have real weights,
+// [gmid[g], goff[g+1]) imaginary ones.  The weight of term t is
+//   w_t = c_t i^phase_t (-1)^popc(x_g & z_t),
+// so that (H psi)[k] = sum_g D_g(k) psi[k ^ x_g] with
+//   D_g(k) = sum_{t in g} w_t (-1)^popc(k & z_t).
+// chunk_g splits the groups into runs whose terms fit the shared-memory
+// stage of the H psi kernel (a run of one group may exceed it).
+//
+// Pool: generator k owns strings [poff[k], poff[k+1]) with one x mask px[k]
+// (real-weight strings first, split at pmid[k]).  pw holds w_t as above and
+// pw2 holds w_t (-1)^popc(x & z_t), so that for a basis pair (b, b ^ x) one
+// parity per string gives both D(b) and D(b ^ x).  porder lists the pool in
+// GOCP family order.
+struct DevTables {
+  int n = 0;
+  int G = 0, n_chunks = 0;
+  int64_t T = 0;
+  const uint32_t* gx = nullptr;
+  const int32_t* goff = nullptr;
+  const int32_t* gmid = nullptr;
+  const int32_t* chunk_g = nullptr;
+  const uint32_t* tz = nullptr;
+  const void* tw = nullptr;
+  int M = 0;
+  int64_t S = 0;
+  const uint32_t* px = nullptr;
+  const int32_t* poff = nullptr;
+  const int32_t* pmid = nullptr;
+  const uint32_t* pz = nullptr;
+  const void* pw = nullptr;
+  const void* pw2 = nullptr;
+  const int32_t* porder = nullptr;
+};
+
+}  // namespace gocp

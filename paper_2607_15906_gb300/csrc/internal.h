@@ -1,0 +1,112 @@
+// Internal declarations shared by the host builder, the C ABI, the kernels'
+// launchers and the request server.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gocp.h"
+
+namespace gocp {
+
+// ------------------------------------------------------------ errors
+
+// Records `msg` as the calling thread's last error and returns `code`.
+int fail(int code, const std::string& msg);
+// Returns GOCP_OK after a CUDA call succeeded, else records and returns GOCP_ECUDA.
+int cuda_status(int cuda_err, const char* what);
+void count_launches(int64_t n);
+
+// Kernel timing (gocp_profile_*): brackets one launch with an event pair on
+// its stream while profiling is enabled.
+struct ProfScope {
+  ProfScope(int kind, void* stream);
+  ~ProfScope();
+  int kind;
+  void* stream;
+  void* start;
+};
+
+// ------------------------------------------------------------ exact sums
+
+// Kulisch-style fixed-point accumulator spanning every finite double: each
+// added value is placed exactly, and round() returns the correctly rounded
+// (half-even) double nearest to the exact sum.
+class ExactSum {
+ public:
+  ExactSum() { clear(); }
+  void clear();
+  void add(double v);
+  double round() const;
+
+ private:
+  static constexpr int kLimbs = 70;     // 32-bit digits in signed 64-bit cells
+  static constexpr int kOffset = 1088;  // bit index of 2^0
+  static constexpr int kMinBit = 14;    // bit index of 2^-1074
+  void normalize(int64_t* l) const;
+  int64_t limb_[kLimbs];
+  int64_t adds_;
+  double special_;                      // sum of non-finite inputs
+  bool has_special_;
+};
+
+// ------------------------------------------------------------ host tables
+
+struct PauliTerms {          // sum_t coeff * i^phase * X^x Z^z
+  int n = 0;
+  std::vector<uint32_t> x, z;
+  std::vector<uint8_t> phase;
+  std::vector<double> coeff;
+  size_t size() const { return x.size(); }
+};
+
+struct Pool {
+  std::vector<int64_t> off;   // size M+1
+  std::vector<uint32_t> x, z;
+  std::vector<uint8_t> phase;
+  std::vector<double> coeff;
+  std::vector<int32_t> family;   // -1 before colouring
+  int n_families = 0;
+  int size() const { return off.empty() ? 0 : (int)off.size() - 1; }
+};
+
+// Ladder-operator strings of an encoding |n> -> |beta n> over GF(2):
+//   a_j = 1/2 X^x Z^zp - 1/2 X^x Z^(zp^ze),  a+_j = 1/2 X^x Z^zp + 1/2 X^x Z^(zp^ze).
+struct Encoding {
+  int n = 0;
+  std::vector<uint32_t> beta_rows;     // row j of beta as a mask
+  std::vector<uint32_t> x, zp, ze;     // per mode
+  uint32_t encode(uint32_t occupation) const;
+};
+Encoding make_encoding(int mapping, int n);
+
+int build_hamiltonian(const gocp_build_args& a, PauliTerms& out);
+void build_pool(int n, int n_elec, const Encoding& enc, Pool& out);
+// Exact per-(x,z) accumulation of raw strings (duplicates summed, zeros and
+// |c| < drop removed, sorted by (x, z)); phases folded into real/imag parts
+// must already agree per key, else GOCP_EINVAL.
+int canonicalize_terms(const std::vector<uint32_t>& x, const std::vector<uint32_t>& z,
+                       const std::vector<uint8_t>& ph, const std::vector<double>& c, double drop,
+                       int n, PauliTerms& out);
+int colour_pool(Pool& pool);   // Algorithm 1; GOCP_EINVAL if weights are not multiples of 1/8
+
+// ------------------------------------------------------------ device side
+
+struct DeviceTables;   // defined in kernels.cu
+
+struct Problem {
+  int n_qubits = 0, n_elec = -1, mapping = -1, precision = GOCP_C64, device = -1;
+  uint32_t ref_index = 0;
+  PauliTerms H;
+  Pool pool;
+  int64_t n_groups = 0;
+  DeviceTables* dev = nullptr;
+  size_t device_bytes = 0;
+};
+
+int upload_problem(Problem& p);
+void free_device(Problem& p);
+
+}  // namespace gocp

@@ -1,0 +1,930 @@
+// sm_103a kernels of the hot path and their launchers.
+//
+//   k_apply_h     (H psi)[k] = sum_g D_g(k) psi[k ^ x_g]   (Eq. 3), with the
+//                 energy <psi|H psi> / <psi|psi> (Eq. 1) as an FP64 epilogue
+//   k_taylor5     psi <- sum_{m<=5} theta^m/m! v_m, v_m = A v_{m-1}, evaluated
+//                 on each basis pair {b, b^x} in registers (Eq. 5, 6)
+//   k_pool_grad   g_k = 2 Re <H psi|A_k psi> / <psi|psi>, all k   (Eq. 4)
+//   k_adjoint     one backward step of the adjoint sweep for dE/dtheta
+//
+// Every reduction is deterministic: each block writes its partial sums and
+// the last block to finish (threadfence + counter) adds them in a fixed
+// order, so a result does not depend on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace gocp {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kAmps = 4;             // amplitudes per thread in H psi
+constexpr int kChunkTerms = 2048;    // shared-memory stage of H psi
+constexpr int kChunkGroups = 512;
+constexpr int kOpsPerBlock = 16;     // pool operators per gradient block
+constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor block
+constexpr int kKahanTerms = 16;      // c64: compensated sums for larger groups
+constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
+
+struct DeviceTables {
+  DevTables t;
+  int sm_count = 0;
+  std::vector<void*> allocs;
+  double* scratch = nullptr;
+  size_t scratch_doubles = 0;
+  unsigned int* counters = nullptr;  // kMaxChunks + 8
+  double* scalars = nullptr;         // [0] E  [1] <psi|psi>  [2] Re<psi|H'psi>
+  double identity = 0.0;             // coefficient of the identity term of H
+  int32_t* stage_ops = nullptr;
+  double* stage_theta = nullptr;
+  double* coefs = nullptr;           // 6 Taylor coefficients per ansatz op
+  double* dtheta = nullptr;          // stage_cap doubles
+  int stage_cap = 0;
+  int32_t* err = nullptr;
+  int32_t* selected = nullptr;
+  double* grads = nullptr;           // pool_size doubles (pool order)
+  double* graw = nullptr;            // pool_size doubles (family order, unscaled)
+};
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Adds v[0..NV) over the nblocks blocks of one grid slice into out[0..NV).
+// partials: NV doubles per block of the slice; counter: one per slice.
+template <int NV>
+__device__ void grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
+                         int nblocks, int bid, double* out) {
+  __shared__ double red[NV][kWarps];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) red[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
+    partials[(size_t)bid * NV + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblocks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += kThreads) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[(size_t)b * NV + i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(acc[i]);
+    if (lane == 0) red[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ------------------------------------------------------------ small kernels
+
+template <typename R>
+__global__ void k_basis_state(C_t<R>* psi, uint64_t dim, uint64_t index) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
+       k += (uint64_t)gridDim.x * blockDim.x)
+    psi[k] = cmake<R>(k == index ? R(1) : R(0), R(0));
+}
+
+// Taylor coefficients theta^m / m!, m = 0..5, of each ansatz operator.
+__global__ void k_series(const double* theta, int n_ops, double* coefs) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_ops) return;
+  double th = theta[j], c = 1.0;
+  coefs[6 * j] = 1.0;
+  for (int m = 1; m <= 5; ++m) {
+    c = c * th / (double)m;
+    coefs[6 * j + m] = c;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_norm(const C_t<R>* psi, uint64_t dim, double* partials, unsigned int* counter, double* out) {
+  double v[1] = {0.0};
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    C_t<R> a = psi[k];
+    v[0] += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  grid_sum<1>(v, partials, counter, gridDim.x, blockIdx.x, out);
+}
+
+// lambda = (hpsi - E psi) / <psi|psi> in place over hpsi (E, <psi|psi> = scal[0..1]).
+template <typename R>
+__global__ void k_residual(const C_t<R>* psi, C_t<R>* hpsi, uint64_t dim, const double* scal) {
+  const R er = (R)scal[0], ir = (R)(1.0 / scal[1]);
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    C_t<R> h = hpsi[k], p = psi[k];
+    hpsi[k] = cmake<R>((h.x - er * p.x) * ir, (h.y - er * p.y) * ir);
+  }
+}
+
+// E = identity + Re<psi|H' psi> / <psi|psi>.
+__global__ void k_energy_final(double* scal, double identity) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) scal[0] = identity + scal[2] / scal[1];
+}
+
+// grads[porder[i]] = 2 raw[i] / <psi|psi>.
+__global__ void k_grad_final(const double* raw, const int32_t* porder, int m, const double* scal,
+                             double* grads) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) grads[porder[i]] = 2.0 * raw[i] / scal[1];
+}
+
+// Largest |g| with a relative tie window; the lowest index among ties wins.
+__global__ void k_select(const double* g, int m, double tie_rel, int32_t* out) {
+  __shared__ double best[kThreads];
+  __shared__ int bidx[kThreads];
+  double mx = 0.0;
+  for (int i = threadIdx.x; i < m; i += kThreads) mx = fmax(mx, fabs(g[i]));
+  best[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) best[threadIdx.x] = fmax(best[threadIdx.x], best[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double thr = best[0] * (1.0 - tie_rel);
+  int idx = m;
+  for (int i = threadIdx.x; i < m; i += kThreads)
+    if (fabs(g[i]) >= thr && i < idx) idx = i;
+  bidx[threadIdx.x] = idx;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) bidx[threadIdx.x] = min(bidx[threadIdx.x], bidx[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = bidx[0] < m ? bidx[0] : -1;
+}
+
+// ------------------------------------------------------------ H psi + energy
+
+// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k[i] & z_t); compensated in FP32
+// for longer groups (the diagonal group of a molecular H holds O(n^2) terms).
+template <typename R>
+__device__ __forceinline__ void sum_group(const uint32_t* zs, const R* ws, int tb, int te,
+                                          const uint32_t (&k)[kAmps], R (&d)[kAmps]) {
+  if (sizeof(R) == 4 && te - tb > kKahanTerms) {
+    R comp[kAmps];
+#pragma unroll
+    for (int i = 0; i < kAmps; ++i) comp[i] = R(0);
+    for (int t = tb; t < te; ++t) {
+      const uint32_t z = zs[t];
+      const R w = ws[t];
+#pragma unroll
+      for (int i = 0; i < kAmps; ++i) {
+        R y = ((__popc(k[i] & z) & 1) ? -w : w) - comp[i];
+        R s = d[i] + y;
+        comp[i] = (s - d[i]) - y;
+        d[i] = s;
+      }
+    }
+  } else {
+    for (int t = tb; t < te; ++t) {
+      const uint32_t z = zs[t];
+      const R w = ws[t];
+#pragma unroll
+      for (int i = 0; i < kAmps; ++i) d[i] += (__popc(k[i] & z) & 1) ? -w : w;
+    }
+  }
+}
+
+// A thread owns kAmps output amplitudes k = tile + i*blockDim + tid.  The
+// group table is staged in shared memory chunk by chunk (a single group too
+// large for the stage is read from global memory).  The identity term of H
+// is excluded from the groups and added as identity * psi[k].  With
+// `partials` set the grid also reduces <psi|psi> -> scal[1] and
+// Re<psi|H' psi> -> scal[2] in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_apply_h(DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, R identity,
+          double* partials, unsigned int* counter, double* scal) {
+  __shared__ uint32_t s_x[kChunkGroups];
+  __shared__ int32_t s_off[kChunkGroups + 1];
+  __shared__ int32_t s_mid[kChunkGroups];
+  __shared__ uint32_t s_z[kChunkTerms];
+  __shared__ R s_w[kChunkTerms];
+  const R* tw = (const R*)tb.tw;
+  const uint64_t dim = 1ull << tb.n;
+  const uint64_t base = (uint64_t)blockIdx.x * (kThreads * kAmps);
+  uint32_t k[kAmps];
+  bool live[kAmps];
+  C_t<R> acc[kAmps];
+#pragma unroll
+  for (int i = 0; i < kAmps; ++i) {
+    uint64_t kk = base + (uint64_t)i * kThreads + threadIdx.x;
+    live[i] = kk < dim;
+    k[i] = live[i] ? (uint32_t)kk : 0u;
+    acc[i] = cmake<R>(0, 0);
+  }
+  for (int c = 0; c < tb.n_chunks; ++c) {
+    const int g0 = tb.chunk_g[c], g1 = tb.chunk_g[c + 1];
+    const int t0 = tb.goff[g0], t1 = tb.goff[g1];
+    const bool staged = (t1 - t0) <= kChunkTerms;   // chunks never exceed kChunkGroups
+    __syncthreads();
+    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
+      s_x[g - g0] = tb.gx[g];
+      s_off[g - g0] = tb.goff[g] - t0;
+      s_mid[g - g0] = tb.gmid[g] - t0;
+    }
+    if (threadIdx.x == 0) s_off[g1 - g0] = t1 - t0;
+    if (staged)
+      for (int t = t0 + threadIdx.x; t < t1; t += kThreads) {
+        s_z[t - t0] = tb.tz[t];
+        s_w[t - t0] = tw[t];
+      }
+    __syncthreads();
+    const uint32_t* zs = staged ? s_z : tb.tz + t0;
+    const R* ws = staged ? s_w : tw + t0;
+    for (int g = g0; g < g1; ++g) {
+      const uint32_t x = s_x[g - g0];
+      const int tbeg = s_off[g - g0], tmid = s_mid[g - g0], tend = s_off[g - g0 + 1];
+      R dr[kAmps], di[kAmps];
+#pragma unroll
+      for (int i = 0; i < kAmps; ++i) {
+        dr[i] = R(0);
+        di[i] = R(0);
+      }
+      sum_group<R>(zs, ws, tbeg, tmid, k, dr);
+      if (tend > tmid) sum_group<R>(zs, ws, tmid, tend, k, di);
+#pragma unroll
+      for (int i = 0; i < kAmps; ++i) {
+        C_t<R> p = psi[k[i] ^ x];   // k[i] = 0 for dead lanes: in bounds
+        acc[i].x += dr[i] * p.x - di[i] * p.y;
+        acc[i].y += dr[i] * p.y + di[i] * p.x;
+      }
+    }
+  }
+  double v[2] = {0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < kAmps; ++i) {
+    if (!live[i]) continue;
+    C_t<R> p = psi[k[i]];
+    v[0] += (double)p.x * p.x + (double)p.y * p.y;
+    v[1] += (double)p.x * acc[i].x + (double)p.y * acc[i].y;
+    out[k[i]] = cmake<R>(acc[i].x + identity * p.x, acc[i].y + identity * p.y);
+  }
+  if (partials) grid_sum<2>(v, partials, counter, gridDim.x, blockIdx.x, scal + 1);
+}
+
+// ------------------------------------------------------------ pool strings
+
+// Loads the strings of operator `op` into shared memory when they fit.
+// D(b) = sum w_t chi_t(b), D(b^x) = sum w2_t chi_t(b) with chi_t(b) = (-1)^popc(b & z_t).
+template <typename R>
+struct OpView {
+  uint32_t x;
+  int nb, nm, ne;        // [0, nm) real weights, [nm, ne) imaginary
+  const uint32_t* z;
+  const R* w;
+  const R* w2;
+};
+
+template <typename R>
+__device__ __forceinline__ void op_d(const OpView<R>& o, uint32_t b, C_t<R>& d1, C_t<R>& d2) {
+  R r1 = 0, r2 = 0, i1 = 0, i2 = 0;
+  for (int t = 0; t < o.nm; ++t) {
+    const bool odd = __popc(b & o.z[t]) & 1;
+    r1 += odd ? -o.w[t] : o.w[t];
+    r2 += odd ? -o.w2[t] : o.w2[t];
+  }
+  for (int t = o.nm; t < o.ne; ++t) {
+    const bool odd = __popc(b & o.z[t]) & 1;
+    i1 += odd ? -o.w[t] : o.w[t];
+    i2 += odd ? -o.w2[t] : o.w2[t];
+  }
+  d1 = cmake<R>(r1, i1);
+  d2 = cmake<R>(r2, i2);
+}
+
+// Resolves ops[j] (flagging out-of-range indices) and stages its strings.
+template <typename R>
+__device__ bool load_op(const DevTables& tb, const int32_t* ops, int j, int32_t* err,
+                        uint32_t* s_z, R* s_w, R* s_w2, OpView<R>& o) {
+  const int op = ops[j];
+  if (op < 0 || op >= tb.M) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
+    return false;
+  }
+  const int sb = tb.poff[op], sm = tb.pmid[op], se = tb.poff[op + 1];
+  const R* pw = (const R*)tb.pw;
+  const R* pw2 = (const R*)tb.pw2;
+  o.x = tb.px[op];
+  o.nm = sm - sb;
+  o.ne = se - sb;
+  if (se - sb <= kStageStrings) {
+    for (int t = threadIdx.x; t < se - sb; t += blockDim.x) {
+      s_z[t] = tb.pz[sb + t];
+      s_w[t] = pw[sb + t];
+      s_w2[t] = pw2[sb + t];
+    }
+    __syncthreads();
+    o.z = s_z;
+    o.w = s_w;
+    o.w2 = s_w2;
+  } else {
+    o.z = tb.pz + sb;
+    o.w = pw + sb;
+    o.w2 = pw2 + sb;
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t pair_base(uint64_t p, int s) {
+  // insert a 0 at bit s of p
+  return (uint32_t)(((p >> s) << (s + 1)) | (p & ((1ull << s) - 1)));
+}
+
+// Compensated complex accumulation (FP32 path; exact-order sum for FP64).
+template <typename R>
+__device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
+  if (sizeof(R) == 4) {
+    R yx = v.x - c.x, yy = v.y - c.y;
+    R tx = s.x + yx, ty = s.y + yy;
+    c.x = (tx - s.x) - yx;
+    c.y = (ty - s.y) - yy;
+    s.x = tx;
+    s.y = ty;
+  } else {
+    s.x += v.x;
+    s.y += v.y;
+  }
+}
+
+// ------------------------------------------------------------ Taylor step
+
+// psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
+// v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5) stay in registers.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
+          int32_t* err) {
+  __shared__ uint32_t s_z[kStageStrings];
+  __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
+  OpView<R> o;
+  if (!load_op<R>(tb, ops, j, err, s_z, s_w, s_w2, o)) return;
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const int s = __ffs(o.x) - 1;
+  const uint64_t npairs = 1ull << (tb.n - 1);
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = pair_base(p, s), b2 = b ^ o.x;
+    C_t<R> d1, d2;
+    op_d<R>(o, b, d1, d2);
+    C_t<R> v1 = psi[b], v2 = psi[b2];
+    C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
+#pragma unroll
+    for (int m = 1; m <= 5; ++m) {
+      C_t<R> n1 = cmul<R>(d1, v2), n2 = cmul<R>(d2, v1);   // (A v)[b] = D(b) v[b^x]
+      v1 = n1;
+      v2 = n2;
+      kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
+      kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
+    }
+    psi[b] = s1;
+    psi[b2] = s2;
+  }
+}
+
+// ------------------------------------------------------------ adjoint step
+
+// Backward step j of the adjoint sweep.  On each pair A = [[0, D1], [D2, 0]],
+// A^2 = mu I with mu = D1 D2, so T = C I + S A with C = c0 + c2 mu + c4 mu^2,
+// S = c1 + c3 mu + c5 mu^2 (c_m = theta^m/m!), T' = dT/dtheta = C' I + S' A
+// with C' = c1 mu + c3 mu^2, S' = C.  In place:
+//   psi <- T^-1 psi = (C I - S A) psi / (C^2 - S^2 mu)      (exact inverse)
+//   dE_j += 2 Re <lambda|T' psi>                            (before the update)
+//   lambda <- T^dagger lambda.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
+          C_t<R>* lam, double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
+  __shared__ uint32_t s_z[kStageStrings];
+  __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
+  OpView<R> o;
+  if (!load_op<R>(tb, ops, j, err, s_z, s_w, s_w2, o)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) dtheta[j] = 0.0;
+    return;
+  }
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const int s = __ffs(o.x) - 1;
+  const uint64_t npairs = 1ull << (tb.n - 1);
+  double v[1] = {0.0};
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = pair_base(p, s), b2 = b ^ o.x;
+    C_t<R> d1, d2;
+    op_d<R>(o, b, d1, d2);
+    const C_t<R> mu = cmul<R>(d1, d2), mu2 = cmul<R>(mu, mu);
+    const C_t<R> cc = cmake<R>(c[0] + c[2] * mu.x + c[4] * mu2.x, c[2] * mu.y + c[4] * mu2.y);
+    const C_t<R> sc = cmake<R>(c[1] + c[3] * mu.x + c[5] * mu2.x, c[3] * mu.y + c[5] * mu2.y);
+    const C_t<R> cd = cmake<R>(c[1] * mu.x + c[3] * mu2.x, c[1] * mu.y + c[3] * mu2.y);
+    const C_t<R> det = csub<R>(cmul<R>(cc, cc), cmul<R>(cmul<R>(sc, sc), mu));
+    const R dn = det.x * det.x + det.y * det.y;
+    const C_t<R> inv = cmake<R>(det.x / dn, -det.y / dn);
+    const C_t<R> sd1 = cmul<R>(sc, d1), sd2 = cmul<R>(sc, d2);
+    const C_t<R> u1 = psi[b], u2 = psi[b2];
+    const C_t<R> q1 = cmul<R>(csub<R>(cmul<R>(cc, u1), cmul<R>(sd1, u2)), inv);
+    const C_t<R> q2 = cmul<R>(csub<R>(cmul<R>(cc, u2), cmul<R>(sd2, u1)), inv);
+    const C_t<R> t1 = cadd<R>(cmul<R>(cd, q1), cmul<R>(cmul<R>(cc, d1), q2));
+    const C_t<R> t2 = cadd<R>(cmul<R>(cd, q2), cmul<R>(cmul<R>(cc, d2), q1));
+    const C_t<R> l1 = lam[b], l2 = lam[b2];
+    v[0] += 2.0 * ((double)l1.x * t1.x + (double)l1.y * t1.y + (double)l2.x * t2.x +
+                   (double)l2.y * t2.y);
+    psi[b] = q1;
+    psi[b2] = q2;
+    lam[b] = cadd<R>(cmul<R>(cconj<R>(cc), l1), cmul<R>(cconj<R>(sd2), l2));
+    lam[b2] = cadd<R>(cmul<R>(cconj<R>(sd1), l1), cmul<R>(cconj<R>(cc), l2));
+  }
+  grid_sum<1>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j);
+}
+
+// ------------------------------------------------------------ pool gradients
+
+// blockIdx.y selects kOpsPerBlock operators in GOCP family order; the
+// x-slice of blocks sweeps all amplitudes.  raw[i] = Re<H psi|A psi> of the
+// i-th operator in family order.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
+            double* partials, unsigned int* counters, double* raw) {
+  __shared__ uint32_t s_x[kOpsPerBlock];
+  __shared__ int s_beg[kOpsPerBlock + 1], s_mid[kOpsPerBlock];
+  __shared__ uint32_t s_z[kStageStrings];
+  __shared__ R s_w[kStageStrings];
+  __shared__ int s_glob[kOpsPerBlock];   // op index when its strings are not staged
+  const int first = blockIdx.y * kOpsPerBlock;
+  const int nops = min(kOpsPerBlock, tb.M - first);
+  const R* pw = (const R*)tb.pw;
+  if (threadIdx.x == 0) {
+    int fill = 0;
+    for (int i = 0; i < nops; ++i) {
+      const int op = tb.porder[first + i];
+      const int sb = tb.poff[op], se = tb.poff[op + 1];
+      s_x[i] = tb.px[op];
+      if (fill + (se - sb) <= kStageStrings) {
+        s_beg[i] = fill;
+        s_mid[i] = fill + tb.pmid[op] - sb;
+        s_glob[i] = -1;
+        fill += se - sb;
+        s_beg[i + 1] = fill;
+      } else {
+        s_beg[i] = fill;
+        s_mid[i] = fill;
+        s_glob[i] = op;
+        s_beg[i + 1] = fill;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < nops; ++i) {
+    const int op = tb.porder[first + i];
+    if (s_glob[i] >= 0) continue;
+    const int sb = tb.poff[op], cnt = s_beg[i + 1] - s_beg[i];
+    for (int t = threadIdx.x; t < cnt; t += kThreads) {
+      s_z[s_beg[i] + t] = tb.pz[sb + t];
+      s_w[s_beg[i] + t] = pw[sb + t];
+    }
+  }
+  __syncthreads();
+  R acc[kOpsPerBlock], cmp[kOpsPerBlock];
+#pragma unroll
+  for (int i = 0; i < kOpsPerBlock; ++i) {
+    acc[i] = R(0);
+    cmp[i] = R(0);
+  }
+  const uint64_t dim = 1ull << tb.n;
+  for (uint64_t kk = blockIdx.x * (uint64_t)kThreads + threadIdx.x; kk < dim;
+       kk += (uint64_t)gridDim.x * kThreads) {
+    const uint32_t k = (uint32_t)kk;
+    const C_t<R> h = hpsi[k];
+#pragma unroll
+    for (int i = 0; i < kOpsPerBlock; ++i) {
+      if (i >= nops) break;
+      R dr = 0, di = 0;
+      if (s_glob[i] < 0) {
+        for (int t = s_beg[i]; t < s_mid[i]; ++t) dr += (__popc(k & s_z[t]) & 1) ? -s_w[t] : s_w[t];
+        for (int t = s_mid[i]; t < s_beg[i + 1]; ++t) di += (__popc(k & s_z[t]) & 1) ? -s_w[t] : s_w[t];
+      } else {
+        const int op = s_glob[i];
+        const int sb = tb.poff[op], sm = tb.pmid[op], se = tb.poff[op + 1];
+        for (int t = sb; t < sm; ++t) dr += (__popc(k & tb.pz[t]) & 1) ? -pw[t] : pw[t];
+        for (int t = sm; t < se; ++t) di += (__popc(k & tb.pz[t]) & 1) ? -pw[t] : pw[t];
+      }
+      const C_t<R> p = psi[k ^ s_x[i]];
+      // Re(conj(h) * D * p)
+      const R ax = dr * p.x - di * p.y, ay = dr * p.y + di * p.x;
+      const R val = h.x * ax + h.y * ay;
+      if (sizeof(R) == 4) {
+        R y = val - cmp[i], t = acc[i] + y;
+        cmp[i] = (t - acc[i]) - y;
+        acc[i] = t;
+      } else {
+        acc[i] += val;
+      }
+    }
+  }
+  double v[kOpsPerBlock];
+#pragma unroll
+  for (int i = 0; i < kOpsPerBlock; ++i) v[i] = (double)acc[i] - (double)cmp[i];
+  // raw holds a whole number of chunks, so the tail chunk's unused slots are padding
+  grid_sum<kOpsPerBlock>(v, partials + (size_t)blockIdx.y * gridDim.x * kOpsPerBlock,
+                         counters + blockIdx.y, gridDim.x, blockIdx.x, raw + first);
+}
+
+// ------------------------------------------------------------ upload
+
+namespace {
+
+template <typename T>
+int dalloc(DeviceTables& d, T** p, size_t count, size_t& bytes) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc");
+  d.allocs.push_back(q);
+  bytes += count * sizeof(T);
+  *p = (T*)q;
+  return GOCP_OK;
+}
+
+template <typename T>
+int upload(DeviceTables& d, T** p, const std::vector<T>& h, size_t& bytes) {
+  int rc = dalloc(d, p, h.size(), bytes);
+  if (rc) return rc;
+  if (h.empty()) return GOCP_OK;
+  return cuda_status(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice),
+                     "cudaMemcpy");
+}
+
+inline int parity32(uint32_t v) { return __builtin_popcount(v) & 1; }
+
+// Effective weight of c i^phase X^x Z^z at output index k:
+//   c i^phase (-1)^popc(x & z) -- real if phase is even, imaginary if odd.
+inline double eff_weight(double c, int phase, uint32_t x, uint32_t z, bool* imag) {
+  double w = (phase & 2) ? -c : c;
+  if (parity32(x & z)) w = -w;
+  *imag = phase & 1;
+  return w;
+}
+
+template <typename R>
+int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
+  const PauliTerms& H = p.H;
+  // ---- Hamiltonian groups (identity term handled apart)
+  std::vector<uint32_t> gx, tz;
+  std::vector<int32_t> goff, gmid;
+  std::vector<R> tw;
+  d.identity = 0.0;
+  size_t i = 0;
+  while (i < H.size()) {
+    size_t j = i;
+    while (j < H.size() && H.x[j] == H.x[i]) ++j;
+    std::vector<uint32_t> zr, zi;
+    std::vector<R> wr, wi;
+    for (size_t t = i; t < j; ++t) {
+      bool imag = false;
+      double w = eff_weight(H.coeff[t], H.phase[t], H.x[t], H.z[t], &imag);
+      if (H.x[t] == 0 && H.z[t] == 0 && !imag) {
+        d.identity += w;
+        continue;
+      }
+      (imag ? zi : zr).push_back(H.z[t]);
+      (imag ? wi : wr).push_back((R)w);
+    }
+    if (!zr.empty() || !zi.empty()) {
+      gx.push_back(H.x[i]);
+      goff.push_back((int32_t)tz.size());
+      tz.insert(tz.end(), zr.begin(), zr.end());
+      tw.insert(tw.end(), wr.begin(), wr.end());
+      gmid.push_back((int32_t)tz.size());
+      tz.insert(tz.end(), zi.begin(), zi.end());
+      tw.insert(tw.end(), wi.begin(), wi.end());
+    }
+    i = j;
+  }
+  goff.push_back((int32_t)tz.size());
+  const int G = (int)gx.size();
+  // chunk plan: runs of groups whose terms fit the shared-memory stage
+  std::vector<int32_t> chunk{0};
+  {
+    int g = 0;
+    while (g < G) {
+      int h = g;
+      while (h < G && h - g < kChunkGroups && goff[h + 1] - goff[g] <= kChunkTerms) ++h;
+      if (h == g) h = g + 1;   // one oversized group: its own chunk
+      chunk.push_back(h);
+      g = h;
+    }
+  }
+  int rc;
+  uint32_t *dgx, *dtz;
+  int32_t *dgoff, *dgmid, *dchunk;
+  R* dtw;
+  if ((rc = upload(d, &dgx, gx, bytes)) || (rc = upload(d, &dgoff, goff, bytes)) ||
+      (rc = upload(d, &dgmid, gmid, bytes)) || (rc = upload(d, &dchunk, chunk, bytes)) ||
+      (rc = upload(d, &dtz, tz, bytes)) || (rc = upload(d, &dtw, tw, bytes)))
+    return rc;
+  d.t.n = p.n_qubits;
+  d.t.G = G;
+  d.t.T = (int64_t)tz.size();
+  d.t.n_chunks = (int)chunk.size() - 1;
+  d.t.gx = dgx;
+  d.t.goff = dgoff;
+  d.t.gmid = dgmid;
+  d.t.chunk_g = dchunk;
+  d.t.tz = dtz;
+  d.t.tw = dtw;
+  // ---- pool
+  const Pool& P = p.pool;
+  const int M = P.size();
+  std::vector<uint32_t> px(M), pz;
+  std::vector<int32_t> poff, pmid(M), porder(M);
+  std::vector<R> pw, pw2;
+  for (int k = 0; k < M; ++k) {
+    poff.push_back((int32_t)pz.size());
+    px[k] = P.off[k + 1] > P.off[k] ? P.x[P.off[k]] : 0u;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) pmid[k] = (int32_t)pz.size();
+      for (int64_t s = P.off[k]; s < P.off[k + 1]; ++s) {
+        bool imag = false;
+        double w = eff_weight(P.coeff[s], P.phase[s], P.x[s], P.z[s], &imag);
+        if ((int)imag != pass) continue;
+        pz.push_back(P.z[s]);
+        pw.push_back((R)w);
+        pw2.push_back((R)(parity32(px[k] & P.z[s]) ? -w : w));
+      }
+    }
+  }
+  poff.push_back((int32_t)pz.size());
+  for (int k = 0; k < M; ++k) porder[k] = k;
+  std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) {
+    return P.family[a] < P.family[b];
+  });
+  uint32_t *dpx, *dpz;
+  int32_t *dpoff, *dpmid, *dporder;
+  R *dpw, *dpw2;
+  if ((rc = upload(d, &dpx, px, bytes)) || (rc = upload(d, &dpoff, poff, bytes)) ||
+      (rc = upload(d, &dpmid, pmid, bytes)) || (rc = upload(d, &dpz, pz, bytes)) ||
+      (rc = upload(d, &dpw, pw, bytes)) || (rc = upload(d, &dpw2, pw2, bytes)) ||
+      (rc = upload(d, &dporder, porder, bytes)))
+    return rc;
+  d.t.M = M;
+  d.t.S = (int64_t)pz.size();
+  d.t.px = dpx;
+  d.t.poff = dpoff;
+  d.t.pmid = dpmid;
+  d.t.pz = dpz;
+  d.t.pw = dpw;
+  d.t.pw2 = dpw2;
+  d.t.porder = dporder;
+  return GOCP_OK;
+}
+
+int grid_for(uint64_t work, int sm_count, int per_sm) {
+  uint64_t want = (work + kThreads - 1) / kThreads;
+  uint64_t cap = (uint64_t)sm_count * per_sm;
+  return (int)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kThreads * kAmps - 1) / (kThreads * kAmps)); }
+int pool_grid_x(const DeviceTables& d) { return grid_for(1ull << d.t.n, d.sm_count, 2); }
+
+}  // namespace
+
+int upload_problem(Problem& p) {
+  if (p.device < 0) return GOCP_OK;
+  cudaError_t e = cudaSetDevice(p.device);
+  if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
+  DeviceTables* d = new DeviceTables();
+  p.dev = d;
+  size_t bytes = 0;
+  int rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes) : upload_typed<double>(p, *d, bytes);
+  if (rc) return rc;
+  int sm = 0;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, p.device);
+  d->sm_count = sm > 0 ? sm : 1;
+  const int M = d->t.M;
+  const int nchunks = (M + kOpsPerBlock - 1) / kOpsPerBlock;
+  if (nchunks > kMaxChunks) return fail(GOCP_EINVAL, "pool too large for the gradient kernel");
+  size_t need = 2 * (size_t)apply_grid(p.n_qubits);
+  need = std::max(need, (size_t)pool_grid_x(*d) * (size_t)std::max(nchunks, 1) * kOpsPerBlock);
+  need = std::max(need, (size_t)d->sm_count * 8);
+  d->scratch_doubles = need;
+  if ((rc = dalloc(*d, &d->scratch, need, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->counters, kMaxChunks + 8, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->scalars, 16, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->err, 1, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->selected, 1, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->grads, std::max(M, 1), bytes))) return rc;
+  if ((rc = dalloc(*d, &d->graw, std::max(nchunks * kOpsPerBlock, 1), bytes))) return rc;
+  cudaMemset(d->counters, 0, (kMaxChunks + 8) * sizeof(unsigned int));
+  cudaMemset(d->err, 0, sizeof(int32_t));
+  cudaMemset(d->scalars, 0, 16 * sizeof(double));
+  p.device_bytes = bytes;
+  p.n_groups = d->t.G;
+  return cuda_status(cudaDeviceSynchronize(), "upload");
+}
+
+void free_device(Problem& p) {
+  if (!p.dev) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (p.device >= 0) cudaSetDevice(p.device);
+  for (void* q : p.dev->allocs) cudaFree(q);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete p.dev;
+  p.dev = nullptr;
+}
+
+// ------------------------------------------------------------ launchers
+
+int ensure_stage(Problem& p, int n_ops) {
+  DeviceTables& d = *p.dev;
+  if (n_ops <= d.stage_cap) return GOCP_OK;
+  int cap = std::max(n_ops, 2 * d.stage_cap);
+  cap = std::max(cap, 256);
+  size_t bytes = 0;
+  int rc;
+  // previous staging buffers stay in `allocs` until the problem is freed
+  if ((rc = dalloc(d, &d.stage_ops, cap, bytes)) || (rc = dalloc(d, &d.stage_theta, cap, bytes)) ||
+      (rc = dalloc(d, &d.coefs, (size_t)cap * 6, bytes)) || (rc = dalloc(d, &d.dtheta, cap, bytes)))
+    return rc;
+  p.device_bytes += bytes;
+  d.stage_cap = cap;
+  return GOCP_OK;
+}
+
+int32_t* stage_ops_ptr(Problem& p) { return p.dev->stage_ops; }
+double* stage_theta_ptr(Problem& p) { return p.dev->stage_theta; }
+double* dtheta_ptr(Problem& p) { return p.dev->dtheta; }
+double* scalars_ptr(Problem& p) { return p.dev->scalars; }
+double* grads_ptr(Problem& p) { return p.dev->grads; }
+int32_t* selected_ptr(Problem& p) { return p.dev->selected; }
+int32_t* err_ptr(Problem& p) { return p.dev->err; }
+
+#define GOCP_LAUNCHED(n) count_launches(n)
+
+template <typename R>
+static int launch_reference(Problem& p, void* psi, cudaStream_t st) {
+  const uint64_t dim = 1ull << p.n_qubits;
+  int grid = grid_for(dim, p.dev->sm_count, 8);
+  k_basis_state<R><<<grid, kThreads, 0, st>>>((C_t<R>*)psi, dim, p.ref_index);
+  GOCP_LAUNCHED(1);
+  return cuda_status(cudaGetLastError(), "k_basis_state");
+}
+
+int dev_reference(Problem& p, void* psi, cudaStream_t st) {
+  return p.precision == GOCP_C64 ? launch_reference<float>(p, psi, st) : launch_reference<double>(p, psi, st);
+}
+
+template <typename R>
+static int launch_taylor_chain(Problem& p, const int32_t* d_ops, const double* d_theta, int n_ops,
+                               void* psi, cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  if (n_ops == 0) return GOCP_OK;
+  k_series<<<(n_ops + 127) / 128, 128, 0, st>>>(d_theta, n_ops, d.coefs);
+  const int grid = grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
+  for (int j = 0; j < n_ops; ++j) {
+    ProfScope ps(GOCP_KERNEL_TAYLOR, st);
+    k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err);
+  }
+  GOCP_LAUNCHED(1 + n_ops);
+  return cuda_status(cudaGetLastError(), "k_taylor5");
+}
+
+int dev_taylor_chain(Problem& p, const int32_t* d_ops, const double* d_theta, int n_ops, void* psi,
+                     cudaStream_t st) {
+  int rc = ensure_stage(p, n_ops);
+  if (rc) return rc;
+  return p.precision == GOCP_C64 ? launch_taylor_chain<float>(p, d_ops, d_theta, n_ops, psi, st)
+                                 : launch_taylor_chain<double>(p, d_ops, d_theta, n_ops, psi, st);
+}
+
+template <typename R>
+static int launch_apply(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  const int grid = apply_grid(p.n_qubits);
+  {
+  ProfScope ps(GOCP_KERNEL_APPLY_H, st);
+  k_apply_h<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (C_t<R>*)hpsi, (R)d.identity,
+                                          energy ? d.scratch : nullptr, d.counters + kMaxChunks,
+                                          d.scalars);
+  }
+  int n = 1;
+  if (energy) {
+    k_energy_final<<<1, 32, 0, st>>>(d.scalars, d.identity);
+    ++n;
+  }
+  GOCP_LAUNCHED(n);
+  return cuda_status(cudaGetLastError(), "k_apply_h");
+}
+
+int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st) {
+  return p.precision == GOCP_C64 ? launch_apply<float>(p, psi, hpsi, energy, st)
+                                 : launch_apply<double>(p, psi, hpsi, energy, st);
+}
+
+template <typename R>
+static int launch_norm(Problem& p, const void* psi, cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  const uint64_t dim = 1ull << p.n_qubits;
+  const int grid = grid_for(dim, d.sm_count, 8);
+  k_norm<R><<<grid, kThreads, 0, st>>>((const C_t<R>*)psi, dim, d.scratch, d.counters + kMaxChunks + 1,
+                                       d.scalars + 1);
+  GOCP_LAUNCHED(1);
+  return cuda_status(cudaGetLastError(), "k_norm");
+}
+
+int dev_norm(Problem& p, const void* psi, cudaStream_t st) {
+  return p.precision == GOCP_C64 ? launch_norm<float>(p, psi, st) : launch_norm<double>(p, psi, st);
+}
+
+template <typename R>
+static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads,
+                             cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  const int M = d.t.M;
+  if (M == 0) return GOCP_OK;
+  const int nchunks = (M + kOpsPerBlock - 1) / kOpsPerBlock;
+  dim3 grid(pool_grid_x(d), nchunks);
+  {
+    ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+    k_pool_grad<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
+                                              d.scratch, d.counters, d.graw);
+  }
+  k_grad_final<<<(M + 255) / 256, 256, 0, st>>>(d.graw, d.t.porder, M, d.scalars, d_grads);
+  GOCP_LAUNCHED(2);
+  return cuda_status(cudaGetLastError(), "k_pool_grad");
+}
+
+int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st) {
+  // needs <psi|psi> in scalars[1]
+  int rc = dev_norm(p, psi, st);
+  if (rc) return rc;
+  return p.precision == GOCP_C64 ? launch_pool_grads<float>(p, psi, hpsi, d_grads, st)
+                                 : launch_pool_grads<double>(p, psi, hpsi, d_grads, st);
+}
+
+template <typename R>
+static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam,
+                          double* d_dE, cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  const uint64_t dim = 1ull << p.n_qubits;
+  const int g1 = grid_for(dim, d.sm_count, 8);
+  k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, dim, d.scalars);
+  const int grid = grid_for(dim / 2, d.sm_count, 8);
+  for (int j = n_ops - 1; j >= 0; --j) {
+    ProfScope ps(GOCP_KERNEL_ADJOINT, st);
+    k_adjoint<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, (C_t<R>*)lam,
+                                            d.scratch, d.counters + kMaxChunks + 2, d_dE, d.err);
+  }
+  GOCP_LAUNCHED(1 + n_ops);
+  return cuda_status(cudaGetLastError(), "k_adjoint");
+}
+
+int dev_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE,
+                cudaStream_t st) {
+  return p.precision == GOCP_C64 ? launch_adjoint<float>(p, d_ops, n_ops, psi, lam, d_dE, st)
+                                 : launch_adjoint<double>(p, d_ops, n_ops, psi, lam, d_dE, st);
+}
+
+int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out, cudaStream_t st) {
+  k_select<<<1, kThreads, 0, st>>>(d_grads, p.dev->t.M, tie_rel, d_out);
+  GOCP_LAUNCHED(1);
+  return cuda_status(cudaGetLastError(), "k_select");
+}
+
+}  // namespace gocp

@@ -1,0 +1,272 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design doc):
+  complex128: relative 1e-10 on states and energies.
+  complex64 : |E - E_oracle| <= 1e-6 Ha, fidelity >= 1 - 1e-6, H psi entries
+              within 2e-5 of max|H psi| (FP32 amplitudes), gradients within
+              2e-6 absolute.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2607_15906_gb300 as gb  # noqa: E402
+from oracle import mapping, pool as opool, statevector as sv  # noqa: E402
+from oracle.pauli import PauliTable, parity  # noqa: E402
+from synth import config_integrals, draw_ansatz, molecular_integrals, random_state  # noqa: E402
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+TOL = {"c128": dict(state=1e-10, energy=1e-10, grad=1e-10),
+       "c64": dict(state=2e-5, energy=1e-6, grad=2e-6)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2607_15906_gb300 import build
+    build.build()
+    gb.load()
+
+
+def _to_dev(p, psi):
+    dt = np.complex64 if p.precision == "c64" else np.complex128
+    return torch.from_numpy(psi.astype(dt)).to(f"cuda:{p.device}")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.complex128).ravel()
+
+
+def _case(n_orb, n_elec, mp, seed=0, decay=True, int_drop=0.0, term_drop=0.0):
+    ints = molecular_integrals(n_orb, seed=seed, decay=decay)
+    h = mapping.hamiltonian_table(ints, mp, int_drop, term_drop)
+    tabs = opool.pool_tables(2 * n_orb, n_elec, mp)
+    return ints, h, tabs
+
+
+SMALL = [(2, 2, "jw", 0), (3, 2, "bk", 1), (4, 4, "jw", 2), (5, 4, "bk", 3), (5, 6, "jw", 4), (7, 6, "jw", 0)]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_orb,n_elec,mp,seed", SMALL)
+def test_apply_h_and_energy(prec, n_orb, n_elec, mp, seed):
+    ints, h, _ = _case(n_orb, n_elec, mp, seed)
+    p = gb.Problem.build(ints, n_elec, mapping=mp, precision=prec, device=0)
+    n = 2 * n_orb
+    psi = random_state(n, seed=10 + seed)
+    d = _to_dev(p, psi)
+    psi_in = _host(d)                          # the rounded input the kernel saw
+    hd = torch.empty_like(d)
+    e, nrm = p.energy(d, hd)
+    ref = sv.apply_terms(h, psi_in)
+    got = _host(hd)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale
+    e_ref = sv.energy(h, psi_in)
+    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    assert abs(nrm - np.vdot(psi_in, psi_in).real) <= 1e-12
+    # apply without the energy epilogue gives the same vector
+    h2 = torch.empty_like(d)
+    p.apply_h(d, h2)
+    assert np.array_equal(_host(h2), got)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_orb,n_elec,mp,seed", SMALL[:5])
+def test_prepare_state_and_fidelity(prec, n_orb, n_elec, mp, seed):
+    ints, h, tabs = _case(n_orb, n_elec, mp, seed)
+    p = gb.Problem.build(ints, n_elec, mapping=mp, precision=prec, device=0)
+    n = 2 * n_orb
+    ops, th = draw_ansatz(len(tabs), 12, seed=seed, theta_sigma=0.3)
+    ref = sv.prepare_state(sv.basis_state(n, p.info["ref_index"]), tabs, ops, th)
+    d = p.new_states(1)[0]
+    p.prepare_state(ops, th, d)
+    got = _host(d)
+    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 4
+    assert 1.0 - sv.fidelity(got, ref) <= (1e-12 if prec == "c128" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_single_taylor_step_on_random_state(prec):
+    ints, h, tabs = _case(5, 4, "jw", 6)
+    p = gb.Problem.build(ints, 4, precision=prec, device=0)
+    psi = random_state(10, seed=1)
+    for k in (0, 7, len(tabs) - 1):
+        d = _to_dev(p, psi)
+        psi_in = _host(d)
+        p.taylor_step(k, 0.37, d)
+        ref = sv.taylor5(tabs[k], 0.37, psi_in)
+        assert np.max(np.abs(_host(d) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_orb,n_elec,mp,seed", [(3, 2, "jw", 0), (5, 4, "bk", 1), (7, 6, "jw", 0)])
+def test_pool_gradients(prec, n_orb, n_elec, mp, seed):
+    ints, h, tabs = _case(n_orb, n_elec, mp, seed)
+    p = gb.Problem.build(ints, n_elec, mapping=mp, precision=prec, device=0)
+    n = 2 * n_orb
+    ops, th = draw_ansatz(len(tabs), 6, seed=seed, theta_sigma=0.3)
+    ws = p.workspace()
+    p.prepare_state(ops, th, ws[0])
+    p.energy(ws[0], ws[1])
+    g = p.pool_gradients(ws[0], ws[1])
+    psi_in = _host(ws[0])
+    g_ref = sv.pool_gradients(h, tabs, psi_in)
+    assert np.max(np.abs(g - g_ref)) <= TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref)))
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n_orb,n_elec,mp,seed", [(2, 2, "jw", 0), (3, 2, "bk", 2), (4, 4, "jw", 3)])
+def test_energy_grad_adjoint(prec, n_orb, n_elec, mp, seed):
+    ints, h, tabs = _case(n_orb, n_elec, mp, seed)
+    p = gb.Problem.build(ints, n_elec, mapping=mp, precision=prec, device=0)
+    n = 2 * n_orb
+    ops, th = draw_ansatz(len(tabs), 8, seed=seed, theta_sigma=0.3)
+    e, de = p.energy_grad(ops, th)
+    ref = sv.basis_state(n, p.info["ref_index"])
+    e_ref, de_ref = sv.energy_grad(h, ref, tabs, ops, th)
+    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 10
+    if prec == "c128":
+        hs = 1e-5
+        for j in range(len(ops)):
+            tp, tm = th.copy(), th.copy()
+            tp[j] += hs
+            tm[j] -= hs
+            fd = (sv.energy(h, sv.prepare_state(ref, tabs, ops, tp))
+                  - sv.energy(h, sv.prepare_state(ref, tabs, ops, tm))) / (2 * hs)
+            assert abs(de[j] - fd) < 1e-8
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_adapt_step_selection(prec):
+    ints, h, tabs = _case(4, 4, "jw", 5)
+    p = gb.Problem.build(ints, 4, precision=prec, device=0)
+    ops, th = draw_ansatz(len(tabs), 3, seed=5, theta_sigma=0.2)
+    e, nrm, g, sel = p.adapt_step(ops, th, tie_rel=1e-8 if prec == "c128" else 1e-4)
+    psi = sv.prepare_state(sv.basis_state(8, p.info["ref_index"]), tabs, ops, th)
+    g_ref = sv.pool_gradients(h, tabs, psi)
+    mag = np.abs(g_ref)
+    allowed = np.flatnonzero(mag >= mag.max() * (1 - 1e-3))
+    assert sel == allowed.min()
+    assert abs(e - sv.energy(h, psi)) <= TOL[prec]["energy"] * 10
+
+
+def _hermitian_random_table(n, t, rng, anti=False):
+    x = rng.integers(0, 1 << n, size=t)
+    z = rng.integers(0, 1 << n, size=t)
+    base = parity(x & z) ^ (1 if anti else 0)
+    ph = base + 2 * rng.integers(0, 2, size=t)       # c i^ph X^x Z^z (anti-)Hermitian
+    c = rng.integers(-8, 9, size=t) / 8.0 if anti else rng.normal(size=t)
+    c[c == 0] = 0.125
+    return PauliTable(n, x.astype(np.int64), z.astype(np.int64), ph.astype(np.int64), c)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 11])
+def test_random_tables_with_phases(prec, n):
+    rng = np.random.default_rng(n)
+    H = _hermitian_random_table(n, 5 * n + 3, rng)
+    gens = []
+    for _ in range(4):
+        x = int(rng.integers(1, 1 << n))
+        z = rng.integers(0, 1 << n, size=3).astype(np.int64)
+        ph = (parity(x & z) ^ 1) + 2 * rng.integers(0, 2, size=3)    # anti-Hermitian strings
+        c = rng.integers(1, 9, size=3) / 8.0
+        gens.append(PauliTable(n, np.full(3, x, np.int64), z, ph.astype(np.int64), c))
+    to_t = lambda t: (t.x.astype(np.uint32), t.z.astype(np.uint32), (t.phase % 4).astype(np.uint8), t.coeff)
+    try:
+        p = gb.Problem.from_tables(n, to_t(H), [to_t(g) for g in gens], ref_index=0, precision=prec, device=0)
+    except gb.GocpError:
+        pytest.skip("random generator summed to zero")
+    psi = random_state(n, seed=3 * n)
+    d = _to_dev(p, psi)
+    psi_in = _host(d)
+    hd = torch.empty_like(d)
+    e, _ = p.energy(d, hd)
+    ref = sv.apply_terms(H, psi_in)
+    assert np.max(np.abs(_host(hd) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 2
+    # generator tables as the library canonicalised them
+    off, gx, gz, gph, gc, fam = p.pool()
+    tabs = [PauliTable(n, gx[off[k]:off[k + 1]].astype(np.int64), gz[off[k]:off[k + 1]].astype(np.int64),
+                       gph[off[k]:off[k + 1]].astype(np.int64), gc[off[k]:off[k + 1]]) for k in range(len(gens))]
+    ops, th = np.array([0, 1, 2, 3, 1], np.int32), np.array([0.3, -0.2, 0.5, 0.1, -0.4])
+    d2 = p.new_states(1)[0]
+    p.prepare_state(ops, th, d2)
+    sref = sv.prepare_state(sv.basis_state(n, 0), tabs, ops, th)
+    assert np.max(np.abs(_host(d2) - sref)) <= TOL[prec]["state"] * np.max(np.abs(sref)) * 4
+    e2, de = p.energy_grad(ops, th)
+    e_ref, de_ref = sv.energy_grad(H, sv.basis_state(n, 0), tabs, ops, th)
+    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
+    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
+
+
+def test_empty_ansatz_gives_reference_energy():
+    ints, h, tabs = _case(4, 4, "bk", 1)
+    p = gb.Problem.build(ints, 4, mapping="bk", precision="c128", device=0)
+    e, de = p.energy_grad(np.zeros(0, np.int32), np.zeros(0))
+    assert de.size == 0
+    hf = sv.basis_state(8, mapping.hf_index("bk", 8, 4))
+    assert abs(e - sv.energy(h, hf)) < 1e-12
+
+
+def test_device_ansatz_out_of_range_is_flagged_not_faulted():
+    ints, h, tabs = _case(3, 2, "jw", 0)
+    p = gb.Problem.build(ints, 2, precision="c128", device=0)
+    ops = torch.tensor([0, 99, 1], dtype=torch.int32, device="cuda:0")
+    th = torch.tensor([0.1, 0.2, 0.3], dtype=torch.float64, device="cuda:0")
+    d = p.new_states(1)[0]
+    p.prepare_state(ops, th, d)
+    assert p.device_errors() == 1
+    ref = sv.prepare_state(sv.basis_state(6, p.info["ref_index"]), tabs, [0, 1], [0.1, 0.3])
+    assert np.max(np.abs(_host(d) - ref)) < 1e-12   # the bad operator acted as identity
+    assert p.device_errors() == 0
+    with pytest.raises(gb.GocpError):
+        p.prepare_state(np.array([0, 99]), np.array([0.1, 0.2]), d)   # host arrays are checked up front
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_full_size_20q_sampled_rows(prec):
+    ints, c = config_integrals("c3_20q")
+    h = mapping.hamiltonian_table(ints, "jw", c["int_drop"], c["term_drop"])
+    p = gb.Problem.build(ints, 10, precision=prec, term_drop=c["term_drop"], device=0)
+    psi = random_state(20, seed=77)
+    d = _to_dev(p, psi)
+    psi_in = _host(d)
+    hd = torch.empty_like(d)
+    e, nrm = p.energy(d, hd)
+    rows = np.random.default_rng(0).integers(0, 1 << 20, size=48)
+    rows = np.concatenate([rows, [0, (1 << 20) - 1, p.info["ref_index"]]])
+    ref = sv.apply_terms_at(h, psi_in, rows)
+    got = _host(hd)[rows]
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale * 5
+
+
+def test_full_size_24q_sparse_prepare_energy_gradients():
+    ints, c = config_integrals("c5_24q")
+    h = mapping.hamiltonian_table(ints, "jw", c["int_drop"], c["term_drop"])
+    tabs = opool.pool_tables(24, 8, "jw")
+    p = gb.Problem.build(ints, 8, precision="c64", int_drop=c["int_drop"], device=0)
+    ops, th = draw_ansatz(len(tabs), 6, seed=0, theta_sigma=0.3)
+    ws = p.workspace()
+    e2, nrm, g, sel = p.adapt_step(ops, th, ws=ws, tie_rel=1e-4)
+    si, svals = sv.prepare_state_sparse(p.info["ref_index"], tabs, ops, th)
+    got = _host(ws[0])
+    ref = np.zeros(1 << 24, np.complex128)
+    ref[si] = svals
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    assert 1.0 - sv.fidelity(got, ref) <= 1e-6
+    hi, hv = sv.apply_terms_sparse(h, si, svals)
+    nn = sv.sparse_dot(si, svals, si, svals).real
+    e_ref = sv.sparse_dot(si, svals, hi, hv).real / nn
+    assert abs(e2 - e_ref) <= 1e-6
+    for k in list(range(0, len(tabs), 97)) + [int(np.argmax(np.abs(g)))]:
+        ai, av = sv.apply_terms_sparse(tabs[k], si, svals)
+        g_ref = 2 * sv.sparse_dot(hi, hv, ai, av).real / nn
+        assert abs(g[k] - g_ref) <= 2e-6, (k, g[k], g_ref)

@@ -134,3 +134,22 @@ def test_sector_preserved_by_taylor():
     # only rounding residue outside it
     assert np.max(np.abs(psi[outside])) < 1e-15
     assert np.linalg.norm(psi[~outside]) > 0.9
+
+
+def test_sparse_paths_equal_dense():
+    ints = molecular_integrals(4, seed=7, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw")
+    tabs = pool.pool_tables(8, 4, "jw")
+    hf = mapping.hf_index("jw", 8, 4)
+    rng = np.random.default_rng(1)
+    ops, th = rng.integers(0, len(tabs), 9), rng.normal(0, 0.3, 9)
+    dense = sv.prepare_state(sv.basis_state(8, hf), tabs, ops, th)
+    si, svals = sv.prepare_state_sparse(hf, tabs, ops, th)
+    rebuilt = np.zeros(256, np.complex128)
+    rebuilt[si] = svals
+    assert np.max(np.abs(rebuilt - dense)) < 1e-14
+    hi, hv = sv.apply_terms_sparse(h, si, svals)
+    hd = np.zeros(256, np.complex128)
+    hd[hi] = hv
+    assert np.max(np.abs(hd - sv.apply_terms(h, dense))) < 1e-13
+    assert abs(sv.sparse_dot(si, svals, hi, hv) - np.vdot(dense, hd)) < 1e-13
