@@ -12,10 +12,6 @@
 
 #include "internal.h"
 
-struct gocp_problem {
-  gocp::Problem p;
-};
-
 namespace gocp {
 
 namespace {
@@ -82,9 +78,8 @@ double* scalars_ptr(Problem& p);
 double* grads_ptr(Problem& p);
 int32_t* selected_ptr(Problem& p);
 int32_t* err_ptr(Problem& p);
-int dev_reference(Problem& p, void* psi, cudaStream_t st);
-int dev_taylor_chain(Problem& p, const int32_t* d_ops, const double* d_theta, int n_ops, void* psi,
-                     cudaStream_t st);
+int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st);
+int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st);
 int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st);
 int dev_norm(Problem& p, const void* psi, cudaStream_t st);
 int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st);
@@ -380,7 +375,7 @@ int gocp_reference_state(const gocp_problem* h, void* psi, void* stream) {
   if (!psi) return fail(GOCP_EINVAL, "psi is NULL");
   Problem& p = const_cast<Problem&>(h->p);
   DeviceGuard g(p.device);
-  return dev_reference(p, psi, (cudaStream_t)stream);
+  return dev_setup(p, psi, nullptr, 0, (cudaStream_t)stream);
 }
 
 int gocp_prepare_state(const gocp_problem* h, const int32_t* ops, const double* theta, int n_ops,
@@ -394,8 +389,8 @@ int gocp_prepare_state(const gocp_problem* h, const int32_t* ops, const double* 
   const int32_t* d_ops;
   const double* d_theta;
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
-  if ((rc = dev_reference(p, psi, st))) return rc;
-  return dev_taylor_chain(p, d_ops, d_theta, n_ops, psi, st);
+  if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
+  return dev_taylor_chain(p, d_ops, n_ops, psi, st);
 }
 
 int gocp_taylor_step(const gocp_problem* h, int op, double theta, void* psi, void* stream) {
@@ -410,7 +405,8 @@ int gocp_taylor_step(const gocp_problem* h, int op, double theta, void* psi, voi
   int32_t ops[1] = {op};
   double th[1] = {theta};
   if ((rc = stage_ansatz(p, ops, th, 1, GOCP_MEM_HOST, st, &d_ops, &d_theta))) return rc;
-  return dev_taylor_chain(p, d_ops, d_theta, 1, psi, st);
+  if ((rc = dev_setup(p, nullptr, d_theta, 1, st))) return rc;
+  return dev_taylor_chain(p, d_ops, 1, psi, st);
 }
 
 int gocp_apply_h(const gocp_problem* h, const void* psi, void* hpsi, void* stream) {
@@ -459,8 +455,8 @@ int gocp_energy_grad(const gocp_problem* h, const int32_t* ops, const double* th
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
   void* psi = ws;
   void* lam = (char*)ws + state_bytes(p);
-  if ((rc = dev_reference(p, psi, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, d_theta, n_ops, psi, st))) return rc;
+  if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
+  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, st))) return rc;
   if ((rc = dev_apply_h(p, psi, lam, true, st))) return rc;
   double* d_dE = mem == GOCP_MEM_DEVICE ? dE : dtheta_ptr(p);
   if (n_ops > 0 && (rc = dev_adjoint(p, d_ops, n_ops, psi, lam, d_dE, st))) return rc;
@@ -489,8 +485,8 @@ int gocp_adapt_step(const gocp_problem* h, const int32_t* ops, const double* the
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
   void* psi = ws;
   void* hpsi = (char*)ws + state_bytes(p);
-  if ((rc = dev_reference(p, psi, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, d_theta, n_ops, psi, st))) return rc;
+  if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
+  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, st))) return rc;
   if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
   double* d_grads = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
   if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, st))) return rc;

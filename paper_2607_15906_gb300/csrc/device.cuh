@@ -35,7 +35,9 @@ __device__ __forceinline__ C_t<R> cconj(C_t<R> a) { return cmake<R>(a.x, -a.y); 
 
 // Device copies of the tables of one problem.
 //
-// Hamiltonian: groups of terms sharing an x mask, ascending x.  Group g owns
+// Hamiltonian: the identity term is a scalar; the diagonal group (x = 0) is
+// kept apart; the other groups of terms sharing an x mask come in ascending
+// x.  Group g owns
 // terms [goff[g], goff[g+1]); terms [goff[g], gmid[g]) have real weights,
 // [gmid[g], goff[g+1]) imaginary ones.  The weight of term t is
 //   w_t = c_t i^phase_t (-1)^popc(x_g & z_t),
@@ -59,6 +61,10 @@ struct DevTables {
   const int32_t* chunk_g = nullptr;
   const uint32_t* tz = nullptr;
   const void* tw = nullptr;
+  // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
+  int nd = 0, nd_mid = 0;
+  const uint32_t* dz = nullptr;
+  const void* dw = nullptr;
   int M = 0;
   int64_t S = 0;
   const uint32_t* px = nullptr;

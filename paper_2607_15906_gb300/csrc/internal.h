@@ -102,6 +102,8 @@ struct Problem {
   PauliTerms H;
   Pool pool;
   int64_t n_groups = 0;
+  double identity = 0.0;   // coefficient of the identity term (set at upload)
+  int sm_count = 0;
   DeviceTables* dev = nullptr;
   size_t device_bytes = 0;
 };
@@ -109,4 +111,39 @@ struct Problem {
 int upload_problem(Problem& p);
 void free_device(Problem& p);
 
+// ------------------------------------------------------------ batched stages
+//
+// One launch advances many resident requests (possibly of different sizes
+// and Hamiltonians) by one stage.  Each item's block count depends only on
+// the item, so its result is the same alone or in any batch.
+struct StageItem {
+  const Problem* prob = nullptr;
+  void* psi = nullptr;             // state (FORWARD, ENERGY, BACKWARD)
+  void* lam = nullptr;             // H psi, then lambda (ENERGY, BACKWARD)
+  const int32_t* ops = nullptr;    // device ansatz of the request
+  const double* theta = nullptr;
+  double* coefs = nullptr;         // 6 per op
+  int n_ops = 0;
+  int j = 0;                       // operator index of this stage
+  double* partials = nullptr;      // >= kMaxItemBlocks doubles
+  unsigned int* counter = nullptr; // 1, zero between launches
+  double* scal = nullptr;          // [0] E [1] <psi|psi> [2] Re<psi|H'psi>
+  double* dtheta = nullptr;        // n_ops doubles
+  int32_t* err = nullptr;
+};
+constexpr int kMaxBatchItems = 256;
+constexpr int kMaxItemBlocks = 1216;
+enum StageKind { STAGE_SETUP = 0, STAGE_FORWARD = 1, STAGE_ENERGY = 2, STAGE_BACKWARD = 3 };
+// Launches one batched stage over items[0..n) of one precision.  host_desc /
+// dev_desc: a pinned host and a device buffer of >= batch_desc_bytes(n)
+// bytes used to ship the item descriptors; they must stay untouched until
+// the launch completes.
+size_t batch_desc_bytes(int n);
+int launch_stage(int kind, const StageItem* items, int n, int precision, void* host_desc,
+                 void* dev_desc, void* stream, int64_t* launches);
+
 }  // namespace gocp
+
+struct gocp_problem {
+  gocp::Problem p;
+};

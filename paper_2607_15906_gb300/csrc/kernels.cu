@@ -1,15 +1,19 @@
 // sm_103a kernels of the hot path and their launchers.
 //
-//   k_apply_h     (H psi)[k] = sum_g D_g(k) psi[k ^ x_g]   (Eq. 3), with the
-//                 energy <psi|H psi> / <psi|psi> (Eq. 1) as an FP64 epilogue
-//   k_taylor5     psi <- sum_{m<=5} theta^m/m! v_m, v_m = A v_{m-1}, evaluated
-//                 on each basis pair {b, b^x} in registers (Eq. 5, 6)
-//   k_pool_grad   g_k = 2 Re <H psi|A_k psi> / <psi|psi>, all k   (Eq. 4)
-//   k_adjoint     one backward step of the adjoint sweep for dE/dtheta
+//   apply_body     (H psi)[k] = sum_g D_g(k) psi[k ^ x_g]   (Eq. 3), with the
+//                  energy <psi|H psi> / <psi|psi> (Eq. 1) as an FP64 epilogue
+//   taylor_body    psi <- sum_{m<=5} theta^m/m! v_m, v_m = A v_{m-1}, evaluated
+//                  on each basis pair {b, b^x} in registers (Eq. 5, 6)
+//   k_pool_grad    g_k = 2 Re <H psi|A_k psi> / <psi|psi>, all k   (Eq. 4)
+//   adjoint_body   one backward step of the adjoint sweep for dE/dtheta
+//
+// Each body takes (block id, block count) of its own work item, so the same
+// code serves one problem (a grid of one item) and the request server (one
+// launch over many resident requests of different sizes).
 //
 // Every reduction is deterministic: each block writes its partial sums and
 // the last block to finish (threadfence + counter) adds them in a fixed
-// order, so a result does not depend on scheduling.
+// order, so a result does not depend on scheduling or on the batch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -23,12 +27,14 @@ namespace gocp {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kAmps = 4;             // amplitudes per thread in H psi
+constexpr int kTile = kThreads * kAmps;
 constexpr int kChunkTerms = 2048;    // shared-memory stage of H psi
 constexpr int kChunkGroups = 512;
 constexpr int kOpsPerBlock = 16;     // pool operators per gradient block
 constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor block
-constexpr int kKahanTerms = 16;      // c64: compensated sums for larger groups
+constexpr int kKahanTerms = 16;      // c64: compensated sums for longer groups
 constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
+constexpr int kItemBlocksPerSm = 2;  // batched stages: blocks per item per SM
 
 struct DeviceTables {
   DevTables t;
@@ -38,7 +44,6 @@ struct DeviceTables {
   size_t scratch_doubles = 0;
   unsigned int* counters = nullptr;  // kMaxChunks + 8
   double* scalars = nullptr;         // [0] E  [1] <psi|psi>  [2] Re<psi|H'psi>
-  double identity = 0.0;             // coefficient of the identity term of H
   int32_t* stage_ops = nullptr;
   double* stage_theta = nullptr;
   double* coefs = nullptr;           // 6 Taylor coefficients per ansatz op
@@ -47,7 +52,7 @@ struct DeviceTables {
   int32_t* err = nullptr;
   int32_t* selected = nullptr;
   double* grads = nullptr;           // pool_size doubles (pool order)
-  double* graw = nullptr;            // pool_size doubles (family order, unscaled)
+  double* graw = nullptr;            // whole chunks, family order, unscaled
 };
 
 // ------------------------------------------------------------ reductions
@@ -57,11 +62,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Adds v[0..NV) over the nblocks blocks of one grid slice into out[0..NV).
-// partials: NV doubles per block of the slice; counter: one per slice.
+// Adds v[0..NV) over the nblocks blocks of one work item into out[0..NV).
+// partials: NV doubles per block; counter: one per item, zero on entry and
+// reset on exit.  Returns true in the last block, where tot[0..NV) (shared)
+// then holds the totals for every thread.
 template <int NV>
-__device__ void grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
-                         int nblocks, int bid, double* out) {
+__device__ bool grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
+                         int nblocks, int bid, double* out, double* tot) {
   __shared__ double red[NV][kWarps];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -80,7 +87,7 @@ __device__ void grid_sum(const double (&v)[NV], double* partials, unsigned int* 
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblocks - 1);
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   double acc[NV];
 #pragma unroll
@@ -100,57 +107,72 @@ __device__ void grid_sum(const double (&v)[NV], double* partials, unsigned int* 
     double s = 0.0;
     for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
     out[threadIdx.x] = s;
+    tot[threadIdx.x] = s;
   }
   if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+// ------------------------------------------------------------ setup
+
+// psi = |index>; block 0 also writes the Taylor coefficients
+// coefs[6j + m] = theta_j^m / m!, m = 0..5, of every ansatz operator.
+template <typename R>
+__device__ void setup_body(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops,
+                           double* coefs, int bid, int nb) {
+  const uint64_t dim = 1ull << n;
+  if (psi)
+    for (uint64_t k = bid * (uint64_t)kThreads + threadIdx.x; k < dim; k += (uint64_t)nb * kThreads)
+      psi[k] = cmake<R>(k == index ? R(1) : R(0), R(0));
+  if (bid == 0)
+    for (int j = threadIdx.x; j < n_ops; j += kThreads) {
+      double th = theta[j], c = 1.0;
+      coefs[6 * j] = 1.0;
+      for (int m = 1; m <= 5; ++m) {
+        c = c * th / (double)m;
+        coefs[6 * j + m] = c;
+      }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs) {
+  setup_body<R>(psi, n, index, theta, n_ops, coefs, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ small kernels
 
 template <typename R>
-__global__ void k_basis_state(C_t<R>* psi, uint64_t dim, uint64_t index) {
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
-       k += (uint64_t)gridDim.x * blockDim.x)
-    psi[k] = cmake<R>(k == index ? R(1) : R(0), R(0));
-}
-
-// Taylor coefficients theta^m / m!, m = 0..5, of each ansatz operator.
-__global__ void k_series(const double* theta, int n_ops, double* coefs) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_ops) return;
-  double th = theta[j], c = 1.0;
-  coefs[6 * j] = 1.0;
-  for (int m = 1; m <= 5; ++m) {
-    c = c * th / (double)m;
-    coefs[6 * j + m] = c;
-  }
-}
-
-template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_norm(const C_t<R>* psi, uint64_t dim, double* partials, unsigned int* counter, double* out) {
+  __shared__ double tot[1];
   double v[1] = {0.0};
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
        k += (uint64_t)gridDim.x * blockDim.x) {
     C_t<R> a = psi[k];
     v[0] += (double)a.x * a.x + (double)a.y * a.y;
   }
-  grid_sum<1>(v, partials, counter, gridDim.x, blockIdx.x, out);
+  grid_sum<1>(v, partials, counter, gridDim.x, blockIdx.x, out, tot);
 }
 
 // lambda = (hpsi - E psi) / <psi|psi> in place over hpsi (E, <psi|psi> = scal[0..1]).
 template <typename R>
-__global__ void k_residual(const C_t<R>* psi, C_t<R>* hpsi, uint64_t dim, const double* scal) {
+__device__ void residual_body(const C_t<R>* psi, C_t<R>* hpsi, int n, const double* scal, int bid,
+                              int nb) {
+  const uint64_t dim = 1ull << n;
   const R er = (R)scal[0], ir = (R)(1.0 / scal[1]);
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < dim;
-       k += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t k = bid * (uint64_t)kThreads + threadIdx.x; k < dim; k += (uint64_t)nb * kThreads) {
     C_t<R> h = hpsi[k], p = psi[k];
     hpsi[k] = cmake<R>((h.x - er * p.x) * ir, (h.y - er * p.y) * ir);
   }
 }
 
-// E = identity + Re<psi|H' psi> / <psi|psi>.
-__global__ void k_energy_final(double* scal, double identity) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) scal[0] = identity + scal[2] / scal[1];
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_residual(const C_t<R>* psi, C_t<R>* hpsi, int n, const double* scal) {
+  residual_body<R>(psi, hpsi, n, scal, blockIdx.x, gridDim.x);
 }
 
 // grads[porder[i]] = 2 raw[i] / <psi|psi>.
@@ -187,15 +209,13 @@ __global__ void k_select(const double* g, int m, double tie_rel, int32_t* out) {
 
 // ------------------------------------------------------------ H psi + energy
 
-// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k[i] & z_t); compensated in FP32
-// for longer groups (the diagonal group of a molecular H holds O(n^2) terms).
+// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k[i] & z_t), compensated in FP32
+// when asked; comp[i] carries the lost low-order part (true sum d - comp).
 template <typename R>
-__device__ __forceinline__ void sum_group(const uint32_t* zs, const R* ws, int tb, int te,
-                                          const uint32_t (&k)[kAmps], R (&d)[kAmps]) {
-  if (sizeof(R) == 4 && te - tb > kKahanTerms) {
-    R comp[kAmps];
-#pragma unroll
-    for (int i = 0; i < kAmps; ++i) comp[i] = R(0);
+__device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int tb, int te,
+                                          const uint32_t (&k)[kAmps], R (&d)[kAmps],
+                                          R (&comp)[kAmps], bool compensate) {
+  if (sizeof(R) == 4 && compensate) {
     for (int t = tb; t < te; ++t) {
       const uint32_t z = zs[t];
       const R w = ws[t];
@@ -217,92 +237,118 @@ __device__ __forceinline__ void sum_group(const uint32_t* zs, const R* ws, int t
   }
 }
 
-// A thread owns kAmps output amplitudes k = tile + i*blockDim + tid.  The
-// group table is staged in shared memory chunk by chunk (a single group too
-// large for the stage is read from global memory).  The identity term of H
-// is excluded from the groups and added as identity * psi[k].  With
-// `partials` set the grid also reduces <psi|psi> -> scal[1] and
-// Re<psi|H' psi> -> scal[2] in FP64.
+// A block sweeps tiles of kTile output amplitudes; a thread owns kAmps of
+// them, k = tile*kTile + i*kThreads + tid.  The diagonal group (x = 0, the
+// identity excluded) is summed first with a compensated sum whose high and
+// low parts both enter the FP64 energy; the off-diagonal groups are staged
+// in shared memory chunk by chunk (a single group too large for the stage is
+// read from global memory).  The identity term is added as identity*psi[k].
+// With `partials` set the item's blocks also reduce <psi|psi> -> scal[1] and
+// Re<psi|H' psi> -> scal[2] in FP64, and the last block sets
+// scal[0] = E = identity + scal[2] / scal[1].
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_apply_h(DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, R identity,
-          double* partials, unsigned int* counter, double* scal) {
+__device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
+                           C_t<R>* __restrict__ out, double identity, double* partials,
+                           unsigned int* counter, double* scal, int bid, int nb) {
   __shared__ uint32_t s_x[kChunkGroups];
   __shared__ int32_t s_off[kChunkGroups + 1];
   __shared__ int32_t s_mid[kChunkGroups];
   __shared__ uint32_t s_z[kChunkTerms];
   __shared__ R s_w[kChunkTerms];
+  __shared__ double tot[2];
   const R* tw = (const R*)tb.tw;
+  const R* dw = (const R*)tb.dw;
+  const R idr = (R)identity;
   const uint64_t dim = 1ull << tb.n;
-  const uint64_t base = (uint64_t)blockIdx.x * (kThreads * kAmps);
-  uint32_t k[kAmps];
-  bool live[kAmps];
-  C_t<R> acc[kAmps];
-#pragma unroll
-  for (int i = 0; i < kAmps; ++i) {
-    uint64_t kk = base + (uint64_t)i * kThreads + threadIdx.x;
-    live[i] = kk < dim;
-    k[i] = live[i] ? (uint32_t)kk : 0u;
-    acc[i] = cmake<R>(0, 0);
-  }
-  for (int c = 0; c < tb.n_chunks; ++c) {
-    const int g0 = tb.chunk_g[c], g1 = tb.chunk_g[c + 1];
-    const int t0 = tb.goff[g0], t1 = tb.goff[g1];
-    const bool staged = (t1 - t0) <= kChunkTerms;   // chunks never exceed kChunkGroups
-    __syncthreads();
-    for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
-      s_x[g - g0] = tb.gx[g];
-      s_off[g - g0] = tb.goff[g] - t0;
-      s_mid[g - g0] = tb.gmid[g] - t0;
-    }
-    if (threadIdx.x == 0) s_off[g1 - g0] = t1 - t0;
-    if (staged)
-      for (int t = t0 + threadIdx.x; t < t1; t += kThreads) {
-        s_z[t - t0] = tb.tz[t];
-        s_w[t - t0] = tw[t];
-      }
-    __syncthreads();
-    const uint32_t* zs = staged ? s_z : tb.tz + t0;
-    const R* ws = staged ? s_w : tw + t0;
-    for (int g = g0; g < g1; ++g) {
-      const uint32_t x = s_x[g - g0];
-      const int tbeg = s_off[g - g0], tmid = s_mid[g - g0], tend = s_off[g - g0 + 1];
-      R dr[kAmps], di[kAmps];
-#pragma unroll
-      for (int i = 0; i < kAmps; ++i) {
-        dr[i] = R(0);
-        di[i] = R(0);
-      }
-      sum_group<R>(zs, ws, tbeg, tmid, k, dr);
-      if (tend > tmid) sum_group<R>(zs, ws, tmid, tend, k, di);
-#pragma unroll
-      for (int i = 0; i < kAmps; ++i) {
-        C_t<R> p = psi[k[i] ^ x];   // k[i] = 0 for dead lanes: in bounds
-        acc[i].x += dr[i] * p.x - di[i] * p.y;
-        acc[i].y += dr[i] * p.y + di[i] * p.x;
-      }
-    }
-  }
+  const uint64_t ntiles = (dim + kTile - 1) / kTile;
   double v[2] = {0.0, 0.0};
+  for (uint64_t tile = bid; tile < ntiles; tile += nb) {
+    const uint64_t base = tile * kTile;
+    uint32_t k[kAmps];
+    bool live[kAmps];
+    C_t<R> acc[kAmps];
+    R dr[kAmps], dc[kAmps], di[kAmps], dd[kAmps];
 #pragma unroll
-  for (int i = 0; i < kAmps; ++i) {
-    if (!live[i]) continue;
-    C_t<R> p = psi[k[i]];
-    v[0] += (double)p.x * p.x + (double)p.y * p.y;
-    v[1] += (double)p.x * acc[i].x + (double)p.y * acc[i].y;
-    out[k[i]] = cmake<R>(acc[i].x + identity * p.x, acc[i].y + identity * p.y);
+    for (int i = 0; i < kAmps; ++i) {
+      uint64_t kk = base + (uint64_t)i * kThreads + threadIdx.x;
+      live[i] = kk < dim;
+      k[i] = live[i] ? (uint32_t)kk : 0u;
+      acc[i] = cmake<R>(0, 0);
+      dr[i] = dc[i] = di[i] = dd[i] = R(0);
+    }
+    // diagonal group
+    sum_terms<R>(tb.dz, dw, 0, tb.nd_mid, k, dr, dc, true);
+    sum_terms<R>(tb.dz, dw, tb.nd_mid, tb.nd, k, di, dd, false);
+    // off-diagonal groups
+    for (int c = 0; c < tb.n_chunks; ++c) {
+      const int g0 = tb.chunk_g[c], g1 = tb.chunk_g[c + 1];
+      const int t0 = tb.goff[g0], t1 = tb.goff[g1];
+      const bool staged = (t1 - t0) <= kChunkTerms;   // chunks never exceed kChunkGroups
+      __syncthreads();
+      for (int g = g0 + threadIdx.x; g < g1; g += kThreads) {
+        s_x[g - g0] = tb.gx[g];
+        s_off[g - g0] = tb.goff[g] - t0;
+        s_mid[g - g0] = tb.gmid[g] - t0;
+      }
+      if (threadIdx.x == 0) s_off[g1 - g0] = t1 - t0;
+      if (staged)
+        for (int t = t0 + threadIdx.x; t < t1; t += kThreads) {
+          s_z[t - t0] = tb.tz[t];
+          s_w[t - t0] = tw[t];
+        }
+      __syncthreads();
+      const uint32_t* zs = staged ? s_z : tb.tz + t0;
+      const R* ws = staged ? s_w : tw + t0;
+      for (int g = g0; g < g1; ++g) {
+        const uint32_t x = s_x[g - g0];
+        const int tbeg = s_off[g - g0], tmid = s_mid[g - g0], tend = s_off[g - g0 + 1];
+        R gr[kAmps], gi[kAmps], cr[kAmps], ci[kAmps];
+#pragma unroll
+        for (int i = 0; i < kAmps; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
+        sum_terms<R>(zs, ws, tbeg, tmid, k, gr, cr, tmid - tbeg > kKahanTerms);
+        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k, gi, ci, tend - tmid > kKahanTerms);
+#pragma unroll
+        for (int i = 0; i < kAmps; ++i) {
+          const R xr = gr[i] - cr[i], xi = gi[i] - ci[i];
+          C_t<R> p = psi[k[i] ^ x];   // k[i] = 0 for dead lanes: in bounds
+          acc[i].x += xr * p.x - xi * p.y;
+          acc[i].y += xr * p.y + xi * p.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kAmps; ++i) {
+      if (!live[i]) continue;
+      const C_t<R> p = psi[k[i]];
+      const double pp = (double)p.x * p.x + (double)p.y * p.y;
+      v[0] += pp;
+      // Re(conj(p) (acc + D0 p)); the imaginary diagonal part adds nothing
+      v[1] += (double)p.x * acc[i].x + (double)p.y * acc[i].y + ((double)dr[i] - (double)dc[i]) * pp;
+      const R d0 = dr[i] - dc[i] + idr;
+      out[k[i]] = cmake<R>(acc[i].x + d0 * p.x - di[i] * p.y, acc[i].y + d0 * p.y + di[i] * p.x);
+    }
   }
-  if (partials) grid_sum<2>(v, partials, counter, gridDim.x, blockIdx.x, scal + 1);
+  if (partials && grid_sum<2>(v, partials, counter, nb, bid, scal + 1, tot)) {
+    if (threadIdx.x == 0) scal[0] = identity + tot[1] / tot[0];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_apply_h(DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, double identity,
+          double* partials, unsigned int* counter, double* scal) {
+  apply_body<R>(tb, psi, out, identity, partials, counter, scal, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ pool strings
 
-// Loads the strings of operator `op` into shared memory when they fit.
-// D(b) = sum w_t chi_t(b), D(b^x) = sum w2_t chi_t(b) with chi_t(b) = (-1)^popc(b & z_t).
+// One generator staged for the pair kernels.  D(b) = sum w_t chi_t(b) and
+// D(b^x) = sum w2_t chi_t(b), chi_t(b) = (-1)^popc(b & z_t): one parity per
+// string gives both ends of a pair.
 template <typename R>
 struct OpView {
   uint32_t x;
-  int nb, nm, ne;        // [0, nm) real weights, [nm, ne) imaginary
+  int nm, ne;            // [0, nm) real weights, [nm, ne) imaginary
   const uint32_t* z;
   const R* w;
   const R* w2;
@@ -325,13 +371,14 @@ __device__ __forceinline__ void op_d(const OpView<R>& o, uint32_t b, C_t<R>& d1,
   d2 = cmake<R>(r2, i2);
 }
 
-// Resolves ops[j] (flagging out-of-range indices) and stages its strings.
+// Resolves ops[j] (flagging out-of-range indices: the step then acts as the
+// identity) and stages its strings in shared memory when they fit.
 template <typename R>
-__device__ bool load_op(const DevTables& tb, const int32_t* ops, int j, int32_t* err,
+__device__ bool load_op(const DevTables& tb, const int32_t* ops, int j, int32_t* err, int bid,
                         uint32_t* s_z, R* s_w, R* s_w2, OpView<R>& o) {
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
+    if (bid == 0 && threadIdx.x == 0) atomicOr(err, 1);
     return false;
   }
   const int sb = tb.poff[op], sm = tb.pmid[op], se = tb.poff[op + 1];
@@ -363,7 +410,7 @@ __device__ __forceinline__ uint32_t pair_base(uint64_t p, int s) {
   return (uint32_t)(((p >> s) << (s + 1)) | (p & ((1ull << s) - 1)));
 }
 
-// Compensated complex accumulation (FP32 path; exact-order sum for FP64).
+// Compensated complex accumulation (FP32 path); plain for FP64.
 template <typename R>
 __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
   if (sizeof(R) == 4) {
@@ -382,22 +429,21 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // ------------------------------------------------------------ Taylor step
 
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
-// v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5) stay in registers.
+// v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
+// m = 0..5, stay in registers.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
-          int32_t* err) {
+__device__ void taylor_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
+                            C_t<R>* psi, int32_t* err, int bid, int nb) {
   __shared__ uint32_t s_z[kStageStrings];
   __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
   OpView<R> o;
-  if (!load_op<R>(tb, ops, j, err, s_z, s_w, s_w2, o)) return;
+  if (!load_op<R>(tb, ops, j, err, bid, s_z, s_w, s_w2, o)) return;
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
   const int s = __ffs(o.x) - 1;
   const uint64_t npairs = 1ull << (tb.n - 1);
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs;
-       p += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
     const uint32_t b = pair_base(p, s), b2 = b ^ o.x;
     C_t<R> d1, d2;
     op_d<R>(o, b, d1, d2);
@@ -411,29 +457,36 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
       kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
       kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
     }
-    psi[b] = s1;
-    psi[b2] = s2;
+    psi[b] = csub<R>(s1, e1);
+    psi[b2] = csub<R>(s2, e2);
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, int32_t* err) {
+  taylor_body<R>(tb, ops, coefs, j, psi, err, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ adjoint step
 
 // Backward step j of the adjoint sweep.  On each pair A = [[0, D1], [D2, 0]],
 // A^2 = mu I with mu = D1 D2, so T = C I + S A with C = c0 + c2 mu + c4 mu^2,
-// S = c1 + c3 mu + c5 mu^2 (c_m = theta^m/m!), T' = dT/dtheta = C' I + S' A
-// with C' = c1 mu + c3 mu^2, S' = C.  In place:
+// S = c1 + c3 mu + c5 mu^2 (c_m = theta^m/m!), and T' = dT/dtheta =
+// C' I + S' A with C' = c1 mu + c3 mu^2, S' = C.  In place:
 //   psi <- T^-1 psi = (C I - S A) psi / (C^2 - S^2 mu)      (exact inverse)
-//   dE_j += 2 Re <lambda|T' psi>                            (before the update)
+//   dE_j += 2 Re <lambda|T' psi>                            (lambda before update)
 //   lambda <- T^dagger lambda.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
-          C_t<R>* lam, double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
+__device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
+                             C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
+                             double* dtheta, int32_t* err, int bid, int nb) {
   __shared__ uint32_t s_z[kStageStrings];
   __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
+  __shared__ double tot[1];
   OpView<R> o;
-  if (!load_op<R>(tb, ops, j, err, s_z, s_w, s_w2, o)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) dtheta[j] = 0.0;
+  if (!load_op<R>(tb, ops, j, err, bid, s_z, s_w, s_w2, o)) {
+    if (bid == 0 && threadIdx.x == 0) dtheta[j] = 0.0;
     return;
   }
   R c[6];
@@ -442,8 +495,7 @@ k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
   const int s = __ffs(o.x) - 1;
   const uint64_t npairs = 1ull << (tb.n - 1);
   double v[1] = {0.0};
-  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs;
-       p += (uint64_t)gridDim.x * blockDim.x) {
+  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
     const uint32_t b = pair_base(p, s), b2 = b ^ o.x;
     C_t<R> d1, d2;
     op_d<R>(o, b, d1, d2);
@@ -468,7 +520,14 @@ k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
     lam[b] = cadd<R>(cmul<R>(cconj<R>(cc), l1), cmul<R>(cconj<R>(sd2), l2));
     lam[b2] = cadd<R>(cmul<R>(cconj<R>(sd1), l1), cmul<R>(cconj<R>(cc), l2));
   }
-  grid_sum<1>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j);
+  grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
+          double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
+  adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------ pool gradients
@@ -485,6 +544,7 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
   __shared__ uint32_t s_z[kStageStrings];
   __shared__ R s_w[kStageStrings];
   __shared__ int s_glob[kOpsPerBlock];   // op index when its strings are not staged
+  __shared__ double tot[kOpsPerBlock];
   const int first = blockIdx.y * kOpsPerBlock;
   const int nops = min(kOpsPerBlock, tb.M - first);
   const R* pw = (const R*)tb.pw;
@@ -494,18 +554,16 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
       const int op = tb.porder[first + i];
       const int sb = tb.poff[op], se = tb.poff[op + 1];
       s_x[i] = tb.px[op];
+      s_beg[i] = fill;
       if (fill + (se - sb) <= kStageStrings) {
-        s_beg[i] = fill;
         s_mid[i] = fill + tb.pmid[op] - sb;
         s_glob[i] = -1;
         fill += se - sb;
-        s_beg[i + 1] = fill;
       } else {
-        s_beg[i] = fill;
         s_mid[i] = fill;
         s_glob[i] = op;
-        s_beg[i + 1] = fill;
       }
+      s_beg[i + 1] = fill;
     }
   }
   __syncthreads();
@@ -561,7 +619,81 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
   for (int i = 0; i < kOpsPerBlock; ++i) v[i] = (double)acc[i] - (double)cmp[i];
   // raw holds a whole number of chunks, so the tail chunk's unused slots are padding
   grid_sum<kOpsPerBlock>(v, partials + (size_t)blockIdx.y * gridDim.x * kOpsPerBlock,
-                         counters + blockIdx.y, gridDim.x, blockIdx.x, raw + first);
+                         counters + blockIdx.y, gridDim.x, blockIdx.x, raw + first, tot);
+}
+
+// ------------------------------------------------------------ batched stages
+
+// One work item of a batched launch (device copy of a StageItem).
+struct BatchItemDev {
+  DevTables t;
+  const int32_t* ops;
+  const double* theta;
+  double* coefs;
+  void* psi;
+  void* lam;
+  double* partials;
+  unsigned int* counter;
+  double* scal;
+  double* dtheta;
+  int32_t* err;
+  double identity;
+  uint32_t ref_index;
+  int n_ops;
+  int j;
+  int nb;
+};
+
+struct BatchIndex {
+  int n;
+  int start[kMaxBatchItems + 1];   // first block of each item
+};
+
+__device__ __forceinline__ int find_item(const BatchIndex& ix, int& bid) {
+  int lo = 0, hi = ix.n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ix.start[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  bid = blockIdx.x - ix.start[lo];
+  return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_stage_setup(const BatchItemDev* items, BatchIndex ix) {
+  int bid;
+  const BatchItemDev& it = items[find_item(ix, bid)];
+  setup_body<R>((C_t<R>*)it.psi, it.t.n, it.ref_index, it.theta, it.n_ops, it.coefs, bid, it.nb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_stage_forward(const BatchItemDev* items, BatchIndex ix) {
+  int bid;
+  const BatchItemDev& it = items[find_item(ix, bid)];
+  taylor_body<R>(it.t, it.ops, it.coefs, it.j, (C_t<R>*)it.psi, it.err, bid, it.nb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_stage_energy(const BatchItemDev* items, BatchIndex ix) {
+  int bid;
+  const BatchItemDev& it = items[find_item(ix, bid)];
+  apply_body<R>(it.t, (const C_t<R>*)it.psi, (C_t<R>*)it.lam, it.identity, it.partials, it.counter,
+                it.scal, bid, it.nb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_stage_residual(const BatchItemDev* items, BatchIndex ix) {
+  int bid;
+  const BatchItemDev& it = items[find_item(ix, bid)];
+  residual_body<R>((const C_t<R>*)it.psi, (C_t<R>*)it.lam, it.t.n, it.scal, bid, it.nb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_stage_backward(const BatchItemDev* items, BatchIndex ix) {
+  int bid;
+  const BatchItemDev& it = items[find_item(ix, bid)];
+  adjoint_body<R>(it.t, it.ops, it.coefs, it.j, (C_t<R>*)it.psi, (C_t<R>*)it.lam, it.partials,
+                  it.counter, it.dtheta, it.err, bid, it.nb);
 }
 
 // ------------------------------------------------------------ upload
@@ -601,13 +733,13 @@ inline double eff_weight(double c, int phase, uint32_t x, uint32_t z, bool* imag
 }
 
 template <typename R>
-int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
+int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   const PauliTerms& H = p.H;
-  // ---- Hamiltonian groups (identity term handled apart)
-  std::vector<uint32_t> gx, tz;
+  // ---- Hamiltonian: identity apart, diagonal group apart, off-diagonal groups
+  std::vector<uint32_t> gx, tz, dz_r, dz_i;
   std::vector<int32_t> goff, gmid;
-  std::vector<R> tw;
-  d.identity = 0.0;
+  std::vector<R> tw, dw_r, dw_i;
+  double ident = 0.0;
   size_t i = 0;
   while (i < H.size()) {
     size_t j = i;
@@ -618,13 +750,18 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
       bool imag = false;
       double w = eff_weight(H.coeff[t], H.phase[t], H.x[t], H.z[t], &imag);
       if (H.x[t] == 0 && H.z[t] == 0 && !imag) {
-        d.identity += w;
+        ident += w;
         continue;
       }
       (imag ? zi : zr).push_back(H.z[t]);
       (imag ? wi : wr).push_back((R)w);
     }
-    if (!zr.empty() || !zi.empty()) {
+    if (H.x[i] == 0) {
+      dz_r = zr;
+      dw_r = wr;
+      dz_i = zi;
+      dw_i = wi;
+    } else if (!zr.empty() || !zi.empty()) {
       gx.push_back(H.x[i]);
       goff.push_back((int32_t)tz.size());
       tz.insert(tz.end(), zr.begin(), zr.end());
@@ -636,6 +773,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
     i = j;
   }
   goff.push_back((int32_t)tz.size());
+  *identity = ident;
   const int G = (int)gx.size();
   // chunk plan: runs of groups whose terms fit the shared-memory stage
   std::vector<int32_t> chunk{0};
@@ -649,13 +787,18 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
       g = h;
     }
   }
+  std::vector<uint32_t> dz(dz_r);
+  dz.insert(dz.end(), dz_i.begin(), dz_i.end());
+  std::vector<R> dw(dw_r);
+  dw.insert(dw.end(), dw_i.begin(), dw_i.end());
   int rc;
-  uint32_t *dgx, *dtz;
+  uint32_t *dgx, *dtz, *ddz;
   int32_t *dgoff, *dgmid, *dchunk;
-  R* dtw;
+  R *dtw, *ddw;
   if ((rc = upload(d, &dgx, gx, bytes)) || (rc = upload(d, &dgoff, goff, bytes)) ||
       (rc = upload(d, &dgmid, gmid, bytes)) || (rc = upload(d, &dchunk, chunk, bytes)) ||
-      (rc = upload(d, &dtz, tz, bytes)) || (rc = upload(d, &dtw, tw, bytes)))
+      (rc = upload(d, &dtz, tz, bytes)) || (rc = upload(d, &dtw, tw, bytes)) ||
+      (rc = upload(d, &ddz, dz, bytes)) || (rc = upload(d, &ddw, dw, bytes)))
     return rc;
   d.t.n = p.n_qubits;
   d.t.G = G;
@@ -667,6 +810,10 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes) {
   d.t.chunk_g = dchunk;
   d.t.tz = dtz;
   d.t.tw = dtw;
+  d.t.nd = (int)dz.size();
+  d.t.nd_mid = (int)dz_r.size();
+  d.t.dz = ddz;
+  d.t.dw = ddw;
   // ---- pool
   const Pool& P = p.pool;
   const int M = P.size();
@@ -719,7 +866,7 @@ int grid_for(uint64_t work, int sm_count, int per_sm) {
   return (int)std::max<uint64_t>(1, std::min(want, cap));
 }
 
-int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kThreads * kAmps - 1) / (kThreads * kAmps)); }
+int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kTile - 1) / kTile); }
 int pool_grid_x(const DeviceTables& d) { return grid_for(1ull << d.t.n, d.sm_count, 2); }
 
 }  // namespace
@@ -731,11 +878,13 @@ int upload_problem(Problem& p) {
   DeviceTables* d = new DeviceTables();
   p.dev = d;
   size_t bytes = 0;
-  int rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes) : upload_typed<double>(p, *d, bytes);
+  int rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
+                                   : upload_typed<double>(p, *d, bytes, &p.identity);
   if (rc) return rc;
   int sm = 0;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, p.device);
   d->sm_count = sm > 0 ? sm : 1;
+  p.sm_count = d->sm_count;
   const int M = d->t.M;
   const int nchunks = (M + kOpsPerBlock - 1) / kOpsPerBlock;
   if (nchunks > kMaxChunks) return fail(GOCP_EINVAL, "pool too large for the gradient kernel");
@@ -754,7 +903,6 @@ int upload_problem(Problem& p) {
   cudaMemset(d->err, 0, sizeof(int32_t));
   cudaMemset(d->scalars, 0, 16 * sizeof(double));
   p.device_bytes = bytes;
-  p.n_groups = d->t.G;
   return cuda_status(cudaDeviceSynchronize(), "upload");
 }
 
@@ -778,7 +926,8 @@ int ensure_stage(Problem& p, int n_ops) {
   cap = std::max(cap, 256);
   size_t bytes = 0;
   int rc;
-  // previous staging buffers stay in `allocs` until the problem is freed
+  // earlier staging buffers stay allocated until the problem is freed, so
+  // work still queued on a stream never sees them disappear
   if ((rc = dalloc(d, &d.stage_ops, cap, bytes)) || (rc = dalloc(d, &d.stage_theta, cap, bytes)) ||
       (rc = dalloc(d, &d.coefs, (size_t)cap * 6, bytes)) || (rc = dalloc(d, &d.dtheta, cap, bytes)))
     return rc;
@@ -795,42 +944,43 @@ double* grads_ptr(Problem& p) { return p.dev->grads; }
 int32_t* selected_ptr(Problem& p) { return p.dev->selected; }
 int32_t* err_ptr(Problem& p) { return p.dev->err; }
 
-#define GOCP_LAUNCHED(n) count_launches(n)
-
 template <typename R>
-static int launch_reference(Problem& p, void* psi, cudaStream_t st) {
-  const uint64_t dim = 1ull << p.n_qubits;
+static int launch_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st) {
+  const uint64_t dim = psi ? 1ull << p.n_qubits : 1;
   int grid = grid_for(dim, p.dev->sm_count, 8);
-  k_basis_state<R><<<grid, kThreads, 0, st>>>((C_t<R>*)psi, dim, p.ref_index);
-  GOCP_LAUNCHED(1);
-  return cuda_status(cudaGetLastError(), "k_basis_state");
+  k_setup<R><<<grid, kThreads, 0, st>>>((C_t<R>*)psi, p.n_qubits, p.ref_index, d_theta, n_ops,
+                                        p.dev->coefs);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_setup");
 }
 
-int dev_reference(Problem& p, void* psi, cudaStream_t st) {
-  return p.precision == GOCP_C64 ? launch_reference<float>(p, psi, st) : launch_reference<double>(p, psi, st);
+// psi = |ref> (skipped when psi is NULL) and the Taylor coefficients of the
+// staged ansatz (n_ops may be 0).
+int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st) {
+  int rc = ensure_stage(p, n_ops);
+  if (rc) return rc;
+  return p.precision == GOCP_C64 ? launch_setup<float>(p, psi, d_theta, n_ops, st)
+                                 : launch_setup<double>(p, psi, d_theta, n_ops, st);
 }
 
 template <typename R>
-static int launch_taylor_chain(Problem& p, const int32_t* d_ops, const double* d_theta, int n_ops,
-                               void* psi, cudaStream_t st) {
+static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
   DeviceTables& d = *p.dev;
-  if (n_ops == 0) return GOCP_OK;
-  k_series<<<(n_ops + 127) / 128, 128, 0, st>>>(d_theta, n_ops, d.coefs);
   const int grid = grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
   for (int j = 0; j < n_ops; ++j) {
     ProfScope ps(GOCP_KERNEL_TAYLOR, st);
     k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err);
   }
-  GOCP_LAUNCHED(1 + n_ops);
+  count_launches(n_ops);
   return cuda_status(cudaGetLastError(), "k_taylor5");
 }
 
-int dev_taylor_chain(Problem& p, const int32_t* d_ops, const double* d_theta, int n_ops, void* psi,
-                     cudaStream_t st) {
-  int rc = ensure_stage(p, n_ops);
-  if (rc) return rc;
-  return p.precision == GOCP_C64 ? launch_taylor_chain<float>(p, d_ops, d_theta, n_ops, psi, st)
-                                 : launch_taylor_chain<double>(p, d_ops, d_theta, n_ops, psi, st);
+// Applies operators 0..n_ops-1 of a staged ansatz whose coefficients were
+// written by dev_setup.
+int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
+  if (n_ops == 0) return GOCP_OK;
+  return p.precision == GOCP_C64 ? launch_taylor_chain<float>(p, d_ops, n_ops, psi, st)
+                                 : launch_taylor_chain<double>(p, d_ops, n_ops, psi, st);
 }
 
 template <typename R>
@@ -838,17 +988,12 @@ static int launch_apply(Problem& p, const void* psi, void* hpsi, bool energy, cu
   DeviceTables& d = *p.dev;
   const int grid = apply_grid(p.n_qubits);
   {
-  ProfScope ps(GOCP_KERNEL_APPLY_H, st);
-  k_apply_h<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (C_t<R>*)hpsi, (R)d.identity,
-                                          energy ? d.scratch : nullptr, d.counters + kMaxChunks,
-                                          d.scalars);
+    ProfScope ps(GOCP_KERNEL_APPLY_H, st);
+    k_apply_h<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (C_t<R>*)hpsi, p.identity,
+                                            energy ? d.scratch : nullptr, d.counters + kMaxChunks,
+                                            d.scalars);
   }
-  int n = 1;
-  if (energy) {
-    k_energy_final<<<1, 32, 0, st>>>(d.scalars, d.identity);
-    ++n;
-  }
-  GOCP_LAUNCHED(n);
+  count_launches(1);
   return cuda_status(cudaGetLastError(), "k_apply_h");
 }
 
@@ -864,7 +1009,7 @@ static int launch_norm(Problem& p, const void* psi, cudaStream_t st) {
   const int grid = grid_for(dim, d.sm_count, 8);
   k_norm<R><<<grid, kThreads, 0, st>>>((const C_t<R>*)psi, dim, d.scratch, d.counters + kMaxChunks + 1,
                                        d.scalars + 1);
-  GOCP_LAUNCHED(1);
+  count_launches(1);
   return cuda_status(cudaGetLastError(), "k_norm");
 }
 
@@ -886,13 +1031,12 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
                                               d.scratch, d.counters, d.graw);
   }
   k_grad_final<<<(M + 255) / 256, 256, 0, st>>>(d.graw, d.t.porder, M, d.scalars, d_grads);
-  GOCP_LAUNCHED(2);
+  count_launches(2);
   return cuda_status(cudaGetLastError(), "k_pool_grad");
 }
 
 int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st) {
-  // needs <psi|psi> in scalars[1]
-  int rc = dev_norm(p, psi, st);
+  int rc = dev_norm(p, psi, st);   // <psi|psi> -> scalars[1]
   if (rc) return rc;
   return p.precision == GOCP_C64 ? launch_pool_grads<float>(p, psi, hpsi, d_grads, st)
                                  : launch_pool_grads<double>(p, psi, hpsi, d_grads, st);
@@ -904,14 +1048,14 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   DeviceTables& d = *p.dev;
   const uint64_t dim = 1ull << p.n_qubits;
   const int g1 = grid_for(dim, d.sm_count, 8);
-  k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, dim, d.scalars);
+  k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, p.n_qubits, d.scalars);
   const int grid = grid_for(dim / 2, d.sm_count, 8);
   for (int j = n_ops - 1; j >= 0; --j) {
     ProfScope ps(GOCP_KERNEL_ADJOINT, st);
     k_adjoint<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, (C_t<R>*)lam,
                                             d.scratch, d.counters + kMaxChunks + 2, d_dE, d.err);
   }
-  GOCP_LAUNCHED(1 + n_ops);
+  count_launches(1 + n_ops);
   return cuda_status(cudaGetLastError(), "k_adjoint");
 }
 
@@ -923,8 +1067,100 @@ int dev_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* la
 
 int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out, cudaStream_t st) {
   k_select<<<1, kThreads, 0, st>>>(d_grads, p.dev->t.M, tie_rel, d_out);
-  GOCP_LAUNCHED(1);
+  count_launches(1);
   return cuda_status(cudaGetLastError(), "k_select");
+}
+
+// ------------------------------------------------------------ batched launch
+
+size_t batch_desc_bytes(int n) { return (size_t)n * sizeof(BatchItemDev); }
+
+namespace {
+
+// Blocks of one item: a fixed function of its size and the stage only.
+int item_blocks(const Problem& p, int kind) {
+  const uint64_t dim = 1ull << p.n_qubits;
+  uint64_t want;
+  if (kind == STAGE_ENERGY) want = (dim + kTile - 1) / kTile;
+  else if (kind == STAGE_FORWARD || kind == STAGE_BACKWARD) want = ((dim >> 1) + kThreads - 1) / kThreads;
+  else want = (dim + kThreads - 1) / kThreads;
+  uint64_t cap = (uint64_t)std::max(p.sm_count, 1) * kItemBlocksPerSm;
+  cap = std::min<uint64_t>(cap, kMaxItemBlocks);
+  return (int)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+template <typename R>
+int launch_stage_typed(int kind, const StageItem* items, int n, void* host_desc, void* dev_desc,
+                       cudaStream_t st, int64_t* launches) {
+  BatchItemDev* hd = (BatchItemDev*)host_desc;
+  BatchIndex ix;
+  ix.n = n;
+  int total = 0;
+  for (int i = 0; i < n; ++i) {
+    const StageItem& s = items[i];
+    const Problem& p = *s.prob;
+    BatchItemDev& d = hd[i];
+    d.t = p.dev->t;
+    d.ops = s.ops;
+    d.theta = s.theta;
+    d.coefs = s.coefs;
+    d.psi = s.psi;
+    d.lam = s.lam;
+    d.partials = s.partials;
+    d.counter = s.counter;
+    d.scal = s.scal;
+    d.dtheta = s.dtheta;
+    d.err = s.err;
+    d.identity = p.identity;
+    d.ref_index = p.ref_index;
+    d.n_ops = s.n_ops;
+    d.j = s.j;
+    d.nb = item_blocks(p, kind);
+    ix.start[i] = total;
+    total += d.nb;
+  }
+  ix.start[n] = total;
+  int rc = cuda_status(cudaMemcpyAsync(dev_desc, host_desc, batch_desc_bytes(n), cudaMemcpyHostToDevice, st),
+                       "batch descriptors");
+  if (rc) return rc;
+  const BatchItemDev* dd = (const BatchItemDev*)dev_desc;
+  switch (kind) {
+    case STAGE_SETUP:
+      k_stage_setup<R><<<total, kThreads, 0, st>>>(dd, ix);
+      *launches += 1;
+      break;
+    case STAGE_FORWARD:
+      k_stage_forward<R><<<total, kThreads, 0, st>>>(dd, ix);
+      *launches += 1;
+      break;
+    case STAGE_ENERGY:
+      // H psi + energy, then lambda = (H psi - E psi)/<psi|psi> once E is known
+      k_stage_energy<R><<<total, kThreads, 0, st>>>(dd, ix);
+      k_stage_residual<R><<<total, kThreads, 0, st>>>(dd, ix);
+      *launches += 2;
+      break;
+    case STAGE_BACKWARD:
+      k_stage_backward<R><<<total, kThreads, 0, st>>>(dd, ix);
+      *launches += 1;
+      break;
+    default:
+      return fail(GOCP_EINVAL, "unknown stage kind");
+  }
+  return cuda_status(cudaGetLastError(), "batched stage");
+}
+
+}  // namespace
+
+int launch_stage(int kind, const StageItem* items, int n, int precision, void* host_desc,
+                 void* dev_desc, void* stream, int64_t* launches) {
+  if (n <= 0) return GOCP_OK;
+  if (n > kMaxBatchItems) return fail(GOCP_EINVAL, "too many items in one batch");
+  int64_t before = *launches;
+  int rc = precision == GOCP_C64
+               ? launch_stage_typed<float>(kind, items, n, host_desc, dev_desc, (cudaStream_t)stream, launches)
+               : launch_stage_typed<double>(kind, items, n, host_desc, dev_desc, (cudaStream_t)stream, launches);
+  count_launches(*launches - before);
+  return rc;
 }
 
 }  // namespace gocp

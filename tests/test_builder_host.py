@@ -129,3 +129,13 @@ def test_library_exports_every_declared_symbol():
     lib = gb.load()
     missing = [n for n in sorted(names) if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_server_needs_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2607_15906_gb300.serving import Server
+    with pytest.raises(gb.GocpError) as e:
+        Server(hbm_budget_bytes=1 << 20)
+    assert e.value.code in (-7, -1)
