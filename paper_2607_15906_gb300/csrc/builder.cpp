@@ -232,6 +232,51 @@ int canonicalize_terms(const std::vector<uint32_t>& x, const std::vector<uint32_
   return GOCP_OK;
 }
 
+// ------------------------------------------------------------ LUT form
+
+LutForm lut_form(const uint32_t* z, const double* w, int count) {
+  LutForm f;
+  if (count <= 0) return f;
+  f.z0 = z[0];
+  // basis of the differences by insertion, each vector reduced against the
+  // previous ones (pivot = highest set bit), coordinates tracked alongside
+  uint32_t basis[32];
+  uint32_t coord_of_basis[32];   // basis[i] expressed in the chosen v's
+  int rank = 0;
+  std::vector<uint32_t> coords(count, 0);
+  for (int t = 0; t < count; ++t) {
+    uint32_t r = z[t] ^ f.z0, c = 0;
+    for (int i = 0; i < rank; ++i)
+      if ((r ^ basis[i]) < r) {
+        r ^= basis[i];
+        c ^= coord_of_basis[i];
+      }
+    if (r) {
+      if (rank == kMaxLutRank) return LutForm();
+      f.v[rank] = r;
+      basis[rank] = r;
+      coord_of_basis[rank] = 1u << rank;
+      c ^= 1u << rank;
+      ++rank;
+      // keep basis sorted by pivot so that the reduction above stays greedy
+      for (int i = rank - 1; i > 0 && basis[i] > basis[i - 1]; --i) {
+        std::swap(basis[i], basis[i - 1]);
+        std::swap(coord_of_basis[i], coord_of_basis[i - 1]);
+      }
+    }
+    coords[t] = c;
+  }
+  f.d = rank;
+  ExactSum acc;
+  for (int sidx = 0; sidx < (1 << rank); ++sidx) {
+    acc.clear();
+    for (int t = 0; t < count; ++t) acc.add(parity32(coords[t] & (uint32_t)sidx) ? -w[t] : w[t]);
+    f.lut[sidx] = acc.round();
+  }
+  f.ok = true;
+  return f;
+}
+
 // ------------------------------------------------------------ GOCP
 
 namespace {

@@ -33,6 +33,28 @@ __device__ __forceinline__ C_t<R> cscale(C_t<R> a, R s) { return cmake<R>(a.x * 
 template <typename R>
 __device__ __forceinline__ C_t<R> cconj(C_t<R> a) { return cmake<R>(a.x, -a.y); }
 
+// An x-group (or generator) in LUT form, see LutForm:
+//   D(b) = (-1)^popc(b & z0) * lut[phi(b)],  phi(b) = sum_i (popc(b & v_i) & 1) << i,
+// with real weights only.  fx holds phi(x) (bits 0..2) and popc(x & z0) & 1
+// (bit 3), so that D(b ^ x) = (-1)^(sigma(b) ^ bit3) * lut[phi(b) ^ phi(x)].
+// s is the lowest set bit of x (the pivot that enumerates pairs {b, b^x}).
+// An exactly zero lut entry means the operator does not touch those basis
+// states: kernels skip them without changing any result.
+template <typename R>
+struct LutDev {
+  uint32_t x, z0, v0, v1, v2;
+  uint32_t fx;
+  int32_t s;
+  int32_t pad;
+  R lut[8];
+};
+
+template <typename R>
+__device__ __forceinline__ uint32_t lut_phi(const LutDev<R>& L, uint32_t b) {
+  return (uint32_t)(__popc(b & L.v0) & 1) | ((uint32_t)(__popc(b & L.v1) & 1) << 1) |
+         ((uint32_t)(__popc(b & L.v2) & 1) << 2);
+}
+
 // Device copies of the tables of one problem.
 //
 // Hamiltonian: the identity term is a scalar; the diagonal group (x = 0) is
@@ -61,6 +83,10 @@ struct DevTables {
   const int32_t* chunk_g = nullptr;
   const uint32_t* tz = nullptr;
   const void* tw = nullptr;
+  // off-diagonal groups in LUT form (real weights, rank <= 3), ascending x;
+  // the term groups above hold the rest
+  int GL = 0;
+  const void* hlut = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;
@@ -74,6 +100,9 @@ struct DevTables {
   const void* pw = nullptr;
   const void* pw2 = nullptr;
   const int32_t* porder = nullptr;
+  // every generator in LUT form (pool order), when all of them qualify
+  bool pool_lut = false;
+  const void* plut = nullptr;
 };
 
 }  // namespace gocp

@@ -92,6 +92,22 @@ int canonicalize_terms(const std::vector<uint32_t>& x, const std::vector<uint32_
                        int n, PauliTerms& out);
 int colour_pool(Pool& pool);   // Algorithm 1; GOCP_EINVAL if weights are not multiples of 1/8
 
+// Compact form of one x-group D(b) = sum_t w_t (-1)^popc(b & z_t) with real
+// weights: with z0 = z of the first term and v_1..v_d a basis of the
+// differences z_t ^ z0,
+//   D(b) = (-1)^popc(b & z0) * lut[phi(b)],  phi(b)_i = popc(b & v_i) & 1,
+// where lut[s] = sum_t w_t (-1)^(c_t . s), c_t the coordinates of z_t ^ z0,
+// is summed exactly and rounded once.  ok = false when d > kMaxLutRank.
+constexpr int kMaxLutRank = 3;
+struct LutForm {
+  bool ok = false;
+  int d = 0;
+  uint32_t z0 = 0;
+  uint32_t v[kMaxLutRank] = {0, 0, 0};
+  double lut[1 << kMaxLutRank] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+LutForm lut_form(const uint32_t* z, const double* w, int count);
+
 // ------------------------------------------------------------ device side
 
 struct DeviceTables;   // defined in kernels.cu

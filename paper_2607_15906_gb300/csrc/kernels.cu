@@ -32,7 +32,8 @@ constexpr int kChunkTerms = 2048;    // shared-memory stage of H psi
 constexpr int kChunkGroups = 512;
 constexpr int kOpsPerBlock = 16;     // pool operators per gradient block
 constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor block
-constexpr int kKahanTerms = 16;      // c64: compensated sums for longer groups
+constexpr int kLutChunk = 128;       // LUT groups staged per H psi chunk
+constexpr int kPairsPerThread = 32;  // pool gradients: pairs per thread per operator
 constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
 constexpr int kItemBlocksPerSm = 2;  // batched stages: blocks per item per SM
 
@@ -240,9 +241,10 @@ __device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int t
 // A block sweeps tiles of kTile output amplitudes; a thread owns kAmps of
 // them, k = tile*kTile + i*kThreads + tid.  The diagonal group (x = 0, the
 // identity excluded) is summed first with a compensated sum whose high and
-// low parts both enter the FP64 energy; the off-diagonal groups are staged
-// in shared memory chunk by chunk (a single group too large for the stage is
-// read from global memory).  The identity term is added as identity*psi[k].
+// low parts both enter the FP64 energy; the off-diagonal groups in LUT form
+// and then the remaining term-list groups are staged in shared memory chunk
+// by chunk (a single group too large for the stage is read from global
+// memory).  The identity term is added as identity*psi[k].
 // With `partials` set the item's blocks also reduce <psi|psi> -> scal[1] and
 // Re<psi|H' psi> -> scal[2] in FP64, and the last block sets
 // scal[0] = E = identity + scal[2] / scal[1].
@@ -256,8 +258,10 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
   __shared__ uint32_t s_z[kChunkTerms];
   __shared__ R s_w[kChunkTerms];
   __shared__ double tot[2];
+  __shared__ LutDev<R> s_l[kLutChunk];
   const R* tw = (const R*)tb.tw;
   const R* dw = (const R*)tb.dw;
+  const LutDev<R>* hl = (const LutDev<R>*)tb.hlut;
   const R idr = (R)identity;
   const uint64_t dim = 1ull << tb.n;
   const uint64_t ntiles = (dim + kTile - 1) / kTile;
@@ -279,7 +283,28 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
     // diagonal group
     sum_terms<R>(tb.dz, dw, 0, tb.nd_mid, k, dr, dc, true);
     sum_terms<R>(tb.dz, dw, tb.nd_mid, tb.nd, k, di, dd, false);
-    // off-diagonal groups
+    // off-diagonal groups in LUT form: D = sigma * lut[phi]; an exact zero
+    // entry means no coupling, so the gather is skipped
+    for (int c0 = 0; c0 < tb.GL; c0 += kLutChunk) {
+      const int cn = min(kLutChunk, tb.GL - c0);
+      __syncthreads();
+      for (int g = threadIdx.x; g < cn; g += kThreads) s_l[g] = hl[c0 + g];
+      __syncthreads();
+      for (int g = 0; g < cn; ++g) {
+        const LutDev<R>& L = s_l[g];
+#pragma unroll
+        for (int i = 0; i < kAmps; ++i) {
+          const R val = L.lut[lut_phi(L, k[i])];
+          if (val != R(0)) {
+            const R dv = (__popc(k[i] & L.z0) & 1) ? -val : val;
+            const C_t<R> p = psi[k[i] ^ L.x];
+            acc[i].x += dv * p.x;
+            acc[i].y += dv * p.y;
+          }
+        }
+      }
+    }
+    // off-diagonal groups as term lists
     for (int c = 0; c < tb.n_chunks; ++c) {
       const int g0 = tb.chunk_g[c], g1 = tb.chunk_g[c + 1];
       const int t0 = tb.goff[g0], t1 = tb.goff[g1];
@@ -305,8 +330,8 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
         R gr[kAmps], gi[kAmps], cr[kAmps], ci[kAmps];
 #pragma unroll
         for (int i = 0; i < kAmps; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
-        sum_terms<R>(zs, ws, tbeg, tmid, k, gr, cr, tmid - tbeg > kKahanTerms);
-        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k, gi, ci, tend - tmid > kKahanTerms);
+        sum_terms<R>(zs, ws, tbeg, tmid, k, gr, cr, false);
+        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k, gi, ci, false);
 #pragma unroll
         for (int i = 0; i < kAmps; ++i) {
           const R xr = gr[i] - cr[i], xi = gi[i] - ci[i];
@@ -431,9 +456,53 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
 // v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
 // m = 0..5, stay in registers.
+// LUT form of the same step: real D on the pair, and pairs the operator does
+// not touch (both lut entries exactly zero, T = I there) are not read or
+// written.
+template <typename R>
+__device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
+                                C_t<R>* psi, int32_t* err, int bid, int nb) {
+  const int op = ops[j];
+  if (op < 0 || op >= tb.M) {
+    if (bid == 0 && threadIdx.x == 0) atomicOr(err, 1);
+    return;
+  }
+  const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const uint64_t npairs = 1ull << (tb.n - 1);
+  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
+    const uint32_t b = pair_base(p, L.s);
+    const uint32_t ph = lut_phi(L, b);
+    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+    if (l1 == R(0) && l2 == R(0)) continue;
+    const uint32_t sg = __popc(b & L.z0) & 1u;
+    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+    const uint32_t b2 = b ^ L.x;
+    C_t<R> v1 = psi[b], v2 = psi[b2];
+    C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
+#pragma unroll
+    for (int m = 1; m <= 5; ++m) {
+      C_t<R> n1 = cscale<R>(v2, d1), n2 = cscale<R>(v1, d2);   // (A v)[b] = D(b) v[b^x]
+      v1 = n1;
+      v2 = n2;
+      kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
+      kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
+    }
+    psi[b] = csub<R>(s1, e1);
+    psi[b2] = csub<R>(s2, e2);
+  }
+}
+
 template <typename R>
 __device__ void taylor_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                             C_t<R>* psi, int32_t* err, int bid, int nb) {
+  if (tb.pool_lut) {
+    taylor_lut_body<R>(tb, ops, coefs, j, psi, err, bid, nb);
+    return;
+  }
   __shared__ uint32_t s_z[kStageStrings];
   __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
   OpView<R> o;
@@ -477,10 +546,66 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 //   psi <- T^-1 psi = (C I - S A) psi / (C^2 - S^2 mu)      (exact inverse)
 //   dE_j += 2 Re <lambda|T' psi>                            (lambda before update)
 //   lambda <- T^dagger lambda.
+// LUT form of the backward step (real D); untouched pairs (both lut entries
+// zero: T = I, T' = 0 there) are skipped.
+template <typename R>
+__device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
+                                 C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
+                                 double* dtheta, int32_t* err, int bid, int nb) {
+  __shared__ double tot[1];
+  const int op = ops[j];
+  if (op < 0 || op >= tb.M) {
+    if (bid == 0 && threadIdx.x == 0) {
+      atomicOr(err, 1);
+      dtheta[j] = 0.0;
+    }
+    return;
+  }
+  const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const uint64_t npairs = 1ull << (tb.n - 1);
+  double v[1] = {0.0};
+  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
+    const uint32_t b = pair_base(p, L.s);
+    const uint32_t ph = lut_phi(L, b);
+    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+    if (l1 == R(0) && l2 == R(0)) continue;
+    const uint32_t sg = __popc(b & L.z0) & 1u;
+    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+    const uint32_t b2 = b ^ L.x;
+    const R mu = d1 * d2, mu2 = mu * mu;
+    const R cc = c[0] + c[2] * mu + c[4] * mu2;
+    const R sc = c[1] + c[3] * mu + c[5] * mu2;
+    const R cd = c[1] * mu + c[3] * mu2;
+    const R inv = R(1) / (cc * cc - sc * sc * mu);
+    const R sd1 = sc * d1, sd2 = sc * d2;
+    const C_t<R> u1 = psi[b], u2 = psi[b2];
+    const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
+    const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
+    const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
+    const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
+    const C_t<R> l1v = lam[b], l2v = lam[b2];
+    v[0] += 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x +
+                   (double)l2v.y * t2.y);
+    psi[b] = q1;
+    psi[b2] = q2;
+    lam[b] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
+    lam[b2] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
+  }
+  grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
+}
+
 template <typename R>
 __device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                              C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
                              double* dtheta, int32_t* err, int bid, int nb) {
+  if (tb.pool_lut) {
+    adjoint_lut_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, bid, nb);
+    return;
+  }
   __shared__ uint32_t s_z[kStageStrings];
   __shared__ R s_w[kStageStrings], s_w2[kStageStrings];
   __shared__ double tot[1];
@@ -622,6 +747,77 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
                          counters + blockIdx.y, gridDim.x, blockIdx.x, raw + first, tot);
 }
 
+// Pool gradients for generators in LUT form.  blockIdx.y picks
+// kOpsPerBlock operators in GOCP family order; blockIdx.x a contiguous range
+// of kThreads * kPairsPerThread basis pairs {b, b^x}.  Operators are taken
+// one after another (one accumulator per thread), and a pair enters only
+// where the operator touches it:
+//   Re<H psi|A psi> over the pair = D(b) Re(conj(h_b) psi_{b^x}) + D(b^x) Re(conj(h_{b^x}) psi_b).
+// Each block writes one FP64 partial per operator: part[pos * nbx + blockIdx.x].
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pool_grad_lut(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
+                double* part, int nbx) {
+  __shared__ LutDev<R> s_op[kOpsPerBlock];
+  __shared__ double s_red[kWarps];
+  const int first = blockIdx.y * kOpsPerBlock;
+  const int nops = min(kOpsPerBlock, tb.M - first);
+  const LutDev<R>* pl = (const LutDev<R>*)tb.plut;
+  if (threadIdx.x < nops) s_op[threadIdx.x] = pl[tb.porder[first + threadIdx.x]];
+  __syncthreads();
+  const uint64_t npairs = 1ull << (tb.n - 1);
+  const uint64_t base = (uint64_t)blockIdx.x * kThreads * kPairsPerThread;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 0; o < nops; ++o) {
+    const LutDev<R>& L = s_op[o];
+    const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+    R acc = 0, cmp = 0;
+#pragma unroll 4
+    for (int jj = 0; jj < kPairsPerThread; ++jj) {
+      const uint64_t pp = base + (uint64_t)jj * kThreads + threadIdx.x;
+      if (pp >= npairs) break;
+      const uint32_t b = pair_base(pp, L.s);
+      const uint32_t ph = lut_phi(L, b);
+      const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+      if (l1 == R(0) && l2 == R(0)) continue;
+      const uint32_t sg = __popc(b & L.z0) & 1u;
+      const uint32_t b2 = b ^ L.x;
+      const C_t<R> h1 = hpsi[b], h2 = hpsi[b2], p1 = psi[b], p2 = psi[b2];
+      const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
+                    ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
+      if (sizeof(R) == 4) {
+        R y = val - cmp, t = acc + y;
+        cmp = (t - acc) - y;
+        acc = t;
+      } else {
+        acc += val;
+      }
+    }
+    double v = (double)acc - (double)cmp;
+    v = warp_sum(v);
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      part[(size_t)(first + o) * nbx + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// raw[i] = sum over the nbx block partials of operator i (family order), in
+// a fixed order: one warp per operator.
+__global__ void k_pool_reduce(const double* part, int nbx, int m, double* raw) {
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int b = lane; b < nbx; b += 32) s += part[(size_t)i * nbx + b];
+  s = warp_sum(s);
+  if (lane == 0) raw[i] = s;
+}
+
 // ------------------------------------------------------------ batched stages
 
 // One work item of a batched launch (device copy of a StageItem).
@@ -732,6 +928,29 @@ inline double eff_weight(double c, int phase, uint32_t x, uint32_t z, bool* imag
   return w;
 }
 
+// LUT descriptor of one x-group with real weights w (effective weights at
+// the output index, as in the term tables); false when the rank exceeds 3.
+template <typename R>
+bool make_lut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<double>& w, LutDev<R>* out) {
+  if (z.empty() || x == 0) return false;
+  LutForm f = lut_form(z.data(), w.data(), (int)z.size());
+  if (!f.ok) return false;
+  LutDev<R> L;
+  std::memset(&L, 0, sizeof(L));
+  L.x = x;
+  L.z0 = f.z0;
+  L.v0 = f.d > 0 ? f.v[0] : 0u;
+  L.v1 = f.d > 1 ? f.v[1] : 0u;
+  L.v2 = f.d > 2 ? f.v[2] : 0u;
+  const uint32_t phx = (uint32_t)parity32(x & L.v0) | ((uint32_t)parity32(x & L.v1) << 1) |
+                       ((uint32_t)parity32(x & L.v2) << 2);
+  L.fx = phx | ((uint32_t)parity32(x & f.z0) << 3);
+  L.s = __builtin_ctz(x);
+  for (int i = 0; i < 8; ++i) L.lut[i] = (R)(i < (1 << f.d) ? f.lut[i] : 0.0);
+  *out = L;
+  return true;
+}
+
 template <typename R>
 int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   const PauliTerms& H = p.H;
@@ -739,6 +958,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   std::vector<uint32_t> gx, tz, dz_r, dz_i;
   std::vector<int32_t> goff, gmid;
   std::vector<R> tw, dw_r, dw_i;
+  std::vector<LutDev<R>> hl;
   double ident = 0.0;
   size_t i = 0;
   while (i < H.size()) {
@@ -746,6 +966,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
     while (j < H.size() && H.x[j] == H.x[i]) ++j;
     std::vector<uint32_t> zr, zi;
     std::vector<R> wr, wi;
+    std::vector<double> wr64;
     for (size_t t = i; t < j; ++t) {
       bool imag = false;
       double w = eff_weight(H.coeff[t], H.phase[t], H.x[t], H.z[t], &imag);
@@ -755,8 +976,12 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
       }
       (imag ? zi : zr).push_back(H.z[t]);
       (imag ? wi : wr).push_back((R)w);
+      if (!imag) wr64.push_back(w);
     }
-    if (H.x[i] == 0) {
+    LutDev<R> L;
+    if (H.x[i] != 0 && zi.empty() && make_lut<R>(H.x[i], zr, wr64, &L)) {
+      hl.push_back(L);
+    } else if (H.x[i] == 0) {
       dz_r = zr;
       dw_r = wr;
       dz_i = zi;
@@ -787,6 +1012,10 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
       g = h;
     }
   }
+  LutDev<R>* dhl;
+  if (int rc0 = upload(d, &dhl, hl, bytes)) return rc0;
+  d.t.GL = (int)hl.size();
+  d.t.hlut = dhl;
   std::vector<uint32_t> dz(dz_r);
   dz.insert(dz.end(), dz_i.begin(), dz_i.end());
   std::vector<R> dw(dw_r);
@@ -836,6 +1065,20 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
     }
   }
   poff.push_back((int32_t)pz.size());
+  std::vector<LutDev<R>> pl(M);
+  bool all_lut = M > 0;
+  for (int k = 0; k < M && all_lut; ++k) {
+    std::vector<uint32_t> zz;
+    std::vector<double> ww;
+    for (int64_t s2 = P.off[k]; s2 < P.off[k + 1]; ++s2) {
+      bool imag = false;
+      double w = eff_weight(P.coeff[s2], P.phase[s2], P.x[s2], P.z[s2], &imag);
+      if (imag) { all_lut = false; break; }
+      zz.push_back(P.z[s2]);
+      ww.push_back(w);
+    }
+    if (all_lut && !make_lut<R>(px[k], zz, ww, &pl[k])) all_lut = false;
+  }
   for (int k = 0; k < M; ++k) porder[k] = k;
   std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) {
     return P.family[a] < P.family[b];
@@ -857,6 +1100,12 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.pw = dpw;
   d.t.pw2 = dpw2;
   d.t.porder = dporder;
+  if (all_lut) {
+    LutDev<R>* dpl;
+    if ((rc = upload(d, &dpl, pl, bytes))) return rc;
+    d.t.plut = dpl;
+    d.t.pool_lut = true;
+  }
   return GOCP_OK;
 }
 
@@ -868,6 +1117,10 @@ int grid_for(uint64_t work, int sm_count, int per_sm) {
 
 int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kTile - 1) / kTile); }
 int pool_grid_x(const DeviceTables& d) { return grid_for(1ull << d.t.n, d.sm_count, 2); }
+int pool_lut_nbx(int n) {
+  const uint64_t per = (uint64_t)kThreads * kPairsPerThread;
+  return (int)std::max<uint64_t>(1, ((1ull << (n - 1)) + per - 1) / per);
+}
 
 }  // namespace
 
@@ -891,6 +1144,8 @@ int upload_problem(Problem& p) {
   size_t need = 2 * (size_t)apply_grid(p.n_qubits);
   need = std::max(need, (size_t)pool_grid_x(*d) * (size_t)std::max(nchunks, 1) * kOpsPerBlock);
   need = std::max(need, (size_t)d->sm_count * 8);
+  if (d->t.pool_lut)
+    need = std::max(need, (size_t)std::max(nchunks, 1) * kOpsPerBlock * (size_t)pool_lut_nbx(p.n_qubits));
   d->scratch_doubles = need;
   if ((rc = dalloc(*d, &d->scratch, need, bytes))) return rc;
   if ((rc = dalloc(*d, &d->counters, kMaxChunks + 8, bytes))) return rc;
@@ -1024,14 +1279,25 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
   const int M = d.t.M;
   if (M == 0) return GOCP_OK;
   const int nchunks = (M + kOpsPerBlock - 1) / kOpsPerBlock;
-  dim3 grid(pool_grid_x(d), nchunks);
-  {
+  int n = 2;
+  if (d.t.pool_lut) {
+    const int nbx = pool_lut_nbx(p.n_qubits);
+    dim3 grid(nbx, nchunks);
+    {
+      ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+      k_pool_grad_lut<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
+                                                    d.scratch, nbx);
+    }
+    k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, nbx, M, d.graw);
+    ++n;
+  } else {
+    dim3 grid(pool_grid_x(d), nchunks);
     ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
     k_pool_grad<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
                                               d.scratch, d.counters, d.graw);
   }
   k_grad_final<<<(M + 255) / 256, 256, 0, st>>>(d.graw, d.t.porder, M, d.scalars, d_grads);
-  count_launches(2);
+  count_launches(n);
   return cuda_status(cudaGetLastError(), "k_pool_grad");
 }
 
