@@ -45,7 +45,7 @@ struct LutDev {
   uint32_t x, z0, v0, v1, v2;
   uint32_t fx;
   int32_t s;
-  int32_t pad;
+  int32_t pad;      // H groups: code flips of the other amplitudes of a thread
   R lut[8];
 };
 

@@ -210,19 +210,32 @@ __global__ void k_select(const double* g, int m, double tie_rel, int32_t* out) {
 
 // ------------------------------------------------------------ H psi + energy
 
-// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k[i] & z_t), compensated in FP32
+// Amplitude i of a thread is k0 | (i << kRegShift) with bits kRegShift and
+// kRegShift+1 of k0 clear, so (-1)^popc(k_i & z) = (-1)^popc(k0 & z) times a
+// flip read off bits kRegShift.. of z: one parity serves all kAmps amplitudes.
+constexpr int kRegShift = 8;
+static_assert(kThreads == (1 << kRegShift) && kAmps == 4, "register-bit layout");
+
+// Sign bits (bit i = amplitude i) of (-1)^popc(k_i & z).
+__device__ __forceinline__ uint32_t amp_signs(uint32_t k0, uint32_t z) {
+  const uint32_t s0 = __popc(k0 & z) & 1u;
+  const uint32_t f1 = (z >> kRegShift) & 1u, f2 = (z >> (kRegShift + 1)) & 1u;
+  return (s0 * 0xFu) ^ ((f1 << 1) | (f2 << 2) | ((f1 ^ f2) << 3));
+}
+
+// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k_i & z_t), compensated in FP32
 // when asked; comp[i] carries the lost low-order part (true sum d - comp).
 template <typename R>
 __device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int tb, int te,
-                                          const uint32_t (&k)[kAmps], R (&d)[kAmps],
-                                          R (&comp)[kAmps], bool compensate) {
+                                          uint32_t k0, R (&d)[kAmps], R (&comp)[kAmps],
+                                          bool compensate) {
   if (sizeof(R) == 4 && compensate) {
     for (int t = tb; t < te; ++t) {
-      const uint32_t z = zs[t];
+      const uint32_t sg = amp_signs(k0, zs[t]);
       const R w = ws[t];
 #pragma unroll
       for (int i = 0; i < kAmps; ++i) {
-        R y = ((__popc(k[i] & z) & 1) ? -w : w) - comp[i];
+        R y = (((sg >> i) & 1u) ? -w : w) - comp[i];
         R s = d[i] + y;
         comp[i] = (s - d[i]) - y;
         d[i] = s;
@@ -230,16 +243,16 @@ __device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int t
     }
   } else {
     for (int t = tb; t < te; ++t) {
-      const uint32_t z = zs[t];
+      const uint32_t sg = amp_signs(k0, zs[t]);
       const R w = ws[t];
 #pragma unroll
-      for (int i = 0; i < kAmps; ++i) d[i] += (__popc(k[i] & z) & 1) ? -w : w;
+      for (int i = 0; i < kAmps; ++i) d[i] += ((sg >> i) & 1u) ? -w : w;
     }
   }
 }
 
 // A block sweeps tiles of kTile output amplitudes; a thread owns kAmps of
-// them, k = tile*kTile + i*kThreads + tid.  The diagonal group (x = 0, the
+// them, k_i = tile*kTile + tid + i*kThreads.  The diagonal group (x = 0, the
 // identity excluded) is summed first with a compensated sum whose high and
 // low parts both enter the FP64 energy; the off-diagonal groups in LUT form
 // and then the remaining term-list groups are staged in shared memory chunk
@@ -267,24 +280,24 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
   const uint64_t ntiles = (dim + kTile - 1) / kTile;
   double v[2] = {0.0, 0.0};
   for (uint64_t tile = bid; tile < ntiles; tile += nb) {
-    const uint64_t base = tile * kTile;
+    const uint32_t k0 = (uint32_t)(tile * kTile) + threadIdx.x;
     uint32_t k[kAmps];
     bool live[kAmps];
     C_t<R> acc[kAmps];
     R dr[kAmps], dc[kAmps], di[kAmps], dd[kAmps];
 #pragma unroll
     for (int i = 0; i < kAmps; ++i) {
-      uint64_t kk = base + (uint64_t)i * kThreads + threadIdx.x;
-      live[i] = kk < dim;
-      k[i] = live[i] ? (uint32_t)kk : 0u;
+      k[i] = k0 | ((uint32_t)i << kRegShift);
+      live[i] = k[i] < dim;
       acc[i] = cmake<R>(0, 0);
       dr[i] = dc[i] = di[i] = dd[i] = R(0);
     }
     // diagonal group
-    sum_terms<R>(tb.dz, dw, 0, tb.nd_mid, k, dr, dc, true);
-    sum_terms<R>(tb.dz, dw, tb.nd_mid, tb.nd, k, di, dd, false);
+    sum_terms<R>(tb.dz, dw, 0, tb.nd_mid, k0, dr, dc, true);
+    sum_terms<R>(tb.dz, dw, tb.nd_mid, tb.nd, k0, di, dd, false);
     // off-diagonal groups in LUT form: D = sigma * lut[phi]; an exact zero
-    // entry means no coupling, so the gather is skipped
+    // entry means no coupling, so the gather is skipped.  phi and sigma of
+    // k_i are those of k0 flipped by the group's constant `pad` bits.
     for (int c0 = 0; c0 < tb.GL; c0 += kLutChunk) {
       const int cn = min(kLutChunk, tb.GL - c0);
       __syncthreads();
@@ -292,11 +305,14 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
       __syncthreads();
       for (int g = 0; g < cn; ++g) {
         const LutDev<R>& L = s_l[g];
+        const uint32_t code0 = lut_phi(L, k0) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
+        const uint32_t reg = (uint32_t)L.pad << 4;   // code flips of amplitudes 1..3
 #pragma unroll
         for (int i = 0; i < kAmps; ++i) {
-          const R val = L.lut[lut_phi(L, k[i])];
-          if (val != R(0)) {
-            const R dv = (__popc(k[i] & L.z0) & 1) ? -val : val;
+          const uint32_t code = code0 ^ ((reg >> (4 * i)) & 0xFu);
+          const R val = L.lut[code & 7u];
+          if (val != R(0) && live[i]) {
+            const R dv = (code & 8u) ? -val : val;
             const C_t<R> p = psi[k[i] ^ L.x];
             acc[i].x += dv * p.x;
             acc[i].y += dv * p.y;
@@ -330,14 +346,14 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
         R gr[kAmps], gi[kAmps], cr[kAmps], ci[kAmps];
 #pragma unroll
         for (int i = 0; i < kAmps; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
-        sum_terms<R>(zs, ws, tbeg, tmid, k, gr, cr, false);
-        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k, gi, ci, false);
+        sum_terms<R>(zs, ws, tbeg, tmid, k0, gr, cr, false);
+        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k0, gi, ci, false);
 #pragma unroll
         for (int i = 0; i < kAmps; ++i) {
-          const R xr = gr[i] - cr[i], xi = gi[i] - ci[i];
-          C_t<R> p = psi[k[i] ^ x];   // k[i] = 0 for dead lanes: in bounds
-          acc[i].x += xr * p.x - xi * p.y;
-          acc[i].y += xr * p.y + xi * p.x;
+          if (!live[i]) continue;
+          C_t<R> p = psi[k[i] ^ x];
+          acc[i].x += gr[i] * p.x - gi[i] * p.y;
+          acc[i].y += gr[i] * p.y + gi[i] * p.x;
         }
       }
     }
@@ -946,6 +962,16 @@ bool make_lut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<doub
                        ((uint32_t)parity32(x & L.v2) << 2);
   L.fx = phx | ((uint32_t)parity32(x & f.z0) << 3);
   L.s = __builtin_ctz(x);
+  // code flips (phi in bits 0..2, sigma in bit 3) of amplitude i = 1..3 of a
+  // thread, whose index differs from the first by i << kRegShift
+  uint32_t reg = 0;
+  for (uint32_t i = 1; i < 4; ++i) {
+    const uint32_t b = i << kRegShift;
+    const uint32_t code = (uint32_t)parity32(b & L.v0) | ((uint32_t)parity32(b & L.v1) << 1) |
+                          ((uint32_t)parity32(b & L.v2) << 2) | ((uint32_t)parity32(b & f.z0) << 3);
+    reg |= code << (4 * (i - 1));
+  }
+  L.pad = (int32_t)reg;
   for (int i = 0; i < 8; ++i) L.lut[i] = (R)(i < (1 << f.d) ? f.lut[i] : 0.0);
   *out = L;
   return true;
