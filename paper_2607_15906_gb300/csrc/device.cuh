@@ -45,7 +45,7 @@ struct LutDev {
   uint32_t x, z0, v0, v1, v2;
   uint32_t fx;
   int32_t s;
-  int32_t pad;      // H groups: code flips of the other amplitudes of a thread
+  int32_t pad;
   R lut[8];
 };
 
@@ -54,6 +54,18 @@ __device__ __forceinline__ uint32_t lut_phi(const LutDev<R>& L, uint32_t b) {
   return (uint32_t)(__popc(b & L.v0) & 1) | ((uint32_t)(__popc(b & L.v1) & 1) << 1) |
          ((uint32_t)(__popc(b & L.v2) & 1) << 2);
 }
+
+// An H x-group in LUT form for the H psi kernel, whose threads own 8
+// adjacent amplitudes k0 + i (k0 a multiple of 8): code(k) = phi(k) | sigma(k) << 3
+// with sigma(k) = popc(k & z0) & 1, so that D(k) = lut16[code(k)] (the sign
+// is folded into the table) and code(k0 + i) = code(k0) ^ ((reg >> 4i) & 15).
+template <typename R>
+struct HLut {
+  uint32_t x, z0, v0, v1, v2;
+  uint32_t reg;
+  uint32_t pad0, pad1;
+  R lut16[16];
+};
 
 // Device copies of the tables of one problem.
 //
@@ -87,6 +99,13 @@ struct DevTables {
   // the term groups above hold the rest
   int GL = 0;
   const void* hlut = nullptr;
+  // groups are sorted by x & 7 and split into chunks that never mix two
+  // values of x & 7; chunk c of LUT groups is [lchunk[c], lchunk[c+1]) with
+  // lchunk_xl[c] = x & 7, and likewise chunk_xl for the term-list chunks
+  int n_lchunks = 0;
+  const int32_t* lchunk = nullptr;
+  const uint8_t* lchunk_xl = nullptr;
+  const uint8_t* chunk_xl = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;

@@ -26,13 +26,10 @@ namespace gocp {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kAmps = 4;             // amplitudes per thread in H psi
-constexpr int kTile = kThreads * kAmps;
 constexpr int kChunkTerms = 2048;    // shared-memory stage of H psi
 constexpr int kChunkGroups = 512;
 constexpr int kOpsPerBlock = 16;     // pool operators per gradient block
 constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor block
-constexpr int kLutChunk = 128;       // LUT groups staged per H psi chunk
 constexpr int kPairsPerThread = 32;  // pool gradients: pairs per thread per operator
 constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
 constexpr int kItemBlocksPerSm = 2;  // batched stages: blocks per item per SM
@@ -210,31 +207,58 @@ __global__ void k_select(const double* g, int m, double tie_rel, int32_t* out) {
 
 // ------------------------------------------------------------ H psi + energy
 
-// Amplitude i of a thread is k0 | (i << kRegShift) with bits kRegShift and
-// kRegShift+1 of k0 clear, so (-1)^popc(k_i & z) = (-1)^popc(k0 & z) times a
-// flip read off bits kRegShift.. of z: one parity serves all kAmps amplitudes.
-constexpr int kRegShift = 8;
-static_assert(kThreads == (1 << kRegShift) && kAmps == 4, "register-bit layout");
+// H psi layout: a thread owns kAmpsH adjacent amplitudes k0 + i (k0 a
+// multiple of kAmpsH), a block a tile of kTileH.  For a group with mask x
+// the sources of those outputs are the aligned octet at k0 ^ (x & ~7),
+// read with vector loads, output i taking source element i ^ (x & 7).
+// Groups are sorted by x & 7 so that this permutation is a compile-time
+// register renaming inside each chunk.
+constexpr int kAmpsH = 8;
+constexpr int kTileH = kThreads * kAmpsH;
+constexpr int kLutChunkH = 64;       // LUT groups staged per chunk
+// Walsh sign patterns: byte m holds bit i = popc(i & m) & 1 for i, m < 8
+constexpr uint64_t kWalsh8 = 0x963C5AF066CCAA00ull;
 
-// Sign bits (bit i = amplitude i) of (-1)^popc(k_i & z).
-__device__ __forceinline__ uint32_t amp_signs(uint32_t k0, uint32_t z) {
-  const uint32_t s0 = __popc(k0 & z) & 1u;
-  const uint32_t f1 = (z >> kRegShift) & 1u, f2 = (z >> (kRegShift + 1)) & 1u;
-  return (s0 * 0xFu) ^ ((f1 << 1) | (f2 << 2) | ((f1 ^ f2) << 3));
+// Sign bits (bit i = amplitude k0 + i) of (-1)^popc((k0 + i) & z).
+__device__ __forceinline__ uint32_t octet_signs(uint32_t k0, uint32_t z) {
+  const uint32_t pat = (uint32_t)(kWalsh8 >> (8 * (z & 7u))) & 0xFFu;
+  return pat ^ ((__popc(k0 & z) & 1u) * 0xFFu);
 }
 
-// d[i] += sum_{t in [tb, te)} w_t (-1)^popc(k_i & z_t), compensated in FP32
-// when asked; comp[i] carries the lost low-order part (true sum d - comp).
 template <typename R>
-__device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int tb, int te,
-                                          uint32_t k0, R (&d)[kAmps], R (&comp)[kAmps],
-                                          bool compensate) {
+__device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t base, uint64_t dim,
+                                           C_t<R> (&v)[kAmpsH]) {
+  if (dim >= kAmpsH) {
+    if (sizeof(R) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(psi + base);
+#pragma unroll
+      for (int q = 0; q < kAmpsH / 2; ++q) {
+        const float4 f = p[q];
+        v[2 * q] = cmake<R>((R)f.x, (R)f.y);
+        v[2 * q + 1] = cmake<R>((R)f.z, (R)f.w);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kAmpsH; ++q) v[q] = psi[base + q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kAmpsH; ++q) v[q] = (base + q < dim) ? psi[base + q] : cmake<R>(0, 0);
+  }
+}
+
+// d[i] += sum_{t in [tb, te)} w_t (-1)^popc((k0+i) & z_t); compensated in
+// FP32 when asked (comp carries the lost low part: true sum d - comp).
+template <typename R>
+__device__ __forceinline__ void sum_terms8(const uint32_t* zs, const R* ws, int tb, int te,
+                                           uint32_t k0, R (&d)[kAmpsH], R (&comp)[kAmpsH],
+                                           bool compensate) {
   if (sizeof(R) == 4 && compensate) {
     for (int t = tb; t < te; ++t) {
-      const uint32_t sg = amp_signs(k0, zs[t]);
+      const uint32_t sg = octet_signs(k0, zs[t]);
       const R w = ws[t];
 #pragma unroll
-      for (int i = 0; i < kAmps; ++i) {
+      for (int i = 0; i < kAmpsH; ++i) {
         R y = (((sg >> i) & 1u) ? -w : w) - comp[i];
         R s = d[i] + y;
         comp[i] = (s - d[i]) - y;
@@ -243,24 +267,95 @@ __device__ __forceinline__ void sum_terms(const uint32_t* zs, const R* ws, int t
     }
   } else {
     for (int t = tb; t < te; ++t) {
-      const uint32_t sg = amp_signs(k0, zs[t]);
+      const uint32_t sg = octet_signs(k0, zs[t]);
       const R w = ws[t];
 #pragma unroll
-      for (int i = 0; i < kAmps; ++i) d[i] += ((sg >> i) & 1u) ? -w : w;
+      for (int i = 0; i < kAmpsH; ++i) d[i] += ((sg >> i) & 1u) ? -w : w;
     }
   }
 }
 
-// A block sweeps tiles of kTile output amplitudes; a thread owns kAmps of
-// them, k_i = tile*kTile + tid + i*kThreads.  The diagonal group (x = 0, the
-// identity excluded) is summed first with a compensated sum whose high and
-// low parts both enter the FP64 energy; the off-diagonal groups in LUT form
-// and then the remaining term-list groups are staged in shared memory chunk
-// by chunk (a single group too large for the stage is read from global
-// memory).  The identity term is added as identity*psi[k].
-// With `partials` set the item's blocks also reduce <psi|psi> -> scal[1] and
-// Re<psi|H' psi> -> scal[2] in FP64, and the last block sets
-// scal[0] = E = identity + scal[2] / scal[1].
+// LUT groups of one chunk, all with x & 7 == XL.
+template <typename R, int XL>
+__device__ __forceinline__ void lut_chunk(const HLut<R>* s_l, int cn, uint32_t k0,
+                                          const C_t<R>* __restrict__ psi, uint64_t dim,
+                                          C_t<R> (&acc)[kAmpsH]) {
+  if (k0 >= dim) return;   // a thread past the end of a short state reads nothing
+  for (int g = 0; g < cn; ++g) {
+    const HLut<R>& L = s_l[g];
+    const uint32_t code0 = (uint32_t)(__popc(k0 & L.v0) & 1) | ((uint32_t)(__popc(k0 & L.v1) & 1) << 1) |
+                           ((uint32_t)(__popc(k0 & L.v2) & 1) << 2) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
+    if (L.reg == 0u) {
+      // the code does not vary over the octet: one value for all eight
+      const R val = L.lut16[code0];
+      if (val == R(0)) continue;
+      C_t<R> src[kAmpsH];
+      load_octet<R>(psi, k0 ^ (L.x & ~7u), dim, src);
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        acc[i].x += val * src[i ^ XL].x;
+        acc[i].y += val * src[i ^ XL].y;
+      }
+    } else {
+      C_t<R> src[kAmpsH];
+      load_octet<R>(psi, k0 ^ (L.x & ~7u), dim, src);
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        const R val = L.lut16[code0 ^ ((L.reg >> (4 * i)) & 0xFu)];
+        acc[i].x += val * src[i ^ XL].x;
+        acc[i].y += val * src[i ^ XL].y;
+      }
+    }
+  }
+}
+
+// Term-list groups of one staged chunk, all with x & 7 == XL.
+template <typename R, int XL>
+__device__ __forceinline__ void term_chunk(const uint32_t* s_x, const int32_t* s_off,
+                                           const int32_t* s_mid, int ng, const uint32_t* zs,
+                                           const R* ws, uint32_t k0, const C_t<R>* __restrict__ psi,
+                                           uint64_t dim, C_t<R> (&acc)[kAmpsH]) {
+  if (k0 >= dim) return;
+  for (int g = 0; g < ng; ++g) {
+    const uint32_t x = s_x[g];
+    const int tbeg = s_off[g], tmid = s_mid[g], tend = s_off[g + 1];
+    R gr[kAmpsH], gi[kAmpsH], cr[kAmpsH], ci[kAmpsH];
+#pragma unroll
+    for (int i = 0; i < kAmpsH; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
+    sum_terms8<R>(zs, ws, tbeg, tmid, k0, gr, cr, false);
+    if (tend > tmid) sum_terms8<R>(zs, ws, tmid, tend, k0, gi, ci, false);
+    C_t<R> src[kAmpsH];
+    load_octet<R>(psi, k0 ^ (x & ~7u), dim, src);
+#pragma unroll
+    for (int i = 0; i < kAmpsH; ++i) {
+      const C_t<R> p = src[i ^ XL];
+      acc[i].x += gr[i] * p.x - gi[i] * p.y;
+      acc[i].y += gr[i] * p.y + gi[i] * p.x;
+    }
+  }
+}
+
+#define GOCP_XL_SWITCH(XLV, CALL) \
+  switch (XLV) {                  \
+    case 0: CALL(0); break;       \
+    case 1: CALL(1); break;       \
+    case 2: CALL(2); break;       \
+    case 3: CALL(3); break;       \
+    case 4: CALL(4); break;       \
+    case 5: CALL(5); break;       \
+    case 6: CALL(6); break;       \
+    default: CALL(7); break;      \
+  }
+
+// A block sweeps tiles of kTileH output amplitudes; a thread owns the octet
+// k0 .. k0+7.  The off-diagonal groups in LUT form and then the term-list
+// groups are staged in shared memory chunk by chunk (a single group too
+// large for the stage is read from global memory); the diagonal group (x = 0,
+// the identity excluded) comes last, with a compensated sum whose high and
+// low parts both enter the FP64 energy.  The identity term
+// is added as identity*psi[k].  With `partials` set the item's blocks also
+// reduce <psi|psi> -> scal[1] and Re<psi|H' psi> -> scal[2] in FP64, and the
+// last block sets scal[0] = E = identity + scal[2] / scal[1].
 template <typename R>
 __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
                            C_t<R>* __restrict__ out, double identity, double* partials,
@@ -271,54 +366,28 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
   __shared__ uint32_t s_z[kChunkTerms];
   __shared__ R s_w[kChunkTerms];
   __shared__ double tot[2];
-  __shared__ LutDev<R> s_l[kLutChunk];
+  __shared__ HLut<R> s_l[kLutChunkH];
   const R* tw = (const R*)tb.tw;
   const R* dw = (const R*)tb.dw;
-  const LutDev<R>* hl = (const LutDev<R>*)tb.hlut;
+  const HLut<R>* hl = (const HLut<R>*)tb.hlut;
   const R idr = (R)identity;
   const uint64_t dim = 1ull << tb.n;
-  const uint64_t ntiles = (dim + kTile - 1) / kTile;
+  const uint64_t ntiles = (dim + kTileH - 1) / kTileH;
   double v[2] = {0.0, 0.0};
   for (uint64_t tile = bid; tile < ntiles; tile += nb) {
-    const uint32_t k0 = (uint32_t)(tile * kTile) + threadIdx.x;
-    uint32_t k[kAmps];
-    bool live[kAmps];
-    C_t<R> acc[kAmps];
-    R dr[kAmps], dc[kAmps], di[kAmps], dd[kAmps];
+    const uint32_t k0 = (uint32_t)(tile * kTileH) + threadIdx.x * kAmpsH;
+    C_t<R> acc[kAmpsH];
 #pragma unroll
-    for (int i = 0; i < kAmps; ++i) {
-      k[i] = k0 | ((uint32_t)i << kRegShift);
-      live[i] = k[i] < dim;
-      acc[i] = cmake<R>(0, 0);
-      dr[i] = dc[i] = di[i] = dd[i] = R(0);
-    }
-    // diagonal group
-    sum_terms<R>(tb.dz, dw, 0, tb.nd_mid, k0, dr, dc, true);
-    sum_terms<R>(tb.dz, dw, tb.nd_mid, tb.nd, k0, di, dd, false);
-    // off-diagonal groups in LUT form: D = sigma * lut[phi]; an exact zero
-    // entry means no coupling, so the gather is skipped.  phi and sigma of
-    // k_i are those of k0 flipped by the group's constant `pad` bits.
-    for (int c0 = 0; c0 < tb.GL; c0 += kLutChunk) {
-      const int cn = min(kLutChunk, tb.GL - c0);
+    for (int i = 0; i < kAmpsH; ++i) acc[i] = cmake<R>(0, 0);
+    // off-diagonal groups in LUT form
+    for (int c = 0; c < tb.n_lchunks; ++c) {
+      const int g0 = tb.lchunk[c], cn = tb.lchunk[c + 1] - g0;
       __syncthreads();
-      for (int g = threadIdx.x; g < cn; g += kThreads) s_l[g] = hl[c0 + g];
+      for (int g = threadIdx.x; g < cn; g += kThreads) s_l[g] = hl[g0 + g];
       __syncthreads();
-      for (int g = 0; g < cn; ++g) {
-        const LutDev<R>& L = s_l[g];
-        const uint32_t code0 = lut_phi(L, k0) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
-        const uint32_t reg = (uint32_t)L.pad << 4;   // code flips of amplitudes 1..3
-#pragma unroll
-        for (int i = 0; i < kAmps; ++i) {
-          const uint32_t code = code0 ^ ((reg >> (4 * i)) & 0xFu);
-          const R val = L.lut[code & 7u];
-          if (val != R(0) && live[i]) {
-            const R dv = (code & 8u) ? -val : val;
-            const C_t<R> p = psi[k[i] ^ L.x];
-            acc[i].x += dv * p.x;
-            acc[i].y += dv * p.y;
-          }
-        }
-      }
+#define GOCP_LUT_CALL(XLV) lut_chunk<R, XLV>(s_l, cn, k0, psi, dim, acc)
+      GOCP_XL_SWITCH(tb.lchunk_xl[c], GOCP_LUT_CALL)
+#undef GOCP_LUT_CALL
     }
     // off-diagonal groups as term lists
     for (int c = 0; c < tb.n_chunks; ++c) {
@@ -340,33 +409,30 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
       __syncthreads();
       const uint32_t* zs = staged ? s_z : tb.tz + t0;
       const R* ws = staged ? s_w : tw + t0;
-      for (int g = g0; g < g1; ++g) {
-        const uint32_t x = s_x[g - g0];
-        const int tbeg = s_off[g - g0], tmid = s_mid[g - g0], tend = s_off[g - g0 + 1];
-        R gr[kAmps], gi[kAmps], cr[kAmps], ci[kAmps];
-#pragma unroll
-        for (int i = 0; i < kAmps; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
-        sum_terms<R>(zs, ws, tbeg, tmid, k0, gr, cr, false);
-        if (tend > tmid) sum_terms<R>(zs, ws, tmid, tend, k0, gi, ci, false);
-#pragma unroll
-        for (int i = 0; i < kAmps; ++i) {
-          if (!live[i]) continue;
-          C_t<R> p = psi[k[i] ^ x];
-          acc[i].x += gr[i] * p.x - gi[i] * p.y;
-          acc[i].y += gr[i] * p.y + gi[i] * p.x;
-        }
-      }
+#define GOCP_TERM_CALL(XLV) term_chunk<R, XLV>(s_x, s_off, s_mid, g1 - g0, zs, ws, k0, psi, dim, acc)
+      GOCP_XL_SWITCH(tb.chunk_xl[c], GOCP_TERM_CALL)
+#undef GOCP_TERM_CALL
     }
+    // diagonal group, last so that its accumulators are not live above
+    R dr[kAmpsH], dc[kAmpsH], di[kAmpsH], dd[kAmpsH];
 #pragma unroll
-    for (int i = 0; i < kAmps; ++i) {
-      if (!live[i]) continue;
-      const C_t<R> p = psi[k[i]];
-      const double pp = (double)p.x * p.x + (double)p.y * p.y;
-      v[0] += pp;
-      // Re(conj(p) (acc + D0 p)); the imaginary diagonal part adds nothing
-      v[1] += (double)p.x * acc[i].x + (double)p.y * acc[i].y + ((double)dr[i] - (double)dc[i]) * pp;
-      const R d0 = dr[i] - dc[i] + idr;
-      out[k[i]] = cmake<R>(acc[i].x + d0 * p.x - di[i] * p.y, acc[i].y + d0 * p.y + di[i] * p.x);
+    for (int i = 0; i < kAmpsH; ++i) dr[i] = dc[i] = di[i] = dd[i] = R(0);
+    sum_terms8<R>(tb.dz, dw, 0, tb.nd_mid, k0, dr, dc, true);
+    sum_terms8<R>(tb.dz, dw, tb.nd_mid, tb.nd, k0, di, dd, false);
+    if (k0 < dim) {
+      C_t<R> own[kAmpsH];
+      load_octet<R>(psi, k0, dim, own);
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        if (k0 + i >= dim) continue;
+        const C_t<R> p = own[i];
+        const double pp = (double)p.x * p.x + (double)p.y * p.y;
+        v[0] += pp;
+        // Re(conj(p) (acc + D0 p)); the imaginary diagonal part adds nothing
+        v[1] += (double)p.x * acc[i].x + (double)p.y * acc[i].y + ((double)dr[i] - (double)dc[i]) * pp;
+        const R d0 = dr[i] - dc[i] + idr;
+        out[k0 + i] = cmake<R>(acc[i].x + d0 * p.x - di[i] * p.y, acc[i].y + d0 * p.y + di[i] * p.x);
+      }
     }
   }
   if (partials && grid_sum<2>(v, partials, counter, nb, bid, scal + 1, tot)) {
@@ -375,7 +441,7 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_apply_h(DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, double identity,
           double* partials, unsigned int* counter, double* scal) {
   apply_body<R>(tb, psi, out, identity, partials, counter, scal, blockIdx.x, gridDim.x);
@@ -886,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_stage_forward(const BatchItemDev* 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_stage_energy(const BatchItemDev* items, BatchIndex ix) {
+__global__ void __launch_bounds__(kThreads, 2) k_stage_energy(const BatchItemDev* items, BatchIndex ix) {
   int bid;
   const BatchItemDev& it = items[find_item(ix, bid)];
   apply_body<R>(it.t, (const C_t<R>*)it.psi, (C_t<R>*)it.lam, it.identity, it.partials, it.counter,
@@ -962,17 +1028,36 @@ bool make_lut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<doub
                        ((uint32_t)parity32(x & L.v2) << 2);
   L.fx = phx | ((uint32_t)parity32(x & f.z0) << 3);
   L.s = __builtin_ctz(x);
-  // code flips (phi in bits 0..2, sigma in bit 3) of amplitude i = 1..3 of a
-  // thread, whose index differs from the first by i << kRegShift
-  uint32_t reg = 0;
-  for (uint32_t i = 1; i < 4; ++i) {
-    const uint32_t b = i << kRegShift;
-    const uint32_t code = (uint32_t)parity32(b & L.v0) | ((uint32_t)parity32(b & L.v1) << 1) |
-                          ((uint32_t)parity32(b & L.v2) << 2) | ((uint32_t)parity32(b & f.z0) << 3);
-    reg |= code << (4 * (i - 1));
-  }
-  L.pad = (int32_t)reg;
   for (int i = 0; i < 8; ++i) L.lut[i] = (R)(i < (1 << f.d) ? f.lut[i] : 0.0);
+  *out = L;
+  return true;
+}
+
+// LUT descriptor of one H x-group for the octet layout of the H psi kernel.
+template <typename R>
+bool make_hlut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<double>& w, HLut<R>* out) {
+  if (z.empty() || x == 0) return false;
+  LutForm f = lut_form(z.data(), w.data(), (int)z.size());
+  if (!f.ok) return false;
+  HLut<R> L;
+  std::memset(&L, 0, sizeof(L));
+  L.x = x;
+  L.z0 = f.z0;
+  L.v0 = f.d > 0 ? f.v[0] : 0u;
+  L.v1 = f.d > 1 ? f.v[1] : 0u;
+  L.v2 = f.d > 2 ? f.v[2] : 0u;
+  uint32_t reg = 0;
+  for (uint32_t i = 0; i < 8; ++i) {
+    const uint32_t code = (uint32_t)parity32(i & L.v0) | ((uint32_t)parity32(i & L.v1) << 1) |
+                          ((uint32_t)parity32(i & L.v2) << 2) | ((uint32_t)parity32(i & f.z0) << 3);
+    reg |= code << (4 * i);
+  }
+  L.reg = reg;
+  for (int c = 0; c < 16; ++c) {
+    const int ph = c & 7;
+    const double val = ph < (1 << f.d) ? f.lut[ph] : 0.0;
+    L.lut16[c] = (R)((c & 8) ? -val : val);
+  }
   *out = L;
   return true;
 }
@@ -980,18 +1065,24 @@ bool make_lut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<doub
 template <typename R>
 int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   const PauliTerms& H = p.H;
-  // ---- Hamiltonian: identity apart, diagonal group apart, off-diagonal groups
-  std::vector<uint32_t> gx, tz, dz_r, dz_i;
-  std::vector<int32_t> goff, gmid;
-  std::vector<R> tw, dw_r, dw_i;
-  std::vector<LutDev<R>> hl;
+  // ---- Hamiltonian: identity apart, diagonal group apart, off-diagonal
+  // groups in LUT form or as term lists, each sorted by (x & 7, x)
+  struct TermGroup {
+    uint32_t x;
+    std::vector<uint32_t> zr, zi;
+    std::vector<R> wr, wi;
+  };
+  std::vector<uint32_t> dz_r, dz_i;
+  std::vector<R> dw_r, dw_i;
+  std::vector<HLut<R>> hl;
+  std::vector<TermGroup> tgs;
   double ident = 0.0;
   size_t i = 0;
   while (i < H.size()) {
     size_t j = i;
     while (j < H.size() && H.x[j] == H.x[i]) ++j;
-    std::vector<uint32_t> zr, zi;
-    std::vector<R> wr, wi;
+    TermGroup tg;
+    tg.x = H.x[i];
     std::vector<double> wr64;
     for (size_t t = i; t < j; ++t) {
       bool imag = false;
@@ -1000,60 +1091,84 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
         ident += w;
         continue;
       }
-      (imag ? zi : zr).push_back(H.z[t]);
-      (imag ? wi : wr).push_back((R)w);
+      (imag ? tg.zi : tg.zr).push_back(H.z[t]);
+      (imag ? tg.wi : tg.wr).push_back((R)w);
       if (!imag) wr64.push_back(w);
     }
-    LutDev<R> L;
-    if (H.x[i] != 0 && zi.empty() && make_lut<R>(H.x[i], zr, wr64, &L)) {
+    HLut<R> L;
+    if (H.x[i] == 0) {
+      dz_r = tg.zr;
+      dw_r = tg.wr;
+      dz_i = tg.zi;
+      dw_i = tg.wi;
+    } else if (tg.zi.empty() && make_hlut<R>(H.x[i], tg.zr, wr64, &L)) {
       hl.push_back(L);
-    } else if (H.x[i] == 0) {
-      dz_r = zr;
-      dw_r = wr;
-      dz_i = zi;
-      dw_i = wi;
-    } else if (!zr.empty() || !zi.empty()) {
-      gx.push_back(H.x[i]);
-      goff.push_back((int32_t)tz.size());
-      tz.insert(tz.end(), zr.begin(), zr.end());
-      tw.insert(tw.end(), wr.begin(), wr.end());
-      gmid.push_back((int32_t)tz.size());
-      tz.insert(tz.end(), zi.begin(), zi.end());
-      tw.insert(tw.end(), wi.begin(), wi.end());
+    } else if (!tg.zr.empty() || !tg.zi.empty()) {
+      tgs.push_back(std::move(tg));
     }
     i = j;
   }
-  goff.push_back((int32_t)tz.size());
   *identity = ident;
-  const int G = (int)gx.size();
-  // chunk plan: runs of groups whose terms fit the shared-memory stage
-  std::vector<int32_t> chunk{0};
-  {
-    int g = 0;
-    while (g < G) {
-      int h = g;
-      while (h < G && h - g < kChunkGroups && goff[h + 1] - goff[g] <= kChunkTerms) ++h;
-      if (h == g) h = g + 1;   // one oversized group: its own chunk
-      chunk.push_back(h);
-      g = h;
-    }
+  std::stable_sort(hl.begin(), hl.end(), [](const HLut<R>& a, const HLut<R>& b) {
+    return (a.x & 7u) != (b.x & 7u) ? (a.x & 7u) < (b.x & 7u) : a.x < b.x;
+  });
+  std::stable_sort(tgs.begin(), tgs.end(), [](const TermGroup& a, const TermGroup& b) {
+    return (a.x & 7u) != (b.x & 7u) ? (a.x & 7u) < (b.x & 7u) : a.x < b.x;
+  });
+  // LUT chunks: runs of equal x & 7 cut every kLutChunkH groups
+  std::vector<int32_t> lchunk{0};
+  std::vector<uint8_t> lchunk_xl;
+  for (int g = 0; g < (int)hl.size();) {
+    int h = g;
+    while (h < (int)hl.size() && h - g < kLutChunkH && (hl[h].x & 7u) == (hl[g].x & 7u)) ++h;
+    lchunk.push_back(h);
+    lchunk_xl.push_back((uint8_t)(hl[g].x & 7u));
+    g = h;
   }
-  LutDev<R>* dhl;
-  if (int rc0 = upload(d, &dhl, hl, bytes)) return rc0;
-  d.t.GL = (int)hl.size();
-  d.t.hlut = dhl;
+  // term-list groups flattened; chunks fit the shared-memory stage and never
+  // mix two values of x & 7 (a single oversized group is its own chunk)
+  std::vector<uint32_t> gx, tz;
+  std::vector<int32_t> goff, gmid;
+  std::vector<R> tw;
+  for (const TermGroup& tg : tgs) {
+    gx.push_back(tg.x);
+    goff.push_back((int32_t)tz.size());
+    tz.insert(tz.end(), tg.zr.begin(), tg.zr.end());
+    tw.insert(tw.end(), tg.wr.begin(), tg.wr.end());
+    gmid.push_back((int32_t)tz.size());
+    tz.insert(tz.end(), tg.zi.begin(), tg.zi.end());
+    tw.insert(tw.end(), tg.wi.begin(), tg.wi.end());
+  }
+  goff.push_back((int32_t)tz.size());
+  const int G = (int)gx.size();
+  std::vector<int32_t> chunk{0};
+  std::vector<uint8_t> chunk_xl;
+  for (int g = 0; g < G;) {
+    int h = g;
+    while (h < G && h - g < kChunkGroups && goff[h + 1] - goff[g] <= kChunkTerms &&
+           (gx[h] & 7u) == (gx[g] & 7u))
+      ++h;
+    if (h == g) h = g + 1;
+    chunk.push_back(h);
+    chunk_xl.push_back((uint8_t)(gx[g] & 7u));
+    g = h;
+  }
   std::vector<uint32_t> dz(dz_r);
   dz.insert(dz.end(), dz_i.begin(), dz_i.end());
   std::vector<R> dw(dw_r);
   dw.insert(dw.end(), dw_i.begin(), dw_i.end());
   int rc;
   uint32_t *dgx, *dtz, *ddz;
-  int32_t *dgoff, *dgmid, *dchunk;
+  int32_t *dgoff, *dgmid, *dchunk, *dlchunk;
+  uint8_t *dchunk_xl, *dlchunk_xl;
   R *dtw, *ddw;
+  HLut<R>* dhl;
   if ((rc = upload(d, &dgx, gx, bytes)) || (rc = upload(d, &dgoff, goff, bytes)) ||
       (rc = upload(d, &dgmid, gmid, bytes)) || (rc = upload(d, &dchunk, chunk, bytes)) ||
-      (rc = upload(d, &dtz, tz, bytes)) || (rc = upload(d, &dtw, tw, bytes)) ||
-      (rc = upload(d, &ddz, dz, bytes)) || (rc = upload(d, &ddw, dw, bytes)))
+      (rc = upload(d, &dchunk_xl, chunk_xl, bytes)) || (rc = upload(d, &dtz, tz, bytes)) ||
+      (rc = upload(d, &dtw, tw, bytes)) || (rc = upload(d, &ddz, dz, bytes)) ||
+      (rc = upload(d, &ddw, dw, bytes)) || (rc = upload(d, &dhl, hl, bytes)) ||
+      (rc = upload(d, &dlchunk, lchunk, bytes)) || (rc = upload(d, &dlchunk_xl, lchunk_xl, bytes)))
     return rc;
   d.t.n = p.n_qubits;
   d.t.G = G;
@@ -1063,12 +1178,18 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.goff = dgoff;
   d.t.gmid = dgmid;
   d.t.chunk_g = dchunk;
+  d.t.chunk_xl = dchunk_xl;
   d.t.tz = dtz;
   d.t.tw = dtw;
   d.t.nd = (int)dz.size();
   d.t.nd_mid = (int)dz_r.size();
   d.t.dz = ddz;
   d.t.dw = ddw;
+  d.t.GL = (int)hl.size();
+  d.t.hlut = dhl;
+  d.t.n_lchunks = (int)lchunk.size() - 1;
+  d.t.lchunk = dlchunk;
+  d.t.lchunk_xl = dlchunk_xl;
   // ---- pool
   const Pool& P = p.pool;
   const int M = P.size();
@@ -1141,7 +1262,7 @@ int grid_for(uint64_t work, int sm_count, int per_sm) {
   return (int)std::max<uint64_t>(1, std::min(want, cap));
 }
 
-int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kTile - 1) / kTile); }
+int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kTileH - 1) / kTileH); }
 int pool_grid_x(const DeviceTables& d) { return grid_for(1ull << d.t.n, d.sm_count, 2); }
 int pool_lut_nbx(int n) {
   const uint64_t per = (uint64_t)kThreads * kPairsPerThread;
@@ -1373,7 +1494,7 @@ namespace {
 int item_blocks(const Problem& p, int kind) {
   const uint64_t dim = 1ull << p.n_qubits;
   uint64_t want;
-  if (kind == STAGE_ENERGY) want = (dim + kTile - 1) / kTile;
+  if (kind == STAGE_ENERGY) want = (dim + kTileH - 1) / kTileH;
   else if (kind == STAGE_FORWARD || kind == STAGE_BACKWARD) want = ((dim >> 1) + kThreads - 1) / kThreads;
   else want = (dim + kThreads - 1) / kThreads;
   uint64_t cap = (uint64_t)std::max(p.sm_count, 1) * kItemBlocksPerSm;
