@@ -212,6 +212,24 @@ int gocp_adapt_step(const gocp_problem* p, const int32_t* ops, const double* the
                     int mem, void* ws, double tie_rel, double* out_e, double* grads,
                     int32_t* selected, void* stream);
 
+/* The same H psi and energy as gocp_energy (identical kernel and results),
+ * allocating nothing: its reduction scratch is a fixed device array inside
+ * this library rather than memory allocated with the problem.  It is meant
+ * for callers that cannot call cudaMalloc where they compute -- a host loop
+ * with real-time or no-blocking guarantees, or a caller whose device memory
+ * is owned by another allocator -- and that pass every input and output
+ * (tables built earlier, psi, hpsi, out) themselves.  The paper has no
+ * counterpart; this is a deployment variant of Eq. (1) and Eq. (3).
+ * Limits: at most 24 qubits (the array holds 8192 block partials, one per
+ * 2048-amplitude tile; larger states return GOCP_EINVAL with the numbers).
+ * The first call on a device resolves the array's address on that device
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call shares the one array: calls that overlap on the GPU
+ * race, so order them on one stream.  out: 2 doubles (E, <psi|psi>), host or
+ * device per `mem`. */
+int gocp_energy_static(const gocp_problem* p, const void* psi, void* hpsi, double* out, int mem,
+                       void* stream);
+
 /* Device-side argument errors flagged since the last call (bit 0: op index
  * out of range in a GOCP_MEM_DEVICE ansatz), and clear them.  Synchronises
  * `stream`. */

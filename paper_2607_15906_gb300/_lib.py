@@ -75,6 +75,7 @@ _SIGS = {
     "gocp_taylor_step": (C.c_int, [P, C.c_int, C.c_double, P, P]),
     "gocp_apply_h": (C.c_int, [P, P, P, P]),
     "gocp_energy": (C.c_int, [P, P, P, P, C.c_int, P]),
+    "gocp_energy_static": (C.c_int, [P, P, P, P, C.c_int, P]),
     "gocp_pool_gradients": (C.c_int, [P, P, P, P, C.c_int, P]),
     "gocp_energy_grad": (C.c_int, [P, P, P, C.c_int, C.c_int, P, P, P, P]),
     "gocp_adapt_step": (C.c_int, [P, P, P, C.c_int, C.c_int, P, C.c_double, P, P, P, P]),

@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "device.cuh"
@@ -1483,6 +1485,97 @@ int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out
   count_launches(1);
   return cuda_status(cudaGetLastError(), "k_select");
 }
+
+
+// ------------------------------------------------------------ allocation-free energy
+//
+// gocp_energy_static: H psi and the energy with the reduction scratch in a
+// file-scope device array instead of the problem's allocated scratch.  For
+// callers that cannot allocate device memory at the point of the call (a
+// real-time or embedded host loop that must not block on cudaMalloc, a
+// caller whose memory is owned by another allocator, work recorded between
+// allocation-free checkpoints).  The problem's tables, the states and the
+// outputs are still the caller's inputs and outputs.
+//
+// The array is shared by every call in the process: calls that overlap on
+// the GPU race on it.  Every GPU that loads this library holds it (128 KiB
+// of partials plus a few scalars) until the process exits.
+
+constexpr int kStaticEnergyBlocks = 8192;   // one block per 2048-amplitude tile: n <= 24
+
+struct StaticEnergyScratch {
+  double partials[2 * kStaticEnergyBlocks];
+  double scal[4];                            // [0] E [1] <psi|psi> [2] Re<psi|H' psi>
+  unsigned int counter;
+};
+
+static __device__ __align__(256) StaticEnergyScratch g_static_energy;
+
+namespace {
+
+std::mutex g_static_mu;
+std::vector<StaticEnergyScratch*> g_static_addr;   // per device ordinal, resolved once
+
+// Device address of g_static_energy on `device`, which must be current.
+int static_scratch(int device, StaticEnergyScratch** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (device >= (int)g_static_addr.size()) g_static_addr.resize(device + 1, nullptr);
+  if (!g_static_addr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_energy);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static energy scratch)");
+    g_static_addr[device] = (StaticEnergyScratch*)ptr;
+  }
+  *out = g_static_addr[device];
+  return GOCP_OK;
+}
+
+template <typename R>
+int launch_energy_static(Problem& p, const void* psi, void* hpsi, StaticEnergyScratch* sc, cudaStream_t st) {
+  const int grid = apply_grid(p.n_qubits);
+  k_apply_h<R><<<grid, kThreads, 0, st>>>(p.dev->t, (const C_t<R>*)psi, (C_t<R>*)hpsi, p.identity,
+                                          sc->partials, &sc->counter, sc->scal);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_apply_h (static scratch)");
+}
+
+}  // namespace
+
+}  // namespace gocp
+
+extern "C" int gocp_energy_static(const gocp_problem* h, const void* psi, void* hpsi, double* out,
+                                  int mem, void* stream) {
+  using namespace gocp;
+  if (!h) return fail(GOCP_EINVAL, "problem is NULL");
+  Problem& p = const_cast<Problem&>(h->p);
+  if (!p.dev) return fail(GOCP_ENODEV, "problem has no device tables (built with device = -1)");
+  if (mem != GOCP_MEM_HOST && mem != GOCP_MEM_DEVICE) return fail(GOCP_EINVAL, "mem must be GOCP_MEM_HOST or GOCP_MEM_DEVICE");
+  if (!psi || !hpsi || psi == hpsi || !out) return fail(GOCP_EINVAL, "psi/hpsi/out NULL or aliased");
+  const int blocks = apply_grid(p.n_qubits);
+  if (blocks > kStaticEnergyBlocks)
+    return fail(GOCP_EINVAL, "gocp_energy_static: a state of 2^" + std::to_string(p.n_qubits) +
+                                 " amplitudes needs " + std::to_string(blocks) +
+                                 " reduction blocks; the static scratch holds 8192 (at most 24 qubits)");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != p.device) cudaSetDevice(p.device);
+  cudaStream_t st = (cudaStream_t)stream;
+  StaticEnergyScratch* sc = nullptr;
+  int rc = static_scratch(p.device, &sc);
+  // the block counter must start at zero (the kernel also leaves it at zero)
+  if (!rc) rc = cuda_status(cudaMemsetAsync(&sc->counter, 0, sizeof(unsigned int), st), "clear counter");
+  if (!rc) rc = p.precision == GOCP_C64 ? launch_energy_static<float>(p, psi, hpsi, sc, st)
+                                        : launch_energy_static<double>(p, psi, hpsi, sc, st);
+  if (!rc) rc = cuda_status(cudaMemcpyAsync(out, sc->scal, 2 * sizeof(double),
+                                            mem == GOCP_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                                 : cudaMemcpyDeviceToDevice, st),
+                            "copy energy");
+  if (!rc && mem == GOCP_MEM_HOST) rc = cuda_status(cudaStreamSynchronize(st), "synchronise");
+  if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
+  return rc;
+}
+
+namespace gocp {
 
 // ------------------------------------------------------------ batched launch
 
