@@ -204,6 +204,120 @@ def run_gpu(args, rank, world, device):
                 h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]))
 
 
+def serving_bench(device: int, n_requests: int = 160, seed: int = 7):
+    """Mixed-size energy+gradient stream through the continuous-batching server.
+
+    Requests follow synth.serving_requests (qubits uniform over 10..22,
+    Hamiltonian seed 1000+i, 10-80 operators, theta ~ N(0, 0.05), complex64).
+    Their Hamiltonians are built before the clock starts.  First every request
+    is submitted at once to find the saturation throughput, then the same
+    stream arrives as a Poisson process at 0.5x and 1x that rate; latency is
+    completion minus arrival.
+    """
+    import torch
+    import paper_2607_15906_gb300 as gb
+    from paper_2607_15906_gb300.serving import Server
+    from synth import molecular_integrals, serving_requests
+
+    reqs = serving_requests(n_requests, rate_per_s=1.0, seed=seed)
+    probs = {}
+    for r in reqs:
+        ints = molecular_integrals(r.n_orb, seed=r.seed, decay=True)
+        probs[r.index] = gb.Problem.build(ints, r.n_elec, precision="c64", device=device, colour=False)
+    ansatz = {r.index: (np.minimum((r.op_draw * probs[r.index].pool_size).astype(np.int32),
+                                   probs[r.index].pool_size - 1), r.theta) for r in reqs}
+    budget = 8 << 30
+
+    def run(arrivals):
+        lat = []
+        with Server(hbm_budget_bytes=budget, max_slots=64, device=device) as srv:
+            t0 = time.perf_counter()
+            pending = {}
+            order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
+            nxt = 0
+            while nxt < len(order) or pending:
+                now = time.perf_counter() - t0
+                while nxt < len(order) and arrivals[order[nxt]] <= now:
+                    i = order[nxt]
+                    ops, th = ansatz[i]
+                    pending[srv.submit(probs[i], ops, th)] = i
+                    nxt += 1
+                done = []
+                for tk, i in pending.items():
+                    if srv.poll(tk, timeout_s=0.0) is not None:
+                        lat.append(time.perf_counter() - t0 - arrivals[i])
+                        done.append(tk)
+                for tk in done:
+                    del pending[tk]
+                if not done:
+                    time.sleep(0.0002)
+            total = time.perf_counter() - t0
+            st = srv.stats()
+        lat = np.array(lat)
+        return {"requests": len(lat), "seconds": total, "throughput_rps": len(lat) / total,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "max_resident": int(st["max_resident"]), "batched_launches": int(st["launches"]),
+                "ticks": int(st["ticks"])}
+
+    run(np.zeros(len(reqs)))                                   # warm-up
+    sat = run(np.zeros(len(reqs)))
+    rate = sat["throughput_rps"]
+    out = {"stream": f"{n_requests} requests, qubits uniform 10..22, 10-80 ops, complex64, seed {seed}",
+           "saturation": sat}
+    for frac in (0.5, 1.0):
+        gaps = np.random.default_rng(seed).exponential(1.0 / (frac * rate), size=len(reqs))
+        out[f"poisson_{frac}x"] = run(np.cumsum(gaps))
+    return out
+
+
+def c128_components(device: int, steps: int = 2):
+    """The plain complex128 GPU form on the same 24-qubit workload: one
+    selection step (gocp_adapt_step) and one energy evaluation (prepare +
+    H psi); a plain iteration with a forward-difference gradient costs one
+    selection step plus (P + 1) energy evaluations of the grown ansatz."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+
+    ints, cfg = config_integrals(WORKLOAD)
+    prob = gb.Problem.build(ints, N_ELEC, mapping="jw", precision="c128",
+                            int_drop=cfg["int_drop"], term_drop=cfg["term_drop"], device=device)
+    ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
+    ws = prob.workspace()
+    dev = f"cuda:{device}"
+    ops_d = torch.from_numpy(ops).to(dev)
+    th_d = torch.from_numpy(theta).to(dev)
+    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
+    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
+    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(device)
+
+    def timeit(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / k
+
+    t_sel = timeit(lambda: prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-8, out=(e2, g, sel)), steps)
+
+    def energy_eval():
+        prob.prepare_state(ops_d, th_d, ws[0])
+        prob.energy(ws[0], ws[1], out=e2)
+
+    t_e = timeit(energy_eval, steps)
+    p = N_OPS + 1
+    return {"selection_step_ms": t_sel * 1e3, "energy_eval_ms": t_e * 1e3,
+            "plain_iteration_s": t_sel + (p + 1) * t_e,
+            "plain_iterations_per_s": 1.0 / (t_sel + (p + 1) * t_e),
+            "note": "plain iteration = selection step + (P+1) energy evaluations (forward differences), "
+                    "each measured with CUDA events; P = 101"}
+
+
 def roofline(res, peaks, how):
     """Dominant kernel vs its roof (see the design doc for the per-unit figures)."""
     info = res["info"]
@@ -278,6 +392,7 @@ def main():
     ap.add_argument("--impl", default="gocp", choices=["gocp", "reference"])
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the serving and complex128 sub-measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,6 +442,10 @@ def main():
             cpu = cpu_baseline_sample()
         kern = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                 for k, v in res["kern"].items()}
+        extras = {}
+        if not args.no_extras and world == 1:
+            extras["serving"] = serving_bench(local)
+            extras["c128_plain"] = c128_components(local)
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -334,7 +453,8 @@ def main():
                 "e2e": {"value": e2e, "unit": "iterations/s", "h2d_bytes_per_step": res["h2d"],
                         "d2h_bytes_per_step": res["d2h"]},
                 "gpu_launches": res["launches"], "roofline": roof, "cpu_baseline": cpu,
-                "clocks": res["clocks"], "kernels": kern, "energy": res["e"], "selected": res["sel"]}
+                "clocks": res["clocks"], "kernels": kern, "energy": res["e"], "selected": res["sel"],
+                **extras}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
