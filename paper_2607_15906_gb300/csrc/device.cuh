@@ -55,6 +55,45 @@ __device__ __forceinline__ uint32_t lut_phi(const LutDev<R>& L, uint32_t b) {
          ((uint32_t)(__popc(b & L.v2) & 1) << 2);
 }
 
+// The basis pairs {b, b^x} (b with bit s clear) that a LUT-form generator
+// touches, i.e. lut[phi(b)] != 0 or lut[phi(b) ^ phi(x)] != 0, as an
+// enumerable set: for each touched code, b is a counter deposited into the
+// free bit positions (all but s and the r pivot positions, `excl`, ascending)
+// with pivot bit k set to the reduced code bit k xor popc(b & pmask[k]).
+// codes: byte j = reduced code (bits 0..2) | original code << 3 of the j-th
+// touched code.  count = ncodes << log2cnt pairs.
+struct PairEnum {
+  uint32_t excl;       // nex positions, one per byte, ascending
+  uint32_t piv;        // r pivot positions, one per byte
+  uint32_t pmask[3];
+  uint32_t codes;      // up to 4 touched codes (generators of rank <= 3 touch at most 4)
+  uint32_t codes_hi;   // codes 4..7
+  uint8_t nex, r, ncodes, log2cnt;
+};
+
+__device__ __forceinline__ uint32_t enum_deposit(uint32_t c, uint32_t excl, int nex) {
+  for (int e = 0; e < nex; ++e) {
+    const uint32_t p = (excl >> (8 * e)) & 0xFFu;
+    c = ((c >> p) << (p + 1)) | (c & ((1u << p) - 1u));
+  }
+  return c;
+}
+
+// Pair base b and original code of enumerated pair `idx`.
+__device__ __forceinline__ uint32_t enum_pair(const PairEnum& e, uint32_t idx, uint32_t* code) {
+  const uint32_t ci = idx >> e.log2cnt;
+  const uint32_t cnt = idx & ((1u << e.log2cnt) - 1u);
+  const uint32_t byte = ((ci < 4 ? e.codes : e.codes_hi) >> (8 * (ci & 3))) & 0xFFu;
+  uint32_t b = enum_deposit(cnt, e.excl, e.nex);
+  const uint32_t bf = b;
+  for (int k = 0; k < e.r; ++k) {
+    const uint32_t bit = ((byte >> k) & 1u) ^ (uint32_t)(__popc(bf & e.pmask[k]) & 1);
+    b |= bit << ((e.piv >> (8 * k)) & 0xFFu);
+  }
+  *code = byte >> 3;
+  return b;
+}
+
 // An H x-group in LUT form for the H psi kernel, whose threads own 8
 // adjacent amplitudes k0 + i (k0 a multiple of 8): code(k) = phi(k) | sigma(k) << 3
 // with sigma(k) = popc(k & z0) & 1, so that D(k) = lut16[code(k)] (the sign
@@ -119,9 +158,12 @@ struct DevTables {
   const void* pw = nullptr;
   const void* pw2 = nullptr;
   const int32_t* porder = nullptr;
-  // every generator in LUT form (pool order), when all of them qualify
+  // every generator in LUT form (pool order), when all of them qualify, and
+  // the enumeration of the pairs each one touches
   bool pool_lut = false;
   const void* plut = nullptr;
+  const PairEnum* penum = nullptr;
+  uint32_t penum_max = 0;   // largest touched-pair count of any generator
 };
 
 }  // namespace gocp

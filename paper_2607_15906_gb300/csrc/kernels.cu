@@ -540,9 +540,9 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
 // v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
 // m = 0..5, stay in registers.
-// LUT form of the same step: real D on the pair, and pairs the operator does
-// not touch (both lut entries exactly zero, T = I there) are not read or
-// written.
+// LUT form of the same step: real D on the pair; only the pairs the
+// operator touches are visited (enumerated, see PairEnum) -- on the others
+// T = I and nothing is read or written.
 template <typename R>
 __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                 C_t<R>* psi, int32_t* err, int bid, int nb) {
@@ -552,16 +552,16 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
     return;
   }
   const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
+  const PairEnum E = tb.penum[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  const uint64_t npairs = 1ull << (tb.n - 1);
-  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
-    const uint32_t b = pair_base(p, L.s);
-    const uint32_t ph = lut_phi(L, b);
+  const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
+  for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
+    uint32_t ph;
+    const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    if (l1 == R(0) && l2 == R(0)) continue;
     const uint32_t sg = __popc(b & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
     const uint32_t b2 = b ^ L.x;
@@ -630,8 +630,8 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 //   psi <- T^-1 psi = (C I - S A) psi / (C^2 - S^2 mu)      (exact inverse)
 //   dE_j += 2 Re <lambda|T' psi>                            (lambda before update)
 //   lambda <- T^dagger lambda.
-// LUT form of the backward step (real D); untouched pairs (both lut entries
-// zero: T = I, T' = 0 there) are skipped.
+// LUT form of the backward step (real D) over the enumerated pairs the
+// operator touches (elsewhere T = I and T' = 0).
 template <typename R>
 __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                  C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
@@ -646,17 +646,17 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
     return;
   }
   const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
+  const PairEnum E = tb.penum[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  const uint64_t npairs = 1ull << (tb.n - 1);
+  const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
   double v[1] = {0.0};
-  for (uint64_t p = bid * (uint64_t)kThreads + threadIdx.x; p < npairs; p += (uint64_t)nb * kThreads) {
-    const uint32_t b = pair_base(p, L.s);
-    const uint32_t ph = lut_phi(L, b);
+  for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
+    uint32_t ph;
+    const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    if (l1 == R(0) && l2 == R(0)) continue;
     const uint32_t sg = __popc(b & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
     const uint32_t b2 = b ^ L.x;
@@ -832,49 +832,56 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
 }
 
 // Pool gradients for generators in LUT form.  blockIdx.y picks
-// kOpsPerBlock operators in GOCP family order; blockIdx.x a contiguous range
-// of kThreads * kPairsPerThread basis pairs {b, b^x}.  Operators are taken
-// one after another (one accumulator per thread), and a pair enters only
-// where the operator touches it:
-//   Re<H psi|A psi> over the pair = D(b) Re(conj(h_b) psi_{b^x}) + D(b^x) Re(conj(h_{b^x}) psi_b).
+// kOpsPerBlock operators in GOCP family order; blockIdx.x a range of
+// kThreads * kPairsPerThread of each operator's enumerated touched pairs
+// {b, b^x} (see PairEnum).  Operators are taken one after another (one
+// accumulator per thread):
+//   Re<H psi|A psi> over a pair = D(b) Re(conj(h_b) psi_{b^x}) + D(b^x) Re(conj(h_{b^x}) psi_b).
 // Each block writes one FP64 partial per operator: part[pos * nbx + blockIdx.x].
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_lut(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
                 double* part, int nbx) {
   __shared__ LutDev<R> s_op[kOpsPerBlock];
+  __shared__ PairEnum s_en[kOpsPerBlock];
   __shared__ double s_red[kWarps];
   const int first = blockIdx.y * kOpsPerBlock;
   const int nops = min(kOpsPerBlock, tb.M - first);
   const LutDev<R>* pl = (const LutDev<R>*)tb.plut;
-  if (threadIdx.x < nops) s_op[threadIdx.x] = pl[tb.porder[first + threadIdx.x]];
+  if (threadIdx.x < nops) {
+    const int op = tb.porder[first + threadIdx.x];
+    s_op[threadIdx.x] = pl[op];
+    s_en[threadIdx.x] = tb.penum[op];
+  }
   __syncthreads();
-  const uint64_t npairs = 1ull << (tb.n - 1);
   const uint64_t base = (uint64_t)blockIdx.x * kThreads * kPairsPerThread;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 0; o < nops; ++o) {
     const LutDev<R>& L = s_op[o];
+    const PairEnum& E = s_en[o];
+    const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
     const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
     R acc = 0, cmp = 0;
+    if (base < count) {
 #pragma unroll 4
-    for (int jj = 0; jj < kPairsPerThread; ++jj) {
-      const uint64_t pp = base + (uint64_t)jj * kThreads + threadIdx.x;
-      if (pp >= npairs) break;
-      const uint32_t b = pair_base(pp, L.s);
-      const uint32_t ph = lut_phi(L, b);
-      const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-      if (l1 == R(0) && l2 == R(0)) continue;
-      const uint32_t sg = __popc(b & L.z0) & 1u;
-      const uint32_t b2 = b ^ L.x;
-      const C_t<R> h1 = hpsi[b], h2 = hpsi[b2], p1 = psi[b], p2 = psi[b2];
-      const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
-                    ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
-      if (sizeof(R) == 4) {
-        R y = val - cmp, t = acc + y;
-        cmp = (t - acc) - y;
-        acc = t;
-      } else {
-        acc += val;
+      for (int jj = 0; jj < kPairsPerThread; ++jj) {
+        const uint64_t q = base + (uint64_t)jj * kThreads + threadIdx.x;
+        if (q >= count) break;
+        uint32_t ph;
+        const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
+        const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+        const uint32_t sg = __popc(b & L.z0) & 1u;
+        const uint32_t b2 = b ^ L.x;
+        const C_t<R> h1 = hpsi[b], h2 = hpsi[b2], p1 = psi[b], p2 = psi[b2];
+        const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
+                      ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
+        if (sizeof(R) == 4) {
+          R y = val - cmp, t = acc + y;
+          cmp = (t - acc) - y;
+          acc = t;
+        } else {
+          acc += val;
+        }
       }
     }
     double v = (double)acc - (double)cmp;
@@ -1032,6 +1039,58 @@ bool make_lut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<doub
   L.s = __builtin_ctz(x);
   for (int i = 0; i < 8; ++i) L.lut[i] = (R)(i < (1 << f.d) ? f.lut[i] : 0.0);
   *out = L;
+  return true;
+}
+
+// Touched-pair enumeration of a LUT-form generator (see PairEnum).
+bool make_enum(const LutForm& f, uint32_t x, int n, PairEnum* out) {
+  const int s = __builtin_ctz(x);
+  const uint32_t sbit = 1u << s;
+  uint32_t R[3], Cm[3], dep[3];
+  int piv[3], r = 0, ndep = 0;
+  for (int i = 0; i < f.d; ++i) {
+    uint32_t v = f.v[i] & ~sbit, c = 1u << i;
+    for (int k = 0; k < r; ++k)
+      if ((v >> piv[k]) & 1u) { v ^= R[k]; c ^= Cm[k]; }
+    if (v == 0) { dep[ndep++] = c; continue; }   // rows in c sum to zero on b with bit s clear
+    const int p = 31 - __builtin_clz(v);
+    for (int k = 0; k < r; ++k)
+      if ((R[k] >> p) & 1u) { R[k] ^= v; Cm[k] ^= c; }
+    R[r] = v; Cm[r] = c; piv[r] = p; ++r;
+  }
+  const uint32_t phx = (uint32_t)parity32(x & f.v[0]) | ((uint32_t)parity32(x & f.v[1]) << 1) |
+                       ((uint32_t)parity32(x & f.v[2]) << 2);
+  PairEnum e;
+  std::memset(&e, 0, sizeof(e));
+  int nc = 0;
+  uint64_t codes = 0;
+  for (uint32_t c = 0; c < (1u << f.d); ++c) {
+    bool ok = true;
+    for (int q = 0; q < ndep; ++q) ok = ok && !parity32(c & dep[q]);
+    if (!ok) continue;
+    const double l1 = f.lut[c], l2 = f.lut[(c ^ phx) & ((1u << f.d) - 1)];
+    if (l1 == 0.0 && l2 == 0.0) continue;
+    uint32_t red = 0;
+    for (int k = 0; k < r; ++k) red |= (uint32_t)parity32(c & Cm[k]) << k;
+    codes |= (uint64_t)(red | (c << 3)) << (8 * nc);
+    ++nc;
+  }
+  if (nc == 0) return false;
+  std::vector<int> ex{s};
+  for (int k = 0; k < r; ++k) ex.push_back(piv[k]);
+  std::sort(ex.begin(), ex.end());
+  for (size_t q = 0; q < ex.size(); ++q) e.excl |= (uint32_t)ex[q] << (8 * q);
+  for (int k = 0; k < r; ++k) {
+    e.piv |= (uint32_t)piv[k] << (8 * k);
+    e.pmask[k] = R[k] & ~(1u << piv[k]);
+  }
+  e.codes = (uint32_t)codes;
+  e.codes_hi = (uint32_t)(codes >> 32);
+  e.nex = (uint8_t)ex.size();
+  e.r = (uint8_t)r;
+  e.ncodes = (uint8_t)nc;
+  e.log2cnt = (uint8_t)(n - 1 - r);
+  *out = e;
   return true;
 }
 
@@ -1215,6 +1274,8 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   }
   poff.push_back((int32_t)pz.size());
   std::vector<LutDev<R>> pl(M);
+  std::vector<PairEnum> pe(M);
+  uint32_t pe_max = 0;
   bool all_lut = M > 0;
   for (int k = 0; k < M && all_lut; ++k) {
     std::vector<uint32_t> zz;
@@ -1227,6 +1288,14 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
       ww.push_back(w);
     }
     if (all_lut && !make_lut<R>(px[k], zz, ww, &pl[k])) all_lut = false;
+    if (all_lut) {
+      LutForm f = lut_form(zz.data(), ww.data(), (int)zz.size());
+      if (!make_enum(f, px[k], p.n_qubits, &pe[k])) {
+        // a generator that touches nothing: an empty enumeration
+        std::memset(&pe[k], 0, sizeof(PairEnum));
+      }
+      pe_max = std::max(pe_max, (uint32_t)pe[k].ncodes << pe[k].log2cnt);
+    }
   }
   for (int k = 0; k < M; ++k) porder[k] = k;
   std::stable_sort(porder.begin(), porder.end(), [&](int a, int b) {
@@ -1251,8 +1320,11 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.porder = dporder;
   if (all_lut) {
     LutDev<R>* dpl;
-    if ((rc = upload(d, &dpl, pl, bytes))) return rc;
+    PairEnum* dpe;
+    if ((rc = upload(d, &dpl, pl, bytes)) || (rc = upload(d, &dpe, pe, bytes))) return rc;
     d.t.plut = dpl;
+    d.t.penum = dpe;
+    d.t.penum_max = pe_max;
     d.t.pool_lut = true;
   }
   return GOCP_OK;
@@ -1266,9 +1338,9 @@ int grid_for(uint64_t work, int sm_count, int per_sm) {
 
 int apply_grid(int n) { return (int)std::max<uint64_t>(1, ((1ull << n) + kTileH - 1) / kTileH); }
 int pool_grid_x(const DeviceTables& d) { return grid_for(1ull << d.t.n, d.sm_count, 2); }
-int pool_lut_nbx(int n) {
+int pool_lut_nbx(uint32_t max_pairs) {
   const uint64_t per = (uint64_t)kThreads * kPairsPerThread;
-  return (int)std::max<uint64_t>(1, ((1ull << (n - 1)) + per - 1) / per);
+  return (int)std::max<uint64_t>(1, (max_pairs + per - 1) / per);
 }
 
 }  // namespace
@@ -1294,7 +1366,7 @@ int upload_problem(Problem& p) {
   need = std::max(need, (size_t)pool_grid_x(*d) * (size_t)std::max(nchunks, 1) * kOpsPerBlock);
   need = std::max(need, (size_t)d->sm_count * 8);
   if (d->t.pool_lut)
-    need = std::max(need, (size_t)std::max(nchunks, 1) * kOpsPerBlock * (size_t)pool_lut_nbx(p.n_qubits));
+    need = std::max(need, (size_t)std::max(nchunks, 1) * kOpsPerBlock * (size_t)pool_lut_nbx(d->t.penum_max));
   d->scratch_doubles = need;
   if ((rc = dalloc(*d, &d->scratch, need, bytes))) return rc;
   if ((rc = dalloc(*d, &d->counters, kMaxChunks + 8, bytes))) return rc;
@@ -1370,7 +1442,8 @@ int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStrea
 template <typename R>
 static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
   DeviceTables& d = *p.dev;
-  const int grid = grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
+  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (p.n_qubits - 1);
+  const int grid = grid_for(pairs, d.sm_count, 8);
   for (int j = 0; j < n_ops; ++j) {
     ProfScope ps(GOCP_KERNEL_TAYLOR, st);
     k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err);
@@ -1430,7 +1503,7 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
   const int nchunks = (M + kOpsPerBlock - 1) / kOpsPerBlock;
   int n = 2;
   if (d.t.pool_lut) {
-    const int nbx = pool_lut_nbx(p.n_qubits);
+    const int nbx = pool_lut_nbx(d.t.penum_max);
     dim3 grid(nbx, nchunks);
     {
       ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
@@ -1464,7 +1537,8 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   const uint64_t dim = 1ull << p.n_qubits;
   const int g1 = grid_for(dim, d.sm_count, 8);
   k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, p.n_qubits, d.scalars);
-  const int grid = grid_for(dim / 2, d.sm_count, 8);
+  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : dim / 2;
+  const int grid = grid_for(pairs, d.sm_count, 8);
   for (int j = n_ops - 1; j >= 0; --j) {
     ProfScope ps(GOCP_KERNEL_ADJOINT, st);
     k_adjoint<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, (C_t<R>*)lam,
