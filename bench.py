@@ -318,6 +318,50 @@ def c128_components(device: int, steps: int = 2):
                     "each measured with CUDA events; P = 101"}
 
 
+def adapt_14q(device: int, max_ops: int = 30):
+    """Full ADAPT runs on the 14-qubit workload (7 orbitals, 6 electrons,
+    204-operator pool) to 30 operators, complex128, under JW and BK: every
+    iteration is a device selection step plus a BFGS re-optimisation whose
+    energies and gradients come from the adjoint sweep."""
+    import paper_2607_15906_gb300 as gb
+    from paper_2607_15906_gb300.adapt import adapt
+
+    ints, cfg = config_integrals("c2_14q")
+    out = {"workload": "14q ADAPT to 30 operators (7 orbitals, 6 electrons, 204-op pool), complex128"}
+    runs = {}
+    for mp in ("jw", "bk"):
+        prob = gb.Problem.build(ints, 6, mapping=mp, precision="c128", device=device)
+        t0 = time.perf_counter()
+        run = adapt(prob, max_ops=max_ops, gtol=1e-4)
+        secs = time.perf_counter() - t0
+        runs[mp] = run
+        out[mp] = {"iterations": len(run.energies) - 1, "seconds": secs,
+                   "iterations_per_s": (len(run.energies) - 1) / secs,
+                   "energy_evaluations": run.evaluations, "final_energy": run.energies[-1],
+                   "grad_norm": run.grad_norms[-1], "families": prob.info["n_families"]}
+    same = 0
+    while same < min(len(runs["jw"].ops), len(runs["bk"].ops)) and runs["jw"].ops[same] == runs["bk"].ops[same]:
+        same += 1
+    out["jw_bk_common_operator_prefix"] = same
+    out["jw_bk_max_energy_diff"] = float(np.max(np.abs(np.array(runs["jw"].energies) -
+                                                        np.array(runs["bk"].energies))))
+    return out
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the ncu capture recorded in profiles/traffic.json,
+    only while the library reports the kernel revision that capture was taken on."""
+    try:
+        import paper_2607_15906_gb300 as gb
+        ver = gb.load().gocp_version().decode()
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
+        if rec and f"{kernel}={rec['revision']}" in ver:
+            return rec["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
 def roofline(res, peaks, how):
     """Dominant kernel vs its roof (see the design doc for the per-unit figures)."""
     info = res["info"]
@@ -344,7 +388,7 @@ def roofline(res, peaks, how):
         achieved = per / per_launch_s / 1e9
         out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs"}
-    out["traffic"] = None
+    out["traffic"] = _traffic(out["kernel"])
     out["launch_ms"] = per_launch_s * 1e3
     out["launches_per_step"] = launches / max(1, res.get("steps", 1))
     return out
@@ -446,6 +490,7 @@ def main():
         if not args.no_extras and world == 1:
             extras["serving"] = serving_bench(local)
             extras["c128_plain"] = c128_components(local)
+            extras["adapt_14q"] = adapt_14q(local)
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

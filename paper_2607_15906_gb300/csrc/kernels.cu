@@ -299,13 +299,20 @@ __device__ __forceinline__ void lut_chunk(const HLut<R>* s_l, int cn, uint32_t k
         acc[i].y += val * src[i ^ XL].y;
       }
     } else {
+      R val[kAmpsH];
+      bool any = false;
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        val[i] = L.lut16[code0 ^ ((L.reg >> (4 * i)) & 0xFu)];
+        any |= val[i] != R(0);
+      }
+      if (!any) continue;   // no output of this octet couples to the group
       C_t<R> src[kAmpsH];
       load_octet<R>(psi, k0 ^ (L.x & ~7u), dim, src);
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
-        const R val = L.lut16[code0 ^ ((L.reg >> (4 * i)) & 0xFu)];
-        acc[i].x += val * src[i ^ XL].x;
-        acc[i].y += val * src[i ^ XL].y;
+        acc[i].x += val[i] * src[i ^ XL].x;
+        acc[i].y += val[i] * src[i ^ XL].y;
       }
     }
   }
