@@ -110,6 +110,20 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
+def slowest_rank(times, device="cpu"):
+    """Each rank's timings -> the maximum over ranks (all_reduce MAX)."""
+    import torch
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_throughput(steps: int, world: int, slowest_secs: float) -> float:
+    """Whole-job value of independent replicas: iterations of all ranks over
+    the slowest rank's time (weak scaling: work per rank is fixed)."""
+    return world * steps / slowest_secs
+
+
 def run_gpu(args, rank, world, device):
     import torch
     import paper_2607_15906_gb300 as gb
@@ -196,9 +210,7 @@ def run_gpu(args, rank, world, device):
     e2e_secs = timed(step_host, args.steps, 1)
 
     if world > 1:
-        t = torch.tensor([secs, e2e_secs], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs, e2e_secs = float(t[0]), float(t[1])
+        secs, e2e_secs = slowest_rank([secs, e2e_secs], device=dev)
     info = prob.info
     return dict(prob=prob, secs=secs, e2e_secs=e2e_secs, kern=kern, clocks=clocks, launches=launches,
                 h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]))
@@ -437,6 +449,8 @@ def main():
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the serving and complex128 sub-measurements")
+    ap.add_argument("--reference-sample-s", type=float, default=4.0,
+                    help="seconds of oracle work per reference-arm step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -454,7 +468,7 @@ def main():
         warm = max(args.warmup, 0)
         vals = []
         for i in range(warm + args.steps):
-            r = cpu_baseline_sample(target_s=4.0)
+            r = cpu_baseline_sample(target_s=args.reference_sample_s)
             if i >= warm:
                 vals.append(1.0 / r["value"])
         secs = float(np.mean(vals))
@@ -478,8 +492,8 @@ def main():
     peaks, how = _peaks()
     if rank == 0:
         secs = res["secs"]
-        value = world * args.steps / secs
-        e2e = world * args.steps / res["e2e_secs"]
+        value = replica_throughput(args.steps, world, secs)
+        e2e = replica_throughput(args.steps, world, res["e2e_secs"])
         roof = roofline(res, peaks, how)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
