@@ -99,9 +99,9 @@ __device__ __forceinline__ uint32_t enum_pair(const PairEnum& e, uint32_t idx, u
 // with sigma(k) = popc(k & z0) & 1, so that D(k) = lut16[code(k)] (the sign
 // is folded into the table) and code(k0 + i) = code(k0) ^ ((reg >> 4i) & 15).
 template <typename R>
-struct HLut {
-  uint32_t x, z0, v0, v1, v2;
-  uint32_t reg;
+struct __align__(16) HLut {
+  uint32_t x, z0, v0, v1;   // read as one 16-byte vector
+  uint32_t v2, reg;         // and one 8-byte vector
   uint32_t pad0, pad1;
   R lut16[16];
 };

@@ -35,6 +35,11 @@ constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor blo
 constexpr int kPairsPerThread = 32;  // pool gradients: pairs per thread per operator
 constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
 constexpr int kItemBlocksPerSm = 2;  // batched stages: blocks per item per SM
+// H psi: resident blocks per SM the register budget must allow (complex64:
+// 4, trading a small spill for occupancy, measured faster; complex128: 2)
+#ifndef GOCP_APPLY_MIN_BLOCKS_C64
+#define GOCP_APPLY_MIN_BLOCKS_C64 4
+#endif
 
 struct DeviceTables {
   DevTables t;
@@ -285,14 +290,15 @@ __device__ __forceinline__ void lut_chunk(const HLut<R>* s_l, int cn, uint32_t k
   if (k0 >= dim) return;   // a thread past the end of a short state reads nothing
   for (int g = 0; g < cn; ++g) {
     const HLut<R>& L = s_l[g];
+    const uint32_t lx = L.x, reg = L.reg;
     const uint32_t code0 = (uint32_t)(__popc(k0 & L.v0) & 1) | ((uint32_t)(__popc(k0 & L.v1) & 1) << 1) |
                            ((uint32_t)(__popc(k0 & L.v2) & 1) << 2) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
-    if (L.reg == 0u) {
+    if (reg == 0u) {
       // the code does not vary over the octet: one value for all eight
       const R val = L.lut16[code0];
       if (val == R(0)) continue;
       C_t<R> src[kAmpsH];
-      load_octet<R>(psi, k0 ^ (L.x & ~7u), dim, src);
+      load_octet<R>(psi, k0 ^ (lx & ~7u), dim, src);
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
         acc[i].x += val * src[i ^ XL].x;
@@ -303,12 +309,12 @@ __device__ __forceinline__ void lut_chunk(const HLut<R>* s_l, int cn, uint32_t k
       bool any = false;
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
-        val[i] = L.lut16[code0 ^ ((L.reg >> (4 * i)) & 0xFu)];
+        val[i] = L.lut16[code0 ^ ((reg >> (4 * i)) & 0xFu)];
         any |= val[i] != R(0);
       }
       if (!any) continue;   // no output of this octet couples to the group
       C_t<R> src[kAmpsH];
-      load_octet<R>(psi, k0 ^ (L.x & ~7u), dim, src);
+      load_octet<R>(psi, k0 ^ (lx & ~7u), dim, src);
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
         acc[i].x += val[i] * src[i ^ XL].x;
@@ -392,7 +398,13 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
     for (int c = 0; c < tb.n_lchunks; ++c) {
       const int g0 = tb.lchunk[c], cn = tb.lchunk[c + 1] - g0;
       __syncthreads();
-      for (int g = threadIdx.x; g < cn; g += kThreads) s_l[g] = hl[g0 + g];
+      {
+        // 16-byte vector copy of the chunk's descriptors (no bank conflicts)
+        const uint4* src4 = reinterpret_cast<const uint4*>(hl + g0);
+        uint4* dst4 = reinterpret_cast<uint4*>(s_l);
+        const int words = cn * (int)(sizeof(HLut<R>) / sizeof(uint4));
+        for (int w = threadIdx.x; w < words; w += kThreads) dst4[w] = src4[w];
+      }
       __syncthreads();
 #define GOCP_LUT_CALL(XLV) lut_chunk<R, XLV>(s_l, cn, k0, psi, dim, acc)
       GOCP_XL_SWITCH(tb.lchunk_xl[c], GOCP_LUT_CALL)
@@ -450,7 +462,7 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? GOCP_APPLY_MIN_BLOCKS_C64 : 2)
 k_apply_h(DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, double identity,
           double* partials, unsigned int* counter, double* scal) {
   apply_body<R>(tb, psi, out, identity, partials, counter, scal, blockIdx.x, gridDim.x);
