@@ -145,6 +145,10 @@ struct DevTables {
   const int32_t* lchunk = nullptr;
   const uint8_t* lchunk_xl = nullptr;
   const uint8_t* chunk_xl = nullptr;
+  // per term-list group: the real terms are sorted by z & 7 and gbk packs the
+  // eight bucket sizes (byte m = terms with z & 7 == m); ~0 when the group
+  // has imaginary terms or a bucket above 255 (then it is summed term by term)
+  const uint64_t* gbk = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;

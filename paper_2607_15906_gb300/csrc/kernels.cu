@@ -327,13 +327,45 @@ __device__ __forceinline__ void lut_chunk(const HLut<R>* s_l, int cn, uint32_t k
 // Term-list groups of one staged chunk, all with x & 7 == XL.
 template <typename R, int XL>
 __device__ __forceinline__ void term_chunk(const uint32_t* s_x, const int32_t* s_off,
-                                           const int32_t* s_mid, int ng, const uint32_t* zs,
-                                           const R* ws, uint32_t k0, const C_t<R>* __restrict__ psi,
-                                           uint64_t dim, C_t<R> (&acc)[kAmpsH]) {
+                                           const int32_t* s_mid, const uint64_t* s_bk, int ng,
+                                           const uint32_t* zs, const R* ws, uint32_t k0,
+                                           const C_t<R>* __restrict__ psi, uint64_t dim,
+                                           C_t<R> (&acc)[kAmpsH]) {
   if (k0 >= dim) return;
   for (int g = 0; g < ng; ++g) {
     const uint32_t x = s_x[g];
     const int tbeg = s_off[g], tmid = s_mid[g], tend = s_off[g + 1];
+    const uint64_t bk = s_bk[g];
+    if (bk != ~0ull) {
+      // real weights, bucket m holding the terms with z & 7 == m: sum each
+      // bucket with the signs of k0, then D(k0 + i) = sum_m B_m (-1)^popc(i & m),
+      // an 8-point Walsh-Hadamard transform
+      R b[kAmpsH];
+      int t = tbeg;
+#pragma unroll
+      for (int m = 0; m < kAmpsH; ++m) {
+        b[m] = R(0);
+        const int cnt = (int)((bk >> (8 * m)) & 0xFFu);
+        for (int c = 0; c < cnt; ++c, ++t) b[m] += (__popc(k0 & zs[t]) & 1) ? -ws[t] : ws[t];
+      }
+#pragma unroll
+      for (int hb = 1; hb < kAmpsH; hb <<= 1)
+#pragma unroll
+        for (int a = 0; a < kAmpsH; ++a)
+          if (!(a & hb)) {
+            const R u = b[a], v = b[a | hb];
+            b[a] = u + v;
+            b[a | hb] = u - v;
+          }
+      C_t<R> src[kAmpsH];
+      load_octet<R>(psi, k0 ^ (x & ~7u), dim, src);
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        acc[i].x += b[i] * src[i ^ XL].x;
+        acc[i].y += b[i] * src[i ^ XL].y;
+      }
+      continue;
+    }
     R gr[kAmpsH], gi[kAmpsH], cr[kAmpsH], ci[kAmpsH];
 #pragma unroll
     for (int i = 0; i < kAmpsH; ++i) gr[i] = gi[i] = cr[i] = ci[i] = R(0);
@@ -378,6 +410,7 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
   __shared__ uint32_t s_x[kChunkGroups];
   __shared__ int32_t s_off[kChunkGroups + 1];
   __shared__ int32_t s_mid[kChunkGroups];
+  __shared__ uint64_t s_bk[kChunkGroups];
   __shared__ uint32_t s_z[kChunkTerms];
   __shared__ R s_w[kChunkTerms];
   __shared__ double tot[2];
@@ -420,6 +453,7 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
         s_x[g - g0] = tb.gx[g];
         s_off[g - g0] = tb.goff[g] - t0;
         s_mid[g - g0] = tb.gmid[g] - t0;
+        s_bk[g - g0] = tb.gbk[g];
       }
       if (threadIdx.x == 0) s_off[g1 - g0] = t1 - t0;
       if (staged)
@@ -430,7 +464,7 @@ __device__ void apply_body(const DevTables& tb, const C_t<R>* __restrict__ psi,
       __syncthreads();
       const uint32_t* zs = staged ? s_z : tb.tz + t0;
       const R* ws = staged ? s_w : tw + t0;
-#define GOCP_TERM_CALL(XLV) term_chunk<R, XLV>(s_x, s_off, s_mid, g1 - g0, zs, ws, k0, psi, dim, acc)
+#define GOCP_TERM_CALL(XLV) term_chunk<R, XLV>(s_x, s_off, s_mid, s_bk, g1 - g0, zs, ws, k0, psi, dim, acc)
       GOCP_XL_SWITCH(tb.chunk_xl[c], GOCP_TERM_CALL)
 #undef GOCP_TERM_CALL
     }
@@ -1210,7 +1244,31 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   std::vector<uint32_t> gx, tz;
   std::vector<int32_t> goff, gmid;
   std::vector<R> tw;
-  for (const TermGroup& tg : tgs) {
+  std::vector<uint64_t> gbk;
+  for (TermGroup& tg : tgs) {
+    uint64_t bk = ~0ull;
+    if (tg.zi.empty()) {
+      std::vector<size_t> idx(tg.zr.size());
+      for (size_t q = 0; q < idx.size(); ++q) idx[q] = q;
+      std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return (tg.zr[a] & 7u) < (tg.zr[b] & 7u); });
+      std::vector<uint32_t> zs2;
+      std::vector<R> ws2;
+      int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (size_t q : idx) {
+        zs2.push_back(tg.zr[q]);
+        ws2.push_back(tg.wr[q]);
+        ++cnt[tg.zr[q] & 7u];
+      }
+      bool fits = true;
+      for (int m = 0; m < 8; ++m) fits = fits && cnt[m] <= 255;
+      if (fits) {
+        tg.zr.swap(zs2);
+        tg.wr.swap(ws2);
+        bk = 0;
+        for (int m = 0; m < 8; ++m) bk |= (uint64_t)cnt[m] << (8 * m);
+      }
+    }
+    gbk.push_back(bk);
     gx.push_back(tg.x);
     goff.push_back((int32_t)tz.size());
     tz.insert(tz.end(), tg.zr.begin(), tg.zr.end());
@@ -1241,6 +1299,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   uint32_t *dgx, *dtz, *ddz;
   int32_t *dgoff, *dgmid, *dchunk, *dlchunk;
   uint8_t *dchunk_xl, *dlchunk_xl;
+  uint64_t* dgbk;
   R *dtw, *ddw;
   HLut<R>* dhl;
   if ((rc = upload(d, &dgx, gx, bytes)) || (rc = upload(d, &dgoff, goff, bytes)) ||
@@ -1248,8 +1307,10 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
       (rc = upload(d, &dchunk_xl, chunk_xl, bytes)) || (rc = upload(d, &dtz, tz, bytes)) ||
       (rc = upload(d, &dtw, tw, bytes)) || (rc = upload(d, &ddz, dz, bytes)) ||
       (rc = upload(d, &ddw, dw, bytes)) || (rc = upload(d, &dhl, hl, bytes)) ||
-      (rc = upload(d, &dlchunk, lchunk, bytes)) || (rc = upload(d, &dlchunk_xl, lchunk_xl, bytes)))
+      (rc = upload(d, &dlchunk, lchunk, bytes)) || (rc = upload(d, &dlchunk_xl, lchunk_xl, bytes)) ||
+      (rc = upload(d, &dgbk, gbk, bytes)))
     return rc;
+  d.t.gbk = dgbk;
   d.t.n = p.n_qubits;
   d.t.G = G;
   d.t.T = (int64_t)tz.size();

@@ -270,3 +270,34 @@ def test_full_size_24q_sparse_prepare_energy_gradients():
         ai, av = sv.apply_terms_sparse(tabs[k], si, svals)
         g_ref = 2 * sv.sparse_dot(hi, hv, ai, av).real / nn
         assert abs(g[k] - g_ref) <= 2e-6, (k, g[k], g_ref)
+
+
+def test_larger_n_26q_c64():
+    """26 qubits (13 orbitals, 12 electrons, integrals < 1e-3 dropped): a
+    512 MiB complex64 state.  Sampled rows of H psi for a random state, and a
+    sparse prepared state's energy, against the oracle."""
+    ints = molecular_integrals(13, seed=0, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw", 1e-3, 0.0)
+    p = gb.Problem.build(ints, 12, precision="c64", int_drop=1e-3, device=0, colour=False)
+    assert p.n_qubits == 26 and p.info["n_terms"] == len(h)
+    psi = random_state(26, seed=26)
+    d = _to_dev(p, psi)
+    del psi
+    psi_in = _host(d)
+    hd = torch.empty_like(d)
+    p.energy(d, hd)
+    rows = np.concatenate([np.random.default_rng(1).integers(0, 1 << 26, size=24), [0, (1 << 26) - 1]])
+    ref = sv.apply_terms_at(h, psi_in, rows)
+    got = _host(hd)[rows]
+    assert np.max(np.abs(got - ref)) <= TOL["c64"]["state"] * np.max(np.abs(ref)) * 5
+    del d, hd, psi_in
+    torch.cuda.empty_cache()
+    tabs = opool.pool_tables(26, 12, "jw")
+    ops, th = draw_ansatz(len(tabs), 4, seed=3, theta_sigma=0.3)
+    ws = p.workspace()
+    p.prepare_state(ops, th, ws[0])
+    e, nrm = p.energy(ws[0], ws[1])
+    si, svals = sv.prepare_state_sparse(p.info["ref_index"], tabs, ops, th)
+    hi, hv = sv.apply_terms_sparse(h, si, svals)
+    nn = sv.sparse_dot(si, svals, si, svals).real
+    assert abs(e - sv.sparse_dot(si, svals, hi, hv).real / nn) <= 1e-6
