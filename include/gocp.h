@@ -230,9 +230,10 @@ int gocp_adapt_step(const gocp_problem* p, const int32_t* ops, const double* the
 int gocp_energy_static(const gocp_problem* p, const void* psi, void* hpsi, double* out, int mem,
                        void* stream);
 
-/* Device-side argument errors flagged since the last call (bit 0: op index
- * out of range in a GOCP_MEM_DEVICE ansatz), and clear them.  Synchronises
- * `stream`. */
+/* Device-side errors flagged since the last call, and clear them.  Bit 0: an
+ * op index out of range in a GOCP_MEM_DEVICE ansatz.  Bit 1: a shared-memory
+ * staging wait of the tiled H psi kernel gave up after 2 s (the H psi and
+ * energy of that call are then undefined).  Synchronises `stream`. */
 int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
 
 /* ---------------------------------------------------------------- serving */

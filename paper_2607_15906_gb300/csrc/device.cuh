@@ -106,6 +106,60 @@ struct __align__(16) HLut {
   R lut16[16];
 };
 
+// H psi by shared-memory tiles (apply_tiled.cu).  A tile is 2^LB amplitudes
+// (64 KiB: LB = 13 for complex64, 12 for complex128); the groups are cut into
+// pieces by their high mask bits x >> LB, so that every group of a piece
+// reads the same source tile.  A piece is a contiguous blob, copied to shared
+// memory in one bulk copy beside its source tile:
+//   TiledHead | HLut<R>[n_lut] | TiledGroup[n_tg] | z[] | w[]
+// with the LUT groups and the term-list groups each sorted by (x & 7, x) and
+// cut into runs of equal x & 7.  The pieces of
+// one high pattern follow each other; the pieces with x >> LB = 0 come last
+// (there is always one), so that the own tile is staged for the diagonal.
+#ifndef GOCP_TILED_LB_C64
+#define GOCP_TILED_LB_C64 13
+#endif
+template <typename R> struct TiledBits;
+template <> struct TiledBits<float> { static constexpr int LB = GOCP_TILED_LB_C64; };
+template <> struct TiledBits<double> { static constexpr int LB = 12; };
+constexpr uint32_t kTiledBlobBytes = 12288;   // largest piece blob
+
+struct TiledHead {
+  uint32_t n_runs, n_lut;
+  uint32_t z_off, w_off;        // byte offsets of the term arrays in the blob
+  // the non-empty runs of equal x & 7: begin (bits 0..11) and end (12..23)
+  // in their list, x & 7 (24..26), list (bit 27: 0 LUT groups, 1 term lists)
+  uint32_t run[16];
+};
+static_assert(sizeof(TiledHead) == 80, "TiledHead is 80 bytes");
+
+struct __align__(16) TiledGroup {
+  uint32_t x;
+  uint32_t tb, tm, te;          // [tb, tm) real, [tm, te) imaginary terms
+  uint64_t bk;                  // Walsh bucket sizes (see DevTables::gbk)
+  uint32_t xa;                  // tiled_swz<R>((x >> 3) & octet mask)
+  uint32_t pad;
+};
+static_assert(sizeof(TiledGroup) == 32, "TiledGroup is 32 bytes");
+
+// Byte offset of octet o in a staged tile.  The tile is rows of 128 bytes
+// whose 16-byte chunks sit at chunk ^ (row & 7) (the 128-byte swizzle of the
+// tensor copy); chunk q of the octet (amplitudes 2q, 2q+1 for complex64,
+// amplitude q for complex128) is at tiled_swz(o) ^ (q << 4).  The map is
+// linear over XOR, tiled_swz(o ^ c) = tiled_swz(o) ^ tiled_swz(c), so the
+// kernel adds a group's source offset c with one XOR of a value the host
+// stores with the group (HLut::pad0, TiledGroup::xa).
+template <typename R>
+__host__ __device__ __forceinline__ uint32_t tiled_swz(uint32_t o) {
+  return sizeof(R) == 4 ? ((o >> 1) << 7) | ((((o & 1u) << 2) ^ ((o >> 1) & 7u)) << 4)
+                        : (o << 7) | ((o & 7u) << 4);
+}
+
+// One piece: x >> LB of its groups, byte offset and size of its blob.
+struct __align__(16) TiledPiece {
+  uint32_t xhi, off, bytes, pad;
+};
+
 // Device copies of the tables of one problem.
 //
 // Hamiltonian: the identity term is a scalar; the diagonal group (x = 0) is
@@ -149,6 +203,10 @@ struct DevTables {
   // eight bucket sizes (byte m = terms with z & 7 == m); ~0 when the group
   // has imaginary terms or a bucket above 255 (then it is summed term by term)
   const uint64_t* gbk = nullptr;
+  // the tiled form of the off-diagonal groups (n_pieces = 0: none)
+  int n_pieces = 0;
+  const uint8_t* tblob = nullptr;
+  const TiledPiece* tpiece = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;
@@ -169,5 +227,114 @@ struct DevTables {
   const PairEnum* penum = nullptr;
   uint32_t penum_max = 0;   // largest touched-pair count of any generator
 };
+
+
+// ------------------------------------------------------------ shared device helpers
+
+// H psi octets: a thread owns kAmpsH = 8 adjacent amplitudes k0 + i (k0 a
+// multiple of 8).
+constexpr int kAmpsH = 8;
+// Walsh sign patterns: byte m holds bit i = popc(i & m) & 1 for i, m < 8
+constexpr uint64_t kWalsh8 = 0x963C5AF066CCAA00ull;
+
+// Sign bits (bit i = amplitude k0 + i) of (-1)^popc((k0 + i) & z).
+__device__ __forceinline__ uint32_t octet_signs(uint32_t k0, uint32_t z) {
+  const uint32_t pat = (uint32_t)(kWalsh8 >> (8 * (z & 7u))) & 0xFFu;
+  return pat ^ ((__popc(k0 & z) & 1u) * 0xFFu);
+}
+
+// d[i] += sum_{t in [tb, te)} w_t (-1)^popc((k0+i) & z_t); compensated in
+// FP32 when asked (comp carries the lost low part: true sum d - comp).
+template <typename R>
+__device__ __forceinline__ void sum_terms8(const uint32_t* zs, const R* ws, int tb, int te,
+                                           uint32_t k0, R (&d)[kAmpsH], R (&comp)[kAmpsH],
+                                           bool compensate) {
+  if (sizeof(R) == 4 && compensate) {
+    for (int t = tb; t < te; ++t) {
+      const uint32_t sg = octet_signs(k0, zs[t]);
+      const R w = ws[t];
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        R y = (((sg >> i) & 1u) ? -w : w) - comp[i];
+        R s = d[i] + y;
+        comp[i] = (s - d[i]) - y;
+        d[i] = s;
+      }
+    }
+  } else {
+    for (int t = tb; t < te; ++t) {
+      const uint32_t sg = octet_signs(k0, zs[t]);
+      const R w = ws[t];
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) d[i] += ((sg >> i) & 1u) ? -w : w;
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Adds v[0..NV) over the nblocks blocks (NTHREADS threads each) of one work
+// item into out[0..NV).
+// partials: NV doubles per block; counter: one per item, zero on entry and
+// reset on exit.  Returns true in the last block, where tot[0..NV) (shared)
+// then holds the totals for every thread.
+template <int NV, int NTHREADS>
+__device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
+                               int nblocks, int bid, double* out, double* tot) {
+  __shared__ double red[NV][NTHREADS / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) red[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < NTHREADS / 32; ++w) s += red[threadIdx.x][w];
+    partials[(size_t)bid * NV + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblocks - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += NTHREADS) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[(size_t)b * NV + i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = warp_sum(acc[i]);
+    if (lane == 0) red[i][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < NTHREADS / 32; ++w) s += red[threadIdx.x][w];
+    out[threadIdx.x] = s;
+    tot[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+// H psi (+ the energy epilogue when partials is set) by the tiled kernel;
+// t.n_pieces must be > 0.  Defined in apply_tiled.cu.
+int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
+                  double identity, double* partials, unsigned int* counter, double* scal,
+                  int32_t* err, cudaStream_t st);
 
 }  // namespace gocp

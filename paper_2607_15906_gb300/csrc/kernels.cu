@@ -62,61 +62,11 @@ struct DeviceTables {
 
 // ------------------------------------------------------------ reductions
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Adds v[0..NV) over the nblocks blocks of one work item into out[0..NV).
-// partials: NV doubles per block; counter: one per item, zero on entry and
-// reset on exit.  Returns true in the last block, where tot[0..NV) (shared)
-// then holds the totals for every thread.
+// Adds v[0..NV) over the nblocks blocks of one work item (see block_grid_sum).
 template <int NV>
 __device__ bool grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
                          int nblocks, int bid, double* out, double* tot) {
-  __shared__ double red[NV][kWarps];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double s = warp_sum(v[i]);
-    if (lane == 0) red[i][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
-    partials[(size_t)bid * NV + threadIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(nblocks - 1);
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  double acc[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += kThreads) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] += ((volatile double*)partials)[(size_t)b * NV + i];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double s = warp_sum(acc[i]);
-    if (lane == 0) red[i][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int w = 0; w < kWarps; ++w) s += red[threadIdx.x][w];
-    out[threadIdx.x] = s;
-    tot[threadIdx.x] = s;
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-  __syncthreads();
-  return true;
+  return block_grid_sum<NV, kThreads>(v, partials, counter, nblocks, bid, out, tot);
 }
 
 // ------------------------------------------------------------ setup
@@ -220,17 +170,8 @@ __global__ void k_select(const double* g, int m, double tie_rel, int32_t* out) {
 // read with vector loads, output i taking source element i ^ (x & 7).
 // Groups are sorted by x & 7 so that this permutation is a compile-time
 // register renaming inside each chunk.
-constexpr int kAmpsH = 8;
 constexpr int kTileH = kThreads * kAmpsH;
 constexpr int kLutChunkH = 64;       // LUT groups staged per chunk
-// Walsh sign patterns: byte m holds bit i = popc(i & m) & 1 for i, m < 8
-constexpr uint64_t kWalsh8 = 0x963C5AF066CCAA00ull;
-
-// Sign bits (bit i = amplitude k0 + i) of (-1)^popc((k0 + i) & z).
-__device__ __forceinline__ uint32_t octet_signs(uint32_t k0, uint32_t z) {
-  const uint32_t pat = (uint32_t)(kWalsh8 >> (8 * (z & 7u))) & 0xFFu;
-  return pat ^ ((__popc(k0 & z) & 1u) * 0xFFu);
-}
 
 template <typename R>
 __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t base, uint64_t dim,
@@ -251,34 +192,6 @@ __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint3
   } else {
 #pragma unroll
     for (int q = 0; q < kAmpsH; ++q) v[q] = (base + q < dim) ? psi[base + q] : cmake<R>(0, 0);
-  }
-}
-
-// d[i] += sum_{t in [tb, te)} w_t (-1)^popc((k0+i) & z_t); compensated in
-// FP32 when asked (comp carries the lost low part: true sum d - comp).
-template <typename R>
-__device__ __forceinline__ void sum_terms8(const uint32_t* zs, const R* ws, int tb, int te,
-                                           uint32_t k0, R (&d)[kAmpsH], R (&comp)[kAmpsH],
-                                           bool compensate) {
-  if (sizeof(R) == 4 && compensate) {
-    for (int t = tb; t < te; ++t) {
-      const uint32_t sg = octet_signs(k0, zs[t]);
-      const R w = ws[t];
-#pragma unroll
-      for (int i = 0; i < kAmpsH; ++i) {
-        R y = (((sg >> i) & 1u) ? -w : w) - comp[i];
-        R s = d[i] + y;
-        comp[i] = (s - d[i]) - y;
-        d[i] = s;
-      }
-    }
-  } else {
-    for (int t = tb; t < te; ++t) {
-      const uint32_t sg = octet_signs(k0, zs[t]);
-      const R w = ws[t];
-#pragma unroll
-      for (int i = 0; i < kAmpsH; ++i) d[i] += ((sg >> i) & 1u) ? -w : w;
-    }
   }
 }
 
@@ -1176,6 +1089,126 @@ bool make_hlut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<dou
   return true;
 }
 
+// Cuts the off-diagonal groups into the pieces of the tiled H psi kernel
+// (see TiledHead).  hl and the term-list groups come sorted by (x & 7, x),
+// an order each piece keeps.  Leaves t.n_pieces = 0 (the untiled kernel
+// serves the problem) when n is below the tile size or a single group does
+// not fit one blob.
+template <typename R>
+int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_t>& gx,
+                const std::vector<int32_t>& goff, const std::vector<int32_t>& gmid,
+                const std::vector<uint64_t>& gbk, const std::vector<uint32_t>& tz,
+                const std::vector<R>& tw, DeviceTables& d, size_t& bytes) {
+  constexpr int LB = TiledBits<R>::LB;
+  constexpr uint32_t octets = 1u << (LB - 3);
+  static_assert(kTiledBlobBytes / sizeof(TiledGroup) < 4096, "run bounds of a piece fit 12 bits");
+  d.t.n_pieces = 0;
+  if (n < LB) return GOCP_OK;
+  auto a16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
+  auto blob_size = [&](size_t nl, size_t ng, size_t nt) {
+    return sizeof(TiledHead) + nl * sizeof(HLut<R>) + ng * sizeof(TiledGroup) + a16(nt * 4) +
+           a16(nt * sizeof(R));
+  };
+  // segments by x >> LB: x_hi != 0 ascending, then x_hi = 0
+  std::vector<uint32_t> his;
+  for (const HLut<R>& L : hl) his.push_back(L.x >> LB);
+  for (uint32_t x : gx) his.push_back(x >> LB);
+  his.push_back(0u);
+  std::sort(his.begin(), his.end());
+  his.erase(std::unique(his.begin(), his.end()), his.end());
+  std::rotate(his.begin(), his.begin() + 1, his.end());   // 0 (the smallest) last
+  std::vector<uint8_t> blob;
+  std::vector<TiledPiece> pieces;
+  for (uint32_t hi : his) {
+    std::vector<int> ls, ts;
+    for (int g = 0; g < (int)hl.size(); ++g)
+      if ((hl[g].x >> LB) == hi) ls.push_back(g);
+    for (int g = 0; g < (int)gx.size(); ++g)
+      if ((gx[g] >> LB) == hi) ts.push_back(g);
+    size_t li = 0, ti = 0;
+    do {
+      std::vector<int> pl, pt;
+      size_t nt = 0;
+      while (li < ls.size() && blob_size(pl.size() + 1, 0, 0) <= kTiledBlobBytes) pl.push_back(ls[li++]);
+      while (ti < ts.size()) {
+        const int g = ts[ti];
+        const size_t add = (size_t)(goff[g + 1] - goff[g]);
+        if (blob_size(pl.size(), pt.size() + 1, nt + add) > kTiledBlobBytes) break;
+        pt.push_back(g);
+        nt += add;
+        ++ti;
+      }
+      if (pl.empty() && pt.empty() && (li < ls.size() || ti < ts.size())) return GOCP_OK;
+      TiledHead h;
+      std::memset(&h, 0, sizeof(h));
+      h.n_lut = (uint32_t)pl.size();
+      const size_t z_off = sizeof(TiledHead) + pl.size() * sizeof(HLut<R>) + pt.size() * sizeof(TiledGroup);
+      h.z_off = (uint32_t)z_off;
+      h.w_off = (uint32_t)(z_off + a16(nt * 4));
+      for (int kind = 0; kind < 2; ++kind) {
+        const int cnt = kind == 0 ? (int)pl.size() : (int)pt.size();
+        auto xl_of = [&](int q) { return (int)((kind == 0 ? hl[pl[q]].x : gx[pt[q]]) & 7u); };
+        for (int q = 0; q < cnt;) {
+          int e = q;
+          while (e < cnt && xl_of(e) == xl_of(q)) ++e;
+          h.run[h.n_runs++] = (uint32_t)q | ((uint32_t)e << 12) | ((uint32_t)xl_of(q) << 24) | ((uint32_t)kind << 27);
+          q = e;
+        }
+      }
+      const size_t total = blob_size(pl.size(), pt.size(), nt);
+      const size_t off = blob.size();
+      blob.resize(off + total, 0);
+      uint8_t* b = blob.data() + off;
+      std::memcpy(b, &h, sizeof(h));
+      size_t w = sizeof(TiledHead);
+      for (int g : pl) {
+        HLut<R> L = hl[g];
+        L.pad0 = tiled_swz<R>((L.x >> 3) & (octets - 1));
+        std::memcpy(b + w, &L, sizeof(HLut<R>));
+        w += sizeof(HLut<R>);
+      }
+      uint32_t tcur = 0;
+      std::vector<uint32_t> zz;
+      std::vector<R> ww;
+      for (int g : pt) {
+        TiledGroup tg;
+        std::memset(&tg, 0, sizeof(tg));
+        tg.x = gx[g];
+        tg.tb = tcur;
+        tg.tm = tcur + (uint32_t)(gmid[g] - goff[g]);
+        tg.te = tcur + (uint32_t)(goff[g + 1] - goff[g]);
+        tg.bk = gbk[g];
+        tg.xa = tiled_swz<R>((gx[g] >> 3) & (octets - 1));
+        for (int32_t t = goff[g]; t < goff[g + 1]; ++t) {
+          zz.push_back(tz[t]);
+          ww.push_back(tw[t]);
+        }
+        tcur = tg.te;
+        std::memcpy(b + w, &tg, sizeof(tg));
+        w += sizeof(tg);
+      }
+      if (!zz.empty()) {
+        std::memcpy(b + h.z_off, zz.data(), zz.size() * 4);
+        std::memcpy(b + h.w_off, ww.data(), ww.size() * sizeof(R));
+      }
+      TiledPiece pc;
+      pc.xhi = hi;
+      pc.off = (uint32_t)off;
+      pc.bytes = (uint32_t)total;
+      pc.pad = 0;
+      pieces.push_back(pc);
+    } while (li < ls.size() || ti < ts.size());
+  }
+  uint8_t* dblob;
+  TiledPiece* dpiece;
+  int rc;
+  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes))) return rc;
+  d.t.tblob = dblob;
+  d.t.tpiece = dpiece;
+  d.t.n_pieces = (int)pieces.size();
+  return GOCP_OK;
+}
+
 template <typename R>
 int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   const PauliTerms& H = p.H;
@@ -1331,6 +1364,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.n_lchunks = (int)lchunk.size() - 1;
   d.t.lchunk = dlchunk;
   d.t.lchunk_xl = dlchunk_xl;
+  if ((rc = build_tiled<R>(p.n_qubits, hl, gx, goff, gmid, gbk, tz, tw, d, bytes))) return rc;
   // ---- pool
   const Pool& P = p.pool;
   const int M = P.size();
@@ -1543,6 +1577,11 @@ int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cud
 template <typename R>
 static int launch_apply(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st) {
   DeviceTables& d = *p.dev;
+  if (d.t.n_pieces > 0) {
+    ProfScope ps(GOCP_KERNEL_APPLY_H, st);
+    return tiled_apply_h(d.t, p.precision, d.sm_count, psi, hpsi, p.identity, energy ? d.scratch : nullptr,
+                         d.counters + kMaxChunks, d.scalars, d.err, st);
+  }
   const int grid = apply_grid(p.n_qubits);
   {
     ProfScope ps(GOCP_KERNEL_APPLY_H, st);
