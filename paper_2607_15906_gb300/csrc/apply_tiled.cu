@@ -14,6 +14,12 @@
 // The pieces with x >> LB = 0 come last, so that the own tile is staged when
 // the diagonal group and the energy terms are added.
 //
+// A pre-pass (k_octet_mask) marks the octets of psi that hold a nonzero
+// amplitude; each piece's copy brings the source tile's slice of that mask,
+// and a group skips a source octet that is entirely zero (its contribution is
+// exactly zero).  States confined to a particle-number sector, as the ADAPT
+// states are, leave most octets zero; a dense state skips nothing.
+//
 // Every wait on an mbarrier gives up after kWaitNs of %globaltimer: the block
 // then records bit 1 in the error flags, waits (bounded again) for its own
 // copies in flight, and leaves the tile loop; results are then undefined and
@@ -74,11 +80,22 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, int row, uint32_t bar) {
+// Rows [row, row + box) of the tensor map into shared memory; the lines are
+// marked to stay in L2 (evict_last policy), since every tile of the state is
+// read again by other pieces while the output streams past.
+__device__ __forceinline__ void tma_rows(uint32_t dst, const CUtensorMap* map, int row, uint32_t bar,
+                                         uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar), "l"(policy)
       : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -106,13 +123,22 @@ __device__ __forceinline__ void tile_octet(const uint8_t* tile, uint32_t off, C_
   }
 }
 
+// Whether source octet so of the staged tile holds a nonzero amplitude (mk:
+// the tile's slice of the nonzero-octet mask).  Within a warp so >> 5 is
+// uniform, so a zero 32-octet block skips a group for the whole warp; a
+// group's product with zero amplitudes is zero, so skipping changes nothing.
+__device__ __forceinline__ bool octet_live(const uint32_t* mk, uint32_t so) {
+  return (mk[so >> 5] >> (so & 31u)) & 1u;
+}
+
 // LUT groups of one x & 7 run; k0 = first global index of the thread's
-// output octet, ao = tiled_swz of its octet in the tile.
+// output octet, o its octet in the tile and ao = tiled_swz(o).
 template <typename R, int XL>
-__device__ __forceinline__ void tiled_lut(const HLut<R>* ls, int cn, uint32_t k0, uint32_t ao,
-                                          const uint8_t* tile, C_t<R> (&acc)[kAmpsH]) {
+__device__ __forceinline__ void tiled_lut(const HLut<R>* ls, int cn, uint32_t k0, uint32_t o, uint32_t ao,
+                                          const uint8_t* tile, const uint32_t* mk, C_t<R> (&acc)[kAmpsH]) {
   for (int g = 0; g < cn; ++g) {
     const HLut<R>& L = ls[g];
+    if (!octet_live(mk, o ^ L.pad1)) continue;
     const uint32_t os = ao ^ L.pad0, reg = L.reg;
     const uint32_t code0 = (uint32_t)(__popc(k0 & L.v0) & 1) | ((uint32_t)(__popc(k0 & L.v1) & 1) << 1) |
                            ((uint32_t)(__popc(k0 & L.v2) & 1) << 2) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
@@ -149,10 +175,11 @@ __device__ __forceinline__ void tiled_lut(const HLut<R>* ls, int cn, uint32_t k0
 // Term-list groups of one x & 7 run.
 template <typename R, int XL>
 __device__ __forceinline__ void tiled_terms(const TiledGroup* gs, int cn, const uint32_t* zs, const R* ws,
-                                            uint32_t k0, uint32_t ao, const uint8_t* tile,
-                                            C_t<R> (&acc)[kAmpsH]) {
+                                            uint32_t k0, uint32_t o, uint32_t ao, const uint8_t* tile,
+                                            const uint32_t* mk, C_t<R> (&acc)[kAmpsH]) {
   for (int g = 0; g < cn; ++g) {
     const TiledGroup& G = gs[g];
+    if (!octet_live(mk, o ^ G.pad)) continue;
     const uint32_t os = ao ^ G.xa;
     if (G.bk != ~0ull) {
       // bucket m: the terms with z & 7 == m, summed with the signs of k0;
@@ -199,10 +226,40 @@ __device__ __forceinline__ void tiled_terms(const TiledGroup* gs, int cn, const 
   }
 }
 
+// mask bit o = octet o of psi holds a nonzero amplitude (-0 counts as zero);
+// one ballot word per warp of 32 consecutive octets.
+template <typename R>
+__global__ void __launch_bounds__(256) k_octet_mask(const C_t<R>* __restrict__ psi, uint32_t n_octets,
+                                                    uint32_t* __restrict__ mask, unsigned int* tile_counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0u;   // for the H psi kernel that follows
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_octets; o += gridDim.x * blockDim.x) {
+    bool nz = false;
+    if (sizeof(R) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(psi) + 4u * o;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = p[q];
+        nz |= (f.x != 0.f) | (f.y != 0.f) | (f.z != 0.f) | (f.w != 0.f);
+      }
+    } else {
+      const double2* p = reinterpret_cast<const double2*>(psi) + 8u * o;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double2 f = p[q];
+        nz |= (f.x != 0.0) | (f.y != 0.0);
+      }
+    }
+    const uint32_t w = __ballot_sync(0xffffffffu, nz);
+    if ((threadIdx.x & 31u) == 0) mask[o >> 5] = w;
+  }
+}
+
 template <typename R>
 struct TiledArgs {
   const uint8_t* blob;
   const TiledPiece* piece;
+  const uint32_t* mask;   // nonzero-octet mask of the source state
+  unsigned int* tile_counter;   // next output tile to claim (zeroed by k_octet_mask)
   int n_pieces;
   int n;
   const uint32_t* dz;   // diagonal group: [0, nd_mid) real, [nd_mid, nd) imaginary
@@ -226,9 +283,17 @@ __host__ __device__ constexpr int tiled_threads() {
   return 1 << (TiledBits<R>::LB - 3);
 }
 
+// bytes of the nonzero-octet mask of one tile (one bit per octet)
+template <typename R>
+__host__ __device__ constexpr uint32_t tile_mask_bytes() {
+  return (1u << (TiledBits<R>::LB - 3)) / 8u;
+}
+
+constexpr int kTiledStages = 3;   // copies of up to two pieces in flight
+
 template <typename R>
 __host__ __device__ constexpr size_t tiled_smem() {
-  return 1024 + 2 * (size_t)tile_bytes<R>() + 2 * (size_t)kTiledBlobBytes;
+  return 1024 + kTiledStages * ((size_t)tile_bytes<R>() + (size_t)kTiledBlobBytes + (size_t)tile_mask_bytes<R>());
 }
 
 // resident blocks per SM the register budget must allow
@@ -244,65 +309,112 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
   constexpr uint32_t kTile = tile_bytes<R>();
   constexpr uint32_t kRows = kTile / 128u;
   constexpr uint32_t kBox = kRows < 256u ? kRows : 256u;
+  constexpr uint32_t kMask = tile_mask_bytes<R>();
+  static_assert(kMask % 16u == 0, "mask slices are whole 16-byte units");
+  constexpr int S = kTiledStages;
+  constexpr uint32_t kWarps = NT / 32;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S];
+  __shared__ volatile int s_abort;
   __shared__ double tot[2];
-  // stage st: tile at base + st * kTile, blob at base + 2 kTile + st * blob size
+  // stage st: tile at base + st kTile, blob at base + S kTile + st kBlob,
+  // mask slice at base + S (kTile + kBlob) + st kMask
   uint8_t* base = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-  const uint32_t base_s = smem_addr(base), bar_s = smem_addr(&bar[0]);
-  auto tile_s = [&](int st) { return base_s + (uint32_t)st * kTile; };
-  auto blob_s = [&](int st) { return base_s + 2u * kTile + (uint32_t)st * kTiledBlobBytes; };
-  auto bar_at = [&](int st) { return bar_s + 8u * (uint32_t)st; };
+  const uint32_t base_s = smem_addr(base), full_s = smem_addr(&bar_full[0]), empty_s = smem_addr(&bar_empty[0]);
+  constexpr uint32_t kBlobOff = S * kTile, kMaskOff = S * (kTile + kTiledBlobBytes);
 
-  // items = (tile, piece) pairs of this block; fewer than 2^32 (tiles <= 2^19)
+  // Items are (tile, piece) pairs.  Output tiles are claimed one at a time
+  // from a global counter when their first piece is issued (tiles differ in
+  // cost when zero octets are skipped), and the tile of each staged item is
+  // passed to the consumers in s_tile; kNoTile ends the sweep.
+  constexpr uint32_t kNoTile = 0xFFFFFFFFu;
   const uint32_t ntiles = 1u << (a.n - LB);
-  const uint32_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const uint32_t nitems = my_tiles * (uint32_t)a.n_pieces;
+  __shared__ uint32_t s_tile[S];
   // per-thread energy partials live in shared memory (touched once per tile)
   __shared__ double2 s_v[NT];
   s_v[threadIdx.x] = make_double2(0.0, 0.0);
 
   if (threadIdx.x == 0) {
-    mbar_init(bar_at(0), 1);
-    mbar_init(bar_at(1), 1);
+    for (int q = 0; q < S; ++q) {
+      mbar_init(full_s + 8u * q, 1);
+      mbar_init(empty_s + 8u * q, kWarps);
+    }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // thread 0: start the copies of item `it` into stage it & 1
-  auto issue = [&](uint32_t it) {
-    const int st = (int)(it & 1);
-    const uint32_t tile = blockIdx.x + (it / (uint32_t)a.n_pieces) * gridDim.x;
-    const TiledPiece pc = a.piece[it % (uint32_t)a.n_pieces];
-    const uint32_t src = tile ^ pc.xhi;
-    mbar_expect_tx(bar_at(st), kTile + pc.bytes);
+  // producer state, thread 0 only: items issued, piece and tile of the next
+  uint32_t next = 0, p_next = 0, t_next = 0;
+  bool done = false;
+  const uint64_t keep = policy_evict_last();
+  // thread 0: issue item `next` into stage next % S, whose previous item
+  // every warp has released.  The stage's tile slot is written before the
+  // barrier arrive (release), so a consumer that sees the phase complete
+  // (acquire) reads it.
+  auto issue_next = [&]() {
+    const uint32_t st = next % S;
+    const uint32_t fb = full_s + 8u * st;
+    if (p_next == 0) t_next = atomicAdd(a.tile_counter, 1u);
+    if (t_next >= ntiles) {
+      s_tile[st] = kNoTile;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+      done = true;
+      ++next;
+      return;
+    }
+    s_tile[st] = t_next;
+    const TiledPiece pc = a.piece[p_next];
+    const uint32_t src = t_next ^ pc.xhi;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(fb, kTile + pc.bytes + kMask);
 #pragma unroll
     for (uint32_t c = 0; c < kRows / kBox; ++c)
-      tma_rows(tile_s(st) + c * kBox * 128u, &tmap, (int)(src * kRows + c * kBox), bar_at(st));
-    if (pc.bytes) bulk_copy(blob_s(st), a.blob + pc.off, pc.bytes, bar_at(st));
+      tma_rows(base_s + st * kTile + c * kBox * 128u, &tmap, (int)(src * kRows + c * kBox), fb, keep);
+    if (pc.bytes) bulk_copy(base_s + kBlobOff + st * kTiledBlobBytes, a.blob + pc.off, pc.bytes, fb);
+    bulk_copy(base_s + kMaskOff + st * kMask, reinterpret_cast<const uint8_t*>(a.mask) + (size_t)src * kMask, kMask,
+              fb);
+    ++next;
+    if (++p_next == (uint32_t)a.n_pieces) p_next = 0;
   };
-  if (threadIdx.x == 0) {
-    if (nitems > 0) issue(0);
-    if (nitems > 1) issue(1);
-  }
+  // Item j (j >= S) may reuse its stage once every warp has released item
+  // j - S: phase (j / S - 1) of that stage's empty barrier.
+  if (threadIdx.x == 0)
+    while (!done && next < (uint32_t)S) issue_next();
 
   const R idr = (R)a.identity;
   const uint32_t o = threadIdx.x, ao = tiled_swz<R>(o);
   C_t<R> acc[kAmpsH];
 #pragma unroll
   for (int i = 0; i < kAmpsH; ++i) acc[i] = cmake<R>(0, 0);
-  uint32_t it = 0, tile = blockIdx.x;
+  uint32_t it = 0, tile = 0, st = 0, ph = 0;
   int pc = 0;
-  bool aborted = false;
-  for (; it < nitems; ++it) {
-    const int st = (int)(it & 1);
-    const uint32_t k0 = (tile << LB) + o * kAmpsH;
-    if (!mbar_wait(bar_at(st), (it >> 1) & 1u)) {
+  for (;; ++it) {
+    // every exit decision is warp-uniform, so that no lane leaves its warp
+    // waiting in __syncwarp
+    if (__shfl_sync(0xffffffffu, s_abort, 0)) break;
+    if (threadIdx.x == 0) {
+      // item it must be issued before anyone waits for it; later items go
+      // out as soon as their stage is released
+      bool ok = true;
+      while (ok && !done && next <= it) {
+        ok = mbar_wait(empty_s + 8u * (next % S), (next / S - 1u) & 1u);
+        if (ok) issue_next();
+      }
+      while (ok && !done && mbar_try(empty_s + 8u * (next % S), (next / S - 1u) & 1u)) issue_next();
+      if (!ok) s_abort = 1;
+    }
+    __syncwarp();
+    if (!__all_sync(0xffffffffu, mbar_wait(full_s + 8u * st, ph))) {
       s_abort = 1;
-    } else {
-      const uint8_t* tl = base + (uint32_t)st * kTile;
-      const uint8_t* bl = base + 2u * kTile + (uint32_t)st * kTiledBlobBytes;
+      break;
+    }
+    tile = s_tile[st];
+    if (tile == kNoTile) break;   // the same item, so the same answer, for every warp
+    {
+      const uint32_t k0 = (tile << LB) + o * kAmpsH;
+      const uint8_t* tl = base + st * kTile;
+      const uint8_t* bl = base + kBlobOff + st * kTiledBlobBytes;
+      const uint32_t* mk = reinterpret_cast<const uint32_t*>(base + kMaskOff + st * kMask);
       const TiledHead* hd = reinterpret_cast<const TiledHead*>(bl);
       const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(bl + sizeof(TiledHead));
       const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(bl + sizeof(TiledHead) + hd->n_lut * sizeof(HLut<R>));
@@ -314,8 +426,8 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
         const int g0 = (int)(rd & 0xFFFu), cn = (int)((rd >> 12) & 0xFFFu) - g0;
         switch (rd >> 24) {
 #define GOCP_CASE(XLV)                                                   \
-  case XLV: tiled_lut<R, XLV>(ls + g0, cn, k0, ao, tl, acc); break;      \
-  case 8 + XLV: tiled_terms<R, XLV>(gs + g0, cn, zs, ws, k0, ao, tl, acc); break;
+  case XLV: tiled_lut<R, XLV>(ls + g0, cn, k0, o, ao, tl, mk, acc); break;      \
+  case 8 + XLV: tiled_terms<R, XLV>(gs + g0, cn, zs, ws, k0, o, ao, tl, mk, acc); break;
           GOCP_CASE(0) GOCP_CASE(1) GOCP_CASE(2) GOCP_CASE(3)
           GOCP_CASE(4) GOCP_CASE(5) GOCP_CASE(6) GOCP_CASE(7)
 #undef GOCP_CASE
@@ -323,59 +435,67 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
         }
       }
       if (pc == a.n_pieces - 1) {
-        // the last piece has x >> LB = 0: tl is the own tile
-        R dr[kAmpsH], dc[kAmpsH], di[kAmpsH], dd[kAmpsH];
-#pragma unroll
-        for (int i = 0; i < kAmpsH; ++i) dr[i] = dc[i] = di[i] = dd[i] = R(0);
-        sum_terms8<R>(a.dz, a.dw, 0, a.nd_mid, k0, dr, dc, true);
-        sum_terms8<R>(a.dz, a.dw, a.nd_mid, a.nd, k0, di, dd, false);
-        C_t<R> own[kAmpsH];
-        tile_octet<R>(tl, ao, own);
+        // the last piece has x >> LB = 0: tl is the own tile.  A zero own
+        // octet adds nothing to the diagonal part or to the energy.
         C_t<R> res[kAmpsH];
-        double2 v = s_v[o];
+        if (!octet_live(mk, o)) {
 #pragma unroll
-        for (int i = 0; i < kAmpsH; ++i) {
-          const C_t<R> p = own[i];
-          const double pp = (double)p.x * p.x + (double)p.y * p.y;
-          v.x += pp;
-          v.y += (double)p.x * acc[i].x + (double)p.y * acc[i].y + ((double)dr[i] - (double)dc[i]) * pp;
-          const R d0 = dr[i] - dc[i] + idr;
-          res[i] = cmake<R>(acc[i].x + d0 * p.x - di[i] * p.y, acc[i].y + d0 * p.y + di[i] * p.x);
-          acc[i] = cmake<R>(0, 0);
+          for (int i = 0; i < kAmpsH; ++i) {
+            res[i] = acc[i];
+            acc[i] = cmake<R>(0, 0);
+          }
+        } else {
+          R dr[kAmpsH], dc[kAmpsH], di[kAmpsH], dd[kAmpsH];
+#pragma unroll
+          for (int i = 0; i < kAmpsH; ++i) dr[i] = dc[i] = di[i] = dd[i] = R(0);
+          sum_terms8<R>(a.dz, a.dw, 0, a.nd_mid, k0, dr, dc, true);
+          sum_terms8<R>(a.dz, a.dw, a.nd_mid, a.nd, k0, di, dd, false);
+          C_t<R> own[kAmpsH];
+          tile_octet<R>(tl, ao, own);
+          double2 v = s_v[o];
+#pragma unroll
+          for (int i = 0; i < kAmpsH; ++i) {
+            const C_t<R> p = own[i];
+            const double pp = (double)p.x * p.x + (double)p.y * p.y;
+            v.x += pp;
+            v.y += (double)p.x * acc[i].x + (double)p.y * acc[i].y + ((double)dr[i] - (double)dc[i]) * pp;
+            const R d0 = dr[i] - dc[i] + idr;
+            res[i] = cmake<R>(acc[i].x + d0 * p.x - di[i] * p.y, acc[i].y + d0 * p.y + di[i] * p.x);
+            acc[i] = cmake<R>(0, 0);
+          }
+          s_v[o] = v;
         }
-        s_v[o] = v;
         C_t<R>* dst = a.out + k0;
+        // streaming stores (evict-first), so that the output does not push
+        // the source state out of L2
         if (sizeof(R) == 4) {
           float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
           for (int q = 0; q < kAmpsH / 2; ++q)
-            d4[q] = make_float4((float)res[2 * q].x, (float)res[2 * q].y, (float)res[2 * q + 1].x,
-                                (float)res[2 * q + 1].y);
+            __stcs(d4 + q, make_float4((float)res[2 * q].x, (float)res[2 * q].y, (float)res[2 * q + 1].x,
+                                       (float)res[2 * q + 1].y));
         } else {
+          double2* d2 = reinterpret_cast<double2*>(dst);
 #pragma unroll
-          for (int q = 0; q < kAmpsH; ++q) dst[q] = res[q];
+          for (int q = 0; q < kAmpsH; ++q) __stcs(d2 + q, make_double2((double)res[q].x, (double)res[q].y));
         }
       }
     }
-    __syncthreads();   // stage st is free again
-    if (s_abort) {
-      aborted = true;
-      break;
+    __syncwarp();
+    if ((threadIdx.x & 31u) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty_s + 8u * st) : "memory");
+    if (++st == (uint32_t)S) {
+      st = 0;
+      ph ^= 1u;
     }
-    if (threadIdx.x == 0 && it + 2u < nitems) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(it + 2);
-    }
-    if (++pc == a.n_pieces) {
-      pc = 0;
-      tile += gridDim.x;
-    }
+    if (++pc == a.n_pieces) pc = 0;
   }
-  if (aborted && threadIdx.x == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort) {
     atomicOr(a.err, kErrStageTimeout);
     // let the copies this block started land before its shared memory goes
-    for (uint32_t j = it; j < nitems && j < it + 2u; ++j) mbar_wait(bar_at((int)(j & 1)), (j >> 1) & 1u);
+    for (uint32_t j = it; j < next; ++j) mbar_wait(full_s + 8u * (j % S), (j / S) & 1u);
   }
+  // (a normal exit consumed every issued item: nothing is in flight)
   const double v[2] = {s_v[threadIdx.x].x, s_v[threadIdx.x].y};
   if (a.partials &&
       block_grid_sum<2, NT>(v, a.partials, a.counter, gridDim.x, blockIdx.x, a.scal + 1, tot)) {
@@ -421,7 +541,8 @@ int smem_optin(int device) {
 
 template <typename R>
 int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, double identity,
-                 double* partials, unsigned int* counter, double* scal, int32_t* err, cudaStream_t st) {
+                 double* partials, unsigned int* counter, unsigned int* tile_counter, double* scal, int32_t* err,
+                 cudaStream_t st) {
   constexpr int LB = TiledBits<R>::LB;
   if (t.n_pieces <= 0 || t.n < LB) return fail(GOCP_EINVAL, "problem has no tiled H psi form");
   if ((reinterpret_cast<uintptr_t>(psi) & 15u) || (reinterpret_cast<uintptr_t>(hpsi) & 15u))
@@ -444,9 +565,14 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
                     const_cast<void*>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(GOCP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+  const uint32_t n_octets = 1u << (t.n - 3);
+  const int mgrid = (int)std::min<uint32_t>((n_octets + 255u) / 256u, (uint32_t)std::max(sm_count, 1) * 8u);
+  k_octet_mask<R><<<mgrid, 256, 0, st>>>(reinterpret_cast<const C_t<R>*>(psi), n_octets, t.octmask, tile_counter);
   TiledArgs<R> a;
   a.blob = t.tblob;
   a.piece = t.tpiece;
+  a.mask = t.octmask;
+  a.tile_counter = tile_counter;
   a.n_pieces = t.n_pieces;
   a.n = t.n;
   a.dz = t.dz;
@@ -463,18 +589,18 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
   const int per_sm = sizeof(R) == 4 ? GOCP_TILED_MINB_C64 : 1;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1) * per_sm);
   k_apply_h_tiled<R><<<grid, tiled_threads<R>(), tiled_smem<R>(), st>>>(map, a);
-  count_launches(1);
+  count_launches(2);
   return cuda_status(cudaGetLastError(), "k_apply_h_tiled");
 }
 
 }  // namespace
 
 int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
-                  double identity, double* partials, unsigned int* counter, double* scal, int32_t* err,
-                  cudaStream_t st) {
+                  double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,
+                  double* scal, int32_t* err, cudaStream_t st) {
   return precision == GOCP_C64
-             ? launch_tiled<float>(t, sm_count, psi, hpsi, identity, partials, counter, scal, err, st)
-             : launch_tiled<double>(t, sm_count, psi, hpsi, identity, partials, counter, scal, err, st);
+             ? launch_tiled<float>(t, sm_count, psi, hpsi, identity, partials, counter, tile_counter, scal, err, st)
+             : launch_tiled<double>(t, sm_count, psi, hpsi, identity, partials, counter, tile_counter, scal, err, st);
 }
 
 }  // namespace gocp

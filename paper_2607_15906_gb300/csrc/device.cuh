@@ -122,7 +122,7 @@ struct __align__(16) HLut {
 template <typename R> struct TiledBits;
 template <> struct TiledBits<float> { static constexpr int LB = GOCP_TILED_LB_C64; };
 template <> struct TiledBits<double> { static constexpr int LB = 12; };
-constexpr uint32_t kTiledBlobBytes = 12288;   // largest piece blob
+constexpr uint32_t kTiledBlobBytes = 4096;    // largest piece blob
 
 struct TiledHead {
   uint32_t n_runs, n_lut;
@@ -137,8 +137,8 @@ struct __align__(16) TiledGroup {
   uint32_t x;
   uint32_t tb, tm, te;          // [tb, tm) real, [tm, te) imaginary terms
   uint64_t bk;                  // Walsh bucket sizes (see DevTables::gbk)
-  uint32_t xa;                  // tiled_swz<R>((x >> 3) & octet mask)
-  uint32_t pad;
+  uint32_t xa;                  // tiled_swz<R>((x >> 3) & (octets - 1))
+  uint32_t pad;                 // (x >> 3) & (octets - 1)
 };
 static_assert(sizeof(TiledGroup) == 32, "TiledGroup is 32 bytes");
 
@@ -148,7 +148,8 @@ static_assert(sizeof(TiledGroup) == 32, "TiledGroup is 32 bytes");
 // amplitude q for complex128) is at tiled_swz(o) ^ (q << 4).  The map is
 // linear over XOR, tiled_swz(o ^ c) = tiled_swz(o) ^ tiled_swz(c), so the
 // kernel adds a group's source offset c with one XOR of a value the host
-// stores with the group (HLut::pad0, TiledGroup::xa).
+// stores with the group (HLut::pad0, TiledGroup::xa); c itself, which indexes
+// the nonzero-octet mask, is stored beside it (HLut::pad1, TiledGroup::pad).
 template <typename R>
 __host__ __device__ __forceinline__ uint32_t tiled_swz(uint32_t o) {
   return sizeof(R) == 4 ? ((o >> 1) << 7) | ((((o & 1u) << 2) ^ ((o >> 1) & 7u)) << 4)
@@ -203,10 +204,13 @@ struct DevTables {
   // eight bucket sizes (byte m = terms with z & 7 == m); ~0 when the group
   // has imaginary terms or a bucket above 255 (then it is summed term by term)
   const uint64_t* gbk = nullptr;
-  // the tiled form of the off-diagonal groups (n_pieces = 0: none)
+  // the tiled form of the off-diagonal groups (n_pieces = 0: none), and a
+  // scratch mask of 2^(n-3) bits, bit o set when octet o of the state being
+  // multiplied holds a nonzero amplitude
   int n_pieces = 0;
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
+  uint32_t* octmask = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;
@@ -334,7 +338,7 @@ __device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned
 // H psi (+ the energy epilogue when partials is set) by the tiled kernel;
 // t.n_pieces must be > 0.  Defined in apply_tiled.cu.
 int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
-                  double identity, double* partials, unsigned int* counter, double* scal,
-                  int32_t* err, cudaStream_t st);
+                  double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,
+                  double* scal, int32_t* err, cudaStream_t st);
 
 }  // namespace gocp

@@ -1164,6 +1164,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       for (int g : pl) {
         HLut<R> L = hl[g];
         L.pad0 = tiled_swz<R>((L.x >> 3) & (octets - 1));
+        L.pad1 = (L.x >> 3) & (octets - 1);
         std::memcpy(b + w, &L, sizeof(HLut<R>));
         w += sizeof(HLut<R>);
       }
@@ -1179,6 +1180,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
         tg.te = tcur + (uint32_t)(goff[g + 1] - goff[g]);
         tg.bk = gbk[g];
         tg.xa = tiled_swz<R>((gx[g] >> 3) & (octets - 1));
+        tg.pad = (gx[g] >> 3) & (octets - 1);
         for (int32_t t = goff[g]; t < goff[g + 1]; ++t) {
           zz.push_back(tz[t]);
           ww.push_back(tw[t]);
@@ -1201,8 +1203,12 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   }
   uint8_t* dblob;
   TiledPiece* dpiece;
+  uint32_t* dmask;
   int rc;
-  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes))) return rc;
+  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
+      (rc = dalloc(d, &dmask, (size_t)1 << (n - 8), bytes)))
+    return rc;
+  d.t.octmask = dmask;
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
   d.t.n_pieces = (int)pieces.size();
@@ -1580,7 +1586,7 @@ static int launch_apply(Problem& p, const void* psi, void* hpsi, bool energy, cu
   if (d.t.n_pieces > 0) {
     ProfScope ps(GOCP_KERNEL_APPLY_H, st);
     return tiled_apply_h(d.t, p.precision, d.sm_count, psi, hpsi, p.identity, energy ? d.scratch : nullptr,
-                         d.counters + kMaxChunks, d.scalars, d.err, st);
+                         d.counters + kMaxChunks, d.counters + kMaxChunks + 3, d.scalars, d.err, st);
   }
   const int grid = apply_grid(p.n_qubits);
   {
