@@ -181,6 +181,38 @@ __device__ __forceinline__ void tiled_terms(const TiledGroup* gs, int cn, const 
     const TiledGroup& G = gs[g];
     if (!octet_live(mk, o ^ G.pad)) continue;
     const uint32_t os = ao ^ G.xa;
+    if (G.delta) {
+      // paired: D = (1 + sigma (-1)^popc(k & delta)) E, the factor 0 or 2
+      const uint32_t f = octet_signs(k0, G.delta);
+      const uint32_t live = G.neg ? f : (~f & 0xFFu);
+      if (!live) continue;
+      R b[kAmpsH];
+      int t = (int)G.tb;
+#pragma unroll
+      for (int m = 0; m < kAmpsH; ++m) {
+        b[m] = R(0);
+        const int cnt = (int)((G.bk >> (8 * m)) & 0xFFu);
+        for (int c = 0; c < cnt; ++c, ++t) b[m] += (__popc(k0 & zs[t]) & 1) ? -ws[t] : ws[t];
+      }
+#pragma unroll
+      for (int hb = 1; hb < kAmpsH; hb <<= 1)
+#pragma unroll
+        for (int q = 0; q < kAmpsH; ++q)
+          if (!(q & hb)) {
+            const R u = b[q], v = b[q | hb];
+            b[q] = u + v;
+            b[q | hb] = u - v;
+          }
+      C_t<R> src[kAmpsH];
+      tile_octet<R>(tile, os, src);
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        const R d = ((live >> i) & 1u) ? R(2) * b[i] : R(0);
+        acc[i].x += d * src[i ^ XL].x;
+        acc[i].y += d * src[i ^ XL].y;
+      }
+      continue;
+    }
     if (G.bk != ~0ull) {
       // bucket m: the terms with z & 7 == m, summed with the signs of k0;
       // D(k0 + i) = sum_m B_m (-1)^popc(i & m)
@@ -226,29 +258,37 @@ __device__ __forceinline__ void tiled_terms(const TiledGroup* gs, int cn, const 
   }
 }
 
-// mask bit o = octet o of psi holds a nonzero amplitude (-0 counts as zero);
-// one ballot word per warp of 32 consecutive octets.
+// mask bit o = octet o of psi (or of psi2, when set) holds a nonzero
+// amplitude (-0 counts as zero); one ballot word per warp of 32 octets.
 template <typename R>
-__global__ void __launch_bounds__(256) k_octet_mask(const C_t<R>* __restrict__ psi, uint32_t n_octets,
-                                                    uint32_t* __restrict__ mask, unsigned int* tile_counter) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0u;   // for the H psi kernel that follows
-  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_octets; o += gridDim.x * blockDim.x) {
-    bool nz = false;
-    if (sizeof(R) == 4) {
-      const float4* p = reinterpret_cast<const float4*>(psi) + 4u * o;
+__device__ __forceinline__ bool octet_nonzero(const C_t<R>* psi, uint32_t o) {
+  bool nz = false;
+  if (sizeof(R) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(psi) + 4u * o;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 f = p[q];
-        nz |= (f.x != 0.f) | (f.y != 0.f) | (f.z != 0.f) | (f.w != 0.f);
-      }
-    } else {
-      const double2* p = reinterpret_cast<const double2*>(psi) + 8u * o;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const double2 f = p[q];
-        nz |= (f.x != 0.0) | (f.y != 0.0);
-      }
+    for (int q = 0; q < 4; ++q) {
+      const float4 f = p[q];
+      nz |= (f.x != 0.f) | (f.y != 0.f) | (f.z != 0.f) | (f.w != 0.f);
     }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(psi) + 8u * o;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double2 f = p[q];
+      nz |= (f.x != 0.0) | (f.y != 0.0);
+    }
+  }
+  return nz;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_octet_mask(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2,
+                                                    uint32_t n_octets, uint32_t* __restrict__ mask,
+                                                    unsigned int* tile_counter) {
+  if (tile_counter && blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0u;   // for the H psi kernel that follows
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_octets; o += gridDim.x * blockDim.x) {
+    bool nz = octet_nonzero<R>(psi, o);
+    if (psi2) nz |= octet_nonzero<R>(psi2, o);
     const uint32_t w = __ballot_sync(0xffffffffu, nz);
     if ((threadIdx.x & 31u) == 0) mask[o >> 5] = w;
   }
@@ -565,9 +605,9 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
                     const_cast<void*>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(GOCP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
-  const uint32_t n_octets = 1u << (t.n - 3);
-  const int mgrid = (int)std::min<uint32_t>((n_octets + 255u) / 256u, (uint32_t)std::max(sm_count, 1) * 8u);
-  k_octet_mask<R><<<mgrid, 256, 0, st>>>(reinterpret_cast<const C_t<R>*>(psi), n_octets, t.octmask, tile_counter);
+  if ((rc = octet_mask(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, psi, nullptr, t.n, t.octmask, tile_counter, sm_count,
+                       st)))
+    return rc;
   TiledArgs<R> a;
   a.blob = t.tblob;
   a.piece = t.tpiece;
@@ -589,11 +629,26 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
   const int per_sm = sizeof(R) == 4 ? GOCP_TILED_MINB_C64 : 1;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1) * per_sm);
   k_apply_h_tiled<R><<<grid, tiled_threads<R>(), tiled_smem<R>(), st>>>(map, a);
-  count_launches(2);
+  count_launches(1);
   return cuda_status(cudaGetLastError(), "k_apply_h_tiled");
 }
 
 }  // namespace
+
+int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t* mask,
+               unsigned int* tile_counter, int sm_count, cudaStream_t st) {
+  if (n < 8 || !mask) return fail(GOCP_EINVAL, "octet mask needs n >= 8 and a buffer");
+  const uint32_t n_octets = 1u << (n - 3);
+  const int grid = (int)std::min<uint32_t>((n_octets + 255u) / 256u, (uint32_t)std::max(sm_count, 1) * 8u);
+  if (precision == GOCP_C64)
+    k_octet_mask<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(psi),
+                                              reinterpret_cast<const float2*>(psi2), n_octets, mask, tile_counter);
+  else
+    k_octet_mask<double><<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(psi),
+                                               reinterpret_cast<const double2*>(psi2), n_octets, mask, tile_counter);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_octet_mask");
+}
 
 int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
                   double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,

@@ -79,10 +79,11 @@ double* grads_ptr(Problem& p);
 int32_t* selected_ptr(Problem& p);
 int32_t* err_ptr(Problem& p);
 int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st);
-int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st);
+int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked, cudaStream_t st);
 int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st);
 int dev_norm(Problem& p, const void* psi, cudaStream_t st);
-int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st);
+int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, bool mask_current,
+                   cudaStream_t st);
 int dev_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE,
                 cudaStream_t st);
 int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out, cudaStream_t st);
@@ -390,7 +391,7 @@ int gocp_prepare_state(const gocp_problem* h, const int32_t* ops, const double* 
   const double* d_theta;
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
   if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
-  return dev_taylor_chain(p, d_ops, n_ops, psi, st);
+  return dev_taylor_chain(p, d_ops, n_ops, psi, true, st);
 }
 
 int gocp_taylor_step(const gocp_problem* h, int op, double theta, void* psi, void* stream) {
@@ -406,7 +407,7 @@ int gocp_taylor_step(const gocp_problem* h, int op, double theta, void* psi, voi
   double th[1] = {theta};
   if ((rc = stage_ansatz(p, ops, th, 1, GOCP_MEM_HOST, st, &d_ops, &d_theta))) return rc;
   if ((rc = dev_setup(p, nullptr, d_theta, 1, st))) return rc;
-  return dev_taylor_chain(p, d_ops, 1, psi, st);
+  return dev_taylor_chain(p, d_ops, 1, psi, false, st);   // psi is the caller's: no mask
 }
 
 int gocp_apply_h(const gocp_problem* h, const void* psi, void* hpsi, void* stream) {
@@ -438,7 +439,7 @@ int gocp_pool_gradients(const gocp_problem* h, const void* psi, const void* hpsi
   DeviceGuard g(p.device);
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
-  if ((rc = dev_pool_grads(p, psi, hpsi, dst, st))) return rc;
+  if ((rc = dev_pool_grads(p, psi, hpsi, dst, false, st))) return rc;
   return deliver(dst, grads, p.pool.size(), mem, st);
 }
 
@@ -456,7 +457,7 @@ int gocp_energy_grad(const gocp_problem* h, const int32_t* ops, const double* th
   void* psi = ws;
   void* lam = (char*)ws + state_bytes(p);
   if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, st))) return rc;
+  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
   if ((rc = dev_apply_h(p, psi, lam, true, st))) return rc;
   double* d_dE = mem == GOCP_MEM_DEVICE ? dE : dtheta_ptr(p);
   if (n_ops > 0 && (rc = dev_adjoint(p, d_ops, n_ops, psi, lam, d_dE, st))) return rc;
@@ -486,10 +487,10 @@ int gocp_adapt_step(const gocp_problem* h, const int32_t* ops, const double* the
   void* psi = ws;
   void* hpsi = (char*)ws + state_bytes(p);
   if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, st))) return rc;
+  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
   if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
   double* d_grads = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
-  if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, st))) return rc;
+  if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, true, st))) return rc;   // the chain's mask
   int32_t* d_sel = mem == GOCP_MEM_DEVICE ? selected : selected_ptr(p);
   if ((rc = dev_select(p, d_grads, tie_rel, d_sel, st))) return rc;
   if (mem == GOCP_MEM_DEVICE) {
@@ -556,6 +557,6 @@ int gocp_profile_read(int kind, int64_t* launches, double* total_ms) {
 const char* gocp_last_error(void) { return t_last_error.c_str(); }
 int64_t gocp_launch_count(void) { return g_launches.load(); }
 // The k_apply_h revision names the kernel that profiles/traffic.json was measured on.
-const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h=tiled-tma-r9)"; }
+const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h=tiled-tma-r10; chain=octet-mask-1)"; }
 
 }  // extern "C"

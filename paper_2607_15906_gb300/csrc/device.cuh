@@ -133,14 +133,21 @@ struct TiledHead {
 };
 static_assert(sizeof(TiledHead) == 80, "TiledHead is 80 bytes");
 
+// A term-list group.  When delta != 0 its terms come in exact pairs
+// (z, w), (z ^ delta, sigma w): then D(k) = (1 + sigma (-1)^popc(k & delta)) E(k),
+// a factor that is exactly 0 or 2, and only one term of each pair is kept
+// (E's terms).  Number-conserving one-body groups have this form.
 struct __align__(16) TiledGroup {
   uint32_t x;
   uint32_t tb, tm, te;          // [tb, tm) real, [tm, te) imaginary terms
   uint64_t bk;                  // Walsh bucket sizes (see DevTables::gbk)
   uint32_t xa;                  // tiled_swz<R>((x >> 3) & (octets - 1))
   uint32_t pad;                 // (x >> 3) & (octets - 1)
+  uint32_t delta;               // pair vector, 0: unpaired
+  uint32_t neg;                 // 1: sigma = -1, 0: sigma = +1
+  uint32_t pad2[2];
 };
-static_assert(sizeof(TiledGroup) == 32, "TiledGroup is 32 bytes");
+static_assert(sizeof(TiledGroup) == 48, "TiledGroup is 48 bytes");
 
 // Byte offset of octet o in a staged tile.  The tile is rows of 128 bytes
 // whose 16-byte chunks sit at chunk ^ (row & 7) (the 128-byte swizzle of the
@@ -204,13 +211,16 @@ struct DevTables {
   // eight bucket sizes (byte m = terms with z & 7 == m); ~0 when the group
   // has imaginary terms or a bucket above 255 (then it is summed term by term)
   const uint64_t* gbk = nullptr;
-  // the tiled form of the off-diagonal groups (n_pieces = 0: none), and a
-  // scratch mask of 2^(n-3) bits, bit o set when octet o of the state being
-  // multiplied holds a nonzero amplitude
+  // the tiled form of the off-diagonal groups (n_pieces = 0: none), and
+  // (n >= 8) a scratch mask of 2^(n-3) bits over the octets of a state: a
+  // clear bit guarantees that the octet's 8 amplitudes are exactly zero (set
+  // bits may be conservative); see octet_mask
   int n_pieces = 0;
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
   uint32_t* octmask = nullptr;
+  // second mask of the same size, for the adjoint sweep (psi and lambda)
+  uint32_t* octmask2 = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;
@@ -334,6 +344,20 @@ __device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned
   __syncthreads();
   return true;
 }
+
+// Nonzero-octet masks (bit o of word o >> 5: octet o = amplitudes 8o..8o+7).
+__device__ __forceinline__ uint32_t octet_bit(const uint32_t* mask, uint32_t b) {
+  return (mask[b >> 8] >> ((b >> 3) & 31u)) & 1u;
+}
+__device__ __forceinline__ void octet_set(uint32_t* mask, uint32_t b) {
+  atomicOr(mask + (b >> 8), 1u << ((b >> 3) & 31u));
+}
+
+// mask = exact nonzero-octet mask of psi (of psi or psi2 when psi2 is set),
+// 2^(n-3) bits, n >= 8; resets *tile_counter when it is set.  Defined in
+// apply_tiled.cu.
+int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t* mask,
+               unsigned int* tile_counter, int sm_count, cudaStream_t st);
 
 // H psi (+ the energy epilogue when partials is set) by the tiled kernel;
 // t.n_pieces must be > 0.  Defined in apply_tiled.cu.

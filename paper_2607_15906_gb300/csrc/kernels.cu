@@ -91,10 +91,17 @@ __device__ void setup_body(C_t<R>* psi, int n, uint64_t index, const double* the
     }
 }
 
+// With `mask` set (psi set, n >= 8) also mask = the nonzero octets of
+// |index>: the one bit of index's octet.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs) {
+k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs, uint32_t* mask) {
   setup_body<R>(psi, n, index, theta, n_ops, coefs, blockIdx.x, gridDim.x);
+  if (mask) {
+    const uint32_t words = 1u << (n - 8), iw = (uint32_t)(index >> 8);
+    for (uint32_t w = blockIdx.x * kThreads + threadIdx.x; w < words; w += gridDim.x * kThreads)
+      mask[w] = w == iw ? 1u << ((index >> 3) & 31u) : 0u;
+  }
 }
 
 // ------------------------------------------------------------ small kernels
@@ -509,9 +516,13 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // LUT form of the same step: real D on the pair; only the pairs the
 // operator touches are visited (enumerated, see PairEnum) -- on the others
 // T = I and nothing is read or written.
+// With `mask` set (a nonzero-octet mask of psi, see octet_bit) a pair whose
+// two octets are marked zero is skipped -- T maps (0, 0) to (0, 0) -- and a
+// pair that is computed marks both of its octets, so that the mask stays
+// valid for the updated psi.
 template <typename R>
 __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
-                                C_t<R>* psi, int32_t* err, int bid, int nb) {
+                                C_t<R>* psi, int32_t* err, int bid, int nb, uint32_t* mask) {
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
     if (bid == 0 && threadIdx.x == 0) atomicOr(err, 1);
@@ -527,10 +538,16 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
   for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
     uint32_t ph;
     const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
+    const uint32_t b2 = b ^ L.x;
+    uint32_t m1 = 1u, m2 = 1u;
+    if (mask) {
+      m1 = octet_bit(mask, b);
+      m2 = octet_bit(mask, b2);
+      if (!(m1 | m2)) continue;
+    }
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
     const uint32_t sg = __popc(b & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-    const uint32_t b2 = b ^ L.x;
     C_t<R> v1 = psi[b], v2 = psi[b2];
     C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
 #pragma unroll
@@ -543,14 +560,18 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
     }
     psi[b] = csub<R>(s1, e1);
     psi[b2] = csub<R>(s2, e2);
+    if (!m1) octet_set(mask, b);
+    if (!m2) octet_set(mask, b2);
   }
 }
 
+// `mask` is used (and kept valid) by the LUT form only; the generic form
+// neither reads nor updates it, so callers pass it only for LUT pools.
 template <typename R>
 __device__ void taylor_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
-                            C_t<R>* psi, int32_t* err, int bid, int nb) {
+                            C_t<R>* psi, int32_t* err, int bid, int nb, uint32_t* mask = nullptr) {
   if (tb.pool_lut) {
-    taylor_lut_body<R>(tb, ops, coefs, j, psi, err, bid, nb);
+    taylor_lut_body<R>(tb, ops, coefs, j, psi, err, bid, nb, mask);
     return;
   }
   __shared__ uint32_t s_z[kStageStrings];
@@ -583,8 +604,9 @@ __device__ void taylor_body(const DevTables& tb, const int32_t* ops, const doubl
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, int32_t* err) {
-  taylor_body<R>(tb, ops, coefs, j, psi, err, blockIdx.x, gridDim.x);
+k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, int32_t* err,
+          uint32_t* mask) {
+  taylor_body<R>(tb, ops, coefs, j, psi, err, blockIdx.x, gridDim.x, mask);
 }
 
 // ------------------------------------------------------------ adjoint step
@@ -598,10 +620,13 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 //   lambda <- T^dagger lambda.
 // LUT form of the backward step (real D) over the enumerated pairs the
 // operator touches (elsewhere T = I and T' = 0).
+// With `mask` set (nonzero octets of psi or lambda) a pair on which both are
+// zero is skipped -- it adds nothing to dE and stays zero -- and a computed
+// pair marks both of its octets.
 template <typename R>
 __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                  C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
-                                 double* dtheta, int32_t* err, int bid, int nb) {
+                                 double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask) {
   __shared__ double tot[1];
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
@@ -622,10 +647,16 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
   for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
     uint32_t ph;
     const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
+    const uint32_t b2 = b ^ L.x;
+    uint32_t m1 = 1u, m2 = 1u;
+    if (mask) {
+      m1 = octet_bit(mask, b);
+      m2 = octet_bit(mask, b2);
+      if (!(m1 | m2)) continue;
+    }
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
     const uint32_t sg = __popc(b & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-    const uint32_t b2 = b ^ L.x;
     const R mu = d1 * d2, mu2 = mu * mu;
     const R cc = c[0] + c[2] * mu + c[4] * mu2;
     const R sc = c[1] + c[3] * mu + c[5] * mu2;
@@ -644,6 +675,8 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
     psi[b2] = q2;
     lam[b] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
     lam[b2] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
+    if (!m1) octet_set(mask, b);
+    if (!m2) octet_set(mask, b2);
   }
   grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
 }
@@ -651,9 +684,9 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
 template <typename R>
 __device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                              C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
-                             double* dtheta, int32_t* err, int bid, int nb) {
+                             double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask = nullptr) {
   if (tb.pool_lut) {
-    adjoint_lut_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, bid, nb);
+    adjoint_lut_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, bid, nb, mask);
     return;
   }
   __shared__ uint32_t s_z[kStageStrings];
@@ -701,8 +734,8 @@ __device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const doub
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
-          double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
-  adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x);
+          double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask) {
+  adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask);
 }
 
 // ------------------------------------------------------------ pool gradients
@@ -804,10 +837,12 @@ k_pool_grad(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restri
 // accumulator per thread):
 //   Re<H psi|A psi> over a pair = D(b) Re(conj(h_b) psi_{b^x}) + D(b^x) Re(conj(h_{b^x}) psi_b).
 // Each block writes one FP64 partial per operator: part[pos * nbx + blockIdx.x].
+// With `mask` set (nonzero octets of psi) a pair on which psi is zero at
+// both ends adds nothing and is skipped before its loads.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_lut(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
-                double* part, int nbx) {
+                double* part, int nbx, const uint32_t* __restrict__ mask) {
   __shared__ LutDev<R> s_op[kOpsPerBlock];
   __shared__ PairEnum s_en[kOpsPerBlock];
   __shared__ double s_red[kWarps];
@@ -835,9 +870,10 @@ k_pool_grad_lut(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __re
         if (q >= count) break;
         uint32_t ph;
         const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
+        const uint32_t b2 = b ^ L.x;
+        if (mask && !(octet_bit(mask, b) | octet_bit(mask, b2))) continue;
         const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
         const uint32_t sg = __popc(b & L.z0) & 1u;
-        const uint32_t b2 = b ^ L.x;
         const C_t<R> h1 = hpsi[b], h2 = hpsi[b2], p1 = psi[b], p2 = psi[b2];
         const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
                       ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
@@ -1089,6 +1125,77 @@ bool make_hlut(uint32_t x, const std::vector<uint32_t>& z, const std::vector<dou
   return true;
 }
 
+// The exact pair structure of a term-list group with real weights (see
+// TiledGroup): a vector delta != 0 and a sign such that every term (z, w) has
+// the partner (z ^ delta, sign * w), found among delta = z_0 ^ z_t.  Returns
+// delta = 0 when there is none (or the group has imaginary terms); else the
+// terms with bit lowbit(delta) of z clear, sorted into Walsh buckets by
+// z & 7, and their bucket sizes.
+template <typename R>
+struct PairedTerms {
+  uint32_t delta = 0, neg = 0;
+  uint64_t bk = ~0ull;
+  std::vector<uint32_t> z;
+  std::vector<R> w;
+};
+
+template <typename R>
+PairedTerms<R> paired_terms(const std::vector<uint32_t>& tz, const std::vector<R>& tw, int32_t beg,
+                             int32_t mid, int32_t end) {
+  PairedTerms<R> out;
+  const int cnt = end - beg;
+  if (mid != end || cnt < 2 || (cnt & 1)) return out;
+  std::vector<std::pair<uint32_t, R>> terms;
+  for (int32_t t = beg; t < end; ++t) terms.push_back({tz[t], tw[t]});
+  std::sort(terms.begin(), terms.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  auto find = [&](uint32_t z, R* w) {
+    auto it = std::lower_bound(terms.begin(), terms.end(), z,
+                               [](const std::pair<uint32_t, R>& a, uint32_t v) { return a.first < v; });
+    if (it == terms.end() || it->first != z) return false;
+    *w = it->second;
+    return true;
+  };
+  for (int c = 1; c < cnt && !out.delta; ++c) {
+    const uint32_t d = terms[0].first ^ terms[c].first;
+    for (int sgn = 0; sgn < 2 && !out.delta; ++sgn) {
+      bool ok = true;
+      for (const auto& tm : terms) {
+        R w2;
+        if (!find(tm.first ^ d, &w2) || w2 != (sgn ? -tm.second : tm.second)) {
+          ok = false;
+          break;
+        }
+      }
+      if (ok) {
+        out.delta = d;
+        out.neg = (uint32_t)sgn;
+      }
+    }
+  }
+  if (!out.delta) return out;
+  const uint32_t low = out.delta & (~out.delta + 1u);
+  int nb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int m = 0; m < 8; ++m)
+    for (const auto& tm : terms)
+      if (!(tm.first & low) && (tm.first & 7u) == (uint32_t)m) {
+        out.z.push_back(tm.first);
+        out.w.push_back(tm.second);
+        ++nb[m];
+      }
+  out.bk = 0;
+  for (int m = 0; m < 8; ++m) {
+    if (nb[m] > 255) {
+      out.delta = 0;   // a bucket too large for the packed sizes: keep the group unpaired
+      out.bk = ~0ull;
+      out.z.clear();
+      out.w.clear();
+      return out;
+    }
+    out.bk |= (uint64_t)nb[m] << (8 * m);
+  }
+  return out;
+}
+
 // Cuts the off-diagonal groups into the pieces of the tiled H psi kernel
 // (see TiledHead).  hl and the term-list groups come sorted by (x & 7, x),
 // an order each piece keeps.  Leaves t.n_pieces = 0 (the untiled kernel
@@ -1117,6 +1224,12 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   std::sort(his.begin(), his.end());
   his.erase(std::unique(his.begin(), his.end()), his.end());
   std::rotate(his.begin(), his.begin() + 1, his.end());   // 0 (the smallest) last
+  // terms each group keeps in the blob (half of them when paired)
+  std::vector<size_t> stored(gx.size());
+  for (size_t g = 0; g < gx.size(); ++g) {
+    const auto pr = paired_terms<R>(tz, tw, goff[g], gmid[g], goff[g + 1]);
+    stored[g] = pr.delta ? pr.z.size() : (size_t)(goff[g + 1] - goff[g]);
+  }
   std::vector<uint8_t> blob;
   std::vector<TiledPiece> pieces;
   for (uint32_t hi : his) {
@@ -1132,7 +1245,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       while (li < ls.size() && blob_size(pl.size() + 1, 0, 0) <= kTiledBlobBytes) pl.push_back(ls[li++]);
       while (ti < ts.size()) {
         const int g = ts[ti];
-        const size_t add = (size_t)(goff[g + 1] - goff[g]);
+        const size_t add = stored[g];
         if (blob_size(pl.size(), pt.size() + 1, nt + add) > kTiledBlobBytes) break;
         pt.push_back(g);
         nt += add;
@@ -1175,15 +1288,25 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
         TiledGroup tg;
         std::memset(&tg, 0, sizeof(tg));
         tg.x = gx[g];
-        tg.tb = tcur;
-        tg.tm = tcur + (uint32_t)(gmid[g] - goff[g]);
-        tg.te = tcur + (uint32_t)(goff[g + 1] - goff[g]);
-        tg.bk = gbk[g];
         tg.xa = tiled_swz<R>((gx[g] >> 3) & (octets - 1));
         tg.pad = (gx[g] >> 3) & (octets - 1);
-        for (int32_t t = goff[g]; t < goff[g + 1]; ++t) {
-          zz.push_back(tz[t]);
-          ww.push_back(tw[t]);
+        const auto pr = paired_terms<R>(tz, tw, goff[g], gmid[g], goff[g + 1]);
+        tg.tb = tcur;
+        if (pr.delta) {
+          tg.delta = pr.delta;
+          tg.neg = pr.neg;
+          tg.bk = pr.bk;
+          tg.tm = tg.te = tcur + (uint32_t)pr.z.size();
+          zz.insert(zz.end(), pr.z.begin(), pr.z.end());
+          ww.insert(ww.end(), pr.w.begin(), pr.w.end());
+        } else {
+          tg.tm = tcur + (uint32_t)(gmid[g] - goff[g]);
+          tg.te = tcur + (uint32_t)(goff[g + 1] - goff[g]);
+          tg.bk = gbk[g];
+          for (int32_t t = goff[g]; t < goff[g + 1]; ++t) {
+            zz.push_back(tz[t]);
+            ww.push_back(tw[t]);
+          }
         }
         tcur = tg.te;
         std::memcpy(b + w, &tg, sizeof(tg));
@@ -1203,12 +1326,8 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   }
   uint8_t* dblob;
   TiledPiece* dpiece;
-  uint32_t* dmask;
   int rc;
-  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
-      (rc = dalloc(d, &dmask, (size_t)1 << (n - 8), bytes)))
-    return rc;
-  d.t.octmask = dmask;
+  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes))) return rc;
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
   d.t.n_pieces = (int)pieces.size();
@@ -1472,8 +1591,12 @@ int upload_problem(Problem& p) {
   DeviceTables* d = new DeviceTables();
   p.dev = d;
   size_t bytes = 0;
-  int rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
-                                   : upload_typed<double>(p, *d, bytes, &p.identity);
+  int rc;
+  if (p.n_qubits >= 8 && ((rc = dalloc(*d, &d->t.octmask, (size_t)1 << (p.n_qubits - 8), bytes)) ||
+                          (rc = dalloc(*d, &d->t.octmask2, (size_t)1 << (p.n_qubits - 8), bytes))))
+    return rc;
+  rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
+                               : upload_typed<double>(p, *d, bytes, &p.identity);
   if (rc) return rc;
   int sm = 0;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, p.device);
@@ -1545,13 +1668,14 @@ static int launch_setup(Problem& p, void* psi, const double* d_theta, int n_ops,
   const uint64_t dim = psi ? 1ull << p.n_qubits : 1;
   int grid = grid_for(dim, p.dev->sm_count, 8);
   k_setup<R><<<grid, kThreads, 0, st>>>((C_t<R>*)psi, p.n_qubits, p.ref_index, d_theta, n_ops,
-                                        p.dev->coefs);
+                                        p.dev->coefs, psi ? p.dev->t.octmask : nullptr);
   count_launches(1);
   return cuda_status(cudaGetLastError(), "k_setup");
 }
 
 // psi = |ref> (skipped when psi is NULL) and the Taylor coefficients of the
-// staged ansatz (n_ops may be 0).
+// staged ansatz (n_ops may be 0).  With psi, the problem's octet mask then
+// describes psi (see dev_taylor_chain).
 int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st) {
   int rc = ensure_stage(p, n_ops);
   if (rc) return rc;
@@ -1560,24 +1684,28 @@ int dev_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStrea
 }
 
 template <typename R>
-static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
+static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked,
+                               cudaStream_t st) {
   DeviceTables& d = *p.dev;
   const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (p.n_qubits - 1);
   const int grid = grid_for(pairs, d.sm_count, 8);
+  uint32_t* mask = tracked && d.t.pool_lut ? d.t.octmask : nullptr;
   for (int j = 0; j < n_ops; ++j) {
     ProfScope ps(GOCP_KERNEL_TAYLOR, st);
-    k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err);
+    k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err, mask);
   }
   count_launches(n_ops);
   return cuda_status(cudaGetLastError(), "k_taylor5");
 }
 
 // Applies operators 0..n_ops-1 of a staged ansatz whose coefficients were
-// written by dev_setup.
-int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
+// written by dev_setup.  `tracked`: psi is the state dev_setup just wrote
+// (and the chain before it advanced), so the octet mask describes it; the
+// chain then skips all-zero pairs and keeps the mask valid.
+int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked, cudaStream_t st) {
   if (n_ops == 0) return GOCP_OK;
-  return p.precision == GOCP_C64 ? launch_taylor_chain<float>(p, d_ops, n_ops, psi, st)
-                                 : launch_taylor_chain<double>(p, d_ops, n_ops, psi, st);
+  return p.precision == GOCP_C64 ? launch_taylor_chain<float>(p, d_ops, n_ops, psi, tracked, st)
+                                 : launch_taylor_chain<double>(p, d_ops, n_ops, psi, tracked, st);
 }
 
 template <typename R>
@@ -1620,7 +1748,7 @@ int dev_norm(Problem& p, const void* psi, cudaStream_t st) {
 }
 
 template <typename R>
-static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads,
+static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, bool mask_current,
                              cudaStream_t st) {
   DeviceTables& d = *p.dev;
   const int M = d.t.M;
@@ -1630,10 +1758,15 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
   if (d.t.pool_lut) {
     const int nbx = pool_lut_nbx(d.t.penum_max);
     dim3 grid(nbx, nchunks);
+    const uint32_t* mask = d.t.octmask;
+    int rc;
+    if (mask && !mask_current &&
+        (rc = octet_mask(p.precision, psi, nullptr, p.n_qubits, d.t.octmask, nullptr, d.sm_count, st)))
+      return rc;
     {
       ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
       k_pool_grad_lut<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
-                                                    d.scratch, nbx);
+                                                    d.scratch, nbx, mask);
     }
     k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, nbx, M, d.graw);
     ++n;
@@ -1648,11 +1781,14 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
   return cuda_status(cudaGetLastError(), "k_pool_grad");
 }
 
-int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st) {
+// `mask_current`: the problem's octet mask already describes psi (a tracked
+// chain produced it); otherwise it is rebuilt from psi first.
+int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, bool mask_current,
+                   cudaStream_t st) {
   int rc = dev_norm(p, psi, st);   // <psi|psi> -> scalars[1]
   if (rc) return rc;
-  return p.precision == GOCP_C64 ? launch_pool_grads<float>(p, psi, hpsi, d_grads, st)
-                                 : launch_pool_grads<double>(p, psi, hpsi, d_grads, st);
+  return p.precision == GOCP_C64 ? launch_pool_grads<float>(p, psi, hpsi, d_grads, mask_current, st)
+                                 : launch_pool_grads<double>(p, psi, hpsi, d_grads, mask_current, st);
 }
 
 template <typename R>
@@ -1664,10 +1800,14 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, p.n_qubits, d.scalars);
   const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : dim / 2;
   const int grid = grid_for(pairs, d.sm_count, 8);
+  // nonzero octets of psi or lambda, kept valid by the sweep
+  uint32_t* mask = d.t.pool_lut ? d.t.octmask2 : nullptr;
+  int rc;
+  if (mask && (rc = octet_mask(p.precision, psi, lam, p.n_qubits, mask, nullptr, d.sm_count, st))) return rc;
   for (int j = n_ops - 1; j >= 0; --j) {
     ProfScope ps(GOCP_KERNEL_ADJOINT, st);
     k_adjoint<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, (C_t<R>*)lam,
-                                            d.scratch, d.counters + kMaxChunks + 2, d_dE, d.err);
+                                            d.scratch, d.counters + kMaxChunks + 2, d_dE, d.err, mask);
   }
   count_launches(1 + n_ops);
   return cuda_status(cudaGetLastError(), "k_adjoint");
