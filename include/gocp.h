@@ -63,7 +63,21 @@ enum {
 enum { GOCP_JW = 0, GOCP_BK = 1 };          /* qubit mapping, Sec. II.A */
 enum { GOCP_C64 = 0, GOCP_C128 = 1 };       /* amplitude precision */
 enum { GOCP_MEM_HOST = 0, GOCP_MEM_DEVICE = 1 };
-enum { GOCP_BUILD_NO_COLOURING = 1 };       /* gocp_build_args.flags */
+/* gocp_build_args.flags.  GOCP_BUILD_SECTOR (gocp_build only) selects the
+ * sector layout: a state holds only the D = C(n_orb, N_a) C(n_orb, N_b)
+ * determinants with the reference state's N_a = ceil(n_elec / 2) alpha and
+ * N_b = floor(n_elec / 2) beta electrons, row r = rank_a * C(n_orb, N_b) +
+ * rank_b (colexicographic ranks of the alpha and beta occupation strings,
+ * spin-orbital 2p + s).  H and every pool generator conserve both counts, so
+ * each operation of the method maps this subspace to itself: states, E,
+ * gradients and dE/dtheta equal the full-layout ones, and H psi equals the
+ * full-layout H psi on the sector rows (a term_drop that removes part of a
+ * number-conserving set of Pauli terms leaves a small full-layout H psi
+ * outside the sector, which this layout does not hold).  Every
+ * state argument below then has gocp_state_bytes() = D * (8 or 16) bytes;
+ * gocp_sector_expand / _compress convert to and from the 2^n layout.  The
+ * request server and gocp_energy_static take full-layout problems only. */
+enum { GOCP_BUILD_NO_COLOURING = 1, GOCP_BUILD_SECTOR = 2 };
 
 typedef struct gocp_problem gocp_problem;
 typedef struct gocp_server gocp_server;
@@ -140,6 +154,9 @@ typedef struct {
   int64_t n_groups;       /* distinct x masks of H */
   int64_t n_pool_strings;
   size_t device_bytes;    /* device memory held by the problem */
+  int64_t state_dim;      /* amplitudes per state: 2^n, or D in the sector layout */
+  int sector;             /* 1: sector layout (GOCP_BUILD_SECTOR) */
+  int n_alpha, n_beta;    /* sector electron counts (0 in the full layout) */
 } gocp_info;
 int gocp_problem_info(const gocp_problem* p, gocp_info* out);
 
@@ -160,8 +177,16 @@ int gocp_exact_sum(const double* v, int64_t n, double* out);
 
 /* ---------------------------------------------------------------- compute */
 
-/* Bytes of one state: 2^n * (8 for C64, 16 for C128). */
+/* Bytes of one state: state_dim * (8 for C64, 16 for C128), state_dim =
+ * 2^n, or D for the sector layout. */
 size_t gocp_state_bytes(const gocp_problem* p);
+
+/* Sector layout only (GOCP_EINVAL otherwise): full <- the 2^n state whose
+ * amplitude at the basis state of row r is psi[r] and zero elsewhere
+ * (full: 2^n amplitudes of the problem's precision, device memory);
+ * compress: psi[r] <- full[basis state of row r], the rest of full ignored. */
+int gocp_sector_expand(const gocp_problem* p, const void* psi, void* full, void* stream);
+int gocp_sector_compress(const gocp_problem* p, const void* full, void* psi, void* stream);
 
 /* psi <- |ref>. */
 int gocp_reference_state(const gocp_problem* p, void* psi, void* stream);

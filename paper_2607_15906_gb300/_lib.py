@@ -16,7 +16,7 @@ GOCP_EAGAIN, GOCP_ETIMEDOUT, GOCP_ECANCELED, GOCP_ENODEV = -4, -5, -6, -7
 GOCP_JW, GOCP_BK = 0, 1
 GOCP_C64, GOCP_C128 = 0, 1
 GOCP_MEM_HOST, GOCP_MEM_DEVICE = 0, 1
-GOCP_BUILD_NO_COLOURING = 1
+GOCP_BUILD_NO_COLOURING, GOCP_BUILD_SECTOR = 1, 2
 KERNEL_APPLY_H, KERNEL_TAYLOR, KERNEL_POOL_GRAD, KERNEL_ADJOINT = 0, 1, 2, 3
 
 _NAMES = {GOCP_EINVAL: "EINVAL", GOCP_ENOMEM: "ENOMEM", GOCP_ECUDA: "ECUDA", GOCP_EAGAIN: "EAGAIN",
@@ -50,7 +50,8 @@ class Info(C.Structure):
     _fields_ = [("n_qubits", C.c_int), ("n_elec", C.c_int), ("mapping", C.c_int), ("precision", C.c_int),
                 ("device", C.c_int), ("pool_size", C.c_int), ("n_families", C.c_int),
                 ("ref_index", C.c_uint32), ("n_terms", C.c_int64), ("n_groups", C.c_int64),
-                ("n_pool_strings", C.c_int64), ("device_bytes", C.c_size_t)]
+                ("n_pool_strings", C.c_int64), ("device_bytes", C.c_size_t), ("state_dim", C.c_int64),
+                ("sector", C.c_int), ("n_alpha", C.c_int), ("n_beta", C.c_int)]
 
 
 class ServerStats(C.Structure):
@@ -74,6 +75,8 @@ _SIGS = {
     "gocp_prepare_state": (C.c_int, [P, P, P, C.c_int, C.c_int, P, P]),
     "gocp_taylor_step": (C.c_int, [P, C.c_int, C.c_double, P, P]),
     "gocp_apply_h": (C.c_int, [P, P, P, P]),
+    "gocp_sector_expand": (C.c_int, [P, P, P, P]),
+    "gocp_sector_compress": (C.c_int, [P, P, P, P]),
     "gocp_energy": (C.c_int, [P, P, P, P, C.c_int, P]),
     "gocp_energy_static": (C.c_int, [P, P, P, P, C.c_int, P]),
     "gocp_pool_gradients": (C.c_int, [P, P, P, P, C.c_int, P]),

@@ -99,6 +99,7 @@ void accumulate(std::vector<Contribution>& c, double drop, int n, PauliTerms& ou
 }  // namespace
 
 uint32_t Encoding::encode(uint32_t occupation) const { return apply_rows(beta_rows, occupation); }
+uint32_t Encoding::decode(uint32_t qubits) const { return apply_rows(inv_rows, qubits); }
 
 Encoding make_encoding(int mapping, int n) {
   Encoding e;
@@ -114,6 +115,7 @@ Encoding make_encoding(int mapping, int n) {
     }
   }
   std::vector<uint32_t> inv = gf2_inverse_rows(e.beta_rows, n);
+  e.inv_rows = inv;
   std::vector<uint32_t> inv_t = transpose_rows(inv, n);          // rows of beta^-T
   e.x.resize(n);
   e.zp.resize(n);

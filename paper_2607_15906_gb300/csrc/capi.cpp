@@ -112,9 +112,9 @@ int check_mem(int mem) {
   return GOCP_OK;
 }
 
-size_t state_bytes(const Problem& p) {
-  return ((size_t)1 << p.n_qubits) * (p.precision == GOCP_C64 ? 8u : 16u);
-}
+size_t state_dim(const Problem& p) { return p.sector ? (size_t)p.sector_dim : (size_t)1 << p.n_qubits; }
+
+size_t state_bytes(const Problem& p) { return state_dim(p) * (p.precision == GOCP_C64 ? 8u : 16u); }
 
 // Makes ops/theta available on the device.  Host arrays are validated and
 // copied into the problem's staging buffers.
@@ -178,7 +178,9 @@ int finish_build(gocp_problem* h, int flags, gocp_problem** out) {
   if (p.device >= 0) {
     DeviceGuard g(p.device);
     int rc = upload_problem(p);
+    if (!rc) rc = upload_sector(p);
     if (rc) {
+      free_sector(p);
       free_device(p);
       return rc;
     }
@@ -235,6 +237,19 @@ int gocp_build(const gocp_build_args* a, gocp_problem** out) {
     Encoding enc = make_encoding(a->mapping, p.n_qubits);
     build_pool(p.n_qubits, a->n_elec, enc, p.pool);
     p.ref_index = enc.encode(a->n_elec >= 32 ? 0xffffffffu : ((1u << a->n_elec) - 1u));
+    if (a->flags & GOCP_BUILD_SECTOR) {
+      // D = C(n_orb, N_a) C(n_orb, N_b), the reference state's electron counts
+      auto binom = [](int n, int k) {
+        int64_t c = 1;
+        for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+        return c;
+      };
+      p.sector = true;
+      p.n_alpha = (a->n_elec + 1) / 2;
+      p.n_beta = a->n_elec / 2;
+      if (p.n_alpha > a->n_orb) { delete h; return fail(GOCP_EINVAL, "too many alpha electrons for the sector layout"); }
+      p.sector_dim = binom(a->n_orb, p.n_alpha) * binom(a->n_orb, p.n_beta);
+    }
   } catch (const std::bad_alloc&) {
     delete h;
     return fail(GOCP_ENOMEM, "out of host memory during build");
@@ -254,6 +269,7 @@ int gocp_build_from_tables(const gocp_table_args* a, gocp_problem** out) {
     return fail(GOCP_EINVAL, "bad generator arrays");
   const uint32_t lim = a->n_qubits == 32 ? 0xffffffffu : ((1u << a->n_qubits) - 1u);
   if (a->ref_index & ~lim) return fail(GOCP_EINVAL, "ref_index out of range");
+  if (a->flags & GOCP_BUILD_SECTOR) return fail(GOCP_EINVAL, "the sector layout needs a problem built from integrals");
   int rc = check_device(a->device);
   if (rc) return rc;
   for (int64_t t = 0; t < a->n_terms; ++t) {
@@ -327,6 +343,10 @@ int gocp_problem_info(const gocp_problem* h, gocp_info* o) {
   o->n_groups = p.n_groups;
   o->n_pool_strings = (int64_t)p.pool.x.size();
   o->device_bytes = p.device_bytes;
+  o->state_dim = (int64_t)state_dim(p);
+  o->sector = p.sector ? 1 : 0;
+  o->n_alpha = p.n_alpha;
+  o->n_beta = p.n_beta;
   return GOCP_OK;
 }
 
@@ -356,6 +376,10 @@ int gocp_export_pool(const gocp_problem* h, int64_t* off, uint32_t* x, uint32_t*
 
 void gocp_problem_free(gocp_problem* h) {
   if (!h) return;
+  if (h->p.sec) {
+    DeviceGuard g(h->p.device);
+    free_sector(h->p);
+  }
   free_device(h->p);
   delete h;
 }
@@ -376,6 +400,7 @@ int gocp_reference_state(const gocp_problem* h, void* psi, void* stream) {
   if (!psi) return fail(GOCP_EINVAL, "psi is NULL");
   Problem& p = const_cast<Problem&>(h->p);
   DeviceGuard g(p.device);
+  if (p.sector) return sec_setup(p, psi, nullptr, 0, stream);
   return dev_setup(p, psi, nullptr, 0, (cudaStream_t)stream);
 }
 
@@ -390,6 +415,10 @@ int gocp_prepare_state(const gocp_problem* h, const int32_t* ops, const double* 
   const int32_t* d_ops;
   const double* d_theta;
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
+  if (p.sector) {
+    if ((rc = sec_setup(p, psi, d_theta, n_ops, st))) return rc;
+    return sec_taylor_chain(p, d_ops, n_ops, psi, st);
+  }
   if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
   return dev_taylor_chain(p, d_ops, n_ops, psi, true, st);
 }
@@ -406,6 +435,10 @@ int gocp_taylor_step(const gocp_problem* h, int op, double theta, void* psi, voi
   int32_t ops[1] = {op};
   double th[1] = {theta};
   if ((rc = stage_ansatz(p, ops, th, 1, GOCP_MEM_HOST, st, &d_ops, &d_theta))) return rc;
+  if (p.sector) {
+    if ((rc = sec_setup(p, nullptr, d_theta, 1, st))) return rc;
+    return sec_taylor_chain(p, d_ops, 1, psi, st);
+  }
   if ((rc = dev_setup(p, nullptr, d_theta, 1, st))) return rc;
   return dev_taylor_chain(p, d_ops, 1, psi, false, st);   // psi is the caller's: no mask
 }
@@ -416,7 +449,26 @@ int gocp_apply_h(const gocp_problem* h, const void* psi, void* hpsi, void* strea
   if (!psi || !hpsi || psi == hpsi) return fail(GOCP_EINVAL, "psi/hpsi NULL or aliased");
   Problem& p = const_cast<Problem&>(h->p);
   DeviceGuard g(p.device);
+  if (p.sector) return sec_apply_h(p, psi, hpsi, false, stream);
   return dev_apply_h(p, psi, hpsi, false, (cudaStream_t)stream);
+}
+
+int gocp_sector_expand(const gocp_problem* h, const void* psi, void* full, void* stream) {
+  int rc = check_problem(h);
+  if (rc) return rc;
+  if (!psi || !full) return fail(GOCP_EINVAL, "psi/full is NULL");
+  Problem& p = const_cast<Problem&>(h->p);
+  DeviceGuard g(p.device);
+  return sec_expand(p, psi, full, stream);
+}
+
+int gocp_sector_compress(const gocp_problem* h, const void* full, void* psi, void* stream) {
+  int rc = check_problem(h);
+  if (rc) return rc;
+  if (!psi || !full) return fail(GOCP_EINVAL, "psi/full is NULL");
+  Problem& p = const_cast<Problem&>(h->p);
+  DeviceGuard g(p.device);
+  return sec_compress(p, full, psi, stream);
 }
 
 int gocp_energy(const gocp_problem* h, const void* psi, void* hpsi, double* out, int mem, void* stream) {
@@ -426,7 +478,7 @@ int gocp_energy(const gocp_problem* h, const void* psi, void* hpsi, double* out,
   Problem& p = const_cast<Problem&>(h->p);
   DeviceGuard g(p.device);
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
+  if ((rc = p.sector ? sec_apply_h(p, psi, hpsi, true, st) : dev_apply_h(p, psi, hpsi, true, st))) return rc;
   return deliver(scalars_ptr(p), out, 2, mem, st);
 }
 
@@ -439,7 +491,8 @@ int gocp_pool_gradients(const gocp_problem* h, const void* psi, const void* hpsi
   DeviceGuard g(p.device);
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
-  if ((rc = dev_pool_grads(p, psi, hpsi, dst, false, st))) return rc;
+  if ((rc = p.sector ? sec_pool_grads(p, psi, hpsi, dst, st) : dev_pool_grads(p, psi, hpsi, dst, false, st)))
+    return rc;
   return deliver(dst, grads, p.pool.size(), mem, st);
 }
 
@@ -456,11 +509,18 @@ int gocp_energy_grad(const gocp_problem* h, const int32_t* ops, const double* th
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
   void* psi = ws;
   void* lam = (char*)ws + state_bytes(p);
-  if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
-  if ((rc = dev_apply_h(p, psi, lam, true, st))) return rc;
   double* d_dE = mem == GOCP_MEM_DEVICE ? dE : dtheta_ptr(p);
-  if (n_ops > 0 && (rc = dev_adjoint(p, d_ops, n_ops, psi, lam, d_dE, st))) return rc;
+  if (p.sector) {
+    if ((rc = sec_setup(p, psi, d_theta, n_ops, st)) || (rc = sec_taylor_chain(p, d_ops, n_ops, psi, st)) ||
+        (rc = sec_apply_h(p, psi, lam, true, st)) ||
+        (n_ops > 0 && (rc = sec_adjoint(p, d_ops, n_ops, psi, lam, d_dE, st))))
+      return rc;
+  } else {
+    if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
+    if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
+    if ((rc = dev_apply_h(p, psi, lam, true, st))) return rc;
+    if (n_ops > 0 && (rc = dev_adjoint(p, d_ops, n_ops, psi, lam, d_dE, st))) return rc;
+  }
   if (mem == GOCP_MEM_DEVICE) {
     return cuda_status(cudaMemcpyAsync(E, scalars_ptr(p), sizeof(double), cudaMemcpyDeviceToDevice, st), "copy E");
   }
@@ -486,11 +546,17 @@ int gocp_adapt_step(const gocp_problem* h, const int32_t* ops, const double* the
   if ((rc = stage_ansatz(p, ops, theta, n_ops, mem, st, &d_ops, &d_theta))) return rc;
   void* psi = ws;
   void* hpsi = (char*)ws + state_bytes(p);
-  if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
-  if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
-  if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
   double* d_grads = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
-  if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, true, st))) return rc;   // the chain's mask
+  if (p.sector) {
+    if ((rc = sec_setup(p, psi, d_theta, n_ops, st)) || (rc = sec_taylor_chain(p, d_ops, n_ops, psi, st)) ||
+        (rc = sec_apply_h(p, psi, hpsi, true, st)) || (rc = sec_pool_grads(p, psi, hpsi, d_grads, st)))
+      return rc;
+  } else {
+    if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
+    if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
+    if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
+    if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, true, st))) return rc;   // the chain's mask
+  }
   int32_t* d_sel = mem == GOCP_MEM_DEVICE ? selected : selected_ptr(p);
   if ((rc = dev_select(p, d_grads, tie_rel, d_sel, st))) return rc;
   if (mem == GOCP_MEM_DEVICE) {

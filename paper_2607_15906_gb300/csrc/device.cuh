@@ -221,6 +221,21 @@ struct DevTables {
   uint32_t* octmask = nullptr;
   // second mask of the same size, for the adjoint sweep (psi and lambda)
   uint32_t* octmask2 = nullptr;
+  // sector layout (see SecDev): per LUT group (hlut order), term-list group
+  // and generator (pool order) the occupation-space flip u = beta^-1 x, its
+  // alpha string in bits 0..15 and its beta string in bits 16..31; and the
+  // term-list groups in paired form where they pair (sp_delta != 0, see
+  // TiledGroup), kept terms [sp_off[g], sp_mid[g]) real and
+  // [sp_mid[g], sp_off[g + 1]) imaginary in sp_z / sp_w
+  const uint32_t* hu = nullptr;
+  const uint32_t* gu = nullptr;
+  const uint32_t* pu = nullptr;
+  const uint32_t* sp_delta = nullptr;
+  const uint32_t* sp_neg = nullptr;
+  const int32_t* sp_off = nullptr;
+  const int32_t* sp_mid = nullptr;
+  const uint32_t* sp_z = nullptr;
+  const void* sp_w = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
   const uint32_t* dz = nullptr;
@@ -345,6 +360,29 @@ __device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned
   return true;
 }
 
+// Rows of the sector layout: the D determinants with na alpha and nb beta
+// electrons among no spatial orbitals, row r = rank_a[alpha] * cb +
+// rank_b[beta] (colexicographic ranks, cb = C(no, nb)).  An occupation is
+// kept as alpha | beta << 16 (bit p = orbital p).  A Pauli group with mask x
+// maps the row of occupation n to occupation n ^ u, u = beta^-1 x.
+struct SecDev {
+  int32_t D;
+  int no, na, nb;
+  uint32_t cb;
+  const uint32_t* occ;      // row -> occupation
+  const uint32_t* kq;       // row -> qubit basis state
+  const uint32_t* rank_a;   // alpha string -> rank (2^no entries)
+  const uint32_t* rank_b;
+};
+
+// Row of occupation n ^ u, false when it leaves the sector.
+__device__ __forceinline__ bool sec_row(const SecDev& s, uint32_t n, uint32_t u, uint32_t* r) {
+  const uint32_t m = n ^ u, a = m & 0xFFFFu, b = m >> 16;
+  if (__popc(a) != s.na || __popc(b) != s.nb) return false;
+  *r = s.rank_a[a] * s.cb + s.rank_b[b];
+  return true;
+}
+
 // Nonzero-octet masks (bit o of word o >> 5: octet o = amplitudes 8o..8o+7).
 __device__ __forceinline__ uint32_t octet_bit(const uint32_t* mask, uint32_t b) {
   return (mask[b >> 8] >> ((b >> 3) & 31u)) & 1u;
@@ -364,5 +402,18 @@ int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t
 int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
                   double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,
                   double* scal, int32_t* err, cudaStream_t st);
+
+// Accessors of a problem's device state for the sector-layout launchers
+// (defined in kernels.cu).
+struct Problem;
+const DevTables& dev_tables(Problem& p);
+double* coefs_ptr(Problem& p);
+double* scratch_ptr(Problem& p, size_t* doubles);
+unsigned int* counters_ptr(Problem& p);
+int pool_finish(Problem& p, const double* part, int nbx, double* d_grads, cudaStream_t st);
+int ensure_stage(Problem& p, int n_ops);
+double* scalars_ptr(Problem& p);
+int32_t* err_ptr(Problem& p);
+int dev_norm(Problem& p, const void* psi, cudaStream_t st);
 
 }  // namespace gocp

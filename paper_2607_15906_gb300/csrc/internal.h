@@ -77,8 +77,10 @@ struct Pool {
 struct Encoding {
   int n = 0;
   std::vector<uint32_t> beta_rows;     // row j of beta as a mask
+  std::vector<uint32_t> inv_rows;      // row j of beta^-1
   std::vector<uint32_t> x, zp, ze;     // per mode
-  uint32_t encode(uint32_t occupation) const;
+  uint32_t encode(uint32_t occupation) const;   // qubit basis state of an occupation
+  uint32_t decode(uint32_t qubits) const;       // occupation of a qubit basis state
 };
 Encoding make_encoding(int mapping, int n);
 
@@ -111,6 +113,7 @@ LutForm lut_form(const uint32_t* z, const double* w, int count);
 // ------------------------------------------------------------ device side
 
 struct DeviceTables;   // defined in kernels.cu
+struct SectorTables;   // defined in sector.cu
 
 struct Problem {
   int n_qubits = 0, n_elec = -1, mapping = -1, precision = GOCP_C64, device = -1;
@@ -122,10 +125,29 @@ struct Problem {
   int sm_count = 0;
   DeviceTables* dev = nullptr;
   size_t device_bytes = 0;
+  // sector layout (GOCP_BUILD_SECTOR): states hold the D determinants with
+  // n_alpha / n_beta electrons
+  bool sector = false;
+  int n_alpha = 0, n_beta = 0;
+  int64_t sector_dim = 0;
+  SectorTables* sec = nullptr;
 };
 
 int upload_problem(Problem& p);
 void free_device(Problem& p);
+
+// Sector layout (sector.cu): row tables, built after upload_problem, and the
+// launchers of the method's steps on D-amplitude states.
+int upload_sector(Problem& p);
+void free_sector(Problem& p);
+// (stream: a cudaStream_t)
+int sec_setup(Problem& p, void* psi, const double* d_theta, int n_ops, void* stream);
+int sec_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* stream);
+int sec_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, void* stream);
+int sec_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, void* stream);
+int sec_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE, void* stream);
+int sec_expand(Problem& p, const void* psi, void* full, void* stream);
+int sec_compress(Problem& p, const void* full, void* psi, void* stream);
 
 // ------------------------------------------------------------ batched stages
 //

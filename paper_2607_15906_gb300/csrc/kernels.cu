@@ -1566,6 +1566,66 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
     d.t.penum_max = pe_max;
     d.t.pool_lut = true;
   }
+  if (p.sector) {
+    // ---- sector layout: occupation-space flips and paired term lists
+    if (!all_lut && M > 0) return fail(GOCP_EINVAL, "sector layout needs generators in LUT form");
+    const Encoding enc = make_encoding(p.mapping, p.n_qubits);
+    auto flip = [&](uint32_t x) {
+      const uint32_t u = enc.decode(x);
+      uint32_t a = 0, b = 0;
+      for (int q = 0; 2 * q < p.n_qubits; ++q) {
+        a |= ((u >> (2 * q)) & 1u) << q;
+        b |= ((u >> (2 * q + 1)) & 1u) << q;
+      }
+      return a | (b << 16);
+    };
+    std::vector<uint32_t> hu, gu, pu;
+    for (const HLut<R>& L : hl) hu.push_back(flip(L.x));
+    for (uint32_t x : gx) gu.push_back(flip(x));
+    for (int k = 0; k < M; ++k) pu.push_back(flip(px[k]));
+    std::vector<uint32_t> sdel, sneg, sz;
+    std::vector<int32_t> soff, smid;
+    std::vector<R> sw;
+    for (int g = 0; g < G; ++g) {
+      const auto pr = paired_terms<R>(tz, tw, goff[g], gmid[g], goff[g + 1]);
+      soff.push_back((int32_t)sz.size());
+      sdel.push_back(pr.delta);
+      sneg.push_back(pr.neg);
+      if (pr.delta) {
+        sz.insert(sz.end(), pr.z.begin(), pr.z.end());
+        sw.insert(sw.end(), pr.w.begin(), pr.w.end());
+        smid.push_back((int32_t)sz.size());
+      } else {
+        for (int32_t t = goff[g]; t < gmid[g]; ++t) {
+          sz.push_back(tz[t]);
+          sw.push_back(tw[t]);
+        }
+        smid.push_back((int32_t)sz.size());
+        for (int32_t t = gmid[g]; t < goff[g + 1]; ++t) {
+          sz.push_back(tz[t]);
+          sw.push_back(tw[t]);
+        }
+      }
+    }
+    soff.push_back((int32_t)sz.size());
+    uint32_t *dhu, *dgu, *dpu, *dsdel, *dsneg, *dsz;
+    int32_t *dsoff, *dsmid;
+    R* dsw;
+    if ((rc = upload(d, &dhu, hu, bytes)) || (rc = upload(d, &dgu, gu, bytes)) || (rc = upload(d, &dpu, pu, bytes)) ||
+        (rc = upload(d, &dsdel, sdel, bytes)) || (rc = upload(d, &dsneg, sneg, bytes)) ||
+        (rc = upload(d, &dsoff, soff, bytes)) || (rc = upload(d, &dsmid, smid, bytes)) ||
+        (rc = upload(d, &dsz, sz, bytes)) || (rc = upload(d, &dsw, sw, bytes)))
+      return rc;
+    d.t.hu = dhu;
+    d.t.gu = dgu;
+    d.t.pu = dpu;
+    d.t.sp_delta = dsdel;
+    d.t.sp_neg = dsneg;
+    d.t.sp_off = dsoff;
+    d.t.sp_mid = dsmid;
+    d.t.sp_z = dsz;
+    d.t.sp_w = dsw;
+  }
   return GOCP_OK;
 }
 
@@ -1662,6 +1722,26 @@ double* scalars_ptr(Problem& p) { return p.dev->scalars; }
 double* grads_ptr(Problem& p) { return p.dev->grads; }
 int32_t* selected_ptr(Problem& p) { return p.dev->selected; }
 int32_t* err_ptr(Problem& p) { return p.dev->err; }
+// for the sector-layout launchers (sector.cu)
+const DevTables& dev_tables(Problem& p) { return p.dev->t; }
+double* coefs_ptr(Problem& p) { return p.dev->coefs; }
+double* scratch_ptr(Problem& p, size_t* doubles) {
+  *doubles = p.dev->scratch_doubles;
+  return p.dev->scratch;
+}
+unsigned int* counters_ptr(Problem& p) { return p.dev->counters + kMaxChunks; }   // 8 slots, zero at rest
+
+// Pool gradients from block partials part[i * nbx + b] (i in GOCP family
+// order): grads[porder[i]] = 2 sum_b part[i nbx + b] / <psi|psi> (scalars[1]).
+int pool_finish(Problem& p, const double* part, int nbx, double* d_grads, cudaStream_t st) {
+  DeviceTables& d = *p.dev;
+  const int M = d.t.M;
+  if (M == 0) return GOCP_OK;
+  k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(part, nbx, M, d.graw);
+  k_grad_final<<<(M + 255) / 256, 256, 0, st>>>(d.graw, d.t.porder, M, d.scalars, d_grads);
+  count_launches(2);
+  return cuda_status(cudaGetLastError(), "pool gradient reduction");
+}
 
 template <typename R>
 static int launch_setup(Problem& p, void* psi, const double* d_theta, int n_ops, cudaStream_t st) {
@@ -1735,7 +1815,7 @@ int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream
 template <typename R>
 static int launch_norm(Problem& p, const void* psi, cudaStream_t st) {
   DeviceTables& d = *p.dev;
-  const uint64_t dim = 1ull << p.n_qubits;
+  const uint64_t dim = p.sector ? (uint64_t)p.sector_dim : 1ull << p.n_qubits;   // amplitudes of one state
   const int grid = grid_for(dim, d.sm_count, 8);
   k_norm<R><<<grid, kThreads, 0, st>>>((const C_t<R>*)psi, dim, d.scratch, d.counters + kMaxChunks + 1,
                                        d.scalars + 1);
@@ -1888,6 +1968,7 @@ extern "C" int gocp_energy_static(const gocp_problem* h, const void* psi, void* 
   if (!h) return fail(GOCP_EINVAL, "problem is NULL");
   Problem& p = const_cast<Problem&>(h->p);
   if (!p.dev) return fail(GOCP_ENODEV, "problem has no device tables (built with device = -1)");
+  if (p.sector) return fail(GOCP_EINVAL, "gocp_energy_static takes full-layout problems only");
   if (mem != GOCP_MEM_HOST && mem != GOCP_MEM_DEVICE) return fail(GOCP_EINVAL, "mem must be GOCP_MEM_HOST or GOCP_MEM_DEVICE");
   if (!psi || !hpsi || psi == hpsi || !out) return fail(GOCP_EINVAL, "psi/hpsi/out NULL or aliased");
   const int blocks = apply_grid(p.n_qubits);

@@ -1,0 +1,570 @@
+// The method's steps on sector-layout states (GOCP_BUILD_SECTOR).
+//
+// H (Eq. 2 -> 3) and every pool generator conserve the numbers of alpha and
+// beta electrons, so the reference state, every Taylor step (Eq. 5, 6), H psi
+// (Eq. 3), the energy (Eq. 1), the gradients (Eq. 4) and the adjoint sweep
+// stay in the span of the determinants with the reference state's counts.
+// A sector-layout state stores only those D amplitudes (SecDev: row r =
+// rank_a * C(no, nb) + rank_b).  A Pauli group with mask x maps the
+// determinant with occupation n to n ^ u, u = beta^-1 x (the mapping's
+// inverse encoding matrix), so the source row of every term is two rank
+// lookups away, and a source outside the sector contributes nothing.  The
+// coefficients D_g(k) are evaluated at the qubit basis state k of the output
+// row exactly as in the full layout (LUT form, paired or plain term lists,
+// compensated diagonal), so the numbers on the sector are those of the full
+// layout there.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace gocp {
+
+struct SectorTables {
+  SecDev s;
+  int32_t ref_row = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int kSecThreads = 256;
+constexpr int kSecChunk = 64;          // LUT groups staged per chunk (H psi)
+constexpr int kSecOps = 16;            // generators per block (pool gradients)
+constexpr int kSecRowsPerThread = 16;  // rows per thread per generator (pool gradients)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int grid_rows(int64_t rows, int sm_count, int per_sm) {
+  const int64_t need = (rows + kSecThreads - 1) / kSecThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_count * per_sm));
+}
+
+template <typename R>
+__device__ __forceinline__ void kahan(R& s, R& c, R v) {
+  if (sizeof(R) == 4) {
+    const R y = v - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+  } else {
+    s += v;
+  }
+}
+
+// psi = row ref; block 0 also writes coefs[6j + m] = theta_j^m / m!.
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_setup(C_t<R>* psi, int32_t D, int32_t ref, const double* theta, int n_ops, double* coefs) {
+  if (psi)
+    for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < D; r += gridDim.x * kSecThreads)
+      psi[r] = cmake<R>(r == ref ? R(1) : R(0), R(0));
+  if (blockIdx.x == 0)
+    for (int j = threadIdx.x; j < n_ops; j += kSecThreads) {
+      double th = theta[j], c = 1.0;
+      coefs[6 * j] = 1.0;
+      for (int m = 1; m <= 5; ++m) {
+        c = c * th / (double)m;
+        coefs[6 * j + m] = c;
+      }
+    }
+}
+
+// One Taylor step (Eq. 5, 6) of generator ops[j] in LUT form.  Each pair
+// {k, k ^ x} is handled from its base side (bit s of k clear); a pair whose
+// partner leaves the sector, or that the generator does not touch, is left
+// as is (T = I there: the coupling is exactly zero).
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_taylor(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
+             int32_t* err) {
+  const int op = ops[j];
+  if (op < 0 || op >= tb.M) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
+    return;
+  }
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
+  const uint32_t u = tb.pu[op];
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < s.D; r += gridDim.x * kSecThreads) {
+    const uint32_t k = s.kq[r];
+    if ((k >> L.s) & 1u) continue;
+    uint32_t r2;
+    if (!sec_row(s, s.occ[r], u, &r2)) continue;
+    const uint32_t ph = lut_phi(L, k);
+    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+    if (l1 == R(0) && l2 == R(0)) continue;
+    const uint32_t sg = __popc(k & L.z0) & 1u;
+    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+    C_t<R> v1 = psi[r], v2 = psi[r2];
+    C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
+#pragma unroll
+    for (int m = 1; m <= 5; ++m) {
+      const C_t<R> n1 = cscale<R>(v2, d1), n2 = cscale<R>(v1, d2);   // (A v)[k] = D(k) v[k ^ x]
+      v1 = n1;
+      v2 = n2;
+      kahan<R>(s1.x, e1.x, v1.x * c[m]);
+      kahan<R>(s1.y, e1.y, v1.y * c[m]);
+      kahan<R>(s2.x, e2.x, v2.x * c[m]);
+      kahan<R>(s2.y, e2.y, v2.y * c[m]);
+    }
+    psi[r] = csub<R>(s1, e1);
+    psi[r2] = csub<R>(s2, e2);
+  }
+}
+
+// D(k) of one term-list group, real and imaginary parts: the paired form
+// (1 + sigma (-1)^popc(k & delta)) E(k) when the group pairs, else the plain
+// sums.
+template <typename R>
+__device__ __forceinline__ void sec_term_d(const DevTables& tb, int g, uint32_t k, R* dr, R* di) {
+  const R* w = (const R*)tb.sp_w;
+  const int tb0 = tb.sp_off[g], tm = tb.sp_mid[g], te = tb.sp_off[g + 1];
+  const uint32_t delta = tb.sp_delta[g];
+  R a = 0, b = 0;
+  if (delta) {
+    const bool odd = __popc(k & delta) & 1;
+    if (tb.sp_neg[g] ? !odd : odd) {
+      *dr = R(0);
+      *di = R(0);
+      return;
+    }
+    for (int t = tb0; t < tm; ++t) a += (__popc(k & tb.sp_z[t]) & 1) ? -w[t] : w[t];
+    *dr = R(2) * a;
+    *di = R(0);
+    return;
+  }
+  for (int t = tb0; t < tm; ++t) a += (__popc(k & tb.sp_z[t]) & 1) ? -w[t] : w[t];
+  for (int t = tm; t < te; ++t) b += (__popc(k & tb.sp_z[t]) & 1) ? -w[t] : w[t];
+  *dr = a;
+  *di = b;
+}
+
+// H psi (Eq. 3) on the sector, one output row per thread, with the FP64
+// energy epilogue (Eq. 1) when partials is set: scal[1] = <psi|psi>,
+// scal[2] = Re<psi|H' psi>, scal[0] = E = identity + scal[2] / scal[1].
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_apply(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out, double identity,
+            double* partials, unsigned int* counter, double* scal) {
+  __shared__ HLut<R> s_l[kSecChunk];
+  __shared__ uint32_t s_u[kSecChunk];
+  __shared__ double tot[2];
+  const HLut<R>* hl = (const HLut<R>*)tb.hlut;
+  const R* dw = (const R*)tb.dw;
+  const R idr = (R)identity;
+  double v[2] = {0.0, 0.0};
+  for (int32_t base = blockIdx.x * kSecThreads; base < s.D; base += gridDim.x * kSecThreads) {
+    const int32_t r = base + threadIdx.x;
+    const bool live = r < s.D;
+    const uint32_t k = live ? s.kq[r] : 0u, n = live ? s.occ[r] : 0u;
+    C_t<R> acc = cmake<R>(0, 0);
+    // LUT groups, staged chunk by chunk
+    for (int g0 = 0; g0 < tb.GL; g0 += kSecChunk) {
+      const int cn = min(kSecChunk, tb.GL - g0);
+      __syncthreads();
+      for (int q = threadIdx.x; q < cn; q += kSecThreads) {
+        s_l[q] = hl[g0 + q];
+        s_u[q] = tb.hu[g0 + q];
+      }
+      __syncthreads();
+      if (!live) continue;
+      for (int q = 0; q < cn; ++q) {
+        uint32_t r2;
+        if (!sec_row(s, n, s_u[q], &r2)) continue;
+        const HLut<R>& L = s_l[q];
+        const uint32_t code = (uint32_t)(__popc(k & L.v0) & 1) | ((uint32_t)(__popc(k & L.v1) & 1) << 1) |
+                              ((uint32_t)(__popc(k & L.v2) & 1) << 2) | ((uint32_t)(__popc(k & L.z0) & 1) << 3);
+        const R val = L.lut16[code];
+        if (val == R(0)) continue;
+        const C_t<R> p = psi[r2];
+        acc.x += val * p.x;
+        acc.y += val * p.y;
+      }
+    }
+    if (live) {
+      // term-list groups
+      for (int g = 0; g < tb.G; ++g) {
+        uint32_t r2;
+        if (!sec_row(s, n, tb.gu[g], &r2)) continue;
+        R dr, di;
+        sec_term_d<R>(tb, g, k, &dr, &di);
+        if (dr == R(0) && di == R(0)) continue;
+        const C_t<R> p = psi[r2];
+        acc.x += dr * p.x - di * p.y;
+        acc.y += dr * p.y + di * p.x;
+      }
+      // diagonal group (compensated real part) and identity
+      R d = 0, dc = 0, e = 0;
+      for (int t = 0; t < tb.nd_mid; ++t) kahan<R>(d, dc, (__popc(k & tb.dz[t]) & 1) ? -dw[t] : dw[t]);
+      for (int t = tb.nd_mid; t < tb.nd; ++t) e += (__popc(k & tb.dz[t]) & 1) ? -dw[t] : dw[t];
+      const C_t<R> p = psi[r];
+      const double pp = (double)p.x * p.x + (double)p.y * p.y;
+      v[0] += pp;
+      v[1] += (double)p.x * acc.x + (double)p.y * acc.y + ((double)d - (double)dc) * pp;
+      const R d0 = d - dc + idr;
+      out[r] = cmake<R>(acc.x + d0 * p.x - e * p.y, acc.y + d0 * p.y + e * p.x);
+    }
+  }
+  if (partials && block_grid_sum<2, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, scal + 1, tot)) {
+    if (threadIdx.x == 0) scal[0] = identity + tot[1] / tot[0];
+  }
+}
+
+// lambda = (H psi - E psi) / <psi|psi> in place (E, <psi|psi> = scal[0..1]).
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_residual(const C_t<R>* psi, C_t<R>* lam, int32_t D, const double* scal) {
+  const R er = (R)scal[0], ir = (R)(1.0 / scal[1]);
+  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < D; r += gridDim.x * kSecThreads) {
+    const C_t<R> h = lam[r], p = psi[r];
+    lam[r] = cmake<R>((h.x - er * p.x) * ir, (h.y - er * p.y) * ir);
+  }
+}
+
+// Pool gradients (Eq. 4): blockIdx.y picks kSecOps generators in GOCP
+// family order, blockIdx.x a range of rows; per pair {k, k ^ x} (base side)
+//   Re<H psi|A psi> += D(k) Re(conj(h_k) psi_{k^x}) + D(k^x) Re(conj(h_{k^x}) psi_k).
+// part[i * nbx + blockIdx.x] = this block's sum for generator i (family order).
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_pool_grad(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
+                double* part, int nbx, int32_t rows_per_block) {
+  __shared__ LutDev<R> s_op[kSecOps];
+  __shared__ uint32_t s_pu[kSecOps];
+  __shared__ double s_red[kSecThreads / 32];
+  const int first = blockIdx.y * kSecOps;
+  const int nops = min(kSecOps, tb.M - first);
+  if (threadIdx.x < nops) {
+    const int op = tb.porder[first + threadIdx.x];
+    s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[op];
+    s_pu[threadIdx.x] = tb.pu[op];
+  }
+  __syncthreads();
+  const int32_t r0 = blockIdx.x * rows_per_block;
+  const int32_t r1 = min(s.D, r0 + rows_per_block);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 0; o < nops; ++o) {
+    const LutDev<R>& L = s_op[o];
+    const uint32_t u = s_pu[o], phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+    R acc = 0, cmp = 0;
+    for (int32_t r = r0 + threadIdx.x; r < r1; r += kSecThreads) {
+      const uint32_t k = s.kq[r];
+      if ((k >> L.s) & 1u) continue;
+      uint32_t r2;
+      if (!sec_row(s, s.occ[r], u, &r2)) continue;
+      const uint32_t ph = lut_phi(L, k);
+      const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+      if (l1 == R(0) && l2 == R(0)) continue;
+      const uint32_t sg = __popc(k & L.z0) & 1u;
+      const C_t<R> h1 = hpsi[r], h2 = hpsi[r2], p1 = psi[r], p2 = psi[r2];
+      const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
+                    ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
+      kahan<R>(acc, cmp, val);
+    }
+    double vv = (double)acc - (double)cmp;
+    vv = warp_sum(vv);
+    if (lane == 0) s_red[warp] = vv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kSecThreads / 32; ++w) t += s_red[w];
+      part[(size_t)(first + o) * nbx + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Backward step j of the adjoint sweep (see the full-layout k_adjoint): on
+// each touched pair inside the sector, psi <- T^-1 psi exactly,
+// dE_j += 2 Re <lambda|T' psi>, lambda <- T^dagger lambda.
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_adjoint(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
+              double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
+  __shared__ double tot[1];
+  const int op = ops[j];
+  if (op < 0 || op >= tb.M) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicOr(err, 1);
+      dtheta[j] = 0.0;
+    }
+    return;
+  }
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
+  const uint32_t u = tb.pu[op];
+  R c[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  double v[1] = {0.0};
+  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < s.D; r += gridDim.x * kSecThreads) {
+    const uint32_t k = s.kq[r];
+    if ((k >> L.s) & 1u) continue;
+    uint32_t r2;
+    if (!sec_row(s, s.occ[r], u, &r2)) continue;
+    const uint32_t ph = lut_phi(L, k);
+    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+    if (l1 == R(0) && l2 == R(0)) continue;
+    const uint32_t sg = __popc(k & L.z0) & 1u;
+    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+    const R mu = d1 * d2, mu2 = mu * mu;
+    const R cc = c[0] + c[2] * mu + c[4] * mu2;
+    const R sc = c[1] + c[3] * mu + c[5] * mu2;
+    const R cd = c[1] * mu + c[3] * mu2;
+    const R inv = R(1) / (cc * cc - sc * sc * mu);
+    const R sd1 = sc * d1, sd2 = sc * d2;
+    const C_t<R> u1 = psi[r], u2 = psi[r2];
+    const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
+    const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
+    const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
+    const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
+    const C_t<R> l1v = lam[r], l2v = lam[r2];
+    v[0] += 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x + (double)l2v.y * t2.y);
+    psi[r] = q1;
+    psi[r2] = q2;
+    lam[r] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
+    lam[r2] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
+  }
+  block_grid_sum<1, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j, tot);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_scatter(const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ full, const uint32_t* kq, int32_t D) {
+  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < D; r += gridDim.x * kSecThreads) full[kq[r]] = psi[r];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_gather(const C_t<R>* __restrict__ full, C_t<R>* __restrict__ psi, const uint32_t* kq, int32_t D) {
+  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < D; r += gridDim.x * kSecThreads) psi[r] = full[kq[r]];
+}
+
+template <typename T>
+int sec_upload(SectorTables& st, T** p, const std::vector<T>& h, size_t& bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(h.size(), 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (sector tables)");
+  st.allocs.push_back(q);
+  bytes += h.size() * sizeof(T);
+  *p = (T*)q;
+  if (h.empty()) return GOCP_OK;
+  return cuda_status(cudaMemcpy(q, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice), "cudaMemcpy (sector)");
+}
+
+int check_sector(const Problem& p) {
+  if (!p.sector || !p.sec) return fail(GOCP_EINVAL, "problem is not in the sector layout");
+  return GOCP_OK;
+}
+
+int sm_of(Problem& p) { return std::max(p.sm_count, 1); }
+
+template <typename R>
+int sec_apply_t(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st) {
+  size_t nd = 0;
+  double* scratch = scratch_ptr(p, &nd);
+  const int grid = std::min<int>(grid_rows(p.sector_dim, sm_of(p), 8), (int)(nd / 2));
+  k_sec_apply<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, dev_tables(p), (const C_t<R>*)psi, (C_t<R>*)hpsi,
+                                               p.identity, energy ? scratch : nullptr, counters_ptr(p),
+                                               scalars_ptr(p));
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_sec_apply");
+}
+
+template <typename R>
+int sec_taylor_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
+  const int grid = grid_rows(p.sector_dim, sm_of(p), 8);
+  const DevTables& tb = dev_tables(p);
+  for (int j = 0; j < n_ops; ++j) {
+    ProfScope ps(GOCP_KERNEL_TAYLOR, st);
+    k_sec_taylor<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, d_ops, coefs_ptr(p), j, (C_t<R>*)psi, err_ptr(p));
+  }
+  count_launches(n_ops);
+  return cuda_status(cudaGetLastError(), "k_sec_taylor");
+}
+
+template <typename R>
+int sec_pool_t(Problem& p, const void* psi, const void* hpsi, double* d_grads, cudaStream_t st) {
+  const DevTables& tb = dev_tables(p);
+  const int M = tb.M;
+  if (M == 0) return GOCP_OK;
+  const int nchunks = (M + kSecOps - 1) / kSecOps;
+  size_t nd = 0;
+  double* scratch = scratch_ptr(p, &nd);
+  const int32_t per = kSecThreads * kSecRowsPerThread;
+  int nbx = (int)((p.sector_dim + per - 1) / per);
+  nbx = std::max(1, std::min<int>(nbx, (int)(nd / ((size_t)nchunks * kSecOps))));
+  const int32_t rows = (int32_t)((p.sector_dim + nbx - 1) / nbx);
+  {
+    ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+    k_sec_pool_grad<R><<<dim3(nbx, nchunks), kSecThreads, 0, st>>>(p.sec->s, tb, (const C_t<R>*)psi,
+                                                                   (const C_t<R>*)hpsi, scratch, nbx, rows);
+  }
+  count_launches(1);
+  int rc = cuda_status(cudaGetLastError(), "k_sec_pool_grad");
+  if (rc) return rc;
+  return pool_finish(p, scratch, nbx, d_grads, st);
+}
+
+template <typename R>
+int sec_adjoint_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE, cudaStream_t st) {
+  const int32_t D = p.sec->s.D;
+  size_t nd = 0;
+  double* scratch = scratch_ptr(p, &nd);
+  const int g1 = grid_rows(D, sm_of(p), 8);
+  k_sec_residual<R><<<g1, kSecThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, D, scalars_ptr(p));
+  const int grid = std::min<int>(g1, (int)nd);
+  const DevTables& tb = dev_tables(p);
+  for (int j = n_ops - 1; j >= 0; --j) {
+    ProfScope ps(GOCP_KERNEL_ADJOINT, st);
+    k_sec_adjoint<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, d_ops, coefs_ptr(p), j, (C_t<R>*)psi,
+                                                   (C_t<R>*)lam, scratch, counters_ptr(p) + 2, d_dE, err_ptr(p));
+  }
+  count_launches(1 + n_ops);
+  return cuda_status(cudaGetLastError(), "k_sec_adjoint");
+}
+
+}  // namespace
+
+int upload_sector(Problem& p) {
+  if (!p.sector) return GOCP_OK;
+  if (p.n_elec < 0 || p.mapping < 0) return fail(GOCP_EINVAL, "sector layout needs a problem built from integrals");
+  const int no = p.n_qubits / 2;
+  if (no > 16) return fail(GOCP_EINVAL, "sector layout supports at most 16 spatial orbitals");
+  const int na = (p.n_elec + 1) / 2, nb = p.n_elec / 2;
+  std::vector<uint32_t> sa, sb, rank_a((size_t)1 << no, 0u), rank_b((size_t)1 << no, 0u);
+  for (uint32_t m = 0; m < (1u << no); ++m) {
+    if (__builtin_popcount(m) == na) {
+      rank_a[m] = (uint32_t)sa.size();
+      sa.push_back(m);
+    }
+    if (__builtin_popcount(m) == nb) {
+      rank_b[m] = (uint32_t)sb.size();
+      sb.push_back(m);
+    }
+  }
+  const int64_t D = (int64_t)sa.size() * (int64_t)sb.size();
+  if (D <= 0 || D > ((int64_t)1 << 30)) return fail(GOCP_EINVAL, "sector dimension out of range");
+  const Encoding enc = make_encoding(p.mapping, p.n_qubits);
+  std::vector<uint32_t> occ((size_t)D), kq((size_t)D);
+  for (size_t ia = 0; ia < sa.size(); ++ia)
+    for (size_t ib = 0; ib < sb.size(); ++ib) {
+      const size_t r = ia * sb.size() + ib;
+      uint32_t spin = 0;   // spin-orbital 2q + s
+      for (int q = 0; q < no; ++q)
+        spin |= (((sa[ia] >> q) & 1u) << (2 * q)) | (((sb[ib] >> q) & 1u) << (2 * q + 1));
+      occ[r] = sa[ia] | (sb[ib] << 16);
+      kq[r] = enc.encode(spin);
+    }
+  SectorTables* st = new SectorTables();
+  p.sec = st;
+  size_t bytes = 0;
+  uint32_t *docc, *dkq, *dra, *drb;
+  int rc;
+  if ((rc = sec_upload(*st, &docc, occ, bytes)) || (rc = sec_upload(*st, &dkq, kq, bytes)) ||
+      (rc = sec_upload(*st, &dra, rank_a, bytes)) || (rc = sec_upload(*st, &drb, rank_b, bytes)))
+    return rc;
+  st->s.D = (int32_t)D;
+  st->s.no = no;
+  st->s.na = na;
+  st->s.nb = nb;
+  st->s.cb = (uint32_t)sb.size();
+  st->s.occ = docc;
+  st->s.kq = dkq;
+  st->s.rank_a = dra;
+  st->s.rank_b = drb;
+  // the reference state: the na lowest alpha and nb lowest beta orbitals
+  st->ref_row = (int32_t)(rank_a[(1u << na) - 1u] * sb.size() + rank_b[(1u << nb) - 1u]);
+  p.sector_dim = D;
+  p.device_bytes += bytes;
+  return GOCP_OK;
+}
+
+void free_sector(Problem& p) {
+  if (!p.sec) return;
+  for (void* q : p.sec->allocs) cudaFree(q);
+  delete p.sec;
+  p.sec = nullptr;
+}
+
+int sec_setup(Problem& p, void* psi, const double* d_theta, int n_ops, void* stream) {
+  int rc = check_sector(p);
+  if (rc || (rc = ensure_stage(p, n_ops))) return rc;
+  cudaStream_t st = as_stream(stream);
+  const int grid = psi ? grid_rows(p.sector_dim, sm_of(p), 8) : 1;
+  if (p.precision == GOCP_C64)
+    k_sec_setup<float><<<grid, kSecThreads, 0, st>>>((float2*)psi, p.sec->s.D, p.sec->ref_row, d_theta, n_ops,
+                                                     coefs_ptr(p));
+  else
+    k_sec_setup<double><<<grid, kSecThreads, 0, st>>>((double2*)psi, p.sec->s.D, p.sec->ref_row, d_theta, n_ops,
+                                                      coefs_ptr(p));
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_sec_setup");
+}
+
+int sec_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* stream) {
+  int rc = check_sector(p);
+  if (rc || n_ops == 0) return rc;
+  return p.precision == GOCP_C64 ? sec_taylor_t<float>(p, d_ops, n_ops, psi, as_stream(stream))
+                                 : sec_taylor_t<double>(p, d_ops, n_ops, psi, as_stream(stream));
+}
+
+int sec_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, void* stream) {
+  int rc = check_sector(p);
+  if (rc) return rc;
+  ProfScope ps(GOCP_KERNEL_APPLY_H, as_stream(stream));
+  return p.precision == GOCP_C64 ? sec_apply_t<float>(p, psi, hpsi, energy, as_stream(stream))
+                                 : sec_apply_t<double>(p, psi, hpsi, energy, as_stream(stream));
+}
+
+int sec_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, void* stream) {
+  int rc = check_sector(p);
+  if (rc || (rc = dev_norm(p, psi, as_stream(stream)))) return rc;   // <psi|psi> -> scalars[1]
+  return p.precision == GOCP_C64 ? sec_pool_t<float>(p, psi, hpsi, d_grads, as_stream(stream))
+                                 : sec_pool_t<double>(p, psi, hpsi, d_grads, as_stream(stream));
+}
+
+int sec_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE, void* stream) {
+  int rc = check_sector(p);
+  if (rc) return rc;
+  return p.precision == GOCP_C64 ? sec_adjoint_t<float>(p, d_ops, n_ops, psi, lam, d_dE, as_stream(stream))
+                                 : sec_adjoint_t<double>(p, d_ops, n_ops, psi, lam, d_dE, as_stream(stream));
+}
+
+int sec_expand(Problem& p, const void* psi, void* full, void* stream) {
+  int rc = check_sector(p);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  const size_t elem = p.precision == GOCP_C64 ? 8u : 16u;
+  if ((rc = cuda_status(cudaMemsetAsync(full, 0, ((size_t)1 << p.n_qubits) * elem, st), "clear full state")))
+    return rc;
+  const int grid = grid_rows(p.sector_dim, sm_of(p), 8);
+  if (p.precision == GOCP_C64)
+    k_sec_scatter<float><<<grid, kSecThreads, 0, st>>>((const float2*)psi, (float2*)full, p.sec->s.kq, p.sec->s.D);
+  else
+    k_sec_scatter<double><<<grid, kSecThreads, 0, st>>>((const double2*)psi, (double2*)full, p.sec->s.kq,
+                                                        p.sec->s.D);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_sec_scatter");
+}
+
+int sec_compress(Problem& p, const void* full, void* psi, void* stream) {
+  int rc = check_sector(p);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  const int grid = grid_rows(p.sector_dim, sm_of(p), 8);
+  if (p.precision == GOCP_C64)
+    k_sec_gather<float><<<grid, kSecThreads, 0, st>>>((const float2*)full, (float2*)psi, p.sec->s.kq, p.sec->s.D);
+  else
+    k_sec_gather<double><<<grid, kSecThreads, 0, st>>>((const double2*)full, (double2*)psi, p.sec->s.kq,
+                                                       p.sec->s.D);
+  count_launches(1);
+  return cuda_status(cudaGetLastError(), "k_sec_gather");
+}
+
+}  // namespace gocp

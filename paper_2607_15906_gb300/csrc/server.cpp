@@ -452,6 +452,7 @@ int gocp_submit(gocp_server* s, const gocp_problem* h, const int32_t* ops, const
   const Problem& p = h->p;
   if (!p.dev) return fail(GOCP_ENODEV, "problem has no device tables");
   if (p.device != s->device) return fail(GOCP_EINVAL, "problem lives on another device");
+  if (p.sector) return fail(GOCP_EINVAL, "the request server takes full-layout problems only");
   if (n_ops < 0 || n_ops > kMaxOps) return fail(GOCP_EINVAL, "n_ops must be in 0..4096");
   if (n_ops > 0 && (!ops || !theta)) return fail(GOCP_EINVAL, "ops/theta is NULL");
   for (int i = 0; i < n_ops; ++i) {

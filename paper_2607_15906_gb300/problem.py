@@ -43,7 +43,9 @@ class Problem:
     @classmethod
     def build(cls, ints, n_elec: int, mapping: str = "jw", precision: str = "c64",
               int_drop: float = 0.0, term_drop: float = 0.0, device: int = 0,
-              colour: bool = True) -> "Problem":
+              colour: bool = True, sector: bool = False) -> "Problem":
+        """sector=True: states hold only the determinants with the reference
+        state's alpha and beta electron counts (gocp.h, GOCP_BUILD_SECTOR)."""
         h = np.ascontiguousarray(ints.h, dtype=np.float64)
         g = np.ascontiguousarray(ints.g, dtype=np.float64)
         a = _lib.BuildArgs(n_orb=h.shape[0], n_elec=n_elec, mapping=_MAPPINGS[mapping],
@@ -51,7 +53,8 @@ class Problem:
                            h=h.ctypes.data_as(C.POINTER(C.c_double)),
                            g=g.ctypes.data_as(C.POINTER(C.c_double)), e0=float(ints.e0),
                            int_drop=int_drop, term_drop=term_drop, device=device,
-                           flags=0 if colour else _lib.GOCP_BUILD_NO_COLOURING)
+                           flags=(0 if colour else _lib.GOCP_BUILD_NO_COLOURING)
+                           | (_lib.GOCP_BUILD_SECTOR if sector else 0))
         out = C.c_void_p()
         check(load().gocp_build(C.byref(a), C.byref(out)), "gocp_build")
         return cls(out)
@@ -105,7 +108,29 @@ class Problem:
 
     @property
     def dim(self) -> int:
-        return 1 << self.n_qubits
+        """Amplitudes per state: 2^n, or D in the sector layout."""
+        return self.info["state_dim"]
+
+    @property
+    def sector(self) -> bool:
+        return bool(self.info["sector"])
+
+    def expand(self, psi):
+        """Sector layout: the 2^n state with psi's amplitudes on the sector."""
+        full = torch.empty(1 << self.n_qubits, dtype=self.torch_dtype, device=f"cuda:{self.device}")
+        check(load().gocp_sector_expand(self._h, self._state(psi), C.c_void_p(full.data_ptr()),
+                                        _stream(self.device)), "sector_expand")
+        return full
+
+    def compress(self, full):
+        """Sector layout: the sector amplitudes of a 2^n state."""
+        if not (isinstance(full, torch.Tensor) and full.is_cuda and full.is_contiguous()
+                and full.dtype == self.torch_dtype and full.numel() >= 1 << self.n_qubits):
+            raise TypeError("full must be a contiguous CUDA state of 2^n amplitudes")
+        psi = self.new_states(1)[0]
+        check(load().gocp_sector_compress(self._h, C.c_void_p(full.data_ptr()), self._state(psi),
+                                          _stream(self.device)), "sector_compress")
+        return psi
 
     @property
     def pool_size(self) -> int:

@@ -121,6 +121,42 @@ def test_bad_arguments_are_rejected():
     assert e.value.code == -7                                     # ENODEV: host-only problem
 
 
+def test_sector_layout_dimensions_host_only():
+    """GOCP_BUILD_SECTOR: D = C(n_orb, ceil(N/2)) C(n_orb, floor(N/2)) amplitudes
+    per state; table-built problems and host-only compute calls are refused."""
+    import ctypes
+    import math
+    for n_orb, n_elec in ((2, 2), (5, 3), (7, 6), (12, 8)):
+        ints = molecular_integrals(n_orb, seed=1)
+        p = gb.Problem.build(ints, n_elec, device=-1, sector=True, colour=False)
+        d = math.comb(n_orb, (n_elec + 1) // 2) * math.comb(n_orb, n_elec // 2)
+        assert p.info["sector"] == 1 and p.info["state_dim"] == d == p.dim
+        assert (p.info["n_alpha"], p.info["n_beta"]) == ((n_elec + 1) // 2, n_elec // 2)
+        assert p.state_bytes() == 8 * d
+        f = gb.Problem.build(ints, n_elec, device=-1, colour=False)
+        assert f.info["sector"] == 0 and f.dim == 1 << (2 * n_orb)
+    with pytest.raises(gb.GocpError) as e:
+        from paper_2607_15906_gb300._lib import check, load
+        check(load().gocp_sector_expand(p.handle, ctypes.c_void_p(1), ctypes.c_void_p(2), None))
+    assert e.value.code == -7
+    from paper_2607_15906_gb300 import _lib
+    x = np.array([1], np.uint32)
+    z = np.array([0], np.uint32)
+    ph = np.array([0], np.uint8)
+    c = np.array([1.0])
+    args = _lib.TableArgs(n_qubits=2, precision=0, device=-1, flags=0, n_terms=1,
+                          x=x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                          z=z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                          phase=ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                          coeff=c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    out = ctypes.c_void_p()
+    assert load().gocp_build_from_tables(ctypes.byref(args), ctypes.byref(out)) == 0
+    load().gocp_problem_free(out)
+    args.flags = _lib.GOCP_BUILD_SECTOR                           # the same tables, sector layout
+    assert load().gocp_build_from_tables(ctypes.byref(args), ctypes.byref(out)) == -1
+    assert b"integrals" in load().gocp_last_error()
+
+
 def test_library_exports_every_declared_symbol():
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "gocp.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
