@@ -216,6 +216,65 @@ def run_gpu(args, rank, world, device):
                 h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]))
 
 
+def sector_layout(device: int, full_e: float, full_sel: int, steps: int = 10, warmup: int = 3):
+    """The same 24-qubit ADAPT step (adapt_step on the 100-operator ansatz +
+    energy_grad of the grown one) on a sector-layout problem: states of the
+    D = C(12,4)^2 = 245025 determinants with 4 alpha and 4 beta electrons
+    instead of 2^24 amplitudes (GOCP_BUILD_SECTOR).  Device-resident, CUDA
+    events; E and the selected operator are compared with the full layout."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+    from paper_2607_15906_gb300 import _lib
+
+    ints, cfg = config_integrals(WORKLOAD)
+    prob = gb.Problem.build(ints, N_ELEC, mapping="jw", precision="c64", int_drop=cfg["int_drop"],
+                            term_drop=cfg["term_drop"], device=device, sector=True)
+    ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
+    dev = f"cuda:{device}"
+    ops_d = torch.from_numpy(ops).to(dev)
+    th_d = torch.from_numpy(theta).to(dev)
+    ops_g = torch.zeros(N_OPS + 1, dtype=torch.int32, device=dev)
+    ops_g[:N_OPS] = ops_d
+    th_g = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    th_g[:N_OPS] = th_d
+    ws = prob.workspace()
+    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
+    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
+    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    e_out = torch.zeros(1, dtype=torch.float64, device=dev)
+    de_out = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-4, out=(e2, g, sel))
+        ops_g[N_OPS:].copy_(sel)
+        prob.energy_grad(ops_g, th_g, ws=ws, out_e=e_out, out_de=de_out)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    _lib.profile_enable(True)
+    for kind in range(4):
+        _lib.profile_read(kind)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    kern = {name: {"launches_per_step": v[0] / steps, "ms_per_step": v[1] / steps}
+            for name, v in ((name, _lib.profile_read(kind)) for kind, name in
+                            enumerate(["apply_h", "taylor5", "pool_grad", "adjoint"]))}
+    ms = a.elapsed_time(b) / steps
+    return {"iterations_per_s": 1e3 / ms, "ms_per_step": ms, "state_dim": prob.dim,
+            "energy": float(e2[0]), "energy_minus_full": float(e2[0]) - full_e,
+            "selected": int(sel[0]), "selected_same_as_full": int(sel[0]) == full_sel,
+            "kernels": kern, "steps": steps, "warmup": warmup,
+            "note": "GOCP_BUILD_SECTOR: same ADAPT step on the N_a = N_b = 4 determinants only"}
+
+
 def serving_bench(device: int, n_requests: int = 160, seed: int = 7):
     """Mixed-size energy+gradient stream through the continuous-batching server.
 
@@ -501,6 +560,8 @@ def main():
         kern = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                 for k, v in res["kern"].items()}
         extras = {}
+        if world == 1 and args.precision == "c64":
+            extras["sector_layout"] = sector_layout(local, res["e"], res["sel"])
         if not args.no_extras and world == 1:
             extras["serving"] = serving_bench(local)
             extras["c128_plain"] = c128_components(local)
