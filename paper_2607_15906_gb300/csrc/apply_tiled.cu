@@ -131,9 +131,11 @@ __device__ __forceinline__ bool octet_live(const uint32_t* mk, uint32_t so) {
   return (mk[so >> 5] >> (so & 31u)) & 1u;
 }
 
-// LUT groups of one x & 7 run; k0 = first global index of the thread's
-// output octet, o its octet in the tile and ao = tiled_swz(o).
-template <typename R, int XL>
+// LUT groups of one run: x & 7 == XL and flip class F (tiled_flip_class);
+// k0 = first global index of the thread's output octet, o its octet in the
+// tile and ao = tiled_swz(o).  Member i of the octet takes the LUT entry of
+// member i & F, so only the 2^popc(F) members i == i & F are looked up.
+template <typename R, int XL, int F>
 __device__ __forceinline__ void tiled_lut(const HLut<R>* ls, int cn, uint32_t k0, uint32_t o, uint32_t ao,
                                           const uint8_t* tile, const uint32_t* mk, C_t<R> (&acc)[kAmpsH]) {
   for (int g = 0; g < cn; ++g) {
@@ -142,32 +144,24 @@ __device__ __forceinline__ void tiled_lut(const HLut<R>* ls, int cn, uint32_t k0
     const uint32_t os = ao ^ L.pad0, reg = L.reg;
     const uint32_t code0 = (uint32_t)(__popc(k0 & L.v0) & 1) | ((uint32_t)(__popc(k0 & L.v1) & 1) << 1) |
                            ((uint32_t)(__popc(k0 & L.v2) & 1) << 2) | ((uint32_t)(__popc(k0 & L.z0) & 1) << 3);
-    if (reg == 0u) {
-      const R val = L.lut16[code0];
-      if (val == R(0)) continue;
-      C_t<R> src[kAmpsH];
-      tile_octet<R>(tile, os, src);
+    R val[kAmpsH];
+    bool any = false;
 #pragma unroll
-      for (int i = 0; i < kAmpsH; ++i) {
-        acc[i].x += val * src[i ^ XL].x;
-        acc[i].y += val * src[i ^ XL].y;
-      }
-    } else {
-      R val[kAmpsH];
-      bool any = false;
-#pragma unroll
-      for (int i = 0; i < kAmpsH; ++i) {
+    for (int i = 0; i < kAmpsH; ++i)
+      if ((i & F) == i) {
         val[i] = L.lut16[code0 ^ ((reg >> (4 * i)) & 0xFu)];
         any |= val[i] != R(0);
       }
-      if (!any) continue;
-      C_t<R> src[kAmpsH];
-      tile_octet<R>(tile, os, src);
 #pragma unroll
-      for (int i = 0; i < kAmpsH; ++i) {
-        acc[i].x += val[i] * src[i ^ XL].x;
-        acc[i].y += val[i] * src[i ^ XL].y;
-      }
+    for (int i = 0; i < kAmpsH; ++i)
+      if ((i & F) != i) val[i] = val[i & F];
+    if (!any) continue;   // no output of this octet couples to the group
+    C_t<R> src[kAmpsH];
+    tile_octet<R>(tile, os, src);
+#pragma unroll
+    for (int i = 0; i < kAmpsH; ++i) {
+      acc[i].x += val[i] * src[i ^ XL].x;
+      acc[i].y += val[i] * src[i ^ XL].y;
     }
   }
 }
@@ -281,16 +275,25 @@ __device__ __forceinline__ bool octet_nonzero(const C_t<R>* psi, uint32_t o) {
   return nz;
 }
 
+// With tile_flags set (zeroed before), bit t of it is set when tile t (the
+// octets o with o >> tile_shift == t) holds a nonzero amplitude.
 template <typename R>
 __global__ void __launch_bounds__(256) k_octet_mask(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2,
                                                     uint32_t n_octets, uint32_t* __restrict__ mask,
-                                                    unsigned int* tile_counter) {
+                                                    unsigned int* tile_counter, uint32_t* tile_flags,
+                                                    int tile_shift) {
   if (tile_counter && blockIdx.x == 0 && threadIdx.x == 0) *tile_counter = 0u;   // for the H psi kernel that follows
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_octets; o += gridDim.x * blockDim.x) {
     bool nz = octet_nonzero<R>(psi, o);
     if (psi2) nz |= octet_nonzero<R>(psi2, o);
     const uint32_t w = __ballot_sync(0xffffffffu, nz);
-    if ((threadIdx.x & 31u) == 0) mask[o >> 5] = w;
+    if ((threadIdx.x & 31u) == 0) {
+      mask[o >> 5] = w;
+      if (w && tile_flags) {
+        const uint32_t t = o >> tile_shift;
+        atomicOr(tile_flags + (t >> 5), 1u << (t & 31u));
+      }
+    }
   }
 }
 
@@ -300,6 +303,7 @@ struct TiledArgs {
   const TiledPiece* piece;
   const uint32_t* mask;   // nonzero-octet mask of the source state
   unsigned int* tile_counter;   // next output tile to claim (zeroed by k_octet_mask)
+  const uint32_t* tile_flags;   // bit t: source tile t holds a nonzero amplitude (k_octet_mask)
   int n_pieces;
   int n;
   const uint32_t* dz;   // diagonal group: [0, nd_mid) real, [nd_mid, nd) imaginary
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
   // passed to the consumers in s_tile; kNoTile ends the sweep.
   constexpr uint32_t kNoTile = 0xFFFFFFFFu;
   const uint32_t ntiles = 1u << (a.n - LB);
-  __shared__ uint32_t s_tile[S];
+  __shared__ uint32_t s_tile[S], s_piece[S];
   // per-thread energy partials live in shared memory (touched once per tile)
   __shared__ double2 s_v[NT];
   s_v[threadIdx.x] = make_double2(0.0, 0.0);
@@ -383,43 +387,54 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // producer state, thread 0 only: items issued, piece and tile of the next
-  uint32_t next = 0, p_next = 0, t_next = 0;
-  bool done = false;
-  const uint64_t keep = policy_evict_last();
-  // thread 0: issue item `next` into stage next % S, whose previous item
-  // every warp has released.  The stage's tile slot is written before the
-  // barrier arrive (release), so a consumer that sees the phase complete
-  // (acquire) reads it.
+  // producer state, thread 0 only, kept in shared memory (not in every
+  // thread's registers): items issued, piece and tile of the next, done
+  __shared__ uint32_t s_next, s_pnext, s_tnext, s_done;
+  if (threadIdx.x == 0) s_next = s_pnext = s_tnext = s_done = 0u;
+  // thread 0: issue item s_next into stage s_next % S, whose previous item
+  // every warp has released.  A piece whose source tile holds no nonzero
+  // amplitude adds nothing and is passed over (never the last piece of a
+  // tile, which carries the diagonal and the output).  The stage's tile and
+  // piece slots are written before the barrier arrive (release), so a
+  // consumer that sees the phase complete (acquire) reads them.
   auto issue_next = [&]() {
-    const uint32_t st = next % S;
+    const uint32_t st = s_next % S;
     const uint32_t fb = full_s + 8u * st;
-    if (p_next == 0) t_next = atomicAdd(a.tile_counter, 1u);
-    if (t_next >= ntiles) {
-      s_tile[st] = kNoTile;
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
-      done = true;
-      ++next;
-      return;
+    uint32_t p = s_pnext, t = s_tnext;
+    for (;;) {
+      if (p == 0) t = atomicAdd(a.tile_counter, 1u);
+      if (t >= ntiles) {
+        s_tile[st] = kNoTile;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+        s_done = 1u;
+        ++s_next;
+        return;
+      }
+      const uint32_t src = t ^ a.piece[p].xhi;
+      if (p + 1u == (uint32_t)a.n_pieces || !a.tile_flags || ((a.tile_flags[src >> 5] >> (src & 31u)) & 1u)) break;
+      ++p;
     }
-    s_tile[st] = t_next;
-    const TiledPiece pc = a.piece[p_next];
-    const uint32_t src = t_next ^ pc.xhi;
+    s_tile[st] = t;
+    s_piece[st] = p;
+    const TiledPiece pc = a.piece[p];
+    const uint32_t src = t ^ pc.xhi;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(fb, kTile + pc.bytes + kMask);
+    const uint64_t keep = policy_evict_last();
 #pragma unroll
     for (uint32_t c = 0; c < kRows / kBox; ++c)
       tma_rows(base_s + st * kTile + c * kBox * 128u, &tmap, (int)(src * kRows + c * kBox), fb, keep);
     if (pc.bytes) bulk_copy(base_s + kBlobOff + st * kTiledBlobBytes, a.blob + pc.off, pc.bytes, fb);
     bulk_copy(base_s + kMaskOff + st * kMask, reinterpret_cast<const uint8_t*>(a.mask) + (size_t)src * kMask, kMask,
               fb);
-    ++next;
-    if (++p_next == (uint32_t)a.n_pieces) p_next = 0;
+    ++s_next;
+    s_pnext = p + 1u == (uint32_t)a.n_pieces ? 0u : p + 1u;
+    s_tnext = t;
   };
   // Item j (j >= S) may reuse its stage once every warp has released item
   // j - S: phase (j / S - 1) of that stage's empty barrier.
   if (threadIdx.x == 0)
-    while (!done && next < (uint32_t)S) issue_next();
+    while (!s_done && s_next < (uint32_t)S) issue_next();
 
   const R idr = (R)a.identity;
   const uint32_t o = threadIdx.x, ao = tiled_swz<R>(o);
@@ -427,7 +442,6 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
 #pragma unroll
   for (int i = 0; i < kAmpsH; ++i) acc[i] = cmake<R>(0, 0);
   uint32_t it = 0, tile = 0, st = 0, ph = 0;
-  int pc = 0;
   for (;; ++it) {
     // every exit decision is warp-uniform, so that no lane leaves its warp
     // waiting in __syncwarp
@@ -436,11 +450,11 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
       // item it must be issued before anyone waits for it; later items go
       // out as soon as their stage is released
       bool ok = true;
-      while (ok && !done && next <= it) {
-        ok = mbar_wait(empty_s + 8u * (next % S), (next / S - 1u) & 1u);
+      while (ok && !s_done && s_next <= it) {
+        ok = mbar_wait(empty_s + 8u * (s_next % S), (s_next / S - 1u) & 1u);
         if (ok) issue_next();
       }
-      while (ok && !done && mbar_try(empty_s + 8u * (next % S), (next / S - 1u) & 1u)) issue_next();
+      while (ok && !s_done && mbar_try(empty_s + 8u * (s_next % S), (s_next / S - 1u) & 1u)) issue_next();
       if (!ok) s_abort = 1;
     }
     __syncwarp();
@@ -450,6 +464,7 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
     }
     tile = s_tile[st];
     if (tile == kNoTile) break;   // the same item, so the same answer, for every warp
+    const int pc = (int)s_piece[st];
     {
       const uint32_t k0 = (tile << LB) + o * kAmpsH;
       const uint8_t* tl = base + st * kTile;
@@ -465,12 +480,21 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
         const uint32_t rd = hd->run[r];
         const int g0 = (int)(rd & 0xFFFu), cn = (int)((rd >> 12) & 0xFFFu) - g0;
         switch (rd >> 24) {
-#define GOCP_CASE(XLV)                                                   \
-  case XLV: tiled_lut<R, XLV>(ls + g0, cn, k0, o, ao, tl, mk, acc); break;      \
-  case 8 + XLV: tiled_terms<R, XLV>(gs + g0, cn, zs, ws, k0, o, ao, tl, mk, acc); break;
-          GOCP_CASE(0) GOCP_CASE(1) GOCP_CASE(2) GOCP_CASE(3)
-          GOCP_CASE(4) GOCP_CASE(5) GOCP_CASE(6) GOCP_CASE(7)
-#undef GOCP_CASE
+#define GOCP_LUT_CASE(SEL)                                                                    \
+  case SEL:                                                                                   \
+    tiled_lut<R, ((SEL) & 7), ((SEL) >> 3)>(ls + g0, cn, k0, o, ao, tl, mk, acc);             \
+    break;
+#define GOCP_LUT_CASES8(F8) GOCP_LUT_CASE(F8 + 0) GOCP_LUT_CASE(F8 + 1) GOCP_LUT_CASE(F8 + 2) \
+  GOCP_LUT_CASE(F8 + 3) GOCP_LUT_CASE(F8 + 4) GOCP_LUT_CASE(F8 + 5) GOCP_LUT_CASE(F8 + 6) GOCP_LUT_CASE(F8 + 7)
+          GOCP_LUT_CASES8(0) GOCP_LUT_CASES8(8) GOCP_LUT_CASES8(16) GOCP_LUT_CASES8(24)
+          GOCP_LUT_CASES8(32) GOCP_LUT_CASES8(40) GOCP_LUT_CASES8(48) GOCP_LUT_CASES8(56)
+#undef GOCP_LUT_CASES8
+#undef GOCP_LUT_CASE
+#define GOCP_TERM_CASE(XLV) \
+  case 64 + XLV: tiled_terms<R, XLV>(gs + g0, cn, zs, ws, k0, o, ao, tl, mk, acc); break;
+          GOCP_TERM_CASE(0) GOCP_TERM_CASE(1) GOCP_TERM_CASE(2) GOCP_TERM_CASE(3)
+          GOCP_TERM_CASE(4) GOCP_TERM_CASE(5) GOCP_TERM_CASE(6) GOCP_TERM_CASE(7)
+#undef GOCP_TERM_CASE
           default: break;
         }
       }
@@ -527,13 +551,12 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
       st = 0;
       ph ^= 1u;
     }
-    if (++pc == a.n_pieces) pc = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0 && s_abort) {
     atomicOr(a.err, kErrStageTimeout);
     // let the copies this block started land before its shared memory goes
-    for (uint32_t j = it; j < next; ++j) mbar_wait(full_s + 8u * (j % S), (j / S) & 1u);
+    for (uint32_t j = it; j < s_next; ++j) mbar_wait(full_s + 8u * (j % S), (j / S) & 1u);
   }
   // (a normal exit consumed every issued item: nothing is in flight)
   const double v[2] = {s_v[threadIdx.x].x, s_v[threadIdx.x].y};
@@ -605,14 +628,17 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
                     const_cast<void*>(psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return fail(GOCP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
-  if ((rc = octet_mask(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, psi, nullptr, t.n, t.octmask, tile_counter, sm_count,
-                       st)))
+  const uint32_t flag_words = ((1u << (t.n - LB)) + 31u) / 32u;
+  if ((rc = cuda_status(cudaMemsetAsync(t.tflags, 0, flag_words * sizeof(uint32_t), st), "clear tile flags")) ||
+      (rc = octet_mask(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, psi, nullptr, t.n, t.octmask, tile_counter, sm_count,
+                       st, t.tflags, LB - 3)))
     return rc;
   TiledArgs<R> a;
   a.blob = t.tblob;
   a.piece = t.tpiece;
   a.mask = t.octmask;
   a.tile_counter = tile_counter;
+  a.tile_flags = t.tflags;
   a.n_pieces = t.n_pieces;
   a.n = t.n;
   a.dz = t.dz;
@@ -636,16 +662,18 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
 }  // namespace
 
 int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t* mask,
-               unsigned int* tile_counter, int sm_count, cudaStream_t st) {
+               unsigned int* tile_counter, int sm_count, cudaStream_t st, uint32_t* tile_flags, int tile_shift) {
   if (n < 8 || !mask) return fail(GOCP_EINVAL, "octet mask needs n >= 8 and a buffer");
   const uint32_t n_octets = 1u << (n - 3);
   const int grid = (int)std::min<uint32_t>((n_octets + 255u) / 256u, (uint32_t)std::max(sm_count, 1) * 8u);
   if (precision == GOCP_C64)
     k_octet_mask<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float2*>(psi),
-                                              reinterpret_cast<const float2*>(psi2), n_octets, mask, tile_counter);
+                                              reinterpret_cast<const float2*>(psi2), n_octets, mask, tile_counter,
+                                              tile_flags, tile_shift);
   else
     k_octet_mask<double><<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(psi),
-                                               reinterpret_cast<const double2*>(psi2), n_octets, mask, tile_counter);
+                                               reinterpret_cast<const double2*>(psi2), n_octets, mask, tile_counter,
+                                               tile_flags, tile_shift);
   count_launches(1);
   return cuda_status(cudaGetLastError(), "k_octet_mask");
 }

@@ -112,8 +112,8 @@ struct __align__(16) HLut {
 // reads the same source tile.  A piece is a contiguous blob, copied to shared
 // memory in one bulk copy beside its source tile:
 //   TiledHead | HLut<R>[n_lut] | TiledGroup[n_tg] | z[] | w[]
-// with the LUT groups and the term-list groups each sorted by (x & 7, x) and
-// cut into runs of equal x & 7.  The pieces of
+// with the LUT groups sorted by (flip class, x & 7, x), the term-list groups
+// by (x & 7, x), each list cut into runs of one kernel variant.  The pieces of
 // one high pattern follow each other; the pieces with x >> LB = 0 come last
 // (there is always one), so that the own tile is staged for the diagonal.
 #ifndef GOCP_TILED_LB_C64
@@ -124,14 +124,25 @@ template <> struct TiledBits<float> { static constexpr int LB = GOCP_TILED_LB_C6
 template <> struct TiledBits<double> { static constexpr int LB = 12; };
 constexpr uint32_t kTiledBlobBytes = 4096;    // largest piece blob
 
+constexpr int kTiledRuns = 32;   // runs per piece
 struct TiledHead {
   uint32_t n_runs, n_lut;
   uint32_t z_off, w_off;        // byte offsets of the term arrays in the blob
-  // the non-empty runs of equal x & 7: begin (bits 0..11) and end (12..23)
-  // in their list, x & 7 (24..26), list (bit 27: 0 LUT groups, 1 term lists)
-  uint32_t run[16];
+  // the non-empty runs: begin (bits 0..11) and end (12..23) in their list,
+  // and a kernel selector (24..30): 8 F + (x & 7) for LUT groups of flip
+  // class F (see tiled_flip_class), 64 + (x & 7) for term-list groups
+  uint32_t run[kTiledRuns];
 };
-static_assert(sizeof(TiledHead) == 80, "TiledHead is 80 bytes");
+static_assert(sizeof(TiledHead) == 144, "TiledHead is 144 bytes");
+
+// Flip class of an H LUT group: bit b set when the code of k0 + 2^b differs
+// from the code of k0 (nibble 2^b of HLut::reg is nonzero).  The code flip
+// of octet member i is the XOR of those of its bits, so member i has the
+// same LUT entry as member i & F.
+__host__ __device__ __forceinline__ uint32_t tiled_flip_class(uint32_t reg) {
+  return (uint32_t)(((reg >> 4) & 15u) != 0u) | ((uint32_t)(((reg >> 8) & 15u) != 0u) << 1) |
+         ((uint32_t)(((reg >> 16) & 15u) != 0u) << 2);
+}
 
 // A term-list group.  When delta != 0 its terms come in exact pairs
 // (z, w), (z ^ delta, sigma w): then D(k) = (1 + sigma (-1)^popc(k & delta)) E(k),
@@ -219,6 +230,7 @@ struct DevTables {
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
   uint32_t* octmask = nullptr;
+  uint32_t* tflags = nullptr;   // tiled form: one bit per tile (scratch)
   // second mask of the same size, for the adjoint sweep (psi and lambda)
   uint32_t* octmask2 = nullptr;
   // sector layout (see SecDev): per LUT group (hlut order), term-list group
@@ -392,10 +404,13 @@ __device__ __forceinline__ void octet_set(uint32_t* mask, uint32_t b) {
 }
 
 // mask = exact nonzero-octet mask of psi (of psi or psi2 when psi2 is set),
-// 2^(n-3) bits, n >= 8; resets *tile_counter when it is set.  Defined in
+// 2^(n-3) bits, n >= 8; resets *tile_counter when it is set; with
+// tile_flags (zeroed by the caller) also sets bit t for every tile t (octets
+// o >> tile_shift == t) holding a nonzero amplitude.  Defined in
 // apply_tiled.cu.
 int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t* mask,
-               unsigned int* tile_counter, int sm_count, cudaStream_t st);
+               unsigned int* tile_counter, int sm_count, cudaStream_t st, uint32_t* tile_flags = nullptr,
+               int tile_shift = 0);
 
 // H psi (+ the energy epilogue when partials is set) by the tiled kernel;
 // t.n_pieces must be > 0.  Defined in apply_tiled.cu.

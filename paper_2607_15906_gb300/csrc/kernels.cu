@@ -1238,15 +1238,27 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       if ((hl[g].x >> LB) == hi) ls.push_back(g);
     for (int g = 0; g < (int)gx.size(); ++g)
       if ((gx[g] >> LB) == hi) ts.push_back(g);
+    // LUT groups by kernel variant (flip class, x & 7), then x
+    auto lut_key = [&](int g) { return (int)(tiled_flip_class(hl[g].reg) * 8u + (hl[g].x & 7u)); };
+    std::stable_sort(ls.begin(), ls.end(), [&](int a, int b) { return lut_key(a) < lut_key(b); });
     size_t li = 0, ti = 0;
     do {
       std::vector<int> pl, pt;
       size_t nt = 0;
-      while (li < ls.size() && blob_size(pl.size() + 1, 0, 0) <= kTiledBlobBytes) pl.push_back(ls[li++]);
+      int lruns = 0, truns = 0;
+      while (li < ls.size() && blob_size(pl.size() + 1, 0, 0) <= kTiledBlobBytes) {
+        const bool fresh = pl.empty() || lut_key(ls[li]) != lut_key(pl.back());
+        if (fresh && lruns == kTiledRuns - 8) break;   // keep 8 runs for the term lists
+        lruns += fresh;
+        pl.push_back(ls[li++]);
+      }
       while (ti < ts.size()) {
         const int g = ts[ti];
         const size_t add = stored[g];
         if (blob_size(pl.size(), pt.size() + 1, nt + add) > kTiledBlobBytes) break;
+        const bool fresh = pt.empty() || (gx[g] & 7u) != (gx[pt.back()] & 7u);
+        if (fresh && lruns + truns == kTiledRuns) break;
+        truns += fresh;
         pt.push_back(g);
         nt += add;
         ++ti;
@@ -1260,11 +1272,11 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       h.w_off = (uint32_t)(z_off + a16(nt * 4));
       for (int kind = 0; kind < 2; ++kind) {
         const int cnt = kind == 0 ? (int)pl.size() : (int)pt.size();
-        auto xl_of = [&](int q) { return (int)((kind == 0 ? hl[pl[q]].x : gx[pt[q]]) & 7u); };
+        auto sel_of = [&](int q) { return kind == 0 ? lut_key(pl[q]) : 64 + (int)(gx[pt[q]] & 7u); };
         for (int q = 0; q < cnt;) {
           int e = q;
-          while (e < cnt && xl_of(e) == xl_of(q)) ++e;
-          h.run[h.n_runs++] = (uint32_t)q | ((uint32_t)e << 12) | ((uint32_t)xl_of(q) << 24) | ((uint32_t)kind << 27);
+          while (e < cnt && sel_of(e) == sel_of(q)) ++e;
+          h.run[h.n_runs++] = (uint32_t)q | ((uint32_t)e << 12) | ((uint32_t)sel_of(q) << 24);
           q = e;
         }
       }
@@ -1327,7 +1339,9 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   uint8_t* dblob;
   TiledPiece* dpiece;
   int rc;
-  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes))) return rc;
+  if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
+      (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)))
+    return rc;
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
   d.t.n_pieces = (int)pieces.size();
