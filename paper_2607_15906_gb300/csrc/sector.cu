@@ -22,9 +22,15 @@
 
 namespace gocp {
 
+// Per-generator pair lists: the pairs {r, r2} (r the base side, bit s of
+// its qubit state clear) that generator k touches inside the sector are
+// pairs[off[k] .. off[k+1]) (pool order), found once at build time.
 struct SectorTables {
   SecDev s;
   int32_t ref_row = 0;
+  const uint2* pairs = nullptr;
+  const int64_t* off = nullptr;     // device, M + 1
+  int64_t max_pairs = 0;            // largest list
   std::vector<void*> allocs;
 };
 
@@ -33,7 +39,7 @@ namespace {
 constexpr int kSecThreads = 256;
 constexpr int kSecChunk = 64;          // LUT groups staged per chunk (H psi)
 constexpr int kSecOps = 16;            // generators per block (pool gradients)
-constexpr int kSecRowsPerThread = 16;  // rows per thread per generator (pool gradients)
+constexpr int kSecRowsPerThread = 16;  // pairs per thread per generator (pool gradients)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -71,36 +77,31 @@ k_sec_setup(C_t<R>* psi, int32_t D, int32_t ref, const double* theta, int n_ops,
     }
 }
 
-// One Taylor step (Eq. 5, 6) of generator ops[j] in LUT form.  Each pair
-// {k, k ^ x} is handled from its base side (bit s of k clear); a pair whose
-// partner leaves the sector, or that the generator does not touch, is left
-// as is (T = I there: the coupling is exactly zero).
+// One Taylor step (Eq. 5, 6) of generator ops[j] in LUT form over its pair
+// list (the pairs it touches inside the sector; elsewhere T = I).
 template <typename R>
 __global__ void __launch_bounds__(kSecThreads)
-k_sec_taylor(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi,
-             int32_t* err) {
+k_sec_taylor(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, const int32_t* ops,
+             const double* coefs, int j, C_t<R>* psi, int32_t* err) {
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
-  const uint32_t u = tb.pu[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < s.D; r += gridDim.x * kSecThreads) {
-    const uint32_t k = s.kq[r];
-    if ((k >> L.s) & 1u) continue;
-    uint32_t r2;
-    if (!sec_row(s, s.occ[r], u, &r2)) continue;
+  const int64_t q0 = off[op], np = off[op + 1] - q0;
+  for (int64_t i = blockIdx.x * kSecThreads + threadIdx.x; i < np; i += (int64_t)gridDim.x * kSecThreads) {
+    const uint2 pr = pairs[q0 + i];
+    const uint32_t k = s.kq[pr.x];
     const uint32_t ph = lut_phi(L, k);
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    if (l1 == R(0) && l2 == R(0)) continue;
     const uint32_t sg = __popc(k & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-    C_t<R> v1 = psi[r], v2 = psi[r2];
+    C_t<R> v1 = psi[pr.x], v2 = psi[pr.y];
     C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
 #pragma unroll
     for (int m = 1; m <= 5; ++m) {
@@ -112,8 +113,8 @@ k_sec_taylor(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, in
       kahan<R>(s2.x, e2.x, v2.x * c[m]);
       kahan<R>(s2.y, e2.y, v2.y * c[m]);
     }
-    psi[r] = csub<R>(s1, e1);
-    psi[r2] = csub<R>(s2, e2);
+    psi[pr.x] = csub<R>(s1, e1);
+    psi[pr.y] = csub<R>(s2, e2);
   }
 }
 
@@ -226,42 +227,33 @@ k_sec_residual(const C_t<R>* psi, C_t<R>* lam, int32_t D, const double* scal) {
   }
 }
 
-// Pool gradients (Eq. 4): blockIdx.y picks kSecOps generators in GOCP
-// family order, blockIdx.x a range of rows; per pair {k, k ^ x} (base side)
+// Pool gradients (Eq. 4) over the pair lists: blockIdx.y picks kSecOps
+// generators in GOCP family order, blockIdx.x a slice of per_block pairs of
+// each; per pair {k, k ^ x}
 //   Re<H psi|A psi> += D(k) Re(conj(h_k) psi_{k^x}) + D(k^x) Re(conj(h_{k^x}) psi_k).
 // part[i * nbx + blockIdx.x] = this block's sum for generator i (family order).
 template <typename R>
 __global__ void __launch_bounds__(kSecThreads)
-k_sec_pool_grad(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
-                double* part, int nbx, int32_t rows_per_block) {
-  __shared__ LutDev<R> s_op[kSecOps];
-  __shared__ uint32_t s_pu[kSecOps];
+k_sec_pool_grad(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, const C_t<R>* __restrict__ psi,
+                const C_t<R>* __restrict__ hpsi, double* part, int nbx, int64_t per_block) {
   __shared__ double s_red[kSecThreads / 32];
   const int first = blockIdx.y * kSecOps;
   const int nops = min(kSecOps, tb.M - first);
-  if (threadIdx.x < nops) {
-    const int op = tb.porder[first + threadIdx.x];
-    s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[op];
-    s_pu[threadIdx.x] = tb.pu[op];
-  }
-  __syncthreads();
-  const int32_t r0 = blockIdx.x * rows_per_block;
-  const int32_t r1 = min(s.D, r0 + rows_per_block);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 0; o < nops; ++o) {
-    const LutDev<R>& L = s_op[o];
-    const uint32_t u = s_pu[o], phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+    const int op = tb.porder[first + o];
+    const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];
+    const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+    const int64_t q0 = off[op] + (int64_t)blockIdx.x * per_block;
+    const int64_t q1 = min(off[op + 1], q0 + per_block);
     R acc = 0, cmp = 0;
-    for (int32_t r = r0 + threadIdx.x; r < r1; r += kSecThreads) {
-      const uint32_t k = s.kq[r];
-      if ((k >> L.s) & 1u) continue;
-      uint32_t r2;
-      if (!sec_row(s, s.occ[r], u, &r2)) continue;
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += kSecThreads) {
+      const uint2 pr = pairs[q];
+      const uint32_t k = s.kq[pr.x];
       const uint32_t ph = lut_phi(L, k);
       const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-      if (l1 == R(0) && l2 == R(0)) continue;
       const uint32_t sg = __popc(k & L.z0) & 1u;
-      const C_t<R> h1 = hpsi[r], h2 = hpsi[r2], p1 = psi[r], p2 = psi[r2];
+      const C_t<R> h1 = hpsi[pr.x], h2 = hpsi[pr.y], p1 = psi[pr.x], p2 = psi[pr.y];
       const R val = (sg ? -l1 : l1) * (h1.x * p2.x + h1.y * p2.y) +
                     ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
       kahan<R>(acc, cmp, val);
@@ -279,13 +271,14 @@ k_sec_pool_grad(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, const C_
   }
 }
 
-// Backward step j of the adjoint sweep (see the full-layout k_adjoint): on
-// each touched pair inside the sector, psi <- T^-1 psi exactly,
-// dE_j += 2 Re <lambda|T' psi>, lambda <- T^dagger lambda.
+// Backward step j of the adjoint sweep (see the full-layout k_adjoint) over
+// the pair list of ops[j]: psi <- T^-1 psi exactly, dE_j += 2 Re <lambda|T' psi>,
+// lambda <- T^dagger lambda.
 template <typename R>
 __global__ void __launch_bounds__(kSecThreads)
-k_sec_adjoint(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
-              double* partials, unsigned int* counter, double* dtheta, int32_t* err) {
+k_sec_adjoint(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, const int32_t* ops,
+              const double* coefs, int j, C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
+              double* dtheta, int32_t* err) {
   __shared__ double tot[1];
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
@@ -296,20 +289,17 @@ k_sec_adjoint(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, i
     return;
   }
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
-  const uint32_t u = tb.pu[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const int64_t q0 = off[op], np = off[op + 1] - q0;
   double v[1] = {0.0};
-  for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < s.D; r += gridDim.x * kSecThreads) {
-    const uint32_t k = s.kq[r];
-    if ((k >> L.s) & 1u) continue;
-    uint32_t r2;
-    if (!sec_row(s, s.occ[r], u, &r2)) continue;
+  for (int64_t i = blockIdx.x * kSecThreads + threadIdx.x; i < np; i += (int64_t)gridDim.x * kSecThreads) {
+    const uint2 pr = pairs[q0 + i];
+    const uint32_t k = s.kq[pr.x];
     const uint32_t ph = lut_phi(L, k);
     const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    if (l1 == R(0) && l2 == R(0)) continue;
     const uint32_t sg = __popc(k & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
     const R mu = d1 * d2, mu2 = mu * mu;
@@ -318,17 +308,17 @@ k_sec_adjoint(SecDev s, DevTables tb, const int32_t* ops, const double* coefs, i
     const R cd = c[1] * mu + c[3] * mu2;
     const R inv = R(1) / (cc * cc - sc * sc * mu);
     const R sd1 = sc * d1, sd2 = sc * d2;
-    const C_t<R> u1 = psi[r], u2 = psi[r2];
+    const C_t<R> u1 = psi[pr.x], u2 = psi[pr.y];
     const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
     const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
     const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
     const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
-    const C_t<R> l1v = lam[r], l2v = lam[r2];
+    const C_t<R> l1v = lam[pr.x], l2v = lam[pr.y];
     v[0] += 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x + (double)l2v.y * t2.y);
-    psi[r] = q1;
-    psi[r2] = q2;
-    lam[r] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
-    lam[r2] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
+    psi[pr.x] = q1;
+    psi[pr.y] = q2;
+    lam[pr.x] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
+    lam[pr.y] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
   }
   block_grid_sum<1, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j, tot);
 }
@@ -343,6 +333,68 @@ template <typename R>
 __global__ void __launch_bounds__(kSecThreads)
 k_sec_gather(const C_t<R>* __restrict__ full, C_t<R>* __restrict__ psi, const uint32_t* kq, int32_t D) {
   for (int32_t r = blockIdx.x * kSecThreads + threadIdx.x; r < D; r += gridDim.x * kSecThreads) psi[r] = full[kq[r]];
+}
+
+// Whether row r is the base of a pair generator L touches inside the
+// sector; *r2 = the partner row.
+template <typename R>
+__device__ __forceinline__ bool sec_pair(const SecDev& s, const LutDev<R>& L, uint32_t u, int32_t r, uint32_t* r2) {
+  const uint32_t k = s.kq[r];
+  if ((k >> L.s) & 1u) return false;
+  if (!sec_row(s, s.occ[r], u, r2)) return false;
+  const uint32_t ph = lut_phi(L, k);
+  return L.lut[ph] != R(0) || L.lut[ph ^ (L.fx & 7u)] != R(0);
+}
+
+// counts[k * nchunk + c] = pairs of generator k (pool order) based in rows
+// [256 c, 256 c + 256).
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads) k_sec_pair_count(SecDev s, DevTables tb, int nchunk, int64_t* counts) {
+  __shared__ int wsum[kSecThreads / 32];
+  const int k = blockIdx.y;
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[k];
+  const uint32_t u = tb.pu[k];
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int32_t r = c * kSecThreads + threadIdx.x;
+    uint32_t r2;
+    const bool hit = r < s.D && sec_pair<R>(s, L, u, r, &r2);
+    const int n = __popc(__ballot_sync(0xffffffffu, hit));
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < kSecThreads / 32; ++w) t += wsum[w];
+      counts[(int64_t)k * nchunk + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Writes the pairs in row order at base[k * nchunk + c] (exclusive prefix
+// sums of the counts).
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_pair_fill(SecDev s, DevTables tb, int nchunk, const int64_t* base, uint2* pairs) {
+  __shared__ int wsum[kSecThreads / 32];
+  const int k = blockIdx.y;
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[k];
+  const uint32_t u = tb.pu[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int32_t r = c * kSecThreads + threadIdx.x;
+    uint32_t r2 = 0;
+    const bool hit = r < s.D && sec_pair<R>(s, L, u, r, &r2);
+    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    if (hit) {
+      const int64_t at = base[(int64_t)k * nchunk + c] + before + __popc(bal & ((1u << lane) - 1u));
+      pairs[at] = make_uint2((uint32_t)r, r2);
+    }
+    __syncthreads();
+  }
 }
 
 template <typename T>
@@ -376,13 +428,19 @@ int sec_apply_t(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream
   return cuda_status(cudaGetLastError(), "k_sec_apply");
 }
 
+int pair_grid(Problem& p, int per_sm) {
+  const int64_t need = (p.sec->max_pairs + kSecThreads - 1) / kSecThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sm_of(p) * per_sm));
+}
+
 template <typename R>
 int sec_taylor_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
-  const int grid = grid_rows(p.sector_dim, sm_of(p), 8);
+  const int grid = pair_grid(p, 8);
   const DevTables& tb = dev_tables(p);
   for (int j = 0; j < n_ops; ++j) {
     ProfScope ps(GOCP_KERNEL_TAYLOR, st);
-    k_sec_taylor<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, d_ops, coefs_ptr(p), j, (C_t<R>*)psi, err_ptr(p));
+    k_sec_taylor<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, p.sec->pairs, p.sec->off, d_ops, coefs_ptr(p), j,
+                                                  (C_t<R>*)psi, err_ptr(p));
   }
   count_launches(n_ops);
   return cuda_status(cudaGetLastError(), "k_sec_taylor");
@@ -396,14 +454,15 @@ int sec_pool_t(Problem& p, const void* psi, const void* hpsi, double* d_grads, c
   const int nchunks = (M + kSecOps - 1) / kSecOps;
   size_t nd = 0;
   double* scratch = scratch_ptr(p, &nd);
-  const int32_t per = kSecThreads * kSecRowsPerThread;
-  int nbx = (int)((p.sector_dim + per - 1) / per);
+  const int64_t per = kSecThreads * kSecRowsPerThread;
+  int nbx = (int)std::max<int64_t>(1, (p.sec->max_pairs + per - 1) / per);
   nbx = std::max(1, std::min<int>(nbx, (int)(nd / ((size_t)nchunks * kSecOps))));
-  const int32_t rows = (int32_t)((p.sector_dim + nbx - 1) / nbx);
+  const int64_t per_block = (p.sec->max_pairs + nbx - 1) / nbx;
   {
     ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
-    k_sec_pool_grad<R><<<dim3(nbx, nchunks), kSecThreads, 0, st>>>(p.sec->s, tb, (const C_t<R>*)psi,
-                                                                   (const C_t<R>*)hpsi, scratch, nbx, rows);
+    k_sec_pool_grad<R><<<dim3(nbx, nchunks), kSecThreads, 0, st>>>(p.sec->s, tb, p.sec->pairs, p.sec->off,
+                                                                   (const C_t<R>*)psi, (const C_t<R>*)hpsi, scratch,
+                                                                   nbx, std::max<int64_t>(per_block, 1));
   }
   count_launches(1);
   int rc = cuda_status(cudaGetLastError(), "k_sec_pool_grad");
@@ -416,17 +475,90 @@ int sec_adjoint_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* 
   const int32_t D = p.sec->s.D;
   size_t nd = 0;
   double* scratch = scratch_ptr(p, &nd);
-  const int g1 = grid_rows(D, sm_of(p), 8);
-  k_sec_residual<R><<<g1, kSecThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, D, scalars_ptr(p));
-  const int grid = std::min<int>(g1, (int)nd);
+  k_sec_residual<R><<<grid_rows(D, sm_of(p), 8), kSecThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, D,
+                                                                       scalars_ptr(p));
+  const int grid = std::min<int>(pair_grid(p, 2), (int)nd);
   const DevTables& tb = dev_tables(p);
   for (int j = n_ops - 1; j >= 0; --j) {
     ProfScope ps(GOCP_KERNEL_ADJOINT, st);
-    k_sec_adjoint<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, d_ops, coefs_ptr(p), j, (C_t<R>*)psi,
-                                                   (C_t<R>*)lam, scratch, counters_ptr(p) + 2, d_dE, err_ptr(p));
+    k_sec_adjoint<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, p.sec->pairs, p.sec->off, d_ops, coefs_ptr(p), j,
+                                                   (C_t<R>*)psi, (C_t<R>*)lam, scratch, counters_ptr(p) + 2, d_dE,
+                                                   err_ptr(p));
   }
   count_launches(1 + n_ops);
   return cuda_status(cudaGetLastError(), "k_sec_adjoint");
+}
+
+// Builds the per-generator pair lists (see SectorTables).
+template <typename R>
+int build_pairs(Problem& p, SectorTables& st, size_t& bytes) {
+  const DevTables& tb = dev_tables(p);
+  const int M = tb.M;
+  std::vector<int64_t> off(M + 1, 0);
+  if (M == 0) {
+    int64_t* doff;
+    int rc = sec_upload(st, &doff, off, bytes);
+    st.off = doff;
+    return rc;
+  }
+  const int nchunk = (int)((st.s.D + kSecThreads - 1) / kSecThreads);
+  const size_t nc = (size_t)M * nchunk;
+  int64_t* dcounts = nullptr;
+  cudaError_t e = cudaMalloc(&dcounts, nc * sizeof(int64_t));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (pair counts)");
+  struct Free {
+    int64_t* q;
+    ~Free() { cudaFree(q); }
+  } hold{dcounts};
+  for (int k0 = 0; k0 < M; k0 += 65535) {
+    const int mk = std::min(M - k0, 65535);
+    DevTables tk = tb;   // generators k0 .. k0 + mk - 1
+    tk.plut = (const LutDev<R>*)tb.plut + k0;
+    tk.pu = tb.pu + k0;
+    k_sec_pair_count<R><<<dim3(std::min(nchunk, 64), mk), kSecThreads>>>(st.s, tk, nchunk, dcounts + (size_t)k0 * nchunk);
+  }
+  count_launches((M + 65534) / 65535);
+  int rc = cuda_status(cudaGetLastError(), "k_sec_pair_count");
+  if (rc) return rc;
+  std::vector<int64_t> counts(nc), base(nc);
+  if ((rc = cuda_status(cudaMemcpy(counts.data(), dcounts, nc * sizeof(int64_t), cudaMemcpyDeviceToHost),
+                        "copy pair counts")))
+    return rc;
+  int64_t total = 0;
+  for (int k = 0; k < M; ++k) {
+    off[k] = total;
+    int64_t mine = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      base[(size_t)k * nchunk + c] = total + mine;
+      mine += counts[(size_t)k * nchunk + c];
+    }
+    total += mine;
+    st.max_pairs = std::max(st.max_pairs, mine);
+  }
+  off[M] = total;
+  int64_t* doff;
+  uint2* dpairs = nullptr;
+  if ((rc = cuda_status(cudaMemcpy(dcounts, base.data(), nc * sizeof(int64_t), cudaMemcpyHostToDevice),
+                        "upload pair offsets")) ||
+      (rc = sec_upload(st, &doff, off, bytes)))
+    return rc;
+  e = cudaMalloc(&dpairs, std::max<int64_t>(total, 1) * sizeof(uint2));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (pair lists)");
+  st.allocs.push_back(dpairs);
+  bytes += (size_t)total * sizeof(uint2);
+  for (int k0 = 0; k0 < M; k0 += 65535) {
+    const int mk = std::min(M - k0, 65535);
+    DevTables tk = tb;
+    tk.plut = (const LutDev<R>*)tb.plut + k0;
+    tk.pu = tb.pu + k0;
+    k_sec_pair_fill<R><<<dim3(std::min(nchunk, 64), mk), kSecThreads>>>(st.s, tk, nchunk,
+                                                                       dcounts + (size_t)k0 * nchunk, dpairs);
+  }
+  count_launches((M + 65534) / 65535);
+  if ((rc = cuda_status(cudaDeviceSynchronize(), "k_sec_pair_fill"))) return rc;
+  st.pairs = dpairs;
+  st.off = doff;
+  return GOCP_OK;
 }
 
 }  // namespace
@@ -481,6 +613,8 @@ int upload_sector(Problem& p) {
   // the reference state: the na lowest alpha and nb lowest beta orbitals
   st->ref_row = (int32_t)(rank_a[(1u << na) - 1u] * sb.size() + rank_b[(1u << nb) - 1u]);
   p.sector_dim = D;
+  if ((rc = p.precision == GOCP_C64 ? build_pairs<float>(p, *st, bytes) : build_pairs<double>(p, *st, bytes)))
+    return rc;
   p.device_bytes += bytes;
   return GOCP_OK;
 }
