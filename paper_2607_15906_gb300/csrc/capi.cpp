@@ -36,6 +36,7 @@ namespace {
 struct ProfRecord {
   int kind;
   cudaEvent_t a, b;
+  int launches;
 };
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
@@ -55,7 +56,7 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-ProfScope::ProfScope(int k, void* st) : kind(k), stream(st), start(nullptr) {
+ProfScope::ProfScope(int k, void* st, int n) : kind(k), stream(st), start(nullptr), launches(n) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
   cudaEvent_t a = take_event();
   if (a && cudaEventRecord(a, (cudaStream_t)st) == cudaSuccess) start = a;
@@ -66,7 +67,7 @@ ProfScope::~ProfScope() {
   cudaEvent_t b = take_event();
   if (!b || cudaEventRecord(b, (cudaStream_t)stream) != cudaSuccess) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  g_prof.push_back({kind, (cudaEvent_t)start, b});
+  g_prof.push_back({kind, (cudaEvent_t)start, b, launches});
 }
 
 // launchers (kernels.cu)
@@ -376,9 +377,10 @@ int gocp_export_pool(const gocp_problem* h, int64_t* off, uint32_t* x, uint32_t*
 
 void gocp_problem_free(gocp_problem* h) {
   if (!h) return;
-  if (h->p.sec) {
+  if (h->p.sec || h->p.chains) {
     DeviceGuard g(h->p.device);
     free_sector(h->p);
+    free_chains(h->p);
   }
   free_device(h->p);
   delete h;
@@ -607,7 +609,7 @@ int gocp_profile_read(int kind, int64_t* launches, double* total_ms) {
     if (rc == GOCP_OK && cudaEventSynchronize(r.b) == cudaSuccess &&
         cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
       ms += t;
-      ++n;
+      n += r.launches;
     } else {
       rc = fail(GOCP_ECUDA, "event timing failed");
     }
@@ -623,6 +625,6 @@ int gocp_profile_read(int kind, int64_t* launches, double* total_ms) {
 const char* gocp_last_error(void) { return t_last_error.c_str(); }
 int64_t gocp_launch_count(void) { return g_launches.load(); }
 // The k_apply_h revision names the kernel that profiles/traffic.json was measured on.
-const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h=tiled-tma-r12; chain=octet-mask-1; sector=pair-lists-1)"; }
+const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h=tiled-tma-r12; chain=octet-mask-1; sector=pair-lists-1; chains=graphs-1)"; }
 
 }  // extern "C"

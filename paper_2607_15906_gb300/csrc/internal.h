@@ -22,11 +22,12 @@ void count_launches(int64_t n);
 // Kernel timing (gocp_profile_*): brackets one launch with an event pair on
 // its stream while profiling is enabled.
 struct ProfScope {
-  ProfScope(int kind, void* stream);
+  ProfScope(int kind, void* stream, int launches = 1);   // `launches` kernels between the events
   ~ProfScope();
   int kind;
   void* stream;
   void* start;
+  int launches;
 };
 
 // ------------------------------------------------------------ exact sums
@@ -131,7 +132,17 @@ struct Problem {
   int n_alpha = 0, n_beta = 0;
   int64_t sector_dim = 0;
   SectorTables* sec = nullptr;
+  struct ChainCache* chains = nullptr;   // replayable launch chains (kernels.cu)
 };
+
+// A chain of n launches of one kernel whose arguments differ only in an
+// int op index (argument jidx, j = 0..n-1, or n-1..0 with reverse), launched
+// on `stream` as one replayable CUDA graph that is built on first use and
+// cached on the problem (keyed by the kernel, the grid and the bytes of the
+// other arguments).  args[i] points to argument i, sizes[i] is its size.
+int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, int n, bool reverse,
+                 void** args, const size_t* sizes, int nargs, int jidx, void* stream);
+void free_chains(Problem& p);
 
 int upload_problem(Problem& p);
 void free_device(Problem& p);

@@ -1736,6 +1736,101 @@ double* scalars_ptr(Problem& p) { return p.dev->scalars; }
 double* grads_ptr(Problem& p) { return p.dev->grads; }
 int32_t* selected_ptr(Problem& p) { return p.dev->selected; }
 int32_t* err_ptr(Problem& p) { return p.dev->err; }
+// ------------------------------------------------------------ launch chains
+
+struct ChainCache {
+  struct Entry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+  };
+  std::vector<Entry> entries;
+  uint64_t clock = 0;
+};
+constexpr size_t kChainCacheSize = 8;
+
+void free_chains(Problem& p) {
+  if (!p.chains) return;
+  for (auto& e : p.chains->entries)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  delete p.chains;
+  p.chains = nullptr;
+}
+
+namespace {
+
+// n plain launches (when a graph cannot be made)
+int launch_plain(const void* kernel, unsigned grid, unsigned block, int n, bool reverse, void** args, int jidx,
+                 cudaStream_t st) {
+  int& j = *static_cast<int*>(args[jidx]);
+  for (int i = 0; i < n; ++i) {
+    j = reverse ? n - 1 - i : i;
+    cudaError_t e = cudaLaunchKernel(kernel, dim3(grid), dim3(block), args, 0, st);
+    if (e != cudaSuccess) return cuda_status(e, "chain launch");
+  }
+  return GOCP_OK;
+}
+
+}  // namespace
+
+int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, int n, bool reverse, void** args,
+                 const size_t* sizes, int nargs, int jidx, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n <= 0) return GOCP_OK;
+  count_launches(n);
+  std::string key((const char*)&kernel, sizeof(kernel));
+  const unsigned hdr[4] = {grid, block, (unsigned)n, reverse ? 1u : 0u};
+  key.append((const char*)hdr, sizeof(hdr));
+  for (int i = 0; i < nargs; ++i)
+    if (i != jidx) key.append((const char*)args[i], sizes[i]);
+  if (!p.chains) p.chains = new ChainCache();
+  ChainCache& c = *p.chains;
+  ++c.clock;
+  for (auto& e : c.entries)
+    if (e.key == key) {
+      e.used = c.clock;
+      return cuda_status(cudaGraphLaunch(e.exec, st), "chain graph launch");
+    }
+  // build the graph: n kernel nodes in a line, node i with op index j(i)
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return launch_plain(kernel, grid, block, n, reverse, args, jidx, st);
+  }
+  int& j = *static_cast<int*>(args[jidx]);
+  const int j_saved = j;
+  cudaGraphNode_t prev = nullptr;
+  bool ok = true;
+  for (int i = 0; i < n && ok; ++i) {
+    j = reverse ? n - 1 - i : i;
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void*>(kernel);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.kernelParams = args;
+    cudaGraphNode_t node;
+    ok = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp) == cudaSuccess;
+    prev = node;
+  }
+  j = j_saved;
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    return launch_plain(kernel, grid, block, n, reverse, args, jidx, st);
+  }
+  if (c.entries.size() >= kChainCacheSize) {
+    auto lru = std::min_element(c.entries.begin(), c.entries.end(),
+                                [](const ChainCache::Entry& a, const ChainCache::Entry& b) { return a.used < b.used; });
+    cudaGraphExecDestroy(lru->exec);
+    c.entries.erase(lru);
+  }
+  c.entries.push_back({key, exec, c.clock});
+  return cuda_status(cudaGraphLaunch(exec, st), "chain graph launch");
+}
+
 // for the sector-layout launchers (sector.cu)
 const DevTables& dev_tables(Problem& p) { return p.dev->t; }
 double* coefs_ptr(Problem& p) { return p.dev->coefs; }
@@ -1784,11 +1879,17 @@ static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void
   const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (p.n_qubits - 1);
   const int grid = grid_for(pairs, d.sm_count, 8);
   uint32_t* mask = tracked && d.t.pool_lut ? d.t.octmask : nullptr;
-  for (int j = 0; j < n_ops; ++j) {
-    ProfScope ps(GOCP_KERNEL_TAYLOR, st);
-    k_taylor5<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, d.err, mask);
-  }
-  count_launches(n_ops);
+  DevTables tb = d.t;
+  const double* coefs = d.coefs;
+  int j = 0;
+  C_t<R>* ps_ = (C_t<R>*)psi;
+  int32_t* err = d.err;
+  void* args[] = {&tb, &d_ops, &coefs, &j, &ps_, &err, &mask};
+  // tb is fixed for the problem's lifetime (and the cache is the problem's): not part of the key
+  const size_t sizes[] = {0, sizeof(d_ops), sizeof(coefs), sizeof(j), sizeof(ps_), sizeof(err), sizeof(mask)};
+  ProfScope ps(GOCP_KERNEL_TAYLOR, st, n_ops);
+  int rc = launch_chain(p, (const void*)k_taylor5<R>, grid, kThreads, n_ops, false, args, sizes, 7, 3, st);
+  if (rc) return rc;
   return cuda_status(cudaGetLastError(), "k_taylor5");
 }
 
@@ -1898,12 +1999,21 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   uint32_t* mask = d.t.pool_lut ? d.t.octmask2 : nullptr;
   int rc;
   if (mask && (rc = octet_mask(p.precision, psi, lam, p.n_qubits, mask, nullptr, d.sm_count, st))) return rc;
-  for (int j = n_ops - 1; j >= 0; --j) {
-    ProfScope ps(GOCP_KERNEL_ADJOINT, st);
-    k_adjoint<R><<<grid, kThreads, 0, st>>>(d.t, d_ops, d.coefs, j, (C_t<R>*)psi, (C_t<R>*)lam,
-                                            d.scratch, d.counters + kMaxChunks + 2, d_dE, d.err, mask);
-  }
-  count_launches(1 + n_ops);
+  count_launches(1);   // k_residual (and k_octet_mask counts itself)
+  DevTables tb = d.t;
+  const double* coefs = d.coefs;
+  int j = 0;
+  C_t<R>* ps_ = (C_t<R>*)psi;
+  C_t<R>* ls_ = (C_t<R>*)lam;
+  double* partials = d.scratch;
+  unsigned int* counter = d.counters + kMaxChunks + 2;
+  int32_t* err = d.err;
+  void* args[] = {&tb, &d_ops, &coefs, &j, &ps_, &ls_, &partials, &counter, &d_dE, &err, &mask};
+  const size_t sizes[] = {0, sizeof(d_ops), sizeof(coefs), sizeof(j), sizeof(ps_), sizeof(ls_),
+                          sizeof(partials), sizeof(counter), sizeof(d_dE), sizeof(err), sizeof(mask)};
+  ProfScope ps(GOCP_KERNEL_ADJOINT, st, n_ops);
+  if ((rc = launch_chain(p, (const void*)k_adjoint<R>, grid, kThreads, n_ops, true, args, sizes, 11, 3, st)))
+    return rc;
   return cuda_status(cudaGetLastError(), "k_adjoint");
 }
 

@@ -436,13 +436,21 @@ int pair_grid(Problem& p, int per_sm) {
 template <typename R>
 int sec_taylor_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, cudaStream_t st) {
   const int grid = pair_grid(p, 8);
-  const DevTables& tb = dev_tables(p);
-  for (int j = 0; j < n_ops; ++j) {
-    ProfScope ps(GOCP_KERNEL_TAYLOR, st);
-    k_sec_taylor<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, p.sec->pairs, p.sec->off, d_ops, coefs_ptr(p), j,
-                                                  (C_t<R>*)psi, err_ptr(p));
-  }
-  count_launches(n_ops);
+  SecDev sd = p.sec->s;
+  DevTables tb = dev_tables(p);
+  const uint2* pairs = p.sec->pairs;
+  const int64_t* off = p.sec->off;
+  const double* coefs = coefs_ptr(p);
+  int j = 0;
+  C_t<R>* ps_ = (C_t<R>*)psi;
+  int32_t* err = err_ptr(p);
+  void* args[] = {&sd, &tb, &pairs, &off, &d_ops, &coefs, &j, &ps_, &err};
+  // sd and tb are fixed for the problem's lifetime: not part of the chain key
+  const size_t sizes[] = {0, 0, sizeof(pairs), sizeof(off), sizeof(d_ops), sizeof(coefs), sizeof(j), sizeof(ps_),
+                          sizeof(err)};
+  ProfScope ps(GOCP_KERNEL_TAYLOR, st, n_ops);
+  int rc = launch_chain(p, (const void*)k_sec_taylor<R>, grid, kSecThreads, n_ops, false, args, sizes, 9, 6, st);
+  if (rc) return rc;
   return cuda_status(cudaGetLastError(), "k_sec_taylor");
 }
 
@@ -477,15 +485,24 @@ int sec_adjoint_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* 
   double* scratch = scratch_ptr(p, &nd);
   k_sec_residual<R><<<grid_rows(D, sm_of(p), 8), kSecThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, D,
                                                                        scalars_ptr(p));
+  count_launches(1);   // k_sec_residual
   const int grid = std::min<int>(pair_grid(p, 2), (int)nd);
-  const DevTables& tb = dev_tables(p);
-  for (int j = n_ops - 1; j >= 0; --j) {
-    ProfScope ps(GOCP_KERNEL_ADJOINT, st);
-    k_sec_adjoint<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, tb, p.sec->pairs, p.sec->off, d_ops, coefs_ptr(p), j,
-                                                   (C_t<R>*)psi, (C_t<R>*)lam, scratch, counters_ptr(p) + 2, d_dE,
-                                                   err_ptr(p));
-  }
-  count_launches(1 + n_ops);
+  SecDev sd = p.sec->s;
+  DevTables tb = dev_tables(p);
+  const uint2* pairs = p.sec->pairs;
+  const int64_t* off = p.sec->off;
+  const double* coefs = coefs_ptr(p);
+  int j = 0;
+  C_t<R>* ps_ = (C_t<R>*)psi;
+  C_t<R>* ls_ = (C_t<R>*)lam;
+  unsigned int* counter = counters_ptr(p) + 2;
+  int32_t* err = err_ptr(p);
+  void* args[] = {&sd, &tb, &pairs, &off, &d_ops, &coefs, &j, &ps_, &ls_, &scratch, &counter, &d_dE, &err};
+  const size_t sizes[] = {0, 0, sizeof(pairs), sizeof(off), sizeof(d_ops), sizeof(coefs), sizeof(j), sizeof(ps_),
+                          sizeof(ls_), sizeof(scratch), sizeof(counter), sizeof(d_dE), sizeof(err)};
+  ProfScope ps(GOCP_KERNEL_ADJOINT, st, n_ops);
+  int rc = launch_chain(p, (const void*)k_sec_adjoint<R>, grid, kSecThreads, n_ops, true, args, sizes, 13, 6, st);
+  if (rc) return rc;
   return cuda_status(cudaGetLastError(), "k_sec_adjoint");
 }
 
