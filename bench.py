@@ -37,7 +37,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import config_integrals, draw_ansatz  # noqa: E402
+from synth import config_integrals, draw_ansatz, molecular_integrals  # noqa: E402
 
 WORKLOAD = "c5_24q"
 N_OPS = 100
@@ -273,6 +273,57 @@ def sector_layout(device: int, full_e: float, full_sel: int, steps: int = 10, wa
             "selected": int(sel[0]), "selected_same_as_full": int(sel[0]) == full_sel,
             "kernels": kern, "steps": steps, "warmup": warmup,
             "note": "GOCP_BUILD_SECTOR: same ADAPT step on the N_a = N_b = 4 determinants only"}
+
+
+def sector_30q(device: int, steps: int = 5, warmup: int = 2):
+    """Larger n in the sector layout: the same ADAPT step at 30 qubits (15
+    orbitals, 8 electrons, integrals < 1e-3 dropped, 100-operator ansatz
+    from the 2684-operator pool): D = C(15,4)^2 = 1,863,225 rows (15 MB per
+    complex64 state; the 2^30 layout would hold 8.6 GB)."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+
+    ints = molecular_integrals(15, seed=0, decay=True)
+    t0 = time.time()
+    prob = gb.Problem.build(ints, 8, mapping="jw", precision="c64", int_drop=1e-3, device=device, sector=True)
+    build_s = time.time() - t0
+    ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
+    dev = f"cuda:{device}"
+    ops_d = torch.from_numpy(ops).to(dev)
+    th_d = torch.from_numpy(theta).to(dev)
+    ops_g = torch.zeros(N_OPS + 1, dtype=torch.int32, device=dev)
+    ops_g[:N_OPS] = ops_d
+    th_g = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    th_g[:N_OPS] = th_d
+    ws = prob.workspace()
+    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
+    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
+    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    e_out = torch.zeros(1, dtype=torch.float64, device=dev)
+    de_out = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-4, out=(e2, g, sel))
+        ops_g[N_OPS:].copy_(sel)
+        prob.energy_grad(ops_g, th_g, ws=ws, out_e=e_out, out_de=de_out)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    info = prob.info
+    return {"qubits": 30, "state_dim": prob.dim, "pool": prob.pool_size, "n_terms": info["n_terms"],
+            "n_groups": info["n_groups"], "build_s": build_s, "device_bytes": info["device_bytes"],
+            "iterations_per_s": 1e3 / ms, "ms_per_step": ms, "energy": float(e2[0]), "selected": int(sel[0]),
+            "steps": steps, "warmup": warmup}
 
 
 def serving_bench(device: int, n_requests: int = 160, seed: int = 7):
@@ -566,6 +617,7 @@ def main():
             extras["serving"] = serving_bench(local)
             extras["c128_plain"] = c128_components(local)
             extras["adapt_14q"] = adapt_14q(local)
+            extras["sector_30q"] = sector_30q(local)
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

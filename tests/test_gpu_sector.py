@@ -185,3 +185,41 @@ def test_sector_rejections():
     full = gb.Problem.build(ints, 2, precision="c64", device=0)
     with pytest.raises(gb._lib.GocpError):
         full.expand(full.new_states(1)[0])
+
+
+def test_sector_28_qubits_vs_sparse_oracle():
+    """28 qubits (14 orbitals, 8 electrons, integrals < 1e-3 dropped) in the
+    sector layout: D = C(14,4)^2 = 1,002,001 rows.  E, a sample of pool
+    gradients and dE/dtheta (central differences of the oracle energy)
+    against the sparse oracle, complex64 tolerances."""
+    ints = molecular_integrals(14, seed=0, decay=True)
+    p = gb.Problem.build(ints, 8, precision="c64", int_drop=1e-3, device=0, sector=True)
+    assert p.n_qubits == 28 and p.dim == math.comb(14, 4) ** 2
+    h = mapping.hamiltonian_table(ints, "jw", 1e-3, 0.0)
+    tabs = opool.pool_tables(28, 8, "jw")
+    assert p.pool_size == len(tabs)
+    ops, th = draw_ansatz(len(tabs), 6, seed=3, theta_sigma=0.3)
+    ref = mapping.hf_index("jw", 28, 8)
+
+    def sparse_energy(theta):
+        si, sv_ = sv.prepare_state_sparse(ref, tabs, ops, theta)
+        hi, hv = sv.apply_terms_sparse(h, si, sv_)
+        return (sv.sparse_dot(si, sv_, hi, hv) / sv.sparse_dot(si, sv_, si, sv_)).real, si, sv_, hi, hv
+
+    e_ref, si, svals, hi, hv = sparse_energy(th)
+    nn = sv.sparse_dot(si, svals, si, svals).real
+    e, nrm, g, sel = p.adapt_step(ops, th, tie_rel=1e-4)
+    assert abs(e - e_ref) <= 1e-6
+    rng = np.random.default_rng(0)
+    for k in list(rng.integers(0, len(tabs), size=6)) + [sel]:
+        ai, av = sv.apply_terms_sparse(tabs[int(k)], si, svals)
+        gk = 2.0 * sv.sparse_dot(hi, hv, ai, av).real / nn
+        assert abs(g[int(k)] - gk) <= 2e-6 * max(1.0, abs(gk))
+    e2, de = p.energy_grad(ops, th)
+    assert abs(e2 - e_ref) <= 1e-6
+    for j in (0, 5):
+        tp, tm = th.copy(), th.copy()
+        tp[j] += 1e-4
+        tm[j] -= 1e-4
+        fd = (sparse_energy(tp)[0] - sparse_energy(tm)[0]) / 2e-4
+        assert abs(de[j] - fd) <= 2e-5 * max(1.0, abs(fd))
