@@ -8,6 +8,12 @@ relative ``tie_rel`` of the largest count as ties, broken by lowest pool
 index (alpha/beta mirror operators have equal |g| in exact arithmetic).
 The commuting families only schedule the gradient evaluation; selection is
 over the whole pool.
+
+With ``families`` given (the GOCP family of each pool operator, Algorithm 1)
+an iteration adds a whole commuting family instead of one operator (the
+"reduced search space" reading of Sec. III.A and IV.B): the family of the
+selected operator, restricted to its members with |g| >= family_rel * max|g|,
+appended in pool-index order, each with angle 0.
 """
 
 from __future__ import annotations
@@ -36,8 +42,17 @@ def select(grads: np.ndarray, tie_rel: float) -> int:
     return int(cand.min())
 
 
+def family_batch(grads: np.ndarray, families, k: int, family_rel: float) -> list:
+    """Members of operator k's family with |g| >= family_rel * max|g|, by index."""
+    mag = np.abs(grads)
+    fam = np.asarray(families)
+    cand = np.flatnonzero((fam == fam[k]) & (mag >= family_rel * mag.max()))
+    return [int(c) for c in cand]
+
+
 def adapt(h, pool, ref, max_ops: int = 30, gtol: float = 1e-4,
-          tie_rel: float = 1e-8, bfgs_gtol: float = 1e-8, maxiter: int = 200) -> AdaptResult:
+          tie_rel: float = 1e-8, bfgs_gtol: float = 1e-8, maxiter: int = 200,
+          families=None, family_rel: float = 0.5) -> AdaptResult:
     ops: list[int] = []
     thetas = np.zeros(0)
     energies, norms = [], []
@@ -53,8 +68,11 @@ def adapt(h, pool, ref, max_ops: int = 30, gtol: float = 1e-4,
             break
         if len(ops) >= max_ops:
             break
-        ops.append(select(g, tie_rel))
-        x0 = np.concatenate([thetas, [0.0]])
+        k = select(g, tie_rel)
+        new = [k] if families is None else family_batch(g, families, k, family_rel)
+        new = new[:max_ops - len(ops)]
+        ops.extend(new)
+        x0 = np.concatenate([thetas, np.zeros(len(new))])
 
         def fun(th, _ops=list(ops)):
             e, dg = sv.energy_grad(h, ref, pool, _ops, th)

@@ -6,6 +6,11 @@ order, argmax with a relative tie window), stops when ||g||_2 < gtol or the
 ansatz holds max_ops operators, else appends the selected operator with
 angle 0 and re-optimises all angles with BFGS, the energy and dE/dtheta of
 each evaluation coming from the adjoint sweep (gocp_energy_grad).
+
+family=True adds a whole commuting family per iteration (the "reduced search
+space" reading of GOCP, Sec. III.A and IV.B): the GOCP family of the
+selected operator, restricted to members with |g| >= family_rel * max|g|,
+appended in pool-index order with angle 0.
 """
 
 from __future__ import annotations
@@ -31,7 +36,8 @@ class AdaptRun:
 
 
 def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None = None,
-          bfgs_gtol: float = 1e-8, maxiter: int = 200, eval_budget: int | None = None) -> AdaptRun:
+          bfgs_gtol: float = 1e-8, maxiter: int = 200, eval_budget: int | None = None,
+          family: bool = False, family_rel: float = 0.5) -> AdaptRun:
     """Run ADAPT-VQE on a built problem.  tie_rel defaults to 1e-8 (c128) or
     1e-4 (c64); eval_budget caps the energy+gradient evaluations of each
     re-optimisation (None: run BFGS to bfgs_gtol / maxiter)."""
@@ -40,6 +46,9 @@ def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None 
     if tie_rel is None:
         tie_rel = 1e-8 if problem.precision == "c128" else 1e-4
     ws = problem.workspace()
+    fam = problem.pool()[5] if family else None
+    if family and np.any(fam < 0):
+        raise ValueError("family=True needs a problem built with GOCP colouring")
     ops: list[int] = []
     thetas = np.zeros(0)
     energies, norms = [], []
@@ -55,8 +64,14 @@ def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None 
             break
         if len(ops) >= max_ops:
             break
-        ops.append(int(sel))
-        x0 = np.concatenate([thetas, [0.0]])
+        if family:
+            mag = np.abs(g)
+            new = [int(c) for c in np.flatnonzero((fam == fam[int(sel)]) & (mag >= family_rel * mag.max()))]
+        else:
+            new = [int(sel)]
+        new = new[:max_ops - len(ops)]
+        ops.extend(new)
+        x0 = np.concatenate([thetas, np.zeros(len(new))])
         op_arr = np.asarray(ops, np.int32)
 
         def fun(th):

@@ -99,3 +99,23 @@ def test_adapt_14q_mapping_invariant_first_iterations():
     assert runs["jw"].ops == runs["bk"].ops
     assert np.max(np.abs(np.array(runs["jw"].energies) - np.array(runs["bk"].energies))) < 1e-9
     assert all(b <= a + 1e-12 for a, b in zip(runs["jw"].energies, runs["jw"].energies[1:]))
+
+
+@pytest.mark.parametrize("n_orb,n_elec,mp,seed", [(2, 2, "jw", 0), (2, 2, "bk", 0), (4, 4, "jw", 2), (4, 4, "bk", 2)])
+def test_family_adapt_follows_oracle(n_orb, n_elec, mp, seed):
+    """Family-batched ADAPT: the GPU driver adds the same commuting batches as
+    the oracle and reaches the same energies (complex128)."""
+    from oracle import gocp
+    from synth import molecular_integrals
+    ints = config_integrals("c1_4q")[0] if n_orb == 2 else molecular_integrals(n_orb, seed=seed)
+    n = 2 * n_orb
+    p = gb.Problem.build(ints, n_elec, mapping=mp, precision="c128", device=0)
+    run = gpu_adapt(p, max_ops=12, gtol=1e-4, family=True)
+    h = mapping.hamiltonian_table(ints, mp)
+    tabs = opool.pool_tables(n, n_elec, mp)
+    fam = gocp.gocp(tabs)
+    assert np.array_equal(p.pool()[5], fam)
+    ref = oadapt.adapt(h, tabs, sv.basis_state(n, mapping.hf_index(mp, n, n_elec)), max_ops=12, gtol=1e-4,
+                       families=fam)
+    assert run.ops == ref.ops
+    assert np.max(np.abs(np.array(run.energies) - np.array(ref.energies))) < 1e-9
