@@ -58,6 +58,11 @@ struct DeviceTables {
   int32_t* selected = nullptr;
   double* grads = nullptr;           // pool_size doubles (pool order)
   double* graw = nullptr;            // whole chunks, family order, unscaled
+  // live-octet list of the pool-gradient pass (n >= 8): 2^(n-3) entries, the
+  // per-2048-word counts and the length
+  uint32_t* live_list = nullptr;
+  uint32_t* live_counts = nullptr;
+  uint32_t* live_len = nullptr;
 };
 
 // ------------------------------------------------------------ reductions
@@ -899,6 +904,135 @@ k_pool_grad_lut(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __re
   }
 }
 
+// ---- pool gradients driven by the live octets (full layout, LUT pool)
+//
+// The octets of psi that hold a nonzero amplitude (8.85 % at 24 qubits for
+// the ADAPT states) are listed in index order (k_live_count, k_live_list);
+// a thread takes one live octet, loads its 8 amplitudes of psi and H psi
+// once, and for each generator of its block's chunk visits the octet's
+// members k = 8o + i: as the base of a pair (bit s of k clear) always, as
+// the partner only when the base octet is not live (then psi is zero there
+// and the pair has no other visitor).  Pairs with psi zero at both ends are
+// never visited; they add nothing.
+
+constexpr int kLiveWordsPerThread = 8;
+
+// counts[b] = live octets in the mask words of block b (2048 words each).
+__global__ void __launch_bounds__(kThreads) k_live_count(const uint32_t* mask, uint32_t words, uint32_t* counts) {
+  __shared__ uint32_t red[kWarps];
+  const uint32_t w0 = (blockIdx.x * kThreads + threadIdx.x) * kLiveWordsPerThread;
+  uint32_t c = 0;
+  for (int q = 0; q < kLiveWordsPerThread; ++q)
+    if (w0 + q < words) c += __popc(mask[w0 + q]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// list[...] = the live octets in index order; list_len[0] = their number.
+__global__ void __launch_bounds__(kThreads)
+k_live_list(const uint32_t* mask, uint32_t words, const uint32_t* counts, uint32_t* list, uint32_t* list_len) {
+  __shared__ uint32_t scan[kThreads];
+  __shared__ uint32_t before;
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t b = 0; b < blockIdx.x; ++b) t += counts[b];
+    before = t;
+    if (blockIdx.x == gridDim.x - 1) *list_len = t + counts[blockIdx.x];
+  }
+  const uint32_t w0 = (blockIdx.x * kThreads + threadIdx.x) * kLiveWordsPerThread;
+  uint32_t c = 0;
+  for (int q = 0; q < kLiveWordsPerThread; ++q)
+    if (w0 + q < words) c += __popc(mask[w0 + q]);
+  scan[threadIdx.x] = c;
+  __syncthreads();
+  for (int d = 1; d < kThreads; d <<= 1) {   // inclusive scan
+    const uint32_t v = threadIdx.x >= d ? scan[threadIdx.x - d] : 0u;
+    __syncthreads();
+    scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t at = before + scan[threadIdx.x] - c;
+  for (int q = 0; q < kLiveWordsPerThread; ++q) {
+    if (w0 + q >= words) break;
+    uint32_t m = mask[w0 + q];
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1u;
+      list[at++] = (w0 + q) * 32u + (uint32_t)b;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pool_grad_live(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
+                 const uint32_t* __restrict__ mask, const uint32_t* __restrict__ list,
+                 const uint32_t* __restrict__ list_len, double* part, int nbx) {
+  __shared__ LutDev<R> s_op[kOpsPerBlock];
+  __shared__ double s_red[kWarps];
+  const int first = blockIdx.y * kOpsPerBlock;
+  const int nops = min(kOpsPerBlock, tb.M - first);
+  if (threadIdx.x < nops) s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[tb.porder[first + threadIdx.x]];
+  __syncthreads();
+  const uint32_t n_live = *list_len;
+  const uint32_t per = (n_live + nbx - 1) / nbx;
+  const uint32_t l0 = blockIdx.x * per, l1 = min(n_live, l0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 0; o < nops; ++o) {
+    const LutDev<R>& L = s_op[o];
+    const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+    R acc = 0, cmp = 0;
+    for (uint32_t l = l0 + threadIdx.x; l < l1; l += kThreads) {
+      const uint32_t k0 = list[l] * kAmpsH;
+      R a = 0;
+#pragma unroll
+      for (int i = 0; i < kAmpsH; ++i) {
+        const uint32_t k = k0 + i;
+        const uint32_t ph = lut_phi(L, k), sg = __popc(k & L.z0) & 1u;
+        if (!((k >> L.s) & 1u)) {
+          // k is the base of pair (k, k ^ x)
+          const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+          if (l1 == R(0) && l2 == R(0)) continue;
+          const uint32_t kp = k ^ L.x;
+          const C_t<R> pk = psi[k], hk = hpsi[k], pp = psi[kp], hp = hpsi[kp];
+          a += (sg ? -l1 : l1) * (hk.x * pp.x + hk.y * pp.y) + ((sg ^ sgx) ? -l2 : l2) * (hp.x * pk.x + hp.y * pk.y);
+        } else {
+          // k is the partner of base b = k ^ x: visited here only when b's octet is not live (psi_b = 0)
+          const uint32_t b = k ^ L.x;
+          if (octet_bit(mask, b)) continue;
+          const uint32_t phb = ph ^ phx, sgb = sg ^ sgx;
+          const R l1 = L.lut[phb];
+          if (l1 == R(0)) continue;
+          const C_t<R> pk = psi[k], hb = hpsi[b];
+          a += (sgb ? -l1 : l1) * (hb.x * pk.x + hb.y * pk.y);
+        }
+      }
+      if (sizeof(R) == 4) {
+        const R y = a - cmp, t = acc + y;
+        cmp = (t - acc) - y;
+        acc = t;
+      } else {
+        acc += a;
+      }
+    }
+    const double v = warp_sum((double)acc - (double)cmp);
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      part[(size_t)(first + o) * nbx + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
 // raw[i] = sum over the nbx block partials of operator i (family order), in
 // a fixed order: one warp per operator.
 __global__ void k_pool_reduce(const double* part, int nbx, int m, double* raw) {
@@ -1666,9 +1800,14 @@ int upload_problem(Problem& p) {
   p.dev = d;
   size_t bytes = 0;
   int rc;
-  if (p.n_qubits >= 8 && ((rc = dalloc(*d, &d->t.octmask, (size_t)1 << (p.n_qubits - 8), bytes)) ||
-                          (rc = dalloc(*d, &d->t.octmask2, (size_t)1 << (p.n_qubits - 8), bytes))))
-    return rc;
+  if (p.n_qubits >= 8) {
+    const size_t words = (size_t)1 << (p.n_qubits - 8);
+    const size_t blocks = (words + kThreads * kLiveWordsPerThread - 1) / (kThreads * kLiveWordsPerThread);
+    if ((rc = dalloc(*d, &d->t.octmask, words, bytes)) || (rc = dalloc(*d, &d->t.octmask2, words, bytes)) ||
+        (rc = dalloc(*d, &d->live_list, words * 32, bytes)) || (rc = dalloc(*d, &d->live_counts, blocks, bytes)) ||
+        (rc = dalloc(*d, &d->live_len, 1, bytes)))
+      return rc;
+  }
   rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
                                : upload_typed<double>(p, *d, bytes, &p.identity);
   if (rc) return rc;
@@ -1958,13 +2097,31 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
     if (mask && !mask_current &&
         (rc = octet_mask(p.precision, psi, nullptr, p.n_qubits, d.t.octmask, nullptr, d.sm_count, st)))
       return rc;
-    {
-      ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
-      k_pool_grad_lut<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
-                                                    d.scratch, nbx, mask);
+    if (mask) {
+      // the live octets of psi, in index order, then one pass over them
+      const uint32_t words = 1u << (p.n_qubits - 8);
+      const int nb = (int)((words + kThreads * kLiveWordsPerThread - 1) / (kThreads * kLiveWordsPerThread));
+      k_live_count<<<nb, kThreads, 0, st>>>(mask, words, d.live_counts);
+      k_live_list<<<nb, kThreads, 0, st>>>(mask, words, d.live_counts, d.live_list, d.live_len);
+      const uint64_t octets = 1ull << (p.n_qubits - 3);
+      int lnbx = (int)std::max<uint64_t>(1, std::min<uint64_t>(64, (octets + kThreads * 64 - 1) / (kThreads * 64)));
+      lnbx = std::max(1, std::min<int>(lnbx, (int)(d.scratch_doubles / ((size_t)nchunks * kOpsPerBlock))));
+      {
+        ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+        k_pool_grad_live<R><<<dim3(lnbx, nchunks), kThreads, 0, st>>>(
+            d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi, mask, d.live_list, d.live_len, d.scratch, lnbx);
+      }
+      k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, lnbx, M, d.graw);
+      n += 3;
+    } else {
+      {
+        ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+        k_pool_grad_lut<R><<<grid, kThreads, 0, st>>>(d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi,
+                                                      d.scratch, nbx, mask);
+      }
+      k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, nbx, M, d.graw);
+      ++n;
     }
-    k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, nbx, M, d.graw);
-    ++n;
   } else {
     dim3 grid(pool_grid_x(d), nchunks);
     ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
