@@ -206,6 +206,63 @@ def test_random_tables_with_phases(prec, n):
     assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
 
 
+def _grouped_random_table(n, rng):
+    """A Hermitian table with x-groups of 1..40 terms (z-ranks from 0 to
+    beyond the LUT limit), real and imaginary weights, a diagonal group, and
+    one exactly paired group (z, w), (z ^ x, -w) of the one-body form (x of
+    even weight, as e_p ^ e_q: then both partners are Hermitian with weights
+    on the same axis)."""
+    xs, zs = [], []
+    for size in [1, 2, 3, 4, 6, 8, 9, 12, 17, 25, 40, 5, 7]:
+        x = int(rng.integers(1, 1 << n))
+        xs += [x] * size
+        zs += list(rng.integers(0, 1 << n, size=size))
+    xs += [0] * 20                                     # diagonal group
+    zs += list(rng.integers(0, 1 << n, size=20))
+    x, z = np.array(xs, np.int64), np.array(zs, np.int64)
+    ph = parity(x & z) + 2 * rng.integers(0, 2, size=len(x))     # c i^ph X^x Z^z Hermitian
+    c = rng.normal(size=len(x))
+    q = rng.choice(n, size=2, replace=False)           # paired group: x = e_q0 ^ e_q1
+    xp = (1 << int(q[0])) | (1 << int(q[1]))
+    zp = rng.integers(0, 1 << n, size=10)
+    zp = zp[(zp & xp) != xp]                           # one of each pair {z, z ^ x}
+    zp = np.unique(np.where((zp >> int(q.min())) & 1, zp ^ xp, zp))
+    php = parity(xp & zp) + 2 * rng.integers(0, 2, size=len(zp))
+    cp = rng.normal(size=len(zp))
+    x = np.concatenate([x, np.full(2 * len(zp), xp, np.int64)])
+    z = np.concatenate([z, zp, zp ^ xp])
+    ph = np.concatenate([ph, php, php ^ 2])            # partner: same c, opposite sign
+    c = np.concatenate([c, cp, cp])
+    return PauliTable(n, x, z, ph.astype(np.int64), c)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [12, 13, 15, 16])
+def test_tiled_h_random_grouped_tables(prec, n):
+    """H psi through the shared-memory tiled kernel (one tile at n = 12
+    complex128 / 13 complex64, several above): LUT groups, term lists with
+    imaginary weights, a paired group, x masks over all bits; a dense random
+    state (no octet is skipped) and a sparse one (most octets skipped)."""
+    rng = np.random.default_rng(100 + n)
+    H = _grouped_random_table(n, rng)
+    to_t = lambda t: (t.x.astype(np.uint32), t.z.astype(np.uint32), (t.phase % 4).astype(np.uint8), t.coeff)
+    p = gb.Problem.from_tables(n, to_t(H), [], ref_index=0, precision=prec, device=0)
+    for kind in ("dense", "sparse"):
+        psi = random_state(n, seed=7 * n)
+        if kind == "sparse":
+            keep = np.zeros(1 << n, bool)
+            keep[np.random.default_rng(n).integers(0, 1 << n, size=40)] = True
+            psi = np.where(keep, psi, 0)
+        d = _to_dev(p, psi)
+        psi_in = _host(d)
+        hd = torch.empty_like(d)
+        e, nrm = p.energy(d, hd)
+        ref = sv.apply_terms(H, psi_in)
+        assert np.max(np.abs(_host(hd) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 4
+        e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
+        assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
+
+
 def test_empty_ansatz_gives_reference_energy():
     ints, h, tabs = _case(4, 4, "bk", 1)
     p = gb.Problem.build(ints, 4, mapping="bk", precision="c128", device=0)
