@@ -31,6 +31,13 @@ struct SectorTables {
   const uint2* pairs = nullptr;
   const int64_t* off = nullptr;     // device, M + 1
   int64_t max_pairs = 0;            // largest list
+  // H on the sector as CSR (built when its couplings are real and it fits
+  // kCsrMaxBytes; else H psi stays matrix-free): rows ptr[r] .. ptr[r+1]
+  const int64_t* csr_ptr = nullptr;
+  const uint32_t* csr_col = nullptr;
+  const void* csr_val = nullptr;
+  const double* csr_diag = nullptr;
+  int64_t csr_nnz = 0;
   std::vector<void*> allocs;
 };
 
@@ -40,6 +47,7 @@ constexpr int kSecThreads = 256;
 constexpr int kSecChunk = 64;          // LUT groups staged per chunk (H psi)
 constexpr int kSecOps = 16;            // generators per block (pool gradients)
 constexpr int kSecRowsPerThread = 16;  // pairs per thread per generator (pool gradients)
+constexpr size_t kCsrMaxBytes = (size_t)8 << 30;   // largest CSR form of H built
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -145,6 +153,44 @@ __device__ __forceinline__ void sec_term_d(const DevTables& tb, int g, uint32_t 
   *di = b;
 }
 
+// The off-diagonal couplings of one output row (qubit state k, occupation
+// n): f(r2, dr, di) for every group whose source row r2 is in the sector and
+// whose D(k) = dr + i di is not zero -- LUT groups first (staged kSecChunk at
+// a time in shared memory, so every thread of the block must call this),
+// then the term-list groups.
+template <typename R, typename F>
+__device__ __forceinline__ void sec_walk(const SecDev& s, const DevTables& tb, HLut<R>* s_l, uint32_t* s_u,
+                                         bool live, uint32_t k, uint32_t n, F&& f) {
+  const HLut<R>* hl = (const HLut<R>*)tb.hlut;
+  for (int g0 = 0; g0 < tb.GL; g0 += kSecChunk) {
+    const int cn = min(kSecChunk, tb.GL - g0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cn; q += kSecThreads) {
+      s_l[q] = hl[g0 + q];
+      s_u[q] = tb.hu[g0 + q];
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int q = 0; q < cn; ++q) {
+      uint32_t r2;
+      if (!sec_row(s, n, s_u[q], &r2)) continue;
+      const HLut<R>& L = s_l[q];
+      const uint32_t code = (uint32_t)(__popc(k & L.v0) & 1) | ((uint32_t)(__popc(k & L.v1) & 1) << 1) |
+                            ((uint32_t)(__popc(k & L.v2) & 1) << 2) | ((uint32_t)(__popc(k & L.z0) & 1) << 3);
+      const R val = L.lut16[code];
+      if (val != R(0)) f(r2, val, R(0));
+    }
+  }
+  if (!live) return;
+  for (int g = 0; g < tb.G; ++g) {
+    uint32_t r2;
+    if (!sec_row(s, n, tb.gu[g], &r2)) continue;
+    R dr, di;
+    sec_term_d<R>(tb, g, k, &dr, &di);
+    if (dr != R(0) || di != R(0)) f(r2, dr, di);
+  }
+}
+
 // H psi (Eq. 3) on the sector, one output row per thread, with the FP64
 // energy epilogue (Eq. 1) when partials is set: scal[1] = <psi|psi>,
 // scal[2] = Re<psi|H' psi>, scal[0] = E = identity + scal[2] / scal[1].
@@ -155,7 +201,6 @@ k_sec_apply(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __re
   __shared__ HLut<R> s_l[kSecChunk];
   __shared__ uint32_t s_u[kSecChunk];
   __shared__ double tot[2];
-  const HLut<R>* hl = (const HLut<R>*)tb.hlut;
   const R* dw = (const R*)tb.dw;
   const R idr = (R)identity;
   double v[2] = {0.0, 0.0};
@@ -164,41 +209,12 @@ k_sec_apply(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __re
     const bool live = r < s.D;
     const uint32_t k = live ? s.kq[r] : 0u, n = live ? s.occ[r] : 0u;
     C_t<R> acc = cmake<R>(0, 0);
-    // LUT groups, staged chunk by chunk
-    for (int g0 = 0; g0 < tb.GL; g0 += kSecChunk) {
-      const int cn = min(kSecChunk, tb.GL - g0);
-      __syncthreads();
-      for (int q = threadIdx.x; q < cn; q += kSecThreads) {
-        s_l[q] = hl[g0 + q];
-        s_u[q] = tb.hu[g0 + q];
-      }
-      __syncthreads();
-      if (!live) continue;
-      for (int q = 0; q < cn; ++q) {
-        uint32_t r2;
-        if (!sec_row(s, n, s_u[q], &r2)) continue;
-        const HLut<R>& L = s_l[q];
-        const uint32_t code = (uint32_t)(__popc(k & L.v0) & 1) | ((uint32_t)(__popc(k & L.v1) & 1) << 1) |
-                              ((uint32_t)(__popc(k & L.v2) & 1) << 2) | ((uint32_t)(__popc(k & L.z0) & 1) << 3);
-        const R val = L.lut16[code];
-        if (val == R(0)) continue;
-        const C_t<R> p = psi[r2];
-        acc.x += val * p.x;
-        acc.y += val * p.y;
-      }
-    }
+    sec_walk<R>(s, tb, s_l, s_u, live, k, n, [&](uint32_t r2, R dr, R di) {
+      const C_t<R> p = psi[r2];
+      acc.x += dr * p.x - di * p.y;
+      acc.y += dr * p.y + di * p.x;
+    });
     if (live) {
-      // term-list groups
-      for (int g = 0; g < tb.G; ++g) {
-        uint32_t r2;
-        if (!sec_row(s, n, tb.gu[g], &r2)) continue;
-        R dr, di;
-        sec_term_d<R>(tb, g, k, &dr, &di);
-        if (dr == R(0) && di == R(0)) continue;
-        const C_t<R> p = psi[r2];
-        acc.x += dr * p.x - di * p.y;
-        acc.y += dr * p.y + di * p.x;
-      }
       // diagonal group (compensated real part) and identity
       R d = 0, dc = 0, e = 0;
       for (int t = 0; t < tb.nd_mid; ++t) kahan<R>(d, dc, (__popc(k & tb.dz[t]) & 1) ? -dw[t] : dw[t]);
@@ -209,6 +225,77 @@ k_sec_apply(SecDev s, DevTables tb, const C_t<R>* __restrict__ psi, C_t<R>* __re
       v[1] += (double)p.x * acc.x + (double)p.y * acc.y + ((double)d - (double)dc) * pp;
       const R d0 = d - dc + idr;
       out[r] = cmake<R>(acc.x + d0 * p.x - e * p.y, acc.y + d0 * p.y + e * p.x);
+    }
+  }
+  if (partials && block_grid_sum<2, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, scal + 1, tot)) {
+    if (threadIdx.x == 0) scal[0] = identity + tot[1] / tot[0];
+  }
+}
+
+// The sector's H as a CSR matrix (real couplings only): FILL = false writes
+// the row counts, FILL = true the columns and values in walk order at
+// ptr[r] and the diagonal D_0(k) (without the identity) summed in FP64.
+template <typename R, bool FILL>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_csr(SecDev s, DevTables tb, int64_t* ptr_or_count, uint32_t* cols, R* vals, double* diag) {
+  __shared__ HLut<R> s_l[kSecChunk];
+  __shared__ uint32_t s_u[kSecChunk];
+  const R* dw = (const R*)tb.dw;
+  for (int32_t base = blockIdx.x * kSecThreads; base < s.D; base += gridDim.x * kSecThreads) {
+    const int32_t r = base + threadIdx.x;
+    const bool live = r < s.D;
+    const uint32_t k = live ? s.kq[r] : 0u, n = live ? s.occ[r] : 0u;
+    int64_t pos = (FILL && live) ? ptr_or_count[r] : 0;
+    sec_walk<R>(s, tb, s_l, s_u, live, k, n, [&](uint32_t r2, R dr, R) {
+      if (FILL) {
+        cols[pos] = r2;
+        vals[pos] = dr;
+      }
+      ++pos;
+    });
+    if (!live) continue;
+    if (FILL) {
+      double d = 0.0;
+      for (int t = 0; t < tb.nd_mid; ++t) d += (__popc(k & tb.dz[t]) & 1) ? -(double)dw[t] : (double)dw[t];
+      diag[r] = d;
+    } else {
+      ptr_or_count[r] = pos;
+    }
+  }
+}
+
+// H psi from the CSR form, one warp per row, with the energy epilogue.
+template <typename R>
+__global__ void __launch_bounds__(kSecThreads)
+k_sec_spmv(int32_t D, const int64_t* __restrict__ ptr, const uint32_t* __restrict__ cols, const R* __restrict__ vals,
+           const double* __restrict__ diag, const C_t<R>* __restrict__ psi, C_t<R>* __restrict__ out,
+           double identity, double* partials, unsigned int* counter, double* scal) {
+  __shared__ double tot[2];
+  const int lane = threadIdx.x & 31;
+  const int32_t warps = gridDim.x * (kSecThreads / 32);
+  double v[2] = {0.0, 0.0};
+  for (int32_t r = blockIdx.x * (kSecThreads / 32) + (threadIdx.x >> 5); r < D; r += warps) {
+    const int64_t q0 = ptr[r], q1 = ptr[r + 1];
+    R ax = 0, ay = 0, cx = 0, cy = 0;   // compensated lane sums (FP32)
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const R w = vals[q];
+      const C_t<R> p = psi[cols[q]];
+      kahan<R>(ax, cx, w * p.x);
+      kahan<R>(ay, cy, w * p.y);
+    }
+    ax -= cx;
+    ay -= cy;
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if (lane == 0) {
+      const C_t<R> p = psi[r];
+      const double pp = (double)p.x * p.x + (double)p.y * p.y, d = diag[r];
+      v[0] += pp;
+      v[1] += (double)p.x * ax + (double)p.y * ay + d * pp;
+      const R d0 = (R)(d + identity);
+      out[r] = cmake<R>(ax + d0 * p.x, ay + d0 * p.y);
     }
   }
   if (partials && block_grid_sum<2, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, scal + 1, tot)) {
@@ -420,6 +507,15 @@ template <typename R>
 int sec_apply_t(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st) {
   size_t nd = 0;
   double* scratch = scratch_ptr(p, &nd);
+  if (p.sec->csr_val) {
+    const int32_t D = p.sec->s.D;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({(D + 7) / 8, (int64_t)sm_of(p) * 16, (int64_t)nd / 2}));
+    k_sec_spmv<R><<<grid, kSecThreads, 0, st>>>(D, p.sec->csr_ptr, p.sec->csr_col, (const R*)p.sec->csr_val,
+                                                p.sec->csr_diag, (const C_t<R>*)psi, (C_t<R>*)hpsi, p.identity,
+                                                energy ? scratch : nullptr, counters_ptr(p), scalars_ptr(p));
+    count_launches(1);
+    return cuda_status(cudaGetLastError(), "k_sec_spmv");
+  }
   const int grid = std::min<int>(grid_rows(p.sector_dim, sm_of(p), 8), (int)(nd / 2));
   k_sec_apply<R><<<grid, kSecThreads, 0, st>>>(p.sec->s, dev_tables(p), (const C_t<R>*)psi, (C_t<R>*)hpsi,
                                                p.identity, energy ? scratch : nullptr, counters_ptr(p),
@@ -504,6 +600,62 @@ int sec_adjoint_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* 
   int rc = launch_chain(p, (const void*)k_sec_adjoint<R>, grid, kSecThreads, n_ops, true, args, sizes, 13, 6, st);
   if (rc) return rc;
   return cuda_status(cudaGetLastError(), "k_sec_adjoint");
+}
+
+// Builds the CSR form of H on the sector (see SectorTables) when every
+// coupling is real and it fits kCsrMaxBytes; leaves it absent otherwise.
+template <typename R>
+int build_csr(Problem& p, SectorTables& st, size_t& bytes) {
+  for (size_t t = 0; t < p.H.size(); ++t)
+    if (p.H.phase[t] & 1) return GOCP_OK;   // an imaginary weight: stay matrix-free
+  const DevTables& tb = dev_tables(p);
+  const int32_t D = st.s.D;
+  int64_t* dptr = nullptr;
+  cudaError_t e = cudaMalloc(&dptr, ((size_t)D + 1) * sizeof(int64_t));
+  if (e != cudaSuccess) return cuda_status(e, "cudaMalloc (CSR rows)");
+  const int grid = grid_rows(D, sm_of(p), 8);
+  k_sec_csr<R, false><<<grid, kSecThreads>>>(st.s, tb, dptr, nullptr, nullptr, nullptr);
+  count_launches(1);
+  std::vector<int64_t> ptr((size_t)D + 1, 0);
+  int rc = cuda_status(cudaMemcpy(ptr.data(), dptr, (size_t)D * sizeof(int64_t), cudaMemcpyDeviceToHost),
+                       "copy CSR counts");
+  int64_t nnz = 0;
+  for (int32_t r = 0; r < D; ++r) {
+    const int64_t c = ptr[r];
+    ptr[r] = nnz;
+    nnz += c;
+  }
+  ptr[D] = nnz;
+  if (rc || (size_t)nnz * (4 + sizeof(R)) > kCsrMaxBytes) {
+    cudaFree(dptr);
+    return rc;
+  }
+  st.allocs.push_back(dptr);
+  uint32_t* dcol = nullptr;
+  R* dval = nullptr;
+  double* ddiag = nullptr;
+  if ((rc = cuda_status(cudaMemcpy(dptr, ptr.data(), ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
+                        "upload CSR rows")))
+    return rc;
+  if ((e = cudaMalloc(&dcol, std::max<int64_t>(nnz, 1) * sizeof(uint32_t))) != cudaSuccess)
+    return cuda_status(e, "cudaMalloc (CSR columns)");
+  st.allocs.push_back(dcol);
+  if ((e = cudaMalloc(&dval, std::max<int64_t>(nnz, 1) * sizeof(R))) != cudaSuccess)
+    return cuda_status(e, "cudaMalloc (CSR values)");
+  st.allocs.push_back(dval);
+  if ((e = cudaMalloc(&ddiag, (size_t)D * sizeof(double))) != cudaSuccess)
+    return cuda_status(e, "cudaMalloc (CSR diagonal)");
+  st.allocs.push_back(ddiag);
+  k_sec_csr<R, true><<<grid, kSecThreads>>>(st.s, tb, dptr, dcol, dval, ddiag);
+  count_launches(1);
+  if ((rc = cuda_status(cudaDeviceSynchronize(), "k_sec_csr"))) return rc;
+  bytes += ((size_t)D + 1) * 8 + (size_t)nnz * (4 + sizeof(R)) + (size_t)D * 8;
+  st.csr_ptr = dptr;
+  st.csr_col = dcol;
+  st.csr_val = dval;
+  st.csr_diag = ddiag;
+  st.csr_nnz = nnz;
+  return GOCP_OK;
 }
 
 // Builds the per-generator pair lists (see SectorTables).
@@ -631,6 +783,8 @@ int upload_sector(Problem& p) {
   st->ref_row = (int32_t)(rank_a[(1u << na) - 1u] * sb.size() + rank_b[(1u << nb) - 1u]);
   p.sector_dim = D;
   if ((rc = p.precision == GOCP_C64 ? build_pairs<float>(p, *st, bytes) : build_pairs<double>(p, *st, bytes)))
+    return rc;
+  if ((rc = p.precision == GOCP_C64 ? build_csr<float>(p, *st, bytes) : build_csr<double>(p, *st, bytes)))
     return rc;
   p.device_bytes += bytes;
   return GOCP_OK;
