@@ -32,7 +32,8 @@ struct SectorTables {
   const int64_t* off = nullptr;     // device, M + 1
   int64_t max_pairs = 0;            // largest list
   // H on the sector as CSR (built when its couplings are real and it fits
-  // kCsrMaxBytes; else H psi stays matrix-free): rows ptr[r] .. ptr[r+1]
+  // kCsrMaxBytes and a quarter of the free device memory; else H psi stays
+  // matrix-free): rows ptr[r] .. ptr[r+1]
   const int64_t* csr_ptr = nullptr;
   const uint32_t* csr_col = nullptr;
   const void* csr_val = nullptr;
@@ -47,7 +48,7 @@ constexpr int kSecThreads = 256;
 constexpr int kSecChunk = 64;          // LUT groups staged per chunk (H psi)
 constexpr int kSecOps = 16;            // generators per block (pool gradients)
 constexpr int kSecRowsPerThread = 16;  // pairs per thread per generator (pool gradients)
-constexpr size_t kCsrMaxBytes = (size_t)8 << 30;   // largest CSR form of H built
+constexpr size_t kCsrMaxBytes = (size_t)64 << 30;  // largest CSR form of H built (and <= 1/4 of free memory)
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -603,7 +604,8 @@ int sec_adjoint_t(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* 
 }
 
 // Builds the CSR form of H on the sector (see SectorTables) when every
-// coupling is real and it fits kCsrMaxBytes; leaves it absent otherwise.
+// coupling is real and it fits kCsrMaxBytes and a quarter of the free device
+// memory; leaves it absent otherwise.
 template <typename R>
 int build_csr(Problem& p, SectorTables& st, size_t& bytes) {
   for (size_t t = 0; t < p.H.size(); ++t)
@@ -626,7 +628,11 @@ int build_csr(Problem& p, SectorTables& st, size_t& bytes) {
     nnz += c;
   }
   ptr[D] = nnz;
-  if (rc || (size_t)nnz * (4 + sizeof(R)) > kCsrMaxBytes) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+  const size_t need = (size_t)nnz * (4 + sizeof(R));
+  if (rc || need > kCsrMaxBytes || need > free_b / 4) {
+    cudaGetLastError();
     cudaFree(dptr);
     return rc;
   }
