@@ -333,11 +333,19 @@ __host__ __device__ constexpr uint32_t tile_mask_bytes() {
   return (1u << (TiledBits<R>::LB - 3)) / 8u;
 }
 
-constexpr int kTiledStages = 3;   // copies of up to two pieces in flight
+// pipeline stages: copies of up to stages - 1 pieces in flight (complex64
+// may use more with smaller tiles; complex128 tiles take 64 KiB each)
+#ifndef GOCP_TILED_STAGES_C64
+#define GOCP_TILED_STAGES_C64 3
+#endif
+template <typename R>
+__host__ __device__ constexpr int tiled_stages() {
+  return sizeof(R) == 4 ? GOCP_TILED_STAGES_C64 : 3;
+}
 
 template <typename R>
 __host__ __device__ constexpr size_t tiled_smem() {
-  return 1024 + kTiledStages * ((size_t)tile_bytes<R>() + (size_t)kTiledBlobBytes + (size_t)tile_mask_bytes<R>());
+  return 1024 + tiled_stages<R>() * ((size_t)tile_bytes<R>() + (size_t)kTiledBlobBytes + (size_t)tile_mask_bytes<R>());
 }
 
 // resident blocks per SM the register budget must allow
@@ -355,7 +363,7 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
   constexpr uint32_t kBox = kRows < 256u ? kRows : 256u;
   constexpr uint32_t kMask = tile_mask_bytes<R>();
   static_assert(kMask % 16u == 0, "mask slices are whole 16-byte units");
-  constexpr int S = kTiledStages;
+  constexpr int S = tiled_stages<R>();
   constexpr uint32_t kWarps = NT / 32;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S];
