@@ -25,7 +25,7 @@ LIB = os.path.join(OUT, "libgocp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["kernels.cu", "apply_tiled.cu", "sector.cu", "capi.cpp", "builder.cpp", "exactsum.cpp", "server.cpp"]
+SOURCES = ["kernels.cu", "apply_tiled.cu", "apply_sparse.cu", "sector.cu", "capi.cpp", "builder.cpp", "exactsum.cpp", "server.cpp"]
 
 
 def nvcc() -> str:

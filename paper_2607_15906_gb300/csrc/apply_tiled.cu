@@ -26,6 +26,9 @@
 // gocp_device_errors reports the flag.
 #include <cuda.h>
 
+#include <cmath>
+#include <cstdlib>
+
 #include <mutex>
 #include <vector>
 
@@ -315,6 +318,10 @@ struct TiledArgs {
   unsigned int* counter;
   double* scal;
   int32_t* err;
+  // set: the kernel returns at once when *gate <= gate_max (the scatter
+  // kernel of apply_sparse.cu takes the state)
+  const uint32_t* gate;
+  uint32_t gate_max;
 };
 
 template <typename R>
@@ -363,6 +370,7 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
   constexpr uint32_t kBox = kRows < 256u ? kRows : 256u;
   constexpr uint32_t kMask = tile_mask_bytes<R>();
   static_assert(kMask % 16u == 0, "mask slices are whole 16-byte units");
+  if (a.gate && *a.gate <= a.gate_max) return;   // the same answer for every thread
   constexpr int S = tiled_stages<R>();
   constexpr uint32_t kWarps = NT / 32;
   extern __shared__ uint8_t smem_raw[];
@@ -610,10 +618,19 @@ int smem_optin(int device) {
   return GOCP_OK;
 }
 
+// Fraction of live octets up to which the scatter kernel takes a state
+// (GOCP_SPARSE_FRAC, 0..1; 0 keeps every state on the staged kernel).
+double sparse_frac() {
+  const char* e = std::getenv("GOCP_SPARSE_FRAC");
+  if (!e || !*e) return 0.25;
+  const double f = std::atof(e);
+  return f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+}
+
 template <typename R>
-int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, double identity,
-                 double* partials, unsigned int* counter, unsigned int* tile_counter, double* scal, int32_t* err,
-                 cudaStream_t st) {
+int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const void* psi, void* hpsi,
+                 double identity, double* partials, unsigned int* counter, unsigned int* tile_counter, double* scal,
+                 int32_t* err, cudaStream_t st) {
   constexpr int LB = TiledBits<R>::LB;
   if (t.n_pieces <= 0 || t.n < LB) return fail(GOCP_EINVAL, "problem has no tiled H psi form");
   if ((reinterpret_cast<uintptr_t>(psi) & 15u) || (reinterpret_cast<uintptr_t>(hpsi) & 15u))
@@ -641,7 +658,36 @@ int launch_tiled(const DevTables& t, int sm_count, const void* psi, void* hpsi, 
       (rc = octet_mask(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, psi, nullptr, t.n, t.octmask, tile_counter, sm_count,
                        st, t.tflags, LB - 3)))
     return rc;
+  // states with few live octets: the scatter kernel (the staged one then
+  // returns at once); the choice is made on the device from the live count
+  const uint64_t octets = 1ull << (t.n - 3);
+  const double frac = sparse_frac();
+  const bool scatter = frac > 0.0 && lv.list && lv.toff && t.n_pieces <= kSpMaxPieces;
+  const uint32_t max_live = (uint32_t)std::min<double>((double)octets, std::floor(frac * (double)octets));
+  if (scatter) {
+    SparseArgs<R> s;
+    s.blob = t.tblob;
+    s.piece = t.tpiece;
+    s.n_pieces = t.n_pieces;
+    s.n = t.n;
+    s.psi = reinterpret_cast<const C_t<R>*>(psi);
+    s.out = reinterpret_cast<C_t<R>*>(hpsi);
+    s.mask = t.octmask;
+    s.max_live = max_live;
+    s.dz = t.dz;
+    s.dw = reinterpret_cast<const R*>(t.dw);
+    s.nd = t.nd;
+    s.nd_mid = t.nd_mid;
+    s.identity = identity;
+    s.partials = partials;
+    s.counter = counter;
+    s.tile_counter = tile_counter;
+    s.scal = scal;
+    if ((rc = live_octets(t.octmask, t.n, lv, st)) || (rc = sparse_apply_h<R>(s, lv, sm_count, st))) return rc;
+  }
   TiledArgs<R> a;
+  a.gate = scatter ? lv.len : nullptr;
+  a.gate_max = max_live;
   a.blob = t.tblob;
   a.piece = t.tpiece;
   a.mask = t.octmask;
@@ -686,12 +732,13 @@ int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t
   return cuda_status(cudaGetLastError(), "k_octet_mask");
 }
 
-int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
-                  double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,
-                  double* scal, int32_t* err, cudaStream_t st) {
-  return precision == GOCP_C64
-             ? launch_tiled<float>(t, sm_count, psi, hpsi, identity, partials, counter, tile_counter, scal, err, st)
-             : launch_tiled<double>(t, sm_count, psi, hpsi, identity, partials, counter, tile_counter, scal, err, st);
+int tiled_apply_h(const DevTables& t, const LiveOctets& lv, int precision, int sm_count, const void* psi,
+                  void* hpsi, double identity, double* partials, unsigned int* counter,
+                  unsigned int* tile_counter, double* scal, int32_t* err, cudaStream_t st) {
+  return precision == GOCP_C64 ? launch_tiled<float>(t, lv, sm_count, psi, hpsi, identity, partials, counter,
+                                                     tile_counter, scal, err, st)
+                               : launch_tiled<double>(t, lv, sm_count, psi, hpsi, identity, partials, counter,
+                                                      tile_counter, scal, err, st);
 }
 
 }  // namespace gocp

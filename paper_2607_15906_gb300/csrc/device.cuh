@@ -412,11 +412,63 @@ int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t
                unsigned int* tile_counter, int sm_count, cudaStream_t st, uint32_t* tile_flags = nullptr,
                int tile_shift = 0);
 
-// H psi (+ the energy epilogue when partials is set) by the tiled kernel;
-// t.n_pieces must be > 0.  Defined in apply_tiled.cu.
-int tiled_apply_h(const DevTables& t, int precision, int sm_count, const void* psi, void* hpsi,
-                  double identity, double* partials, unsigned int* counter, unsigned int* tile_counter,
-                  double* scal, int32_t* err, cudaStream_t st);
+// The live octets of a state (those the nonzero-octet mask marks), listed in
+// index order, with the per-block counts of the listing pass, the length,
+// and (tiled form) the first list entry of every tile: toff[u] .. toff[u+1]
+// are the live octets of tile u.
+struct LiveOctets {
+  uint32_t* list = nullptr;     // 2^(n-3) entries
+  uint32_t* counts = nullptr;   // one per listing block
+  uint32_t* len = nullptr;      // one entry
+  uint32_t* toff = nullptr;     // 2^(n-LB) + 1 entries
+};
+
+// Lists the live octets of `mask` (2^(n-3) bits, n >= 8) into lv.list and
+// lv.len.  Defined in kernels.cu.
+int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st);
+
+// H psi (+ the energy epilogue when partials is set) by the tiled kernels;
+// t.n_pieces must be > 0.  States whose live octets are at most the fraction
+// GOCP_SPARSE_FRAC (default 0.25) of all octets take the scatter kernel of
+// apply_sparse.cu, the others the staged kernel; the choice is made on the
+// device from the live count.  Defined in apply_tiled.cu.
+int tiled_apply_h(const DevTables& t, const LiveOctets& lv, int precision, int sm_count, const void* psi,
+                  void* hpsi, double identity, double* partials, unsigned int* counter,
+                  unsigned int* tile_counter, double* scal, int32_t* err, cudaStream_t st);
+
+// Pieces the scatter kernel takes (one byte of shared memory each); a
+// problem with more keeps every state on the staged kernel.
+constexpr int kSpMaxPieces = 8192;
+
+// Arguments of the scatter kernel (apply_sparse.cu); see sparse_apply_h.
+template <typename R>
+struct SparseArgs {
+  const uint8_t* blob;
+  const TiledPiece* piece;
+  int n_pieces, n;
+  const C_t<R>* psi;
+  C_t<R>* out;
+  const uint32_t* mask;
+  const uint32_t* list;
+  const uint32_t* len;
+  const uint32_t* toff;
+  uint32_t max_live;            // the kernel runs only when *len <= max_live
+  const uint32_t* dz;
+  const R* dw;
+  int nd, nd_mid;
+  double identity;
+  double* partials;
+  unsigned int* counter;
+  unsigned int* tile_counter;   // reset by octet_mask
+  double* scal;
+};
+
+// Launches the tile offsets of lv (whose list and length describe a.psi)
+// and the scatter H psi kernel, a no-op on the device when the live count
+// exceeds a.max_live; a.list, a.len and a.toff are taken from lv.  Defined
+// in apply_sparse.cu.
+template <typename R>
+int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStream_t st);
 
 // Accessors of a problem's device state for the sector-layout launchers
 // (defined in kernels.cu).

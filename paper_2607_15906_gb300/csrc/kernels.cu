@@ -58,11 +58,9 @@ struct DeviceTables {
   int32_t* selected = nullptr;
   double* grads = nullptr;           // pool_size doubles (pool order)
   double* graw = nullptr;            // whole chunks, family order, unscaled
-  // live-octet list of the pool-gradient pass (n >= 8): 2^(n-3) entries, the
-  // per-2048-word counts and the length
-  uint32_t* live_list = nullptr;
-  uint32_t* live_counts = nullptr;
-  uint32_t* live_len = nullptr;
+  // live-octet list of the pool-gradient pass and of the scatter H psi
+  // kernel (n >= 8)
+  LiveOctets live;
 };
 
 // ------------------------------------------------------------ reductions
@@ -969,6 +967,16 @@ k_live_list(const uint32_t* mask, uint32_t words, const uint32_t* counts, uint32
   }
 }
 
+int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st) {
+  if (n < 8 || !mask || !lv.list) return fail(GOCP_EINVAL, "live octets need n >= 8 and buffers");
+  const uint32_t words = 1u << (n - 8);
+  const int nb = (int)((words + kThreads * kLiveWordsPerThread - 1) / (kThreads * kLiveWordsPerThread));
+  k_live_count<<<nb, kThreads, 0, st>>>(mask, words, lv.counts);
+  k_live_list<<<nb, kThreads, 0, st>>>(mask, words, lv.counts, lv.list, lv.len);
+  count_launches(2);
+  return cuda_status(cudaGetLastError(), "k_live_list");
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_live(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
@@ -1474,7 +1482,8 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   TiledPiece* dpiece;
   int rc;
   if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
-      (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)))
+      (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)) ||
+      (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)))
     return rc;
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
@@ -1804,8 +1813,8 @@ int upload_problem(Problem& p) {
     const size_t words = (size_t)1 << (p.n_qubits - 8);
     const size_t blocks = (words + kThreads * kLiveWordsPerThread - 1) / (kThreads * kLiveWordsPerThread);
     if ((rc = dalloc(*d, &d->t.octmask, words, bytes)) || (rc = dalloc(*d, &d->t.octmask2, words, bytes)) ||
-        (rc = dalloc(*d, &d->live_list, words * 32, bytes)) || (rc = dalloc(*d, &d->live_counts, blocks, bytes)) ||
-        (rc = dalloc(*d, &d->live_len, 1, bytes)))
+        (rc = dalloc(*d, &d->live.list, words * 32, bytes)) || (rc = dalloc(*d, &d->live.counts, blocks, bytes)) ||
+        (rc = dalloc(*d, &d->live.len, 1, bytes)))
       return rc;
   }
   rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
@@ -2047,7 +2056,7 @@ static int launch_apply(Problem& p, const void* psi, void* hpsi, bool energy, cu
   DeviceTables& d = *p.dev;
   if (d.t.n_pieces > 0) {
     ProfScope ps(GOCP_KERNEL_APPLY_H, st);
-    return tiled_apply_h(d.t, p.precision, d.sm_count, psi, hpsi, p.identity, energy ? d.scratch : nullptr,
+    return tiled_apply_h(d.t, d.live, p.precision, d.sm_count, psi, hpsi, p.identity, energy ? d.scratch : nullptr,
                          d.counters + kMaxChunks, d.counters + kMaxChunks + 3, d.scalars, d.err, st);
   }
   const int grid = apply_grid(p.n_qubits);
@@ -2099,20 +2108,17 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
       return rc;
     if (mask) {
       // the live octets of psi, in index order, then one pass over them
-      const uint32_t words = 1u << (p.n_qubits - 8);
-      const int nb = (int)((words + kThreads * kLiveWordsPerThread - 1) / (kThreads * kLiveWordsPerThread));
-      k_live_count<<<nb, kThreads, 0, st>>>(mask, words, d.live_counts);
-      k_live_list<<<nb, kThreads, 0, st>>>(mask, words, d.live_counts, d.live_list, d.live_len);
+      if ((rc = live_octets(mask, p.n_qubits, d.live, st))) return rc;
       const uint64_t octets = 1ull << (p.n_qubits - 3);
       int lnbx = (int)std::max<uint64_t>(1, std::min<uint64_t>(64, (octets + kThreads * 64 - 1) / (kThreads * 64)));
       lnbx = std::max(1, std::min<int>(lnbx, (int)(d.scratch_doubles / ((size_t)nchunks * kOpsPerBlock))));
       {
         ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
         k_pool_grad_live<R><<<dim3(lnbx, nchunks), kThreads, 0, st>>>(
-            d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi, mask, d.live_list, d.live_len, d.scratch, lnbx);
+            d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi, mask, d.live.list, d.live.len, d.scratch, lnbx);
       }
       k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, lnbx, M, d.graw);
-      n += 3;
+      ++n;
     } else {
       {
         ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);

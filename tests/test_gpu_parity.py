@@ -236,13 +236,26 @@ def _grouped_random_table(n, rng):
     return PauliTable(n, x, z, ph.astype(np.int64), c)
 
 
+@pytest.fixture(params=["auto", "staged", "scatter"])
+def hpsi_path(request, monkeypatch):
+    """Which tiled H psi kernel runs: chosen from the live-octet count (auto),
+    the staged kernel for every state, or the scatter kernel for every state."""
+    frac = {"auto": None, "staged": "0", "scatter": "1"}[request.param]
+    if frac is None:
+        monkeypatch.delenv("GOCP_SPARSE_FRAC", raising=False)
+    else:
+        monkeypatch.setenv("GOCP_SPARSE_FRAC", frac)
+    return request.param
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n", [12, 13, 15, 16])
-def test_tiled_h_random_grouped_tables(prec, n):
-    """H psi through the shared-memory tiled kernel (one tile at n = 12
-    complex128 / 13 complex64, several above): LUT groups, term lists with
-    imaginary weights, a paired group, x masks over all bits; a dense random
-    state (no octet is skipped) and a sparse one (most octets skipped)."""
+def test_tiled_h_random_grouped_tables(prec, n, hpsi_path):
+    """H psi through the tiled kernels (one tile at n = 12 complex128 / 13
+    complex64, several above): LUT groups, term lists with imaginary weights,
+    a paired group, x masks over all bits; a dense random state (no octet is
+    skipped) and a sparse one (most octets skipped), each through the staged
+    kernel, the scatter kernel and the automatic choice."""
     rng = np.random.default_rng(100 + n)
     H = _grouped_random_table(n, rng)
     to_t = lambda t: (t.x.astype(np.uint32), t.z.astype(np.uint32), (t.phase % 4).astype(np.uint8), t.coeff)
@@ -261,6 +274,33 @@ def test_tiled_h_random_grouped_tables(prec, n):
         assert np.max(np.abs(_host(hd) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 4
         e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
         assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("path", ["staged", "scatter"])
+def test_tiled_h_on_sector_states(prec, path, monkeypatch):
+    """Prepared ADAPT states (16 qubits, 8 electrons: only the N = 8, S_z = 0
+    determinants are nonzero, a quarter of the octets at most) through the
+    staged and the scatter H psi kernel: every entry of H psi and the energy
+    against the oracle, and the pool gradients that read H psi."""
+    monkeypatch.setenv("GOCP_SPARSE_FRAC", "0" if path == "staged" else "1")
+    ints, h, tabs = _case(8, 8, "jw", 5)
+    p = gb.Problem.build(ints, 8, precision=prec, device=0)
+    ops, th = draw_ansatz(len(tabs), 24, seed=5, theta_sigma=0.3)
+    ws = p.workspace()
+    p.prepare_state(ops, th, ws[0])
+    psi_in = _host(ws[0])
+    live = np.any(psi_in.reshape(-1, 8) != 0, axis=1).mean()
+    assert 0 < live <= 0.25
+    e, nrm = p.energy(ws[0], ws[1])
+    ref = sv.apply_terms(h, psi_in)
+    assert np.max(np.abs(_host(ws[1]) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref))
+    e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
+    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    e2, _, g, sel = p.adapt_step(ops, th, ws=ws, tie_rel=1e-4)
+    g_ref = sv.pool_gradients(h, tabs, psi_in)
+    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    assert np.max(np.abs(g - g_ref)) <= TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref)))
 
 
 def test_empty_ansatz_gives_reference_energy():
@@ -305,7 +345,14 @@ def test_full_size_20q_sampled_rows(prec):
     assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale * 5
 
 
-def test_full_size_24q_sparse_prepare_energy_gradients():
+@pytest.mark.parametrize("path", ["auto", "staged"])
+def test_full_size_24q_sparse_prepare_energy_gradients(path, monkeypatch):
+    """The 24-qubit ADAPT step (the automatic choice takes the scatter H psi
+    kernel for these states) against the sparse oracle."""
+    if path == "staged":
+        monkeypatch.setenv("GOCP_SPARSE_FRAC", "0")
+    else:
+        monkeypatch.delenv("GOCP_SPARSE_FRAC", raising=False)
     ints, c = config_integrals("c5_24q")
     h = mapping.hamiltonian_table(ints, "jw", c["int_drop"], c["term_drop"])
     tabs = opool.pool_tables(24, 8, "jw")
