@@ -1,31 +1,37 @@
-// H psi (Eq. 3) with the energy epilogue (Eq. 1) for states whose nonzero
-// amplitudes fill few octets, by scattering from the live source octets.
+// H psi (Eq. 3) with the energy epilogue (Eq. 1) for states with few
+// nonzero amplitudes, by scattering from the nonzero source amplitudes.
 //
 // The staged kernel (apply_tiled.cu) gives every thread an output octet and
-// walks the groups of a piece; a group is skipped only where the source
-// octet is zero, so in a state confined to a particle-number sector (8.9 %
-// of octets live at 24 qubits) most lanes of a warp idle while a few work.
-// This kernel turns the loop around.  A block owns an output tile t of 2^LB
-// amplitudes and accumulates it in shared memory; for each piece (groups of
-// one x >> LB, source tile u = t ^ (x >> LB)) its warps take the live octets
-// l of u, 32 at a time (one per lane, from the index-ordered live list), load
-// each lane's 8 source amplitudes once, and walk the piece's groups together:
-// group g sends source octet l to output octet l ^ s_g (s_g = (x >> 3) within
-// the tile), output member i taking source member i ^ (x & 7) with
-// D_g(k) computed exactly as in the staged kernel (LUT entries, Walsh
-// buckets, paired or term-by-term).  Every product that is nonzero (D and
-// the source amplitude both nonzero) is added to the tile's accumulator with
-// a shared-memory atomic; a product with a zero factor is exactly zero and
-// is left out.  After the last piece the block adds the diagonal group and
-// the identity on the live octets of its own tile, the energy partials, and
-// streams the whole tile (zeros included) to H psi.
+// walks the groups of a piece, skipping a group only where the whole source
+// octet is zero; in a state confined to a particle-number sector (1.5 % of
+// the amplitudes nonzero at 24 qubits, in 8.9 % of the octets) most lanes of
+// a warp idle while a few work.  This kernel turns the loop around:
 //
-// The order in which products reach an accumulator element is not fixed, so
-// the result may differ from run to run in the last bits of a sum (and from
-// the staged kernel's fixed order); every term is the same.
+//  * a listing pass writes the nonzero amplitudes (index, value) in index
+//    order, and the first entry of every tile;
+//  * a block owns an output tile t of 2^LB amplitudes and accumulates it in
+//    shared memory.  Its work units are (chunk, piece): 32 consecutive
+//    nonzero amplitudes of the piece's source tile u = t ^ (x >> LB), one per
+//    lane, against the piece's groups, which the warp walks together.  For a
+//    group with mask x the lane's amplitude psi(k') goes to output
+//    k = k' ^ x with weight D(k): a LUT group reads its entry at code(k)
+//    (the code is linear in k over GF(2)), a term-list group sums its terms'
+//    signs at k (times the factor 0 or 2 of a paired group).  A nonzero
+//    product is added to the accumulator with a shared-memory atomic; a zero
+//    weight adds nothing and is left out;
+//  * after the last piece the block adds the diagonal group and the identity
+//    on the live octets of its own tile, the energy partials, and streams
+//    the whole tile (zeros included) to H psi.
+//
+// Every lane does the same work for every group, whatever the sparsity
+// pattern, and a group's descriptor and LUT are read at one address per
+// warp.  The order in which products reach an accumulator element is not
+// fixed, so the result may differ from run to run in the last bits of a sum
+// (and from the staged kernel's order); every term is the same.
 //
 // The kernel is launched with the staged one; each returns at once unless
-// the live count selects it, so the choice needs no host round trip.
+// the count of nonzero amplitudes selects it, so the choice needs no host
+// round trip.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -38,108 +44,7 @@ namespace gocp {
 namespace {
 
 constexpr int kSpThreads = 512;
-
-// The tile's accumulator is component-major: component j (2i: real part,
-// 2i + 1: imaginary part of member i) of octet o at j * kOct + o, so that
-// the epilogue's reads are consecutive and a warp's atomics on one component
-// spread over the banks by octet.
-template <typename R>
-__device__ __forceinline__ void acc_add(R* acc, uint32_t at, R re, R im, uint32_t koct) {
-  atomicAdd(acc + at, re);
-  atomicAdd(acc + at + koct, im);
-}
-
-// The group arithmetic is indexed by the lane's source member m: output
-// member i = m ^ xl (xl = x & 7 of the run) takes source member m.  Every
-// sign and LUT code is linear in the index over GF(2), so evaluating them at
-// k0x = k0 | xl (k0 = first index of the output octet) gives at member m the
-// value of output index k0 + (m ^ xl); xl then enters only the accumulator
-// address, and one code path serves every xl.
-
-// LUT groups of one run: l = the lane's source octet within its tile, src
-// its amplitudes, nz its nonzero members; kb = first index of the output
-// tile.  Every member looks its entry up: members that differ only in bits
-// outside the group's flip class have the same code (tiled_flip_class), so
-// those lookups read one word.
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ ls, int cn, uint32_t xl, uint32_t kb, uint32_t l,
-                                       const C_t<R> (&src)[kAmpsH], uint32_t nz, R* acc) {
-  for (int g = 0; g < cn; ++g) {
-    const HLut<R>& L = ls[g];
-    const uint4 h0 = *reinterpret_cast<const uint4*>(&L.x);     // x, z0, v0, v1
-    const uint4 h1 = *reinterpret_cast<const uint4*>(&L.v2);    // v2, reg, pad0, pad1
-    const uint32_t ol = l ^ h1.w, k0x = kb | (ol << 3) | xl, reg = h1.y;
-    const uint32_t code0 = (uint32_t)(__popc(k0x & h0.z) & 1) | ((uint32_t)(__popc(k0x & h0.w) & 1) << 1) |
-                           ((uint32_t)(__popc(k0x & h1.x) & 1) << 2) | ((uint32_t)(__popc(k0x & h0.y) & 1) << 3);
-#pragma unroll
-    for (int m = 0; m < kAmpsH; ++m) {
-      const R v = L.lut16[code0 ^ ((reg >> (4 * m)) & 0xFu)];
-      if (v != R(0) && ((nz >> m) & 1u))
-        acc_add<R>(acc, ((2u * ((uint32_t)m ^ xl)) * kOct) + ol, v * src[m].x, v * src[m].y, kOct);
-    }
-  }
-}
-
-// Term-list groups of one run: paired, Walsh-bucketed or term by term.
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ gs, int cn, uint32_t xl,
-                                         const uint32_t* __restrict__ zs, const R* __restrict__ ws, uint32_t kb,
-                                         uint32_t l, const C_t<R> (&src)[kAmpsH], uint32_t nz, R* acc) {
-  for (int g = 0; g < cn; ++g) {
-    const TiledGroup& G = gs[g];
-    const uint32_t ol = l ^ G.pad, k0x = kb | (ol << 3) | xl;
-    if (G.delta || G.bk != ~0ull) {
-      uint32_t live = 0xFFu;
-      if (G.delta) {
-        // paired: D = (1 + sigma (-1)^popc(k & delta)) E, the factor 0 or 2
-        const uint32_t f = octet_signs(k0x, G.delta);
-        live = G.neg ? f : (~f & 0xFFu);
-      }
-      live &= nz;
-      if (!live) continue;
-      // bucket m': the terms with z & 7 == m'; D at member m is
-      // sum_m' B_m' (-1)^popc(m & m') (a Walsh transform)
-      R b[kAmpsH];
-      int t = (int)G.tb;
-#pragma unroll
-      for (int m = 0; m < kAmpsH; ++m) {
-        b[m] = R(0);
-        const int cnt = (int)((G.bk >> (8 * m)) & 0xFFu);
-        for (int c = 0; c < cnt; ++c, ++t) b[m] += (__popc(k0x & zs[t]) & 1) ? -ws[t] : ws[t];
-      }
-#pragma unroll
-      for (int hb = 1; hb < kAmpsH; hb <<= 1)
-#pragma unroll
-        for (int q = 0; q < kAmpsH; ++q)
-          if (!(q & hb)) {
-            const R u = b[q], v = b[q | hb];
-            b[q] = u + v;
-            b[q | hb] = u - v;
-          }
-      const R f2 = G.delta ? R(2) : R(1);
-#pragma unroll
-      for (int m = 0; m < kAmpsH; ++m) {
-        const R d = f2 * b[m];
-        if (((live >> m) & 1u) && d != R(0))
-          acc_add<R>(acc, ((2u * ((uint32_t)m ^ xl)) * kOct) + ol, d * src[m].x, d * src[m].y, kOct);
-      }
-      continue;
-    }
-    if (!nz) continue;
-    R gr[kAmpsH], gi[kAmpsH], cr[kAmpsH], ci[kAmpsH];
-#pragma unroll
-    for (int m = 0; m < kAmpsH; ++m) gr[m] = gi[m] = cr[m] = ci[m] = R(0);
-    sum_terms8<R>(zs, ws, (int)G.tb, (int)G.tm, k0x, gr, cr, false);
-    if (G.te > G.tm) sum_terms8<R>(zs, ws, (int)G.tm, (int)G.te, k0x, gi, ci, false);
-#pragma unroll
-    for (int m = 0; m < kAmpsH; ++m)
-      if (((nz >> m) & 1u) && (gr[m] != R(0) || gi[m] != R(0))) {
-        const C_t<R> p = src[m];
-        acc_add<R>(acc, ((2u * ((uint32_t)m ^ xl)) * kOct) + ol, gr[m] * p.x - gi[m] * p.y, gr[m] * p.y + gi[m] * p.x,
-                   kOct);
-      }
-  }
-}
+constexpr int kAmpBlock = 256;   // listing passes: one mask word (32 octets) per thread
 
 template <typename R>
 __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t octet, C_t<R> (&v)[kAmpsH]) {
@@ -161,31 +66,185 @@ __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint3
   }
 }
 
-// off[u] = first entry of the index-ordered live list in tile u (octets
-// o >> shift == u), u = 0 .. ntiles; off[ntiles] = the list's length.
+template <typename R>
+__device__ __forceinline__ uint32_t nonzero_members(const C_t<R> (&v)[kAmpsH]) {
+  uint32_t nz = 0;
+#pragma unroll
+  for (int m = 0; m < kAmpsH; ++m) nz |= (uint32_t)(v[m].x != R(0) || v[m].y != R(0)) << m;
+  return nz;
+}
+
+// counts[b] = the nonzero amplitudes in the live octets of mask words
+// kAmpBlock b .. kAmpBlock (b + 1) - 1.
+template <typename R>
+__global__ void __launch_bounds__(kAmpBlock)
+k_amp_count(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, uint32_t words, uint32_t* counts) {
+  __shared__ uint32_t red[kAmpBlock / 32];
+  const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
+  uint32_t c = 0;
+  if (w < words) {
+    for (uint32_t m = mask[w]; m; m &= m - 1u) {
+      C_t<R> v[kAmpsH];
+      load_octet<R>(psi, w * 32u + (uint32_t)(__ffs(m) - 1), v);
+      c += __popc(nonzero_members<R>(v));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int q = 0; q < kAmpBlock / 32; ++q) t += red[q];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// counts[0..nb) -> exclusive prefix sums in place; *total = the sum.  One
+// block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total) {
+  __shared__ uint32_t s[1024];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  for (uint32_t base = 0; base < nb; base += 1024u) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nb ? counts[i] : 0u;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {   // inclusive scan
+      const uint32_t u = (int)threadIdx.x >= d ? s[threadIdx.x - d] : 0u;
+      __syncthreads();
+      s[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (i < nb) counts[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Writes (index, value) of every nonzero amplitude, in index order, at the
+// offsets of k_amp_scan; entries at or beyond cap are not stored.
+template <typename R>
+__global__ void __launch_bounds__(kAmpBlock)
+k_amp_list(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, uint32_t words,
+           const uint32_t* __restrict__ offs, uint32_t* aidx, C_t<R>* aval, uint32_t cap) {
+  __shared__ uint32_t red[kAmpBlock / 32];
+  const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
+  const uint32_t mw = w < words ? mask[w] : 0u;
+  uint32_t c = 0;
+  for (uint32_t m = mw; m; m &= m - 1u) {
+    C_t<R> v[kAmpsH];
+    load_octet<R>(psi, w * 32u + (uint32_t)(__ffs(m) - 1), v);
+    c += __popc(nonzero_members<R>(v));
+  }
+  // exclusive scan over the block: lanes by shuffles, warps through red
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) red[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int q = 0; q < warp; ++q) before += red[q];
+  uint32_t at = offs[blockIdx.x] + before + incl - c;
+  for (uint32_t m = mw; m; m &= m - 1u) {
+    const uint32_t o = w * 32u + (uint32_t)(__ffs(m) - 1);
+    C_t<R> v[kAmpsH];
+    load_octet<R>(psi, o, v);
+#pragma unroll
+    for (int q = 0; q < kAmpsH; ++q)
+      if (v[q].x != R(0) || v[q].y != R(0)) {
+        if (at < cap) {
+          aidx[at] = o * 8u + (uint32_t)q;
+          aval[at] = v[q];
+        }
+        ++at;
+      }
+  }
+}
+
+// off[u] = first stored entry with index >> shift >= u, u = 0 .. ntiles
+// (off[ntiles] = the number of stored entries).
 __global__ void __launch_bounds__(256)
-k_tile_offsets(const uint32_t* __restrict__ list, const uint32_t* __restrict__ len, uint32_t ntiles, int shift,
-               uint32_t* off) {
+k_tile_offsets(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ len, uint32_t cap, uint32_t ntiles,
+               int shift, uint32_t* off) {
   const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u > ntiles) return;
-  uint32_t lo = 0, hi = *len;
+  uint32_t lo = 0, hi = min(*len, cap);
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if ((list[mid] >> shift) < u) lo = mid + 1;
+    if ((idx[mid] >> shift) < u) lo = mid + 1;
     else hi = mid;
   }
   off[u] = lo;
+}
+
+// The tile's accumulator holds component j (2i: real part, 2i + 1:
+// imaginary part of member i) of octet o at j kOct + (o ^ 4i): a warp's
+// atomics on one component spread over the banks by octet, two members of
+// one octet fall on different banks, and the epilogue's reads of one
+// component stay a permutation of 32 consecutive words.
+template <uint32_t kOct>
+__device__ __forceinline__ uint32_t acc_at(uint32_t k) {
+  const uint32_t i = k & 7u, o = (k >> 3) & (kOct - 1u);
+  return (2u * i) * kOct + (o ^ (i << 2));
+}
+
+template <typename R, uint32_t kOct>
+__device__ __forceinline__ void acc_add(R* acc, uint32_t k, R re, R im) {
+  const uint32_t at = acc_at<kOct>(k);
+  atomicAdd(acc + at, re);
+  atomicAdd(acc + at + kOct, im);
+}
+
+// One LUT group against the lane's nonzero amplitude psi(ks) = v.
+template <typename R, uint32_t kOct>
+__device__ __forceinline__ void sp_lut(const HLut<R>& L, uint32_t ks, C_t<R> v, bool valid, R* acc) {
+  const uint4 h0 = *reinterpret_cast<const uint4*>(&L.x);     // x, z0, v0, v1
+  const uint4 h1 = *reinterpret_cast<const uint4*>(&L.v2);    // v2, reg, pad0, pad1
+  const uint32_t k = ks ^ h0.x;
+  const uint32_t code = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
+                        ((uint32_t)(__popc(k & h1.x) & 1) << 2) | ((uint32_t)(__popc(k & h0.y) & 1) << 3);
+  const R d = L.lut16[code];
+  if (valid && d != R(0)) acc_add<R, kOct>(acc, k, d * v.x, d * v.y);
+}
+
+// One term-list group: D(k) = sum_t w_t (-1)^popc(k & z_t), real terms
+// [tb, tm), imaginary [tm, te); a paired group keeps one term of each pair
+// and D = (1 + sigma (-1)^popc(k & delta)) E(k), the factor 0 or 2.  Called
+// by every lane of the warp (the group is warp-uniform).
+template <typename R, uint32_t kOct>
+__device__ __forceinline__ void sp_terms(const TiledGroup& G, const uint32_t* __restrict__ zs,
+                                         const R* __restrict__ ws, uint32_t ks, C_t<R> v, bool valid, R* acc) {
+  const uint32_t k = ks ^ G.x;
+  R f = R(1);
+  if (G.delta) {
+    const uint32_t p = __popc(k & G.delta) & 1u;
+    f = (G.neg ? p : p ^ 1u) ? R(2) : R(0);
+  }
+  const bool on = valid && f != R(0);
+  if (!__any_sync(0xffffffffu, on)) return;
+  R dr = R(0), di = R(0);
+  for (uint32_t t = G.tb; t < G.tm; ++t) dr += (__popc(k & zs[t]) & 1) ? -ws[t] : ws[t];
+  for (uint32_t t = G.tm; t < G.te; ++t) di += (__popc(k & zs[t]) & 1) ? -ws[t] : ws[t];
+  dr *= f;
+  di *= f;
+  if (on && (dr != R(0) || di != R(0))) acc_add<R, kOct>(acc, k, dr * v.x - di * v.y, dr * v.y + di * v.x);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_sparse(const SparseArgs<R> a) {
   constexpr int LB = TiledBits<R>::LB;
   constexpr uint32_t kOct = 1u << (LB - 3);   // octets per tile
-  if (*a.len > a.max_live) return;            // the staged kernel takes this state
+  if (*a.alen > a.max_amps) return;           // the staged kernel takes this state
   extern __shared__ __align__(16) uint8_t sp_raw[];
   R* acc = reinterpret_cast<R*>(sp_raw);      // 16 components x kOct octets
   __shared__ uint32_t s_tile, s_unext, s_maxch;
-  __shared__ uint8_t s_nch[kSpMaxPieces];
+  __shared__ uint16_t s_nch[kSpMaxPieces];
   __shared__ double tot[2];
   const uint32_t ntiles = 1u << (a.n - LB);
   const int lane = threadIdx.x & 31;
@@ -204,16 +263,15 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= ntiles) break;
-    const uint32_t kb = t << LB;
-    // scatter.  Work units are (chunk c, piece p): the live octets
-    // 32c .. 32c + 31 of p's source tile u = t ^ (x >> LB) against p's groups.
-    // The units are handed out chunk-major from a block counter, so that the
-    // last units of the tile are small; s_nch[p] = p's chunk count.
+    // scatter.  Work units are (chunk c, piece p): the nonzero amplitudes
+    // 32c .. 32c + 31 of p's source tile u = t ^ (x >> LB) against p's
+    // groups.  The units are handed out chunk-major from a block counter, so
+    // that the last units of the tile are small; s_nch[p] = p's chunk count.
     for (int p = (int)threadIdx.x; p < a.n_pieces; p += kSpThreads) {
       const TiledPiece pc = a.piece[p];
       const uint32_t u = t ^ pc.xhi;
       const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + 31u) >> 5 : 0u;
-      s_nch[p] = (uint8_t)nch;
+      s_nch[p] = (uint16_t)nch;
       if (nch) atomicMax(&s_maxch, nch);
     }
     __syncthreads();
@@ -227,45 +285,41 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_
       if (c >= s_nch[p]) continue;
       const TiledPiece pc = a.piece[p];
       const uint32_t u = t ^ pc.xhi;
-      const uint32_t l0 = a.toff[u], l1 = a.toff[u + 1];
+      const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
       const uint8_t* bl = a.blob + pc.off;
       const TiledHead* hd = reinterpret_cast<const TiledHead*>(bl);
       const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(bl + sizeof(TiledHead));
       const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(bl + sizeof(TiledHead) + hd->n_lut * sizeof(HLut<R>));
       const uint32_t* zs = reinterpret_cast<const uint32_t*>(bl + hd->z_off);
       const R* ws = reinterpret_cast<const R*>(bl + hd->w_off);
+      const uint32_t li = a0 + 32u * c + (uint32_t)lane;
+      const bool valid = li < a1;
+      const uint32_t ks = a.aidx[valid ? li : a0];
+      const C_t<R> v = a.aval[valid ? li : a0];
+      const int nl = (int)hd->n_lut;
+      for (int g = 0; g < nl; ++g) sp_lut<R, kOct>(ls[g], ks, v, valid, acc);
+      // the term-list runs follow the LUT runs
       const int nr = (int)hd->n_runs;
-      const uint32_t li = l0 + 32u * c + (uint32_t)lane;
-      const bool valid = li < l1;
-      const uint32_t so = a.list[valid ? li : l0];
-      C_t<R> src[kAmpsH];
-      load_octet<R>(a.psi, so, src);
-      uint32_t nz = 0;
-#pragma unroll
-      for (int m = 0; m < kAmpsH; ++m) nz |= (uint32_t)(src[m].x != R(0) || src[m].y != R(0)) << m;
-      if (!valid) nz = 0;
-      const uint32_t l = so & (kOct - 1u);
       for (int r = 0; r < nr; ++r) {
         const uint32_t rd = hd->run[r];
-        const int g0 = (int)(rd & 0xFFFu), cn = (int)((rd >> 12) & 0xFFFu) - g0;
-        const uint32_t sel = rd >> 24, xl = sel & 7u;
-        if (sel < 64) sp_lut<R, kOct>(ls + g0, cn, xl, kb, l, src, nz, acc);
-        else sp_terms<R, kOct>(gs + g0, cn, xl, zs, ws, kb, l, src, nz, acc);
+        if ((rd >> 24) < 64u) continue;
+        const int g0 = (int)(rd & 0xFFFu), g1 = (int)((rd >> 12) & 0xFFFu);
+        for (int g = g0; g < g1; ++g) sp_terms<R, kOct>(gs[g], zs, ws, ks, v, valid, acc);
       }
     }
     __syncthreads();
     // epilogue: diagonal, identity and energy on the live own octets; the
     // whole tile out; the accumulator cleared for the next tile
     for (uint32_t o = threadIdx.x; o < kOct; o += kSpThreads) {
+      const uint32_t go = (t << (LB - 3)) | o, k0 = go << 3;
       C_t<R> res[kAmpsH];
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
-        R* e = acc + (2u * i) * kOct + o;
+        R* e = acc + acc_at<kOct>(k0 | (uint32_t)i);
         res[i] = cmake<R>(e[0], e[kOct]);
         e[0] = R(0);
         e[kOct] = R(0);
       }
-      const uint32_t go = (t << (LB - 3)) | o, k0 = go << 3;
       if ((a.mask[go >> 5] >> (go & 31u)) & 1u) {
         R dr[kAmpsH], dc[kAmpsH], di[kAmpsH], dd[kAmpsH];
 #pragma unroll
@@ -274,17 +328,17 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_
         sum_terms8<R>(a.dz, a.dw, a.nd_mid, a.nd, k0, di, dd, false);
         C_t<R> own[kAmpsH];
         load_octet<R>(a.psi, go, own);
-        double2 v = s_v[threadIdx.x];
+        double2 w = s_v[threadIdx.x];
 #pragma unroll
         for (int i = 0; i < kAmpsH; ++i) {
           const C_t<R> q = own[i];
           const double pp = (double)q.x * q.x + (double)q.y * q.y;
-          v.x += pp;
-          v.y += (double)q.x * res[i].x + (double)q.y * res[i].y + ((double)dr[i] - (double)dc[i]) * pp;
+          w.x += pp;
+          w.y += (double)q.x * res[i].x + (double)q.y * res[i].y + ((double)dr[i] - (double)dc[i]) * pp;
           const R d0 = dr[i] - dc[i] + idr;
           res[i] = cmake<R>(res[i].x + d0 * q.x - di[i] * q.y, res[i].y + d0 * q.y + di[i] * q.x);
         }
-        s_v[threadIdx.x] = v;
+        s_v[threadIdx.x] = w;
       }
       C_t<R>* dst = a.out + k0;
       if (sizeof(R) == 4) {
@@ -317,9 +371,11 @@ constexpr uint32_t sparse_smem() {
 template <typename R>
 int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStream_t st) {
   constexpr int LB = TiledBits<R>::LB;
-  if (a.n < LB || !lv.toff || !lv.list || !lv.len) return fail(GOCP_EINVAL, "scatter H psi needs the live list");
-  a.list = lv.list;
-  a.len = lv.len;
+  if (a.n < LB || !lv.toff || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts || a.max_amps > lv.acap)
+    return fail(GOCP_EINVAL, "scatter H psi needs the amplitude list");
+  a.aidx = lv.aidx;
+  a.aval = reinterpret_cast<const C_t<R>*>(lv.aval);
+  a.alen = lv.alen;
   a.toff = lv.toff;
   static std::mutex mu;
   static std::vector<bool> done;
@@ -336,11 +392,17 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
       done[device] = true;
     }
   }
+  const uint32_t words = 1u << (a.n - 8);
+  const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
   const uint32_t ntiles = 1u << (a.n - LB);
-  k_tile_offsets<<<(ntiles + 256u) / 256u, 256, 0, st>>>(lv.list, lv.len, ntiles, LB - 3, lv.toff);
+  k_amp_count<R><<<nb, kAmpBlock, 0, st>>>(a.psi, a.mask, words, lv.acounts);
+  k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
+  k_amp_list<R><<<nb, kAmpBlock, 0, st>>>(a.psi, a.mask, words, lv.acounts, lv.aidx,
+                                          reinterpret_cast<C_t<R>*>(lv.aval), lv.acap);
+  k_tile_offsets<<<(ntiles + 256u) / 256u, 256, 0, st>>>(lv.aidx, lv.alen, lv.acap, ntiles, LB, lv.toff);
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1) * 2u);
   k_apply_h_sparse<R><<<grid, kSpThreads, sparse_smem<R>(), st>>>(a);
-  count_launches(2);
+  count_launches(5);
   return cuda_status(cudaGetLastError(), "k_apply_h_sparse");
 }
 

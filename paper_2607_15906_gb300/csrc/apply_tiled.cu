@@ -618,13 +618,14 @@ int smem_optin(int device) {
   return GOCP_OK;
 }
 
-// Fraction of live octets up to which the scatter kernel takes a state
-// (GOCP_SPARSE_FRAC, 0..1; 0 keeps every state on the staged kernel).
+// Fraction of nonzero amplitudes up to which the scatter kernel takes a
+// state (GOCP_SPARSE_FRAC; 0 keeps every state on the staged kernel; the
+// amplitude list holds a quarter of the state at most).
 double sparse_frac() {
   const char* e = std::getenv("GOCP_SPARSE_FRAC");
-  if (!e || !*e) return 0.25;
+  if (!e || !*e) return 0.125;
   const double f = std::atof(e);
-  return f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+  return f < 0.0 ? 0.0 : (f > 0.25 ? 0.25 : f);
 }
 
 template <typename R>
@@ -658,12 +659,12 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
       (rc = octet_mask(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, psi, nullptr, t.n, t.octmask, tile_counter, sm_count,
                        st, t.tflags, LB - 3)))
     return rc;
-  // states with few live octets: the scatter kernel (the staged one then
-  // returns at once); the choice is made on the device from the live count
-  const uint64_t octets = 1ull << (t.n - 3);
+  // states with few nonzero amplitudes: the scatter kernel (the staged one
+  // then returns at once); the choice is made on the device from the count
   const double frac = sparse_frac();
-  const bool scatter = frac > 0.0 && lv.list && lv.toff && t.n_pieces <= kSpMaxPieces;
-  const uint32_t max_live = (uint32_t)std::min<double>((double)octets, std::floor(frac * (double)octets));
+  const bool scatter = frac > 0.0 && lv.aidx && lv.toff && t.n_pieces <= kSpMaxPieces;
+  const uint32_t max_amps =
+      (uint32_t)std::min<double>((double)lv.acap, std::floor(frac * (double)(1ull << t.n)));
   if (scatter) {
     SparseArgs<R> s;
     s.blob = t.tblob;
@@ -673,7 +674,7 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     s.psi = reinterpret_cast<const C_t<R>*>(psi);
     s.out = reinterpret_cast<C_t<R>*>(hpsi);
     s.mask = t.octmask;
-    s.max_live = max_live;
+    s.max_amps = max_amps;
     s.dz = t.dz;
     s.dw = reinterpret_cast<const R*>(t.dw);
     s.nd = t.nd;
@@ -683,11 +684,11 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     s.counter = counter;
     s.tile_counter = tile_counter;
     s.scal = scal;
-    if ((rc = live_octets(t.octmask, t.n, lv, st)) || (rc = sparse_apply_h<R>(s, lv, sm_count, st))) return rc;
+    if ((rc = sparse_apply_h<R>(s, lv, sm_count, st))) return rc;
   }
   TiledArgs<R> a;
-  a.gate = scatter ? lv.len : nullptr;
-  a.gate_max = max_live;
+  a.gate = scatter ? lv.alen : nullptr;
+  a.gate_max = max_amps;
   a.blob = t.tblob;
   a.piece = t.tpiece;
   a.mask = t.octmask;

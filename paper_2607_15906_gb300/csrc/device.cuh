@@ -416,11 +416,21 @@ int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t
 // index order, with the per-block counts of the listing pass, the length,
 // and (tiled form) the first list entry of every tile: toff[u] .. toff[u+1]
 // are the live octets of tile u.
+//
+// The tiled form adds the nonzero amplitudes of a state in index order
+// (aidx: index, aval: value; at most acap of them are stored, alen = their
+// number, which may exceed acap), their per-block counts and offsets, and
+// the first entry of every tile in toff.
 struct LiveOctets {
   uint32_t* list = nullptr;     // 2^(n-3) entries
   uint32_t* counts = nullptr;   // one per listing block
   uint32_t* len = nullptr;      // one entry
   uint32_t* toff = nullptr;     // 2^(n-LB) + 1 entries
+  uint32_t* aidx = nullptr;     // acap entries
+  void* aval = nullptr;         // acap complex amplitudes of the problem's precision
+  uint32_t acap = 0;
+  uint32_t* alen = nullptr;     // one entry
+  uint32_t* acounts = nullptr;  // one per block of 256 mask words, + 1
 };
 
 // Lists the live octets of `mask` (2^(n-3) bits, n >= 8) into lv.list and
@@ -428,17 +438,17 @@ struct LiveOctets {
 int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st);
 
 // H psi (+ the energy epilogue when partials is set) by the tiled kernels;
-// t.n_pieces must be > 0.  States whose live octets are at most the fraction
-// GOCP_SPARSE_FRAC (default 0.25) of all octets take the scatter kernel of
-// apply_sparse.cu, the others the staged kernel; the choice is made on the
-// device from the live count.  Defined in apply_tiled.cu.
+// t.n_pieces must be > 0.  States whose nonzero amplitudes are at most the
+// fraction GOCP_SPARSE_FRAC (default 0.125, at most 0.25) of all take the
+// scatter kernel of apply_sparse.cu, the others the staged kernel; the
+// choice is made on the device from the count.  Defined in apply_tiled.cu.
 int tiled_apply_h(const DevTables& t, const LiveOctets& lv, int precision, int sm_count, const void* psi,
                   void* hpsi, double identity, double* partials, unsigned int* counter,
                   unsigned int* tile_counter, double* scal, int32_t* err, cudaStream_t st);
 
-// Pieces the scatter kernel takes (one byte of shared memory each); a
+// Pieces the scatter kernel takes (two bytes of shared memory each); a
 // problem with more keeps every state on the staged kernel.
-constexpr int kSpMaxPieces = 8192;
+constexpr int kSpMaxPieces = 4096;
 
 // Arguments of the scatter kernel (apply_sparse.cu); see sparse_apply_h.
 template <typename R>
@@ -449,10 +459,11 @@ struct SparseArgs {
   const C_t<R>* psi;
   C_t<R>* out;
   const uint32_t* mask;
-  const uint32_t* list;
-  const uint32_t* len;
+  const uint32_t* aidx;
+  const C_t<R>* aval;
+  const uint32_t* alen;
   const uint32_t* toff;
-  uint32_t max_live;            // the kernel runs only when *len <= max_live
+  uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
   const uint32_t* dz;
   const R* dw;
   int nd, nd_mid;
@@ -463,10 +474,10 @@ struct SparseArgs {
   double* scal;
 };
 
-// Launches the tile offsets of lv (whose list and length describe a.psi)
-// and the scatter H psi kernel, a no-op on the device when the live count
-// exceeds a.max_live; a.list, a.len and a.toff are taken from lv.  Defined
-// in apply_sparse.cu.
+// Lists the nonzero amplitudes of a.psi (whose exact octet mask is a.mask)
+// into lv, their tile offsets, and launches the scatter H psi kernel, a
+// no-op on the device when there are more than a.max_amps; a.aidx, a.aval,
+// a.alen and a.toff are taken from lv.  Defined in apply_sparse.cu.
 template <typename R>
 int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStream_t st);
 

@@ -1483,8 +1483,12 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   int rc;
   if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
       (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)) ||
-      (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)))
+      (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)) ||
+      (rc = dalloc(d, &d.live.aidx, (size_t)1 << (n - 2), bytes)) ||
+      (rc = dalloc(d, reinterpret_cast<C_t<R>**>(&d.live.aval), (size_t)1 << (n - 2), bytes)) ||
+      (rc = dalloc(d, &d.live.alen, 1, bytes)) || (rc = dalloc(d, &d.live.acounts, ((((size_t)1 << (n - 8)) + 255) / 256) + 1, bytes)))
     return rc;
+  d.live.acap = 1u << (n - 2);
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
   d.t.n_pieces = (int)pieces.size();
