@@ -43,8 +43,12 @@ namespace gocp {
 
 namespace {
 
-constexpr int kSpThreads = 512;
 constexpr int kAmpBlock = 256;   // listing passes: one mask word (32 octets) per thread
+
+// One block per SM: 1024 threads for complex64 (64 registers), 512 for
+// complex128 (128 registers).
+template <typename R>
+__host__ __device__ constexpr int sp_threads() { return sizeof(R) == 4 ? 1024 : 512; }
 
 template <typename R>
 __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t octet, C_t<R> (&v)[kAmpsH]) {
@@ -237,61 +241,109 @@ __device__ __forceinline__ void sp_terms(const TiledGroup& G, const uint32_t* __
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_sparse(const SparseArgs<R> a) {
+__global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const SparseArgs<R> a) {
   constexpr int LB = TiledBits<R>::LB;
+  constexpr int NT = sp_threads<R>();
   constexpr uint32_t kOct = 1u << (LB - 3);   // octets per tile
   if (*a.alen > a.max_amps) return;           // the staged kernel takes this state
+  // dynamic shared memory: the tile's accumulator (16 components x kOct
+  // octets), then one piece blob per warp
   extern __shared__ __align__(16) uint8_t sp_raw[];
-  R* acc = reinterpret_cast<R*>(sp_raw);      // 16 components x kOct octets
-  __shared__ uint32_t s_tile, s_unext, s_maxch;
-  __shared__ uint16_t s_nch[kSpMaxPieces];
+  R* acc = reinterpret_cast<R*>(sp_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* wblob = sp_raw + kOct * 16u * sizeof(R) + (size_t)warp * kTiledBlobBytes;
+  __shared__ uint32_t s_tile, s_unext;
+  __shared__ uint32_t s_pre[kSpMaxPieces + 1];   // first unit of each piece; s_pre[P] = units
+  __shared__ uint32_t s_wsum[32];
   __shared__ double tot[2];
   const uint32_t ntiles = 1u << (a.n - LB);
-  const int lane = threadIdx.x & 31;
-  for (uint32_t j = threadIdx.x; j < kOct * 16u; j += kSpThreads) acc[j] = R(0);
+  const uint32_t P = (uint32_t)a.n_pieces;
+  for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) acc[j] = R(0);
   const R idr = (R)a.identity;
   // this thread's |psi|^2 and <psi|H - identity|psi> partials (in shared
   // memory: touched once per tile)
-  __shared__ double2 s_v[kSpThreads];
+  __shared__ double2 s_v[NT];
   s_v[threadIdx.x] = make_double2(0.0, 0.0);
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(a.tile_counter, 1u);
       s_unext = 0u;
-      s_maxch = 0u;
     }
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= ntiles) break;
-    // scatter.  Work units are (chunk c, piece p): the nonzero amplitudes
-    // 32c .. 32c + 31 of p's source tile u = t ^ (x >> LB) against p's
-    // groups.  The units are handed out chunk-major from a block counter, so
-    // that the last units of the tile are small; s_nch[p] = p's chunk count.
-    for (int p = (int)threadIdx.x; p < a.n_pieces; p += kSpThreads) {
-      const TiledPiece pc = a.piece[p];
-      const uint32_t u = t ^ pc.xhi;
-      const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + 31u) >> 5 : 0u;
-      s_nch[p] = (uint16_t)nch;
-      if (nch) atomicMax(&s_maxch, nch);
+    // Work units are (piece p, chunk c): the nonzero amplitudes 32c .. 32c + 31
+    // of p's source tile u = t ^ (x >> LB) against p's groups, numbered piece
+    // by piece (s_pre: a block scan of the chunk counts).
+    {
+      const uint32_t per = (P + NT - 1) / NT, p0 = threadIdx.x * per, p1 = min(P, p0 + per);
+      uint32_t mine = 0;
+      for (uint32_t p = p0; p < p1; ++p) {
+        const TiledPiece pc = a.piece[p];
+        const uint32_t u = t ^ pc.xhi;
+        const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + 31u) >> 5 : 0u;
+        s_pre[p] = nch;
+        mine += nch;
+      }
+      uint32_t incl = mine;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t q = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += q;
+      }
+      if (lane == 31) s_wsum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t w = lane < NT / 32 ? s_wsum[lane] : 0u, wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t q = __shfl_up_sync(0xffffffffu, wi, o);
+          if (lane >= o) wi += q;
+        }
+        if (lane < NT / 32) s_wsum[lane] = wi - w;   // exclusive
+        if (lane == NT / 32 - 1) s_pre[P] = wi;
+      }
+      __syncthreads();
+      uint32_t run = s_wsum[warp] + incl - mine;
+      for (uint32_t p = p0; p < p1; ++p) {
+        const uint32_t nch = s_pre[p];
+        s_pre[p] = run;
+        run += nch;
+      }
     }
     __syncthreads();
-    const uint32_t P = (uint32_t)a.n_pieces, n_units = s_maxch * P;
+    const uint32_t n_units = s_pre[P];
+    uint32_t cur = 0xFFFFFFFFu;   // piece whose blob this warp holds
     for (;;) {
       uint32_t j = 0;
       if (lane == 0) j = atomicAdd(&s_unext, 1u);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= n_units) break;
-      const uint32_t c = j / P, p = j - c * P;
-      if (c >= s_nch[p]) continue;
+      // p = the last piece with s_pre[p] <= j (pieces without units share
+      // their successor's start and are passed over)
+      uint32_t lo = 0, hi = P - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint32_t p = lo, c = j - s_pre[p];
       const TiledPiece pc = a.piece[p];
+      if (p != cur) {
+        // the piece's blob into this warp's buffer, 16 bytes per lane
+        __syncwarp();
+        const uint4* src = reinterpret_cast<const uint4*>(a.blob + pc.off);
+        uint4* dst = reinterpret_cast<uint4*>(wblob);
+        for (uint32_t q = (uint32_t)lane; q < pc.bytes / 16u; q += 32u) dst[q] = __ldg(src + q);
+        __syncwarp();
+        cur = p;
+      }
       const uint32_t u = t ^ pc.xhi;
       const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
-      const uint8_t* bl = a.blob + pc.off;
-      const TiledHead* hd = reinterpret_cast<const TiledHead*>(bl);
-      const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(bl + sizeof(TiledHead));
-      const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(bl + sizeof(TiledHead) + hd->n_lut * sizeof(HLut<R>));
-      const uint32_t* zs = reinterpret_cast<const uint32_t*>(bl + hd->z_off);
-      const R* ws = reinterpret_cast<const R*>(bl + hd->w_off);
+      const TiledHead* hd = reinterpret_cast<const TiledHead*>(wblob);
+      const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(wblob + sizeof(TiledHead));
+      const TiledGroup* gs =
+          reinterpret_cast<const TiledGroup*>(wblob + sizeof(TiledHead) + hd->n_lut * sizeof(HLut<R>));
+      const uint32_t* zs = reinterpret_cast<const uint32_t*>(wblob + hd->z_off);
+      const R* ws = reinterpret_cast<const R*>(wblob + hd->w_off);
       const uint32_t li = a0 + 32u * c + (uint32_t)lane;
       const bool valid = li < a1;
       const uint32_t ks = a.aidx[valid ? li : a0];
@@ -310,7 +362,7 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_
     __syncthreads();
     // epilogue: diagonal, identity and energy on the live own octets; the
     // whole tile out; the accumulator cleared for the next tile
-    for (uint32_t o = threadIdx.x; o < kOct; o += kSpThreads) {
+    for (uint32_t o = threadIdx.x; o < kOct; o += NT) {
       const uint32_t go = (t << (LB - 3)) | o, k0 = go << 3;
       C_t<R> res[kAmpsH];
 #pragma unroll
@@ -356,14 +408,14 @@ __global__ void __launch_bounds__(kSpThreads, sizeof(R) == 4 ? 2 : 1) k_apply_h_
     __syncthreads();
   }
   const double v[2] = {s_v[threadIdx.x].x, s_v[threadIdx.x].y};
-  if (a.partials && block_grid_sum<2, kSpThreads>(v, a.partials, a.counter, gridDim.x, blockIdx.x, a.scal + 1, tot)) {
+  if (a.partials && block_grid_sum<2, NT>(v, a.partials, a.counter, gridDim.x, blockIdx.x, a.scal + 1, tot)) {
     if (threadIdx.x == 0) a.scal[0] = a.identity + tot[1] / tot[0];
   }
 }
 
 template <typename R>
 constexpr uint32_t sparse_smem() {
-  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(R);
+  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(R) + (sp_threads<R>() / 32) * kTiledBlobBytes;
 }
 
 }  // namespace
@@ -400,8 +452,8 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
   k_amp_list<R><<<nb, kAmpBlock, 0, st>>>(a.psi, a.mask, words, lv.acounts, lv.aidx,
                                           reinterpret_cast<C_t<R>*>(lv.aval), lv.acap);
   k_tile_offsets<<<(ntiles + 256u) / 256u, 256, 0, st>>>(lv.aidx, lv.alen, lv.acap, ntiles, LB, lv.toff);
-  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1) * 2u);
-  k_apply_h_sparse<R><<<grid, kSpThreads, sparse_smem<R>(), st>>>(a);
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1));
+  k_apply_h_sparse<R><<<grid, sp_threads<R>(), sparse_smem<R>(), st>>>(a);
   count_launches(5);
   return cuda_status(cudaGetLastError(), "k_apply_h_sparse");
 }
