@@ -211,9 +211,14 @@ def run_gpu(args, rank, world, device):
 
     if world > 1:
         secs, e2e_secs = slowest_rank([secs, e2e_secs], device=dev)
+    # nonzero amplitudes of the prepared state psi(theta), on which both H psi
+    # calls of a step act (the appended operator has theta = 0); outside the
+    # timed regions
+    prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-4, out=(e2, grads, sel))
+    nnz = int(torch.view_as_real(ws[0]).ne(0).any(-1).sum().item())
     info = prob.info
     return dict(prob=prob, secs=secs, e2e_secs=e2e_secs, kern=kern, clocks=clocks, launches=launches,
-                h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]))
+                h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]), nnz=nnz)
 
 
 def sector_layout(device: int, full_e: float, full_sel: int, steps: int = 10, warmup: int = 3):
@@ -498,12 +503,20 @@ def roofline(res, peaks, how):
     fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if top == "apply_h":
         t, g = info["n_terms"], info["n_groups"]
-        # per amplitude: one signed add per term, one complex x real multiply-add per group
-        flops = dim * (t + 4 * g)
+        # per nonzero source amplitude: one signed add per term, one complex x
+        # real multiply-add per group (a zero amplitude contributes nothing,
+        # and the kernels do no work for it); dense states: nnz = 2^n
+        nnz = res.get("nnz", dim)
+        flops = nnz * (t + 4 * g)
         achieved = flops / per_launch_s / 1e12
-        out = {"kernel": "k_apply_h", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+        # the library's choice (GOCP_SPARSE_FRAC of the amplitudes, default
+        # 1/8, at most 1/4): the scatter kernel at or below it
+        frac = min(0.25, max(0.0, float(os.environ.get("GOCP_SPARSE_FRAC", "") or 0.125)))
+        name = "k_apply_h_sparse" if nnz <= int(frac * dim) else "k_apply_h_tiled"
+        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-               "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)"}
+               "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)",
+               "flops_per_launch": flops, "nonzero_amplitudes": nnz}
     else:
         state = dim * 8
         per = {"taylor5": 2 * state, "adjoint": 4 * state, "pool_grad": 2 * state}[top]
