@@ -444,18 +444,36 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
       done[device] = true;
     }
   }
-  const uint32_t words = 1u << (a.n - 8);
-  const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
+  int rc = amp_list(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128, a.psi, a.mask, a.n, lv, st);
+  if (rc) return rc;
   const uint32_t ntiles = 1u << (a.n - LB);
-  k_amp_count<R><<<nb, kAmpBlock, 0, st>>>(a.psi, a.mask, words, lv.acounts);
-  k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
-  k_amp_list<R><<<nb, kAmpBlock, 0, st>>>(a.psi, a.mask, words, lv.acounts, lv.aidx,
-                                          reinterpret_cast<C_t<R>*>(lv.aval), lv.acap);
   k_tile_offsets<<<(ntiles + 256u) / 256u, 256, 0, st>>>(lv.aidx, lv.alen, lv.acap, ntiles, LB, lv.toff);
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1));
   k_apply_h_sparse<R><<<grid, sp_threads<R>(), sparse_smem<R>(), st>>>(a);
-  count_launches(5);
+  count_launches(2);
   return cuda_status(cudaGetLastError(), "k_apply_h_sparse");
+}
+
+int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st) {
+  if (n < 8 || !mask || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts)
+    return fail(GOCP_EINVAL, "amplitude list needs n >= 8 and its buffers");
+  const uint32_t words = 1u << (n - 8);
+  const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
+  if (precision == GOCP_C64) {
+    const float2* p = reinterpret_cast<const float2*>(psi);
+    k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
+    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts, lv.aidx,
+                                                reinterpret_cast<float2*>(lv.aval), lv.acap);
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(psi);
+    k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
+    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts, lv.aidx,
+                                                 reinterpret_cast<double2*>(lv.aval), lv.acap);
+  }
+  count_launches(3);
+  return cuda_status(cudaGetLastError(), "k_amp_list");
 }
 
 template int sparse_apply_h<float>(SparseArgs<float>, const LiveOctets&, int, cudaStream_t);

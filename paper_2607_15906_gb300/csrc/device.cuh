@@ -474,6 +474,12 @@ struct SparseArgs {
   double* scal;
 };
 
+// Lists the nonzero amplitudes of psi into lv.aidx / lv.aval (index order,
+// the first lv.acap of them) and their number into lv.alen; mask must mark
+// every octet of psi holding a nonzero amplitude (extra set bits only cost
+// time).  Defined in apply_sparse.cu.
+int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st);
+
 // Lists the nonzero amplitudes of a.psi (whose exact octet mask is a.mask)
 // into lv, their tile offsets, and launches the scatter H psi kernel, a
 // no-op on the device when there are more than a.max_amps; a.aidx, a.aval,

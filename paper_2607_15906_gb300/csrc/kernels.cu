@@ -977,11 +977,76 @@ int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t 
   return cuda_status(cudaGetLastError(), "k_live_list");
 }
 
+// ---- pool gradients driven by the nonzero amplitudes (full layout, LUT pool)
+//
+// raw_k = sum_b Re(conj((H psi)_b) D_k(b) psi_{b ^ x}) needs only the b with
+// psi_{b ^ x} != 0, i.e. b = k' ^ x for the listed nonzero amplitudes psi(k')
+// (amp_list); every such b is reached exactly once.  A thread takes one
+// amplitude at a time and runs it against the block's kOpsPerBlock
+// generators (per-thread compensated sums, one per generator); (H psi)_b is
+// read only where D_k(b) != 0.  Returns at once when the list is incomplete
+// (more than acap amplitudes): the live-octet kernel then runs.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* __restrict__ aidx,
+                const C_t<R>* __restrict__ aval, const uint32_t* __restrict__ alen, uint32_t acap, double* part,
+                int nbx) {
+  if (*alen > acap) return;
+  __shared__ LutDev<R> s_op[kOpsPerBlock];
+  __shared__ double s_red[kOpsPerBlock][kWarps];
+  const int first = blockIdx.y * kOpsPerBlock;
+  const int nops = min(kOpsPerBlock, tb.M - first);
+  if (threadIdx.x < nops) s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[tb.porder[first + threadIdx.x]];
+  __syncthreads();
+  const uint32_t n = *alen;
+  const uint32_t per = (n + nbx - 1) / nbx;
+  const uint32_t l0 = blockIdx.x * per, l1 = min(n, l0 + per);
+  R acc[kOpsPerBlock], cmp[kOpsPerBlock];
+#pragma unroll
+  for (int o = 0; o < kOpsPerBlock; ++o) acc[o] = cmp[o] = R(0);
+  for (uint32_t l = l0 + threadIdx.x; l < l1; l += kThreads) {
+    const uint32_t kp = aidx[l];
+    const C_t<R> p = aval[l];
+#pragma unroll
+    for (int o = 0; o < kOpsPerBlock; ++o) {
+      if (o >= nops) break;
+      const LutDev<R>& L = s_op[o];
+      const uint32_t b = kp ^ L.x;
+      const R d = L.lut[lut_phi(L, b)];
+      if (d == R(0)) continue;
+      const C_t<R> h = hpsi[b];
+      const R a = ((__popc(b & L.z0) & 1) ? -d : d) * (h.x * p.x + h.y * p.y);
+      if (sizeof(R) == 4) {
+        const R y = a - cmp[o], t = acc[o] + y;
+        cmp[o] = (t - acc[o]) - y;
+        acc[o] = t;
+      } else {
+        acc[o] += a;
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 0; o < kOpsPerBlock; ++o) {
+    const double v = warp_sum((double)acc[o] - (double)cmp[o]);
+    if (lane == 0) s_red[o][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nops) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s_red[threadIdx.x][w];
+    part[(size_t)(first + threadIdx.x) * nbx + blockIdx.x] = t;
+  }
+}
+
+// gate set: returns at once when *gate <= gate_max (k_pool_grad_amp runs).
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_live(DevTables tb, const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ hpsi,
                  const uint32_t* __restrict__ mask, const uint32_t* __restrict__ list,
-                 const uint32_t* __restrict__ list_len, double* part, int nbx) {
+                 const uint32_t* __restrict__ list_len, double* part, int nbx, const uint32_t* gate,
+                 uint32_t gate_max) {
+  if (gate && *gate <= gate_max) return;
   __shared__ LutDev<R> s_op[kOpsPerBlock];
   __shared__ double s_red[kWarps];
   const int first = blockIdx.y * kOpsPerBlock;
@@ -2111,16 +2176,26 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
         (rc = octet_mask(p.precision, psi, nullptr, p.n_qubits, d.t.octmask, nullptr, d.sm_count, st)))
       return rc;
     if (mask) {
-      // the live octets of psi, in index order, then one pass over them
-      if ((rc = live_octets(mask, p.n_qubits, d.live, st))) return rc;
+      // the nonzero amplitudes of psi, one pass over them (k_pool_grad_amp);
+      // when they do not fit the list (or the problem has none), the live
+      // octets in index order and one pass over those (k_pool_grad_live)
+      const bool amps = d.live.aidx != nullptr;
       const uint64_t octets = 1ull << (p.n_qubits - 3);
       int lnbx = (int)std::max<uint64_t>(1, std::min<uint64_t>(64, (octets + kThreads * 64 - 1) / (kThreads * 64)));
       lnbx = std::max(1, std::min<int>(lnbx, (int)(d.scratch_doubles / ((size_t)nchunks * kOpsPerBlock))));
+      if (amps && (rc = amp_list(p.precision, psi, mask, p.n_qubits, d.live, st))) return rc;
+      if ((rc = live_octets(mask, p.n_qubits, d.live, st))) return rc;
       {
-        ProfScope ps(GOCP_KERNEL_POOL_GRAD, st);
+        ProfScope ps(GOCP_KERNEL_POOL_GRAD, st, amps ? 2 : 1);
+        if (amps)
+          k_pool_grad_amp<R><<<dim3(lnbx, nchunks), kThreads, 0, st>>>(
+              d.t, (const C_t<R>*)hpsi, d.live.aidx, (const C_t<R>*)d.live.aval, d.live.alen, d.live.acap,
+              d.scratch, lnbx);
         k_pool_grad_live<R><<<dim3(lnbx, nchunks), kThreads, 0, st>>>(
-            d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi, mask, d.live.list, d.live.len, d.scratch, lnbx);
+            d.t, (const C_t<R>*)psi, (const C_t<R>*)hpsi, mask, d.live.list, d.live.len, d.scratch, lnbx,
+            amps ? d.live.alen : nullptr, d.live.acap);
       }
+      if (amps) ++n;
       k_pool_reduce<<<(M + 7) / 8, 256, 0, st>>>(d.scratch, lnbx, M, d.graw);
       ++n;
     } else {
