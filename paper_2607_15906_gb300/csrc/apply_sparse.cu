@@ -78,20 +78,32 @@ __device__ __forceinline__ uint32_t nonzero_members(const C_t<R> (&v)[kAmpsH]) {
   return nz;
 }
 
-// counts[b] = the nonzero amplitudes in the live octets of mask words
-// kAmpBlock b .. kAmpBlock (b + 1) - 1.
+// Members of octet o nonzero in psi or (when set) psi2.
+template <typename R>
+__device__ __forceinline__ uint32_t octet_nonzero2(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2,
+                                                   uint32_t o) {
+  C_t<R> v[kAmpsH];
+  load_octet<R>(psi, o, v);
+  uint32_t nz = nonzero_members<R>(v);
+  if (psi2) {
+    load_octet<R>(psi2, o, v);
+    nz |= nonzero_members<R>(v);
+  }
+  return nz;
+}
+
+// counts[b] = the amplitudes nonzero in psi or psi2 in the live octets of
+// mask words kAmpBlock b .. kAmpBlock (b + 1) - 1.
 template <typename R>
 __global__ void __launch_bounds__(kAmpBlock)
-k_amp_count(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, uint32_t words, uint32_t* counts) {
+k_amp_count(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, const uint32_t* __restrict__ mask,
+            uint32_t words, uint32_t* counts) {
   __shared__ uint32_t red[kAmpBlock / 32];
   const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
   uint32_t c = 0;
   if (w < words) {
-    for (uint32_t m = mask[w]; m; m &= m - 1u) {
-      C_t<R> v[kAmpsH];
-      load_octet<R>(psi, w * 32u + (uint32_t)(__ffs(m) - 1), v);
-      c += __popc(nonzero_members<R>(v));
-    }
+    for (uint32_t m = mask[w]; m; m &= m - 1u)
+      c += __popc(octet_nonzero2<R>(psi, psi2, w * 32u + (uint32_t)(__ffs(m) - 1)));
   }
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -103,9 +115,9 @@ k_amp_count(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, u
   }
 }
 
-// counts[0..nb) -> exclusive prefix sums in place; *total = the sum.  One
-// block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total) {
+// counts[0..nb) -> exclusive prefix sums in place; *total = the sum (and,
+// when set, also[0] = the sum, also[1] = 0).  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* also) {
   __shared__ uint32_t s[1024];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -125,24 +137,31 @@ __global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb
     if (threadIdx.x == 0) carry += s[1023];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry;
+  if (threadIdx.x == 0) {
+    *total = carry;
+    if (also) {
+      also[0] = carry;
+      also[1] = 0u;
+    }
+  }
 }
 
-// Writes (index, value) of every nonzero amplitude, in index order, at the
-// offsets of k_amp_scan; entries at or beyond cap are not stored.
+// Writes the index (and, when aval is set, the psi value) of every amplitude
+// nonzero in psi or psi2, in index order, at the offsets of k_amp_scan;
+// entries at or beyond cap are not stored.  With amask set, also writes the
+// 8 words of amask (one bit per amplitude) that cover this thread's mask
+// word, zeros included.
 template <typename R>
 __global__ void __launch_bounds__(kAmpBlock)
-k_amp_list(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, uint32_t words,
-           const uint32_t* __restrict__ offs, uint32_t* aidx, C_t<R>* aval, uint32_t cap) {
+k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, const uint32_t* __restrict__ mask,
+           uint32_t words, const uint32_t* __restrict__ offs, uint32_t* aidx, C_t<R>* aval, uint32_t* amask,
+           uint32_t cap) {
   __shared__ uint32_t red[kAmpBlock / 32];
   const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
   const uint32_t mw = w < words ? mask[w] : 0u;
   uint32_t c = 0;
-  for (uint32_t m = mw; m; m &= m - 1u) {
-    C_t<R> v[kAmpsH];
-    load_octet<R>(psi, w * 32u + (uint32_t)(__ffs(m) - 1), v);
-    c += __popc(nonzero_members<R>(v));
-  }
+  for (uint32_t m = mw; m; m &= m - 1u)
+    c += __popc(octet_nonzero2<R>(psi, psi2, w * 32u + (uint32_t)(__ffs(m) - 1)));
   // exclusive scan over the block: lanes by shuffles, warps through red
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = c;
@@ -155,19 +174,31 @@ k_amp_list(const C_t<R>* __restrict__ psi, const uint32_t* __restrict__ mask, ui
   uint32_t before = 0;
   for (int q = 0; q < warp; ++q) before += red[q];
   uint32_t at = offs[blockIdx.x] + before + incl - c;
+  uint32_t am[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // amask words 8w .. 8w + 7
   for (uint32_t m = mw; m; m &= m - 1u) {
-    const uint32_t o = w * 32u + (uint32_t)(__ffs(m) - 1);
+    const uint32_t ob = (uint32_t)(__ffs(m) - 1), o = w * 32u + ob;
     C_t<R> v[kAmpsH];
     load_octet<R>(psi, o, v);
+    uint32_t nz = nonzero_members<R>(v);
+    if (psi2) {
+      C_t<R> v2[kAmpsH];
+      load_octet<R>(psi2, o, v2);
+      nz |= nonzero_members<R>(v2);
+    }
+    am[ob >> 2] |= nz << (8u * (ob & 3u));
 #pragma unroll
     for (int q = 0; q < kAmpsH; ++q)
-      if (v[q].x != R(0) || v[q].y != R(0)) {
+      if ((nz >> q) & 1u) {
         if (at < cap) {
           aidx[at] = o * 8u + (uint32_t)q;
-          aval[at] = v[q];
+          if (aval) aval[at] = v[q];
         }
         ++at;
       }
+  }
+  if (amask && w < words) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) amask[8u * w + q] = am[q];
   }
 }
 
@@ -461,19 +492,42 @@ int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const 
   const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
   if (precision == GOCP_C64) {
     const float2* p = reinterpret_cast<const float2*>(psi);
-    k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
-    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts, lv.aidx,
-                                                reinterpret_cast<float2*>(lv.aval), lv.acap);
+    k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr);
+    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
+                                                reinterpret_cast<float2*>(lv.aval), nullptr, lv.acap);
   } else {
     const double2* p = reinterpret_cast<const double2*>(psi);
-    k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen);
-    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, mask, words, lv.acounts, lv.aidx,
-                                                 reinterpret_cast<double2*>(lv.aval), lv.acap);
+    k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr);
+    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
+                                                 reinterpret_cast<double2*>(lv.aval), nullptr, lv.acap);
   }
   count_launches(3);
   return cuda_status(cudaGetLastError(), "k_amp_list");
+}
+
+int chain_list(int precision, const void* psi, const void* lam, const uint32_t* mask, int n, const ChainList& cl,
+               uint32_t* counts, cudaStream_t st) {
+  if (n < 8 || !mask || !cl.list || !cl.amask || !cl.cnt || !counts)
+    return fail(GOCP_EINVAL, "chain list needs n >= 8 and its buffers");
+  const uint32_t words = 1u << (n - 8);
+  const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
+  if (precision == GOCP_C64) {
+    const float2* p = reinterpret_cast<const float2*>(psi);
+    const float2* q = reinterpret_cast<const float2*>(lam);
+    k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, cl.cnt, cl.cnt + 1);
+    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(psi);
+    const double2* q = reinterpret_cast<const double2*>(lam);
+    k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, cl.cnt, cl.cnt + 1);
+    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
+  }
+  count_launches(3);
+  return cuda_status(cudaGetLastError(), "chain list");
 }
 
 template int sparse_apply_h<float>(SparseArgs<float>, const LiveOctets&, int, cudaStream_t);

@@ -179,6 +179,20 @@ struct __align__(16) TiledPiece {
   uint32_t xhi, off, bytes, pad;
 };
 
+// Nonzero-amplitude list carried through a tracked chain of Taylor or
+// adjoint steps (LUT pools, n >= 8): list[0 .. min(cnt[0], cap)) holds every
+// nonzero amplitude index of the chain's state(s) (and possibly indices whose
+// amplitude became zero again) and amask has their bits (2^n bits); cnt[1]
+// is the list length when the current step began (written by the previous
+// step's last block), cnt[2] counts finished blocks.  cnt[0] > cap: the list
+// is incomplete and the steps enumerate the operator's pairs instead.
+struct ChainList {
+  uint32_t* list = nullptr;
+  uint32_t* amask = nullptr;
+  uint32_t* cnt = nullptr;
+  uint32_t cap = 0;
+};
+
 // Device copies of the tables of one problem.
 //
 // Hamiltonian: the identity term is a scalar; the diagonal group (x = 0) is
@@ -267,6 +281,7 @@ struct DevTables {
   const void* plut = nullptr;
   const PairEnum* penum = nullptr;
   uint32_t penum_max = 0;   // largest touched-pair count of any generator
+  ChainList cl;             // tracked chains (list == nullptr: none)
 };
 
 
@@ -473,6 +488,13 @@ struct SparseArgs {
   unsigned int* tile_counter;   // reset by octet_mask
   double* scal;
 };
+
+// Lists the amplitudes nonzero in psi or lam into cl (index order, the first
+// cl.cap of them), writes cl.amask, and sets cl.cnt = {count, count, 0};
+// mask must mark every octet where psi or lam is nonzero.  Defined in
+// apply_sparse.cu.
+int chain_list(int precision, const void* psi, const void* lam, const uint32_t* mask, int n, const ChainList& cl,
+               uint32_t* counts, cudaStream_t st);
 
 // Lists the nonzero amplitudes of psi into lv.aidx / lv.aval (index order,
 // the first lv.acap of them) and their number into lv.alen; mask must mark

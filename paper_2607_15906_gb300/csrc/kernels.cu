@@ -61,6 +61,7 @@ struct DeviceTables {
   // live-octet list of the pool-gradient pass and of the scatter H psi
   // kernel (n >= 8)
   LiveOctets live;
+  uint32_t* chain_counts = nullptr;   // per-block counts of chain_list
 };
 
 // ------------------------------------------------------------ reductions
@@ -95,15 +96,28 @@ __device__ void setup_body(C_t<R>* psi, int n, uint64_t index, const double* the
 }
 
 // With `mask` set (psi set, n >= 8) also mask = the nonzero octets of
-// |index>: the one bit of index's octet.
+// |index>: the one bit of index's octet; with a chain list as well, the list
+// = {index} (its amplitude mask the one bit of index, cnt = {1, 1, 0}).
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
-k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs, uint32_t* mask) {
+k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs, uint32_t* mask,
+        ChainList cl) {
   setup_body<R>(psi, n, index, theta, n_ops, coefs, blockIdx.x, gridDim.x);
   if (mask) {
     const uint32_t words = 1u << (n - 8), iw = (uint32_t)(index >> 8);
     for (uint32_t w = blockIdx.x * kThreads + threadIdx.x; w < words; w += gridDim.x * kThreads)
       mask[w] = w == iw ? 1u << ((index >> 3) & 31u) : 0u;
+    if (cl.list) {
+      const uint32_t aw = 1u << (n - 5), ia = (uint32_t)(index >> 5);
+      for (uint32_t w = blockIdx.x * kThreads + threadIdx.x; w < aw; w += gridDim.x * kThreads)
+        cl.amask[w] = w == ia ? 1u << (index & 31u) : 0u;
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cl.list[0] = (uint32_t)index;
+        cl.cnt[0] = 1u;
+        cl.cnt[1] = 1u;
+        cl.cnt[2] = 0u;
+      }
+    }
   }
 }
 
@@ -516,6 +530,45 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
 // v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
 // m = 0..5, stay in registers.
+// Chain lists (ChainList): membership, append, and the end of a step.
+__device__ __forceinline__ bool chain_listed(const ChainList& cl, uint32_t k) {
+  return (cl.amask[k >> 5] >> (k & 31u)) & 1u;
+}
+
+// k (not listed, its amplitude now nonzero) joins the list; its octet's bit
+// is set in mask as well.  Past cap the index is not stored (the list is then
+// incomplete and later steps enumerate pairs).
+__device__ __forceinline__ void chain_append(const ChainList& cl, uint32_t k, uint32_t* mask) {
+  const uint32_t bit = 1u << (k & 31u);
+  if (atomicOr(cl.amask + (k >> 5), bit) & bit) return;
+  const uint32_t pos = atomicAdd(cl.cnt, 1u);
+  if (pos < cl.cap) cl.list[pos] = k;
+  octet_set(mask, k);
+}
+
+// The pair of listed index k for mask x (lowest set bit s): its base b
+// (bit s clear) and whether k's entry computes it -- the base's entry when
+// the base is listed, else the partner's.
+__device__ __forceinline__ bool chain_pair(const ChainList& cl, uint32_t k, uint32_t x, int s, uint32_t* b) {
+  *b = ((k >> s) & 1u) ? k ^ x : k;
+  return *b == k || !chain_listed(cl, *b);
+}
+
+// Called by every thread of every block at the end of a list-mode Taylor
+// step: the last block to finish publishes the list length for the next
+// step.
+__device__ __forceinline__ void chain_step_done(const ChainList& cl, int nb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(cl.cnt + 2, 1u) == (unsigned)(nb - 1)) {
+      __threadfence();
+      cl.cnt[1] = *(volatile uint32_t*)cl.cnt;
+      cl.cnt[2] = 0u;
+    }
+  }
+}
+
 // LUT form of the same step: real D on the pair; only the pairs the
 // operator touches are visited (enumerated, see PairEnum) -- on the others
 // T = I and nothing is read or written.
@@ -523,6 +576,35 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // two octets are marked zero is skipped -- T maps (0, 0) to (0, 0) -- and a
 // pair that is computed marks both of its octets, so that the mask stays
 // valid for the updated psi.
+// With `mask` and a complete chain list (tb.cl), the step walks the listed
+// nonzero amplitudes instead of the operator's pairs: a touched pair is
+// computed once, by its base's entry if the base is listed, else by its
+// partner's; a pair with neither end listed is zero and stays zero; the
+// unlisted end of a computed pair joins the list when it becomes nonzero.
+template <typename R>
+__device__ __forceinline__ void taylor_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph, C_t<R>* psi,
+                                            C_t<R>& o1, C_t<R>& o2) {
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const uint32_t b2 = b ^ L.x;
+  const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+  const uint32_t sg = __popc(b & L.z0) & 1u;
+  const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+  C_t<R> v1 = psi[b], v2 = psi[b2];
+  C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
+#pragma unroll
+  for (int m = 1; m <= 5; ++m) {
+    C_t<R> n1 = cscale<R>(v2, d1), n2 = cscale<R>(v1, d2);   // (A v)[b] = D(b) v[b^x]
+    v1 = n1;
+    v2 = n2;
+    kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
+    kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
+  }
+  o1 = csub<R>(s1, e1);
+  o2 = csub<R>(s2, e2);
+  psi[b] = o1;
+  psi[b2] = o2;
+}
+
 template <typename R>
 __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                 C_t<R>* psi, int32_t* err, int bid, int nb, uint32_t* mask) {
@@ -536,7 +618,27 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
-  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const uint32_t phx = L.fx & 7u;
+  const ChainList& cl = tb.cl;
+  if (mask && cl.list) {
+    const uint32_t n0 = cl.cnt[1];
+    if (n0 <= cl.cap) {
+      for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
+        const uint32_t k = cl.list[q];
+        uint32_t b;
+        if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
+        const uint32_t ph = lut_phi(L, b);
+        if (L.lut[ph] == R(0) && L.lut[ph ^ phx] == R(0)) continue;   // T = I on the pair
+        C_t<R> o1, o2;
+        taylor_pair<R>(L, c, b, ph, psi, o1, o2);
+        const uint32_t other = b == k ? b ^ L.x : b;
+        const C_t<R> ov = b == k ? o2 : o1;
+        if ((ov.x != R(0) || ov.y != R(0)) && !chain_listed(cl, other)) chain_append(cl, other, mask);
+      }
+      chain_step_done(cl, nb);
+      return;
+    }
+  }
   const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
   for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
     uint32_t ph;
@@ -548,21 +650,8 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
       m2 = octet_bit(mask, b2);
       if (!(m1 | m2)) continue;
     }
-    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    const uint32_t sg = __popc(b & L.z0) & 1u;
-    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-    C_t<R> v1 = psi[b], v2 = psi[b2];
-    C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
-#pragma unroll
-    for (int m = 1; m <= 5; ++m) {
-      C_t<R> n1 = cscale<R>(v2, d1), n2 = cscale<R>(v1, d2);   // (A v)[b] = D(b) v[b^x]
-      v1 = n1;
-      v2 = n2;
-      kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
-      kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
-    }
-    psi[b] = csub<R>(s1, e1);
-    psi[b2] = csub<R>(s2, e2);
+    C_t<R> o1, o2;
+    taylor_pair<R>(L, c, b, ph, psi, o1, o2);
     if (!m1) octet_set(mask, b);
     if (!m2) octet_set(mask, b2);
   }
@@ -627,6 +716,39 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 // zero is skipped -- it adds nothing to dE and stays zero -- and a computed
 // pair marks both of its octets.
 template <typename R>
+__device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph,
+                                               C_t<R>* psi, C_t<R>* lam, C_t<R> (&out)[4]) {
+  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
+  const uint32_t b2 = b ^ L.x;
+  const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
+  const uint32_t sg = __popc(b & L.z0) & 1u;
+  const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
+  const R mu = d1 * d2, mu2 = mu * mu;
+  const R cc = c[0] + c[2] * mu + c[4] * mu2;
+  const R sc = c[1] + c[3] * mu + c[5] * mu2;
+  const R cd = c[1] * mu + c[3] * mu2;
+  const R inv = R(1) / (cc * cc - sc * sc * mu);
+  const R sd1 = sc * d1, sd2 = sc * d2;
+  const C_t<R> u1 = psi[b], u2 = psi[b2];
+  const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
+  const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
+  const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
+  const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
+  const C_t<R> l1v = lam[b], l2v = lam[b2];
+  const double v = 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x +
+                          (double)l2v.y * t2.y);
+  out[0] = q1;
+  out[1] = q2;
+  out[2] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
+  out[3] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
+  psi[b] = out[0];
+  psi[b2] = out[1];
+  lam[b] = out[2];
+  lam[b2] = out[3];
+  return v;
+}
+
+template <typename R>
 __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                  C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
                                  double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask) {
@@ -644,44 +766,51 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
-  const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
+  const uint32_t phx = L.fx & 7u;
   double v[1] = {0.0};
-  for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
-    uint32_t ph;
-    const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
-    const uint32_t b2 = b ^ L.x;
-    uint32_t m1 = 1u, m2 = 1u;
-    if (mask) {
-      m1 = octet_bit(mask, b);
-      m2 = octet_bit(mask, b2);
-      if (!(m1 | m2)) continue;
+  const ChainList& cl = tb.cl;
+  const bool listed = mask && cl.list && cl.cnt[1] <= cl.cap;
+  if (listed) {
+    // the listed amplitudes, nonzero in psi or lambda (see taylor_lut_body)
+    const uint32_t n0 = cl.cnt[1];
+    for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
+      const uint32_t k = cl.list[q];
+      uint32_t b;
+      if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
+      const uint32_t ph = lut_phi(L, b);
+      if (L.lut[ph] == R(0) && L.lut[ph ^ phx] == R(0)) continue;   // T = I, T' = 0 on the pair
+      C_t<R> o[4];
+      v[0] += adjoint_pair<R>(L, c, b, ph, psi, lam, o);
+      const bool base = b == k;
+      const uint32_t other = base ? b ^ L.x : b;
+      const C_t<R> op1 = base ? o[1] : o[0], ol1 = base ? o[3] : o[2];
+      if ((op1.x != R(0) || op1.y != R(0) || ol1.x != R(0) || ol1.y != R(0)) && !chain_listed(cl, other))
+        chain_append(cl, other, mask);
     }
-    const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
-    const uint32_t sg = __popc(b & L.z0) & 1u;
-    const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-    const R mu = d1 * d2, mu2 = mu * mu;
-    const R cc = c[0] + c[2] * mu + c[4] * mu2;
-    const R sc = c[1] + c[3] * mu + c[5] * mu2;
-    const R cd = c[1] * mu + c[3] * mu2;
-    const R inv = R(1) / (cc * cc - sc * sc * mu);
-    const R sd1 = sc * d1, sd2 = sc * d2;
-    const C_t<R> u1 = psi[b], u2 = psi[b2];
-    const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
-    const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
-    const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
-    const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
-    const C_t<R> l1v = lam[b], l2v = lam[b2];
-    v[0] += 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x +
-                   (double)l2v.y * t2.y);
-    psi[b] = q1;
-    psi[b2] = q2;
-    lam[b] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
-    lam[b2] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
-    if (!m1) octet_set(mask, b);
-    if (!m2) octet_set(mask, b2);
+  } else {
+    const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
+    for (uint64_t q = bid * (uint64_t)kThreads + threadIdx.x; q < count; q += (uint64_t)nb * kThreads) {
+      uint32_t ph;
+      const uint32_t b = enum_pair(E, (uint32_t)q, &ph);
+      const uint32_t b2 = b ^ L.x;
+      uint32_t m1 = 1u, m2 = 1u;
+      if (mask) {
+        m1 = octet_bit(mask, b);
+        m2 = octet_bit(mask, b2);
+        if (!(m1 | m2)) continue;
+      }
+      C_t<R> o[4];
+      v[0] += adjoint_pair<R>(L, c, b, ph, psi, lam, o);
+      if (!m1) octet_set(mask, b);
+      if (!m2) octet_set(mask, b2);
+    }
   }
-  grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
+  // the last block also publishes the list length for the next step (every
+  // block has added its entries before it arrives)
+  if (grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot) && listed && threadIdx.x == 0) {
+    __threadfence();
+    cl.cnt[1] = *(volatile uint32_t*)cl.cnt;
+  }
 }
 
 template <typename R>
@@ -1889,6 +2018,16 @@ int upload_problem(Problem& p) {
   rc = p.precision == GOCP_C64 ? upload_typed<float>(p, *d, bytes, &p.identity)
                                : upload_typed<double>(p, *d, bytes, &p.identity);
   if (rc) return rc;
+  if (p.n_qubits >= 8 && d->t.pool_lut) {
+    // chain list: a quarter of the state's indices at most, one amplitude-mask bit each
+    const int n = p.n_qubits;
+    const size_t nb = ((((size_t)1 << (n - 8)) + 255) / 256) + 1;
+    if ((rc = dalloc(*d, &d->t.cl.list, (size_t)1 << (n - 2), bytes)) ||
+        (rc = dalloc(*d, &d->t.cl.amask, (size_t)1 << (n - 5), bytes)) || (rc = dalloc(*d, &d->t.cl.cnt, 4, bytes)) ||
+        (rc = dalloc(*d, &d->chain_counts, nb, bytes)))
+      return rc;
+    d->t.cl.cap = 1u << (n - 2);
+  }
   int sm = 0;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, p.device);
   d->sm_count = sm > 0 ? sm : 1;
@@ -2074,7 +2213,7 @@ static int launch_setup(Problem& p, void* psi, const double* d_theta, int n_ops,
   const uint64_t dim = psi ? 1ull << p.n_qubits : 1;
   int grid = grid_for(dim, p.dev->sm_count, 8);
   k_setup<R><<<grid, kThreads, 0, st>>>((C_t<R>*)psi, p.n_qubits, p.ref_index, d_theta, n_ops,
-                                        p.dev->coefs, psi ? p.dev->t.octmask : nullptr);
+                                        p.dev->coefs, psi ? p.dev->t.octmask : nullptr, p.dev->t.cl);
   count_launches(1);
   return cuda_status(cudaGetLastError(), "k_setup");
 }
@@ -2241,6 +2380,10 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   uint32_t* mask = d.t.pool_lut ? d.t.octmask2 : nullptr;
   int rc;
   if (mask && (rc = octet_mask(p.precision, psi, lam, p.n_qubits, mask, nullptr, d.sm_count, st))) return rc;
+  // the amplitudes nonzero in psi or lambda, kept complete by the sweep
+  if (mask && d.t.cl.list &&
+      (rc = chain_list(p.precision, psi, lam, mask, p.n_qubits, d.t.cl, d.chain_counts, st)))
+    return rc;
   count_launches(1);   // k_residual (and k_octet_mask counts itself)
   DevTables tb = d.t;
   const double* coefs = d.coefs;

@@ -206,6 +206,44 @@ def test_random_tables_with_phases(prec, n):
     assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [8, 10])
+def test_chain_list_overflow_falls_back(prec, n):
+    """Tracked Taylor and adjoint chains follow a list of the state's nonzero
+    amplitudes, with room for a quarter of them; generators with one-qubit x
+    masks spread |0> over all 2^n amplitudes, so the list overflows part-way
+    through the forward chain (and before the adjoint sweep) and the steps
+    enumerate pairs from there on.  States, E and dE/dtheta against the oracle."""
+    rng = np.random.default_rng(40 + n)
+    H = _hermitian_random_table(n, 6 * n, rng)
+    gens = []
+    for q in range(n):
+        x = 1 << q
+        z = rng.integers(0, 1 << n, size=2).astype(np.int64)
+        ph = (parity(x & z) ^ 1) + 2 * rng.integers(0, 2, size=2)    # anti-Hermitian strings
+        c = rng.integers(1, 9, size=2) / 8.0
+        gens.append(PauliTable(n, np.full(2, x, np.int64), z, ph.astype(np.int64), c))
+    to_t = lambda t: (t.x.astype(np.uint32), t.z.astype(np.uint32), (t.phase % 4).astype(np.uint8), t.coeff)
+    try:
+        p = gb.Problem.from_tables(n, to_t(H), [to_t(g) for g in gens], ref_index=0, precision=prec, device=0)
+    except gb.GocpError:
+        pytest.skip("random generator summed to zero")
+    off, gx, gz, gph, gc, fam = p.pool()
+    tabs = [PauliTable(n, gx[off[k]:off[k + 1]].astype(np.int64), gz[off[k]:off[k + 1]].astype(np.int64),
+                       gph[off[k]:off[k + 1]].astype(np.int64), gc[off[k]:off[k + 1]]) for k in range(len(gens))]
+    ops = np.concatenate([np.arange(len(tabs)), rng.permutation(len(tabs))[:4]]).astype(np.int32)
+    th = rng.uniform(0.2, 0.7, size=len(ops)) * rng.choice([-1.0, 1.0], size=len(ops))
+    d = p.new_states(1)[0]
+    p.prepare_state(ops, th, d)
+    sref = sv.prepare_state(sv.basis_state(n, 0), tabs, ops, th)
+    assert np.count_nonzero(sref) > (1 << n) // 4
+    assert np.max(np.abs(_host(d) - sref)) <= TOL[prec]["state"] * np.max(np.abs(sref)) * 4
+    e2, de = p.energy_grad(ops, th)
+    e_ref, de_ref = sv.energy_grad(H, sv.basis_state(n, 0), tabs, ops, th)
+    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
+    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
+
+
 def _grouped_random_table(n, rng):
     """A Hermitian table with x-groups of 1..40 terms (z-ranks from 0 to
     beyond the LUT limit), real and imaginary weights, a diagonal group, and
