@@ -115,9 +115,11 @@ k_amp_count(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, con
   }
 }
 
-// counts[0..nb) -> exclusive prefix sums in place; *total = the sum (and,
-// when set, also[0] = the sum, also[1] = 0).  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* also) {
+// counts[0..nb) -> exclusive prefix sums in place; *total = the sum (when
+// set; and, when ring is set, the chain-list ring's base(slot) = the sum,
+// count(slot) = count(first) = 0).  One block of 1024 threads.
+__global__ void __launch_bounds__(1024)
+k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int slot, int first) {
   __shared__ uint32_t s[1024];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -138,10 +140,11 @@ __global__ void __launch_bounds__(1024) k_amp_scan(uint32_t* counts, uint32_t nb
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *total = carry;
-    if (also) {
-      also[0] = carry;
-      also[1] = 0u;
+    if (total) *total = carry;
+    if (ring) {
+      ring[kRingBase(slot)] = carry;
+      ring[kRingAdd(slot)] = 0u;
+      ring[kRingAdd(first)] = 0u;
     }
   }
 }
@@ -493,13 +496,13 @@ int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const 
   if (precision == GOCP_C64) {
     const float2* p = reinterpret_cast<const float2*>(psi);
     k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0);
     k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
                                                 reinterpret_cast<float2*>(lv.aval), nullptr, lv.acap);
   } else {
     const double2* p = reinterpret_cast<const double2*>(psi);
     k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0);
     k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
                                                  reinterpret_cast<double2*>(lv.aval), nullptr, lv.acap);
   }
@@ -508,7 +511,7 @@ int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const 
 }
 
 int chain_list(int precision, const void* psi, const void* lam, const uint32_t* mask, int n, const ChainList& cl,
-               uint32_t* counts, cudaStream_t st) {
+               uint32_t* counts, int slot, int first, cudaStream_t st) {
   if (n < 8 || !mask || !cl.list || !cl.amask || !cl.cnt || !counts)
     return fail(GOCP_EINVAL, "chain list needs n >= 8 and its buffers");
   const uint32_t words = 1u << (n - 8);
@@ -517,13 +520,13 @@ int chain_list(int precision, const void* psi, const void* lam, const uint32_t* 
     const float2* p = reinterpret_cast<const float2*>(psi);
     const float2* q = reinterpret_cast<const float2*>(lam);
     k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
-    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, cl.cnt, cl.cnt + 1);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first);
     k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
   } else {
     const double2* p = reinterpret_cast<const double2*>(psi);
     const double2* q = reinterpret_cast<const double2*>(lam);
     k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
-    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, cl.cnt, cl.cnt + 1);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first);
     k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
   }
   count_launches(3);

@@ -180,12 +180,21 @@ struct __align__(16) TiledPiece {
 };
 
 // Nonzero-amplitude list carried through a tracked chain of Taylor or
-// adjoint steps (LUT pools, n >= 8): list[0 .. min(cnt[0], cap)) holds every
+// adjoint steps (LUT pools, n >= 8): the first entries of list hold every
 // nonzero amplitude index of the chain's state(s) (and possibly indices whose
-// amplitude became zero again) and amask has their bits (2^n bits); cnt[1]
-// is the list length when the current step began (written by the previous
-// step's last block), cnt[2] counts finished blocks.  cnt[0] > cap: the list
-// is incomplete and the steps enumerate the operator's pairs instead.
+// amplitude became zero again) and amask has their bits (2^n bits).  The
+// list length is kept in a ring of three slots, slot i = step j mod 3: a
+// step starts at length base(p) + count(p) (p = the previous step's slot:
+// its start + the entries it appended), records that start as its own base,
+// appends by counting in its own count, and zeroes the next step's count.
+// A length above cap: the list is incomplete and the steps enumerate the
+// operator's pairs instead.
+// Ring words: slot i's base at cnt[kRingBase(i)], its count at
+// cnt[kRingAdd(i)], each in its own 32-byte sector.
+__host__ __device__ constexpr int kRingBase(int i) { return 8 * i; }
+__host__ __device__ constexpr int kRingAdd(int i) { return 24 + 8 * i; }
+constexpr int kRingWords = 48;
+
 struct ChainList {
   uint32_t* list = nullptr;
   uint32_t* amask = nullptr;
@@ -490,11 +499,13 @@ struct SparseArgs {
 };
 
 // Lists the amplitudes nonzero in psi or lam into cl (index order, the first
-// cl.cap of them), writes cl.amask, and sets cl.cnt = {count, count, 0};
-// mask must mark every octet where psi or lam is nonzero.  Defined in
+// cl.cap of them), writes cl.amask, and sets the ring so that a step whose
+// previous slot is `slot` starts from the whole list: base(slot) = count,
+// count(slot) = 0, and the first step's count(first) = 0; mask
+// must mark every octet where psi or lam is nonzero.  Defined in
 // apply_sparse.cu.
 int chain_list(int precision, const void* psi, const void* lam, const uint32_t* mask, int n, const ChainList& cl,
-               uint32_t* counts, cudaStream_t st);
+               uint32_t* counts, int slot, int first, cudaStream_t st);
 
 // Lists the nonzero amplitudes of psi into lv.aidx / lv.aval (index order,
 // the first lv.acap of them) and their number into lv.alen; mask must mark

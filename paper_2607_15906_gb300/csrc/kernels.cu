@@ -62,6 +62,7 @@ struct DeviceTables {
   // kernel (n >= 8)
   LiveOctets live;
   uint32_t* chain_counts = nullptr;   // per-block counts of chain_list
+  double* dpart = nullptr;            // stage_cap x adjoint_grid partials of dE/dtheta
 };
 
 // ------------------------------------------------------------ reductions
@@ -97,7 +98,8 @@ __device__ void setup_body(C_t<R>* psi, int n, uint64_t index, const double* the
 
 // With `mask` set (psi set, n >= 8) also mask = the nonzero octets of
 // |index>: the one bit of index's octet; with a chain list as well, the list
-// = {index} (its amplitude mask the one bit of index, cnt = {1, 1, 0}).
+// = {index} (its amplitude mask the one bit of index), ready for a forward
+// chain.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, double* coefs, uint32_t* mask,
@@ -112,10 +114,11 @@ k_setup(C_t<R>* psi, int n, uint64_t index, const double* theta, int n_ops, doub
       for (uint32_t w = blockIdx.x * kThreads + threadIdx.x; w < aw; w += gridDim.x * kThreads)
         cl.amask[w] = w == ia ? 1u << (index & 31u) : 0u;
       if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the forward chain's step 0 reads slot 2 and appends in slot 0
         cl.list[0] = (uint32_t)index;
-        cl.cnt[0] = 1u;
-        cl.cnt[1] = 1u;
-        cl.cnt[2] = 0u;
+        cl.cnt[kRingBase(2)] = 1u;
+        cl.cnt[kRingAdd(2)] = 0u;
+        cl.cnt[kRingAdd(0)] = 0u;
       }
     }
   }
@@ -535,13 +538,15 @@ __device__ __forceinline__ bool chain_listed(const ChainList& cl, uint32_t k) {
   return (cl.amask[k >> 5] >> (k & 31u)) & 1u;
 }
 
-// k (not listed, its amplitude now nonzero) joins the list; its octet's bit
-// is set in mask as well.  Past cap the index is not stored (the list is then
-// incomplete and later steps enumerate pairs).
-__device__ __forceinline__ void chain_append(const ChainList& cl, uint32_t k, uint32_t* mask) {
+// k (not listed, its amplitude now nonzero) joins the list at base + the
+// step's count (ring slot cur); its octet's bit is set in mask as well.  Past
+// cap the index is not stored (the list is then incomplete and later steps
+// enumerate pairs).
+__device__ __forceinline__ void chain_append(const ChainList& cl, uint32_t k, uint32_t base, int cur,
+                                             uint32_t* mask) {
   const uint32_t bit = 1u << (k & 31u);
   if (atomicOr(cl.amask + (k >> 5), bit) & bit) return;
-  const uint32_t pos = atomicAdd(cl.cnt, 1u);
+  const uint32_t pos = base + atomicAdd(cl.cnt + kRingAdd(cur), 1u);
   if (pos < cl.cap) cl.list[pos] = k;
   octet_set(mask, k);
 }
@@ -554,19 +559,23 @@ __device__ __forceinline__ bool chain_pair(const ChainList& cl, uint32_t k, uint
   return *b == k || !chain_listed(cl, *b);
 }
 
-// Called by every thread of every block at the end of a list-mode Taylor
-// step: the last block to finish publishes the list length for the next
-// step.
-__device__ __forceinline__ void chain_step_done(const ChainList& cl, int nb) {
-  __syncthreads();
+// Start of step j of a chain (forward: the previous step was j - 1, the
+// next is j + 1; reverse: j + 1 and j - 1): the list length at the start
+// (read once per block), recorded in this step's slot by block 0, and the
+// next step's counter cleared.  Called by every thread of the block.
+__device__ __forceinline__ uint32_t chain_begin(const ChainList& cl, int j, bool forward, int* cur) {
+  __shared__ uint32_t s_n0;
+  const int prev = (j + (forward ? 2 : 1)) % 3, next = (j + (forward ? 1 : 2)) % 3;
+  *cur = j % 3;
   if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(cl.cnt + 2, 1u) == (unsigned)(nb - 1)) {
-      __threadfence();
-      cl.cnt[1] = *(volatile uint32_t*)cl.cnt;
-      cl.cnt[2] = 0u;
+    s_n0 = cl.cnt[kRingBase(prev)] + cl.cnt[kRingAdd(prev)];
+    if (blockIdx.x == 0) {
+      cl.cnt[kRingBase(*cur)] = s_n0;
+      cl.cnt[kRingAdd(next)] = 0u;
     }
   }
+  __syncthreads();
+  return s_n0;
 }
 
 // LUT form of the same step: real D on the pair; only the pairs the
@@ -621,7 +630,8 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
   const uint32_t phx = L.fx & 7u;
   const ChainList& cl = tb.cl;
   if (mask && cl.list) {
-    const uint32_t n0 = cl.cnt[1];
+    int cur;
+    const uint32_t n0 = chain_begin(cl, j, true, &cur);
     if (n0 <= cl.cap) {
       for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
         const uint32_t k = cl.list[q];
@@ -633,9 +643,8 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
         taylor_pair<R>(L, c, b, ph, psi, o1, o2);
         const uint32_t other = b == k ? b ^ L.x : b;
         const C_t<R> ov = b == k ? o2 : o1;
-        if ((ov.x != R(0) || ov.y != R(0)) && !chain_listed(cl, other)) chain_append(cl, other, mask);
+        if ((ov.x != R(0) || ov.y != R(0)) && !chain_listed(cl, other)) chain_append(cl, other, n0, cur, mask);
       }
-      chain_step_done(cl, nb);
       return;
     }
   }
@@ -748,17 +757,22 @@ __device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[
   return v;
 }
 
+// dpart set: each block writes its partial of dE_j to dpart[j nb + bid]
+// (k_dtheta_reduce adds them after the sweep) instead of the in-step grid
+// reduction into dtheta[j].
 template <typename R>
 __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                                  C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
-                                 double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask) {
+                                 double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask, double* dpart) {
   __shared__ double tot[1];
+  __shared__ double s_red[kWarps];
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
     if (bid == 0 && threadIdx.x == 0) {
       atomicOr(err, 1);
       dtheta[j] = 0.0;
     }
+    if (dpart && threadIdx.x == 0) dpart[(size_t)j * nb + bid] = 0.0;
     return;
   }
   const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
@@ -769,10 +783,10 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
   const uint32_t phx = L.fx & 7u;
   double v[1] = {0.0};
   const ChainList& cl = tb.cl;
-  const bool listed = mask && cl.list && cl.cnt[1] <= cl.cap;
-  if (listed) {
+  int cur = 0;
+  const uint32_t n0 = mask && cl.list ? chain_begin(cl, j, false, &cur) : 0xFFFFFFFFu;
+  if (n0 <= cl.cap) {
     // the listed amplitudes, nonzero in psi or lambda (see taylor_lut_body)
-    const uint32_t n0 = cl.cnt[1];
     for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
       const uint32_t k = cl.list[q];
       uint32_t b;
@@ -785,7 +799,7 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
       const uint32_t other = base ? b ^ L.x : b;
       const C_t<R> op1 = base ? o[1] : o[0], ol1 = base ? o[3] : o[2];
       if ((op1.x != R(0) || op1.y != R(0) || ol1.x != R(0) || ol1.y != R(0)) && !chain_listed(cl, other))
-        chain_append(cl, other, mask);
+        chain_append(cl, other, n0, cur, mask);
     }
   } else {
     const uint64_t count = (uint64_t)E.ncodes << E.log2cnt;
@@ -805,20 +819,43 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
       if (!m2) octet_set(mask, b2);
     }
   }
-  // the last block also publishes the list length for the next step (every
-  // block has added its entries before it arrives)
-  if (grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot) && listed && threadIdx.x == 0) {
-    __threadfence();
-    cl.cnt[1] = *(volatile uint32_t*)cl.cnt;
+  if (!dpart) {
+    grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
+    return;
+  }
+  const double w = warp_sum(v[0]);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kWarps; ++q) t += s_red[q];
+    dpart[(size_t)j * nb + bid] = t;
+  }
+}
+
+// dtheta[j] = sum_b dpart[j nb + b], j < n_ops (one block per j).
+__global__ void __launch_bounds__(kThreads) k_dtheta_reduce(const double* dpart, int nb, double* dtheta) {
+  __shared__ double s_red[kWarps];
+  const int j = blockIdx.x;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kThreads) t += dpart[(size_t)j * nb + b];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int q = 0; q < kWarps; ++q) u += s_red[q];
+    dtheta[j] = u;
   }
 }
 
 template <typename R>
 __device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const double* coefs, int j,
                              C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
-                             double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask = nullptr) {
+                             double* dtheta, int32_t* err, int bid, int nb, uint32_t* mask = nullptr,
+                             double* dpart = nullptr) {
   if (tb.pool_lut) {
-    adjoint_lut_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, bid, nb, mask);
+    adjoint_lut_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, bid, nb, mask, dpart);
     return;
   }
   __shared__ uint32_t s_z[kStageStrings];
@@ -866,8 +903,9 @@ __device__ void adjoint_body(const DevTables& tb, const int32_t* ops, const doub
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
-          double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask) {
-  adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask);
+          double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask, double* dpart) {
+  adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask,
+                  dpart);
 }
 
 // ------------------------------------------------------------ pool gradients
@@ -2023,7 +2061,7 @@ int upload_problem(Problem& p) {
     const int n = p.n_qubits;
     const size_t nb = ((((size_t)1 << (n - 8)) + 255) / 256) + 1;
     if ((rc = dalloc(*d, &d->t.cl.list, (size_t)1 << (n - 2), bytes)) ||
-        (rc = dalloc(*d, &d->t.cl.amask, (size_t)1 << (n - 5), bytes)) || (rc = dalloc(*d, &d->t.cl.cnt, 4, bytes)) ||
+        (rc = dalloc(*d, &d->t.cl.amask, (size_t)1 << (n - 5), bytes)) || (rc = dalloc(*d, &d->t.cl.cnt, kRingWords, bytes)) ||
         (rc = dalloc(*d, &d->chain_counts, nb, bytes)))
       return rc;
     d->t.cl.cap = 1u << (n - 2);
@@ -2068,6 +2106,12 @@ void free_device(Problem& p) {
 
 // ------------------------------------------------------------ launchers
 
+// Blocks of an adjoint step (k_adjoint).
+int adjoint_grid(const DeviceTables& d) {
+  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (d.t.n - 1);
+  return grid_for(pairs, d.sm_count, 8);
+}
+
 int ensure_stage(Problem& p, int n_ops) {
   DeviceTables& d = *p.dev;
   if (n_ops <= d.stage_cap) return GOCP_OK;
@@ -2080,6 +2124,8 @@ int ensure_stage(Problem& p, int n_ops) {
   if ((rc = dalloc(d, &d.stage_ops, cap, bytes)) || (rc = dalloc(d, &d.stage_theta, cap, bytes)) ||
       (rc = dalloc(d, &d.coefs, (size_t)cap * 6, bytes)) || (rc = dalloc(d, &d.dtheta, cap, bytes)))
     return rc;
+  // per-block partials of the adjoint sweep (LUT pools): one row of blocks per op
+  if (d.t.pool_lut && (rc = dalloc(d, &d.dpart, (size_t)cap * adjoint_grid(d), bytes))) return rc;
   p.device_bytes += bytes;
   d.stage_cap = cap;
   return GOCP_OK;
@@ -2374,16 +2420,19 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   const uint64_t dim = 1ull << p.n_qubits;
   const int g1 = grid_for(dim, d.sm_count, 8);
   k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, p.n_qubits, d.scalars);
-  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : dim / 2;
-  const int grid = grid_for(pairs, d.sm_count, 8);
+  const int grid = adjoint_grid(d);
   // nonzero octets of psi or lambda, kept valid by the sweep
   uint32_t* mask = d.t.pool_lut ? d.t.octmask2 : nullptr;
   int rc;
   if (mask && (rc = octet_mask(p.precision, psi, lam, p.n_qubits, mask, nullptr, d.sm_count, st))) return rc;
-  // the amplitudes nonzero in psi or lambda, kept complete by the sweep
+  // the amplitudes nonzero in psi or lambda, kept complete by the sweep; its
+  // first step, j = n_ops - 1, reads slot n_ops mod 3 and appends in slot
+  // (n_ops - 1) mod 3
   if (mask && d.t.cl.list &&
-      (rc = chain_list(p.precision, psi, lam, mask, p.n_qubits, d.t.cl, d.chain_counts, st)))
+      (rc = chain_list(p.precision, psi, lam, mask, p.n_qubits, d.t.cl, d.chain_counts, n_ops % 3,
+                       (n_ops - 1) % 3, st)))
     return rc;
+  double* dpart = d.t.pool_lut ? d.dpart : nullptr;
   count_launches(1);   // k_residual (and k_octet_mask counts itself)
   DevTables tb = d.t;
   const double* coefs = d.coefs;
@@ -2393,12 +2442,16 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   double* partials = d.scratch;
   unsigned int* counter = d.counters + kMaxChunks + 2;
   int32_t* err = d.err;
-  void* args[] = {&tb, &d_ops, &coefs, &j, &ps_, &ls_, &partials, &counter, &d_dE, &err, &mask};
-  const size_t sizes[] = {0, sizeof(d_ops), sizeof(coefs), sizeof(j), sizeof(ps_), sizeof(ls_),
-                          sizeof(partials), sizeof(counter), sizeof(d_dE), sizeof(err), sizeof(mask)};
-  ProfScope ps(GOCP_KERNEL_ADJOINT, st, n_ops);
-  if ((rc = launch_chain(p, (const void*)k_adjoint<R>, grid, kThreads, n_ops, true, args, sizes, 11, 3, st)))
+  void* args[] = {&tb, &d_ops, &coefs, &j, &ps_, &ls_, &partials, &counter, &d_dE, &err, &mask, &dpart};
+  const size_t sizes[] = {0,           sizeof(d_ops),   sizeof(coefs), sizeof(j),    sizeof(ps_),  sizeof(ls_),
+                          sizeof(partials), sizeof(counter), sizeof(d_dE), sizeof(err), sizeof(mask), sizeof(dpart)};
+  ProfScope ps(GOCP_KERNEL_ADJOINT, st, n_ops + (dpart ? 1 : 0));
+  if ((rc = launch_chain(p, (const void*)k_adjoint<R>, grid, kThreads, n_ops, true, args, sizes, 12, 3, st)))
     return rc;
+  if (dpart) {
+    k_dtheta_reduce<<<n_ops, kThreads, 0, st>>>(dpart, grid, d_dE);
+    count_launches(1);
+  }
   return cuda_status(cudaGetLastError(), "k_adjoint");
 }
 
