@@ -44,6 +44,7 @@ namespace gocp {
 namespace {
 
 constexpr int kAmpBlock = 256;   // listing passes: one mask word (32 octets) per thread
+constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
 
 // One block per SM: 1024 threads for complex64 (64 registers), 512 for
 // complex128 (128 registers).
@@ -347,10 +348,14 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     const uint32_t n_units = s_pre[P];
     uint32_t cur = 0xFFFFFFFFu;   // piece whose blob this warp holds
     for (;;) {
-      uint32_t j = 0;
-      if (lane == 0) j = atomicAdd(&s_unext, 1u);
-      j = __shfl_sync(0xffffffffu, j, 0);
-      if (j >= n_units) break;
+      // kUnitBatch consecutive units per claim: mostly chunks of one piece,
+      // whose blob is then copied once
+      uint32_t j0 = 0;
+      if (lane == 0) j0 = atomicAdd(&s_unext, kUnitBatch);
+      j0 = __shfl_sync(0xffffffffu, j0, 0);
+      if (j0 >= n_units) break;
+      const uint32_t j1 = min(n_units, j0 + kUnitBatch);
+      for (uint32_t j = j0; j < j1; ++j) {
       // p = the last piece with s_pre[p] <= j (pieces without units share
       // their successor's start and are passed over)
       uint32_t lo = 0, hi = P - 1;
@@ -392,12 +397,46 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         const int g0 = (int)(rd & 0xFFFu), g1 = (int)((rd >> 12) & 0xFFFu);
         for (int g = g0; g < g1; ++g) sp_terms<R, kOct>(gs[g], zs, ws, ks, v, valid, acc);
       }
+      }
     }
     __syncthreads();
-    // epilogue: diagonal, identity and energy on the live own octets; the
-    // whole tile out; the accumulator cleared for the next tile
+    // epilogue, first the nonzero amplitudes of the own tile (one lane
+    // each): the diagonal group and the identity, which act on psi(k) alone,
+    // and the energy partials (zero amplitudes add to neither); each k is
+    // one lane's, so its accumulator entry is updated without atomics
+    {
+      const uint32_t e0 = a.toff[t], e1 = a.toff[t + 1];
+      double2 w = s_v[threadIdx.x];
+      for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
+        const uint32_t k = a.aidx[e];
+        const C_t<R> q = a.aval[e];
+        R dr = R(0), dc = R(0), di = R(0);
+        for (int m = 0; m < a.nd_mid; ++m) {
+          const R y = ((__popc(k & a.dz[m]) & 1) ? -a.dw[m] : a.dw[m]) - dc;
+          if (sizeof(R) == 4) {   // compensated in FP32
+            const R s2 = dr + y;
+            dc = (s2 - dr) - y;
+            dr = s2;
+          } else {
+            dr += y;
+          }
+        }
+        for (int m = a.nd_mid; m < a.nd; ++m) di += (__popc(k & a.dz[m]) & 1) ? -a.dw[m] : a.dw[m];
+        R* e2 = acc + acc_at<kOct>(k);
+        const C_t<R> off = cmake<R>(e2[0], e2[kOct]);
+        const double pp = (double)q.x * q.x + (double)q.y * q.y;
+        w.x += pp;
+        w.y += (double)q.x * off.x + (double)q.y * off.y + ((double)dr - (double)dc) * pp;
+        const R d0 = dr - dc + idr;
+        e2[0] = off.x + d0 * q.x - di * q.y;
+        e2[kOct] = off.y + d0 * q.y + di * q.x;
+      }
+      s_v[threadIdx.x] = w;
+    }
+    __syncthreads();
+    // then the whole tile out (zeros included) and the accumulator cleared
     for (uint32_t o = threadIdx.x; o < kOct; o += NT) {
-      const uint32_t go = (t << (LB - 3)) | o, k0 = go << 3;
+      const uint32_t k0 = ((t << (LB - 3)) | o) << 3;
       C_t<R> res[kAmpsH];
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
@@ -405,26 +444,6 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         res[i] = cmake<R>(e[0], e[kOct]);
         e[0] = R(0);
         e[kOct] = R(0);
-      }
-      if ((a.mask[go >> 5] >> (go & 31u)) & 1u) {
-        R dr[kAmpsH], dc[kAmpsH], di[kAmpsH], dd[kAmpsH];
-#pragma unroll
-        for (int i = 0; i < kAmpsH; ++i) dr[i] = dc[i] = di[i] = dd[i] = R(0);
-        sum_terms8<R>(a.dz, a.dw, 0, a.nd_mid, k0, dr, dc, true);
-        sum_terms8<R>(a.dz, a.dw, a.nd_mid, a.nd, k0, di, dd, false);
-        C_t<R> own[kAmpsH];
-        load_octet<R>(a.psi, go, own);
-        double2 w = s_v[threadIdx.x];
-#pragma unroll
-        for (int i = 0; i < kAmpsH; ++i) {
-          const C_t<R> q = own[i];
-          const double pp = (double)q.x * q.x + (double)q.y * q.y;
-          w.x += pp;
-          w.y += (double)q.x * res[i].x + (double)q.y * res[i].y + ((double)dr[i] - (double)dc[i]) * pp;
-          const R d0 = dr[i] - dc[i] + idr;
-          res[i] = cmake<R>(res[i].x + d0 * q.x - di[i] * q.y, res[i].y + d0 * q.y + di[i] * q.x);
-        }
-        s_v[threadIdx.x] = w;
       }
       C_t<R>* dst = a.out + k0;
       if (sizeof(R) == 4) {
