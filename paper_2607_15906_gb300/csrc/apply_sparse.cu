@@ -355,16 +355,22 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       j0 = __shfl_sync(0xffffffffu, j0, 0);
       if (j0 >= n_units) break;
       const uint32_t j1 = min(n_units, j0 + kUnitBatch);
-      for (uint32_t j = j0; j < j1; ++j) {
-      // p = the last piece with s_pre[p] <= j (pieces without units share
-      // their successor's start and are passed over)
-      uint32_t lo = 0, hi = P - 1;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (s_pre[mid] <= j) lo = mid;
-        else hi = mid - 1;
+      // p = the last piece with s_pre[p] <= j0 (pieces without units share
+      // their successor's start and are passed over), then advanced along
+      // the batch
+      uint32_t p;
+      {
+        uint32_t lo = 0, hi = P - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (s_pre[mid] <= j0) lo = mid;
+          else hi = mid - 1;
+        }
+        p = lo;
       }
-      const uint32_t p = lo, c = j - s_pre[p];
+      for (uint32_t j = j0; j < j1; ++j) {
+      while (p + 1 < P && s_pre[p + 1] <= j) ++p;
+      const uint32_t c = j - s_pre[p];
       const TiledPiece pc = a.piece[p];
       if (p != cur) {
         // the piece's blob into this warp's buffer, 16 bytes per lane
@@ -389,14 +395,9 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       const C_t<R> v = a.aval[valid ? li : a0];
       const int nl = (int)hd->n_lut;
       for (int g = 0; g < nl; ++g) sp_lut<R, kOct>(ls[g], ks, v, valid, acc);
-      // the term-list runs follow the LUT runs
-      const int nr = (int)hd->n_runs;
-      for (int r = 0; r < nr; ++r) {
-        const uint32_t rd = hd->run[r];
-        if ((rd >> 24) < 64u) continue;
-        const int g0 = (int)(rd & 0xFFFu), g1 = (int)((rd >> 12) & 0xFFFu);
-        for (int g = g0; g < g1; ++g) sp_terms<R, kOct>(gs[g], zs, ws, ks, v, valid, acc);
-      }
+      // the term-list groups fill the blob from the LUT groups to z_off
+      const int nt = (int)((hd->z_off - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
+      for (int g = 0; g < nt; ++g) sp_terms<R, kOct>(gs[g], zs, ws, ks, v, valid, acc);
       }
     }
     __syncthreads();
