@@ -518,8 +518,12 @@ def roofline(res, peaks, how):
                "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)",
                "flops_per_launch": flops, "nonzero_amplitudes": nnz}
     else:
-        state = dim * 8
-        per = {"taylor5": 2 * state, "adjoint": 4 * state, "pool_grad": 2 * state}[top]
+        # the nonzero amplitudes, read and written once per launch (psi; psi
+        # and lambda for the adjoint; psi and H psi for the gradients): the
+        # kernels do no work for zero amplitudes
+        amp = 8 if res["prob"].precision == "c64" else 16
+        nnz = res.get("nnz", dim)
+        per = {"taylor5": 2 * nnz * amp, "adjoint": 4 * nnz * amp, "pool_grad": 2 * nnz * amp}[top]
         achieved = per / per_launch_s / 1e9
         out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs"}
