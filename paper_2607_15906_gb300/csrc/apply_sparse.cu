@@ -178,7 +178,7 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
   uint32_t before = 0;
   for (int q = 0; q < warp; ++q) before += red[q];
   uint32_t at = offs[blockIdx.x] + before + incl - c;
-  uint32_t am[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // amask words 8w .. 8w + 7
+  uint64_t am0 = 0, am1 = 0, am2 = 0, am3 = 0;   // amask words 8w .. 8w + 7, two per register
   for (uint32_t m = mw; m; m &= m - 1u) {
     const uint32_t ob = (uint32_t)(__ffs(m) - 1), o = w * 32u + ob;
     C_t<R> v[kAmpsH];
@@ -189,7 +189,11 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
       load_octet<R>(psi2, o, v2);
       nz |= nonzero_members<R>(v2);
     }
-    am[ob >> 2] |= nz << (8u * (ob & 3u));
+    const uint64_t bits = (uint64_t)nz << (8u * (ob & 7u));
+    if (ob < 8u) am0 |= bits;
+    else if (ob < 16u) am1 |= bits;
+    else if (ob < 24u) am2 |= bits;
+    else am3 |= bits;
 #pragma unroll
     for (int q = 0; q < kAmpsH; ++q)
       if ((nz >> q) & 1u) {
@@ -201,8 +205,11 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
       }
   }
   if (amask && w < words) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) amask[8u * w + q] = am[q];
+    uint2* dst = reinterpret_cast<uint2*>(amask + 8u * w);
+    dst[0] = make_uint2((uint32_t)am0, (uint32_t)(am0 >> 32));
+    dst[1] = make_uint2((uint32_t)am1, (uint32_t)(am1 >> 32));
+    dst[2] = make_uint2((uint32_t)am2, (uint32_t)(am2 >> 32));
+    dst[3] = make_uint2((uint32_t)am3, (uint32_t)(am3 >> 32));
   }
 }
 

@@ -622,8 +622,8 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
     if (bid == 0 && threadIdx.x == 0) atomicOr(err, 1);
     return;
   }
-  const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
-  const PairEnum E = tb.penum[op];
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place: L.lut is indexed at run time
+  const PairEnum& E = tb.penum[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
@@ -775,8 +775,8 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
     if (dpart && threadIdx.x == 0) dpart[(size_t)j * nb + bid] = 0.0;
     return;
   }
-  const LutDev<R> L = ((const LutDev<R>*)tb.plut)[op];
-  const PairEnum E = tb.penum[op];
+  const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place: L.lut is indexed at run time
+  const PairEnum& E = tb.penum[op];
   R c[6];
 #pragma unroll
   for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
