@@ -246,10 +246,12 @@ def test_chain_list_overflow_falls_back(prec, n):
 
 def _grouped_random_table(n, rng):
     """A Hermitian table with x-groups of 1..40 terms (z-ranks from 0 to
-    beyond the LUT limit), real and imaginary weights, a diagonal group, and
-    one exactly paired group (z, w), (z ^ x, -w) of the one-body form (x of
+    beyond the LUT limit), real and imaginary weights, a diagonal group, one
+    exactly paired group (z, w), (z ^ x, -w) of the one-body form (x of
     even weight, as e_p ^ e_q: then both partners are Hermitian with weights
-    on the same axis)."""
+    on the same axis), and one group whose masks lie within one bit of a
+    centre (the one-body-with-spectators shape, with real and imaginary
+    weights)."""
     xs, zs = [], []
     for size in [1, 2, 3, 4, 6, 8, 9, 12, 17, 25, 40, 5, 7]:
         x = int(rng.integers(1, 1 << n))
@@ -271,6 +273,16 @@ def _grouped_random_table(n, rng):
     z = np.concatenate([z, zp, zp ^ xp])
     ph = np.concatenate([ph, php, php ^ 2])            # partner: same c, opposite sign
     c = np.concatenate([c, cp, cp])
+    # a group whose masks lie within one bit of a centre, the flipped bits
+    # partly inside x (so its weights are real and imaginary)
+    xl = int(rng.integers(1, 1 << n))
+    zc = int(rng.integers(0, 1 << n))
+    zl = np.array([zc] + [zc ^ (1 << int(r)) for r in rng.choice(n, size=min(n, 11), replace=False)], np.int64)
+    phl = parity(xl & zl) + 2 * rng.integers(0, 2, size=len(zl))
+    x = np.concatenate([x, np.full(len(zl), xl, np.int64)])
+    z = np.concatenate([z, zl])
+    ph = np.concatenate([ph, phl])
+    c = np.concatenate([c, rng.normal(size=len(zl))])
     return PauliTable(n, x, z, ph.astype(np.int64), c)
 
 
