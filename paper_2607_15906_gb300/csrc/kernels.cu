@@ -31,6 +31,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kChunkTerms = 2048;    // shared-memory stage of H psi
 constexpr int kChunkGroups = 512;
 constexpr int kOpsPerBlock = 16;     // pool operators per gradient block
+constexpr int kChainBlocksPerSm = 4; // blocks per SM of a Taylor or adjoint step (LUT pools)
 constexpr int kStageStrings = 256;   // strings staged per gradient / Taylor block
 constexpr int kPairsPerThread = 32;  // pool gradients: pairs per thread per operator
 constexpr int kMaxChunks = 8192;     // gradient op chunks (pool <= 131072)
@@ -1148,11 +1149,12 @@ int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t 
 //
 // raw_k = sum_b Re(conj((H psi)_b) D_k(b) psi_{b ^ x}) needs only the b with
 // psi_{b ^ x} != 0, i.e. b = k' ^ x for the listed nonzero amplitudes psi(k')
-// (amp_list); every such b is reached exactly once.  A thread takes one
-// amplitude at a time and runs it against the block's kOpsPerBlock
-// generators (per-thread compensated sums, one per generator); (H psi)_b is
-// read only where D_k(b) != 0.  Returns at once when the list is incomplete
-// (more than acap amplitudes): the live-octet kernel then runs.
+// (amp_list); every such b is reached exactly once.  A block takes a slice
+// of the list and its kOpsPerBlock generators one after the other (the
+// slice stays in L1 across them); a thread sums its few amplitudes per
+// generator in R, the block in FP64; (H psi)_b is read only where
+// D_k(b) != 0.  Returns at once when the list is incomplete (more than acap
+// amplitudes): the live-octet kernel then runs.
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* __restrict__ aidx,
@@ -1168,34 +1170,18 @@ k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* _
   const uint32_t n = *alen;
   const uint32_t per = (n + nbx - 1) / nbx;
   const uint32_t l0 = blockIdx.x * per, l1 = min(n, l0 + per);
-  R acc[kOpsPerBlock], cmp[kOpsPerBlock];
-#pragma unroll
-  for (int o = 0; o < kOpsPerBlock; ++o) acc[o] = cmp[o] = R(0);
-  for (uint32_t l = l0 + threadIdx.x; l < l1; l += kThreads) {
-    const uint32_t kp = aidx[l];
-    const C_t<R> p = aval[l];
-#pragma unroll
-    for (int o = 0; o < kOpsPerBlock; ++o) {
-      if (o >= nops) break;
-      const LutDev<R>& L = s_op[o];
-      const uint32_t b = kp ^ L.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 0; o < nops; ++o) {
+    const LutDev<R>& L = s_op[o];
+    R acc = R(0);
+    for (uint32_t l = l0 + threadIdx.x; l < l1; l += kThreads) {
+      const uint32_t b = aidx[l] ^ L.x;
       const R d = L.lut[lut_phi(L, b)];
       if (d == R(0)) continue;
-      const C_t<R> h = hpsi[b];
-      const R a = ((__popc(b & L.z0) & 1) ? -d : d) * (h.x * p.x + h.y * p.y);
-      if (sizeof(R) == 4) {
-        const R y = a - cmp[o], t = acc[o] + y;
-        cmp[o] = (t - acc[o]) - y;
-        acc[o] = t;
-      } else {
-        acc[o] += a;
-      }
+      const C_t<R> p = aval[l], h = hpsi[b];
+      acc += ((__popc(b & L.z0) & 1) ? -d : d) * (h.x * p.x + h.y * p.y);
     }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 0; o < kOpsPerBlock; ++o) {
-    const double v = warp_sum((double)acc[o] - (double)cmp[o]);
+    const double v = warp_sum((double)acc);
     if (lane == 0) s_red[o][warp] = v;
   }
   __syncthreads();
@@ -2108,8 +2094,8 @@ void free_device(Problem& p) {
 
 // Blocks of an adjoint step (k_adjoint).
 int adjoint_grid(const DeviceTables& d) {
-  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (d.t.n - 1);
-  return grid_for(pairs, d.sm_count, 8);
+  if (d.t.pool_lut) return grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm);
+  return grid_for(1ull << (d.t.n - 1), d.sm_count, 8);
 }
 
 int ensure_stage(Problem& p, int n_ops) {
@@ -2278,8 +2264,8 @@ template <typename R>
 static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked,
                                cudaStream_t st) {
   DeviceTables& d = *p.dev;
-  const uint64_t pairs = d.t.pool_lut ? (uint64_t)d.t.penum_max : 1ull << (p.n_qubits - 1);
-  const int grid = grid_for(pairs, d.sm_count, 8);
+  const int grid = d.t.pool_lut ? grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm)
+                                : grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
   uint32_t* mask = tracked && d.t.pool_lut ? d.t.octmask : nullptr;
   DevTables tb = d.t;
   const double* coefs = d.coefs;
