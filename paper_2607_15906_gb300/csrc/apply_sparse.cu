@@ -43,7 +43,7 @@ namespace gocp {
 
 namespace {
 
-constexpr int kAmpBlock = 256;   // listing passes: one mask word (32 octets) per thread
+constexpr int kAmpBlock = 256;   // listing passes: one amplitude word (4 octets) per thread
 constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
 
 // One block per SM: 1024 threads for complex64 (64 registers), 512 for
@@ -93,19 +93,28 @@ __device__ __forceinline__ uint32_t octet_nonzero2(const C_t<R>* __restrict__ ps
   return nz;
 }
 
-// counts[b] = the amplitudes nonzero in psi or psi2 in the live octets of
-// mask words kAmpBlock b .. kAmpBlock (b + 1) - 1.
+// Amplitude word w: bit 8j + i = member i of octet 4w + j nonzero in psi or
+// (when set) psi2, read only from the octets the octet mask marks live.
+template <typename R>
+__device__ __forceinline__ uint32_t amp_word(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2,
+                                             const uint32_t* __restrict__ mask, uint32_t w) {
+  const uint32_t mb = (mask[w >> 3] >> ((w & 7u) * 4u)) & 0xFu;
+  uint32_t word = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 4; ++j)
+    if ((mb >> j) & 1u) word |= octet_nonzero2<R>(psi, psi2, 4u * w + j) << (8u * j);
+  return word;
+}
+
+// counts[b] = the amplitudes nonzero in psi or psi2 in amplitude words
+// kAmpBlock b .. kAmpBlock (b + 1) - 1 (one thread per word of 32).
 template <typename R>
 __global__ void __launch_bounds__(kAmpBlock)
 k_amp_count(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, const uint32_t* __restrict__ mask,
             uint32_t words, uint32_t* counts) {
   __shared__ uint32_t red[kAmpBlock / 32];
   const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
-  uint32_t c = 0;
-  if (w < words) {
-    for (uint32_t m = mask[w]; m; m &= m - 1u)
-      c += __popc(octet_nonzero2<R>(psi, psi2, w * 32u + (uint32_t)(__ffs(m) - 1)));
-  }
+  uint32_t c = w < words ? __popc(amp_word<R>(psi, psi2, mask, w)) : 0u;
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
   __syncthreads();
@@ -152,9 +161,8 @@ k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int s
 
 // Writes the index (and, when aval is set, the psi value) of every amplitude
 // nonzero in psi or psi2, in index order, at the offsets of k_amp_scan;
-// entries at or beyond cap are not stored.  With amask set, also writes the
-// 8 words of amask (one bit per amplitude) that cover this thread's mask
-// word, zeros included.
+// entries at or beyond cap are not stored.  With amask set, also writes
+// amask[w] = amplitude word w (one bit per amplitude, zeros included).
 template <typename R>
 __global__ void __launch_bounds__(kAmpBlock)
 k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, const uint32_t* __restrict__ mask,
@@ -162,10 +170,8 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
            uint32_t cap) {
   __shared__ uint32_t red[kAmpBlock / 32];
   const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
-  const uint32_t mw = w < words ? mask[w] : 0u;
-  uint32_t c = 0;
-  for (uint32_t m = mw; m; m &= m - 1u)
-    c += __popc(octet_nonzero2<R>(psi, psi2, w * 32u + (uint32_t)(__ffs(m) - 1)));
+  const uint32_t word = w < words ? amp_word<R>(psi, psi2, mask, w) : 0u;
+  const uint32_t c = __popc(word);
   // exclusive scan over the block: lanes by shuffles, warps through red
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = c;
@@ -178,39 +184,13 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
   uint32_t before = 0;
   for (int q = 0; q < warp; ++q) before += red[q];
   uint32_t at = offs[blockIdx.x] + before + incl - c;
-  uint64_t am0 = 0, am1 = 0, am2 = 0, am3 = 0;   // amask words 8w .. 8w + 7, two per register
-  for (uint32_t m = mw; m; m &= m - 1u) {
-    const uint32_t ob = (uint32_t)(__ffs(m) - 1), o = w * 32u + ob;
-    C_t<R> v[kAmpsH];
-    load_octet<R>(psi, o, v);
-    uint32_t nz = nonzero_members<R>(v);
-    if (psi2) {
-      C_t<R> v2[kAmpsH];
-      load_octet<R>(psi2, o, v2);
-      nz |= nonzero_members<R>(v2);
-    }
-    const uint64_t bits = (uint64_t)nz << (8u * (ob & 7u));
-    if (ob < 8u) am0 |= bits;
-    else if (ob < 16u) am1 |= bits;
-    else if (ob < 24u) am2 |= bits;
-    else am3 |= bits;
-#pragma unroll
-    for (int q = 0; q < kAmpsH; ++q)
-      if ((nz >> q) & 1u) {
-        if (at < cap) {
-          aidx[at] = o * 8u + (uint32_t)q;
-          if (aval) aval[at] = v[q];
-        }
-        ++at;
-      }
+  for (uint32_t m = word; m; m &= m - 1u, ++at) {
+    if (at >= cap) break;
+    const uint32_t k = 32u * w + (uint32_t)(__ffs(m) - 1);
+    aidx[at] = k;
+    if (aval) aval[at] = psi[k];
   }
-  if (amask && w < words) {
-    uint2* dst = reinterpret_cast<uint2*>(amask + 8u * w);
-    dst[0] = make_uint2((uint32_t)am0, (uint32_t)(am0 >> 32));
-    dst[1] = make_uint2((uint32_t)am1, (uint32_t)(am1 >> 32));
-    dst[2] = make_uint2((uint32_t)am2, (uint32_t)(am2 >> 32));
-    dst[3] = make_uint2((uint32_t)am3, (uint32_t)(am3 >> 32));
-  }
+  if (amask && w < words) amask[w] = word;
 }
 
 // off[u] = first stored entry with index >> shift >= u, u = 0 .. ntiles
@@ -247,16 +227,21 @@ __device__ __forceinline__ void acc_add(R* acc, uint32_t k, R re, R im) {
   atomicAdd(acc + at + kOct, im);
 }
 
-// One LUT group against the lane's nonzero amplitude psi(ks) = v.
+// One LUT group against the lane's nonzero amplitude psi(ks) = v.  The
+// entry's magnitude depends on phi(k) alone (lut16[phi | 8] = -lut16[phi]),
+// so the sign parity is taken only for a nonzero entry.
 template <typename R, uint32_t kOct>
 __device__ __forceinline__ void sp_lut(const HLut<R>& L, uint32_t ks, C_t<R> v, bool valid, R* acc) {
   const uint4 h0 = *reinterpret_cast<const uint4*>(&L.x);     // x, z0, v0, v1
-  const uint4 h1 = *reinterpret_cast<const uint4*>(&L.v2);    // v2, reg, pad0, pad1
+  const uint32_t v2 = L.v2;
   const uint32_t k = ks ^ h0.x;
-  const uint32_t code = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
-                        ((uint32_t)(__popc(k & h1.x) & 1) << 2) | ((uint32_t)(__popc(k & h0.y) & 1) << 3);
-  const R d = L.lut16[code];
-  if (valid && d != R(0)) acc_add<R, kOct>(acc, k, d * v.x, d * v.y);
+  const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
+                       ((uint32_t)(__popc(k & v2) & 1) << 2);
+  const R d0 = L.lut16[phi];
+  if (valid && d0 != R(0)) {
+    const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
+    acc_add<R, kOct>(acc, k, d * v.x, d * v.y);
+  }
 }
 
 // One term-list group: D(k) = sum_t w_t (-1)^popc(k & z_t), real terms
@@ -518,7 +503,7 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
 int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t st) {
   if (n < 8 || !mask || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts)
     return fail(GOCP_EINVAL, "amplitude list needs n >= 8 and its buffers");
-  const uint32_t words = 1u << (n - 8);
+  const uint32_t words = 1u << (n - 5);   // amplitude words
   const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
   if (precision == GOCP_C64) {
     const float2* p = reinterpret_cast<const float2*>(psi);
@@ -541,7 +526,7 @@ int chain_list(int precision, const void* psi, const void* lam, const uint32_t* 
                uint32_t* counts, int slot, int first, cudaStream_t st) {
   if (n < 8 || !mask || !cl.list || !cl.amask || !cl.cnt || !counts)
     return fail(GOCP_EINVAL, "chain list needs n >= 8 and its buffers");
-  const uint32_t words = 1u << (n - 8);
+  const uint32_t words = 1u << (n - 5);   // amplitude words
   const uint32_t nb = (words + kAmpBlock - 1u) / kAmpBlock;
   if (precision == GOCP_C64) {
     const float2* p = reinterpret_cast<const float2*>(psi);

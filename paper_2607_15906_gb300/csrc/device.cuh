@@ -454,7 +454,7 @@ struct LiveOctets {
   void* aval = nullptr;         // acap complex amplitudes of the problem's precision
   uint32_t acap = 0;
   uint32_t* alen = nullptr;     // one entry
-  uint32_t* acounts = nullptr;  // one per block of 256 mask words, + 1
+  uint32_t* acounts = nullptr;  // one per block of 256 amplitude words (32 amplitudes each), + 1
 };
 
 // Lists the live octets of `mask` (2^(n-3) bits, n >= 8) into lv.list and

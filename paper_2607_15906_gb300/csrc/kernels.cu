@@ -1704,7 +1704,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)) ||
       (rc = dalloc(d, &d.live.aidx, (size_t)1 << (n - 2), bytes)) ||
       (rc = dalloc(d, reinterpret_cast<C_t<R>**>(&d.live.aval), (size_t)1 << (n - 2), bytes)) ||
-      (rc = dalloc(d, &d.live.alen, 1, bytes)) || (rc = dalloc(d, &d.live.acounts, ((((size_t)1 << (n - 8)) + 255) / 256) + 1, bytes)))
+      (rc = dalloc(d, &d.live.alen, 1, bytes)) || (rc = dalloc(d, &d.live.acounts, ((((size_t)1 << (n - 5)) + 255) / 256) + 1, bytes)))
     return rc;
   d.live.acap = 1u << (n - 2);
   d.t.tblob = dblob;
@@ -2045,7 +2045,7 @@ int upload_problem(Problem& p) {
   if (p.n_qubits >= 8 && d->t.pool_lut) {
     // chain list: a quarter of the state's indices at most, one amplitude-mask bit each
     const int n = p.n_qubits;
-    const size_t nb = ((((size_t)1 << (n - 8)) + 255) / 256) + 1;
+    const size_t nb = ((((size_t)1 << (n - 5)) + 255) / 256) + 1;
     if ((rc = dalloc(*d, &d->t.cl.list, (size_t)1 << (n - 2), bytes)) ||
         (rc = dalloc(*d, &d->t.cl.amask, (size_t)1 << (n - 5), bytes)) || (rc = dalloc(*d, &d->t.cl.cnt, kRingWords, bytes)) ||
         (rc = dalloc(*d, &d->chain_counts, nb, bytes)))
