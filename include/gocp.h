@@ -203,7 +203,13 @@ int gocp_prepare_state(const gocp_problem* p, const int32_t* ops, const double* 
 /* Apply the Taylor step of pool operator `op` to psi in place. */
 int gocp_taylor_step(const gocp_problem* p, int op, double theta, void* psi, void* stream);
 
-/* hpsi <- H psi (Eq. 3), matrix-free.  psi and hpsi must not overlap. */
+/* hpsi <- H psi (Eq. 3), matrix-free.  psi and hpsi must not overlap.
+ * Full layout from 13 (complex64) / 12 (complex128) qubits: a state whose
+ * nonzero amplitudes are at most GOCP_SPARSE_FRAC (environment, default
+ * 0.125, at most 0.25; 0 = never) of 2^n goes through the scatter kernel,
+ * which sums with shared-memory atomics (results reproducible to rounding,
+ * not bit for bit); other states through the staged kernel (fixed order).
+ * The choice is made on the device from the count of nonzero amplitudes. */
 int gocp_apply_h(const gocp_problem* p, const void* psi, void* hpsi, void* stream);
 
 /* hpsi <- H psi, and out[0] = E = Re<psi|H psi>/<psi|psi> (Eq. 1),
