@@ -534,6 +534,18 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
 // v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
 // m = 0..5, stay in registers.
+// c[m] = theta^m / m! of step j in R, converted once per block (FP64 is a
+// slow pipe on this part; a conversion in every thread costs microseconds
+// per step).  Called by every thread of the block.
+template <typename R>
+__device__ __forceinline__ void step_coefs(const double* coefs, int j, R (&c)[6]) {
+  __shared__ R s_c[6];
+  if (threadIdx.x < 6) s_c[threadIdx.x] = (R)coefs[6 * j + threadIdx.x];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = s_c[m];
+}
+
 // Chain lists (ChainList): membership, append, and the end of a step.
 __device__ __forceinline__ bool chain_listed(const ChainList& cl, uint32_t k) {
   return (cl.amask[k >> 5] >> (k & 31u)) & 1u;
@@ -626,8 +638,7 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place: L.lut is indexed at run time
   const PairEnum& E = tb.penum[op];
   R c[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  step_coefs<R>(coefs, j, c);
   const uint32_t phx = L.fx & 7u;
   const ChainList& cl = tb.cl;
   if (mask && cl.list) {
@@ -745,8 +756,8 @@ __device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[
   const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
   const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
   const C_t<R> l1v = lam[b], l2v = lam[b2];
-  const double v = 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x +
-                          (double)l2v.y * t2.y);
+  // the pair's term of 2 Re<lambda|T' psi>, formed in R (one conversion)
+  const double v = 2.0 * (double)(l1v.x * t1.x + l1v.y * t1.y + l2v.x * t2.x + l2v.y * t2.y);
   out[0] = q1;
   out[1] = q2;
   out[2] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
@@ -779,8 +790,7 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place: L.lut is indexed at run time
   const PairEnum& E = tb.penum[op];
   R c[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  step_coefs<R>(coefs, j, c);
   const uint32_t phx = L.fx & 7u;
   double v[1] = {0.0};
   const ChainList& cl = tb.cl;
@@ -824,7 +834,8 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
     grid_sum<1>(v, partials, counter, nb, bid, dtheta + j, tot);
     return;
   }
-  const double w = warp_sum(v[0]);
+  // most warps touched no pair: their FP64 reduction is skipped
+  const double w = __any_sync(0xffffffffu, v[0] != 0.0) ? warp_sum(v[0]) : 0.0;
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = w;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1151,8 +1162,8 @@ int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t 
 // psi_{b ^ x} != 0, i.e. b = k' ^ x for the listed nonzero amplitudes psi(k')
 // (amp_list); every such b is reached exactly once.  A block takes a slice
 // of the list and its kOpsPerBlock generators one after the other (the
-// slice stays in L1 across them); a thread sums its few amplitudes per
-// generator in R, the block in FP64; (H psi)_b is read only where
+// slice stays in L1 across them); a thread and its warp sum in R, the
+// block in FP64; (H psi)_b is read only where
 // D_k(b) != 0.  Returns at once when the list is incomplete (more than acap
 // amplitudes): the live-octet kernel then runs.
 template <typename R>
@@ -1181,8 +1192,9 @@ k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* _
       const C_t<R> p = aval[l], h = hpsi[b];
       acc += ((__popc(b & L.z0) & 1) ? -d : d) * (h.x * p.x + h.y * p.y);
     }
-    const double v = warp_sum((double)acc);
-    if (lane == 0) s_red[o][warp] = v;
+    // the warp's sum in R (FP64 is a slow pipe here), the block's in FP64
+    for (int q = 16; q > 0; q >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, q);
+    if (lane == 0) s_red[o][warp] = (double)acc;
   }
   __syncthreads();
   if (threadIdx.x < nops) {
