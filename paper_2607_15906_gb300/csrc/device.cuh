@@ -343,12 +343,33 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// c[m] = theta^m / m! of step j in R, converted once per block (FP64 is a
+// slow pipe on this part; a conversion in every thread costs microseconds
+// per step).  Called by every thread of the block.
+template <typename R>
+__device__ __forceinline__ void step_coefs(const double* coefs, int j, R (&c)[6]) {
+  __shared__ R s_c[6];
+  if (threadIdx.x < 6) s_c[threadIdx.x] = (R)coefs[6 * j + threadIdx.x];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < 6; ++m) c[m] = s_c[m];
+}
+
+// Sum over the warp in R; the total in lane 0.
+template <typename R>
+__device__ __forceinline__ R warp_total(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Adds v[0..NV) over the nblocks blocks (NTHREADS threads each) of one work
-// item into out[0..NV).
+// item into out[0..NV).  WarpReduced: the caller has already summed each
+// warp (the total in lane 0, the other lanes ignored), so the FP64 warp
+// reduction is skipped.
 // partials: NV doubles per block; counter: one per item, zero on entry and
 // reset on exit.  Returns true in the last block, where tot[0..NV) (shared)
 // then holds the totals for every thread.
-template <int NV, int NTHREADS>
+template <int NV, int NTHREADS, bool WarpReduced = false>
 __device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned int* counter,
                                int nblocks, int bid, double* out, double* tot) {
   __shared__ double red[NV][NTHREADS / 32];
@@ -356,7 +377,7 @@ __device__ bool block_grid_sum(const double (&v)[NV], double* partials, unsigned
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    double s = warp_sum(v[i]);
+    double s = WarpReduced ? v[i] : warp_sum(v[i]);
     if (lane == 0) red[i][warp] = s;
   }
   __syncthreads();

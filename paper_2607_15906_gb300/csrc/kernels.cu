@@ -534,18 +534,6 @@ __device__ __forceinline__ void kahan_add(C_t<R>& s, C_t<R>& c, C_t<R> v) {
 // psi <- T(theta_j A_{ops[j]}) psi: on each pair (b, b^x) the chain
 // v_m = A v_{m-1} (Eq. 6) and the partial sum of Eq. (5), taken in order
 // m = 0..5, stay in registers.
-// c[m] = theta^m / m! of step j in R, converted once per block (FP64 is a
-// slow pipe on this part; a conversion in every thread costs microseconds
-// per step).  Called by every thread of the block.
-template <typename R>
-__device__ __forceinline__ void step_coefs(const double* coefs, int j, R (&c)[6]) {
-  __shared__ R s_c[6];
-  if (threadIdx.x < 6) s_c[threadIdx.x] = (R)coefs[6 * j + threadIdx.x];
-  __syncthreads();
-#pragma unroll
-  for (int m = 0; m < 6; ++m) c[m] = s_c[m];
-}
-
 // Chain lists (ChainList): membership, append, and the end of a step.
 __device__ __forceinline__ bool chain_listed(const ChainList& cl, uint32_t k) {
   return (cl.amask[k >> 5] >> (k & 31u)) & 1u;

@@ -99,8 +99,7 @@ k_sec_taylor(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, con
   }
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
   R c[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  step_coefs<R>(coefs, j, c);
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
   const int64_t q0 = off[op], np = off[op + 1] - q0;
   for (int64_t i = blockIdx.x * kSecThreads + threadIdx.x; i < np; i += (int64_t)gridDim.x * kSecThreads) {
@@ -346,9 +345,9 @@ k_sec_pool_grad(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, 
                     ((sg ^ sgx) ? -l2 : l2) * (h2.x * p1.x + h2.y * p1.y);
       kahan<R>(acc, cmp, val);
     }
-    double vv = (double)acc - (double)cmp;
-    vv = warp_sum(vv);
-    if (lane == 0) s_red[warp] = vv;
+    // the warp's sum in R (FP64 is a slow pipe here), the block's in FP64
+    const R wv = warp_total<R>(acc - cmp);
+    if (lane == 0) s_red[warp] = (double)wv;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -378,11 +377,12 @@ k_sec_adjoint(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, co
   }
   const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];   // read in place (lut is indexed at run time)
   R c[6];
-#pragma unroll
-  for (int m = 0; m < 6; ++m) c[m] = (R)coefs[6 * j + m];
+  step_coefs<R>(coefs, j, c);
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
   const int64_t q0 = off[op], np = off[op + 1] - q0;
-  double v[1] = {0.0};
+  // this thread's part of dE_j, compensated in R; warps then sum in R and
+  // blocks in FP64 (FP64 is a slow pipe on this part)
+  R acc = R(0), cmp = R(0);
   for (int64_t i = blockIdx.x * kSecThreads + threadIdx.x; i < np; i += (int64_t)gridDim.x * kSecThreads) {
     const uint2 pr = pairs[q0 + i];
     const uint32_t k = s.kq[pr.x];
@@ -402,13 +402,14 @@ k_sec_adjoint(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, co
     const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
     const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
     const C_t<R> l1v = lam[pr.x], l2v = lam[pr.y];
-    v[0] += 2.0 * ((double)l1v.x * t1.x + (double)l1v.y * t1.y + (double)l2v.x * t2.x + (double)l2v.y * t2.y);
+    kahan<R>(acc, cmp, R(2) * (l1v.x * t1.x + l1v.y * t1.y + l2v.x * t2.x + l2v.y * t2.y));
     psi[pr.x] = q1;
     psi[pr.y] = q2;
     lam[pr.x] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
     lam[pr.y] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
   }
-  block_grid_sum<1, kSecThreads>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j, tot);
+  const double v[1] = {(double)warp_total<R>(acc - cmp)};
+  block_grid_sum<1, kSecThreads, true>(v, partials, counter, gridDim.x, blockIdx.x, dtheta + j, tot);
 }
 
 template <typename R>
