@@ -9,19 +9,21 @@
 //
 //  * a listing pass writes the nonzero amplitudes (index, value) in index
 //    order, and the first entry of every tile;
-//  * a block owns an output tile t of 2^LB amplitudes and accumulates it in
-//    shared memory.  Its work units are (chunk, piece): 32 consecutive
-//    nonzero amplitudes of the piece's source tile u = t ^ (x >> LB), one per
-//    lane, against the piece's groups, which the warp walks together.  For a
-//    group with mask x the lane's amplitude psi(k') goes to output
-//    k = k' ^ x with weight D(k): a LUT group reads its entry at code(k)
-//    (the code is linear in k over GF(2)), a term-list group sums its terms'
-//    signs at k (times the factor 0 or 2 of a paired group).  A nonzero
-//    product is added to the accumulator with a shared-memory atomic; a zero
-//    weight adds nothing and is left out;
-//  * after the last piece the block adds the diagonal group and the identity
-//    on the live octets of its own tile, the energy partials, and streams
-//    the whole tile (zeros included) to H psi.
+//  * a block (one per SM) owns an output tile t of 2^LB amplitudes and
+//    accumulates it in shared memory.  Its work units are (piece, chunk): 32
+//    consecutive nonzero amplitudes of the piece's source tile
+//    u = t ^ (x >> LB), one per lane, against the piece's groups, which the
+//    warp walks together from its own shared-memory copy of the piece's
+//    blob.  Units are numbered piece by piece from a per-tile scan of chunk
+//    counts and claimed a few at a time.  For a group with mask x the lane's
+//    amplitude psi(k') goes to output k = k' ^ x with weight D(k): a LUT
+//    group reads its entry at code(k) (the code is linear in k over GF(2)),
+//    a term-list group sums its terms' signs at k (times the factor 0 or 2
+//    of a paired group).  A nonzero product is added to the accumulator with
+//    a shared-memory atomic; a zero weight adds nothing and is left out;
+//  * after the last unit, lanes over the nonzero amplitudes of the own tile
+//    add the diagonal group and the identity and take the energy partials;
+//    then the whole tile (zeros included) is streamed to H psi.
 //
 // Every lane does the same work for every group, whatever the sparsity
 // pattern, and a group's descriptor and LUT are read at one address per

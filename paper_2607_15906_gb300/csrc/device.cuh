@@ -458,14 +458,14 @@ int octet_mask(int precision, const void* psi, const void* psi2, int n, uint32_t
                int tile_shift = 0);
 
 // The live octets of a state (those the nonzero-octet mask marks), listed in
-// index order, with the per-block counts of the listing pass, the length,
-// and (tiled form) the first list entry of every tile: toff[u] .. toff[u+1]
-// are the live octets of tile u.
+// index order (the live-octet pool-gradient kernel), with the per-block
+// counts of the listing pass and the length.
 //
 // The tiled form adds the nonzero amplitudes of a state in index order
 // (aidx: index, aval: value; at most acap of them are stored, alen = their
 // number, which may exceed acap), their per-block counts and offsets, and
-// the first entry of every tile in toff.
+// the first amplitude entry of every tile: toff[u] .. toff[u+1] are the
+// nonzero amplitudes of tile u.
 struct LiveOctets {
   uint32_t* list = nullptr;     // 2^(n-3) entries
   uint32_t* counts = nullptr;   // one per listing block
