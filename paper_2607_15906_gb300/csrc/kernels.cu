@@ -1838,7 +1838,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   uint8_t *dchunk_xl, *dlchunk_xl;
   uint64_t* dgbk;
   R *dtw, *ddw;
-  HLut<R>* dhl;
+  HLut<R>* dhl = nullptr;
   if ((rc = upload(d, &dgx, gx, bytes)) || (rc = upload(d, &dgoff, goff, bytes)) ||
       (rc = upload(d, &dgmid, gmid, bytes)) || (rc = upload(d, &dchunk, chunk, bytes)) ||
       (rc = upload(d, &dchunk_xl, chunk_xl, bytes)) || (rc = upload(d, &dtz, tz, bytes)) ||
@@ -1937,7 +1937,7 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.pw2 = dpw2;
   d.t.porder = dporder;
   if (all_lut) {
-    LutDev<R>* dpl;
+    LutDev<R>* dpl = nullptr;
     PairEnum* dpe;
     if ((rc = upload(d, &dpl, pl, bytes)) || (rc = upload(d, &dpe, pe, bytes))) return rc;
     d.t.plut = dpl;
@@ -2191,8 +2191,7 @@ int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, 
   bool ok = true;
   for (int i = 0; i < n && ok; ++i) {
     j = reverse ? n - 1 - i : i;
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof(kp));
+    cudaKernelNodeParams kp = {};
     kp.func = const_cast<void*>(kernel);
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(block);
