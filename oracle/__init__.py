@@ -18,6 +18,9 @@ order, in float64 / complex128 (the paper fixes no precision):
                     (Eq. 5, Eq. 6), the Rayleigh quotient (Eq. 1), pool
                     gradients (Eq. 4) and forward-mode dE/dtheta.
   * ``adapt``       the ADAPT-VQE loop (Sec. II.B).
+  * ``parallel``    the same statevector functions on slices of rows or of
+                    pool operators in spawned worker processes (no
+                    arithmetic of its own), for full-size checks and timing.
 
 Pauli convention: a term (x, z, phase, c) is c * i**phase * X^x Z^z with x, z
 bit masks (bit j = qubit j); it maps |b> to c * i**phase * (-1)**popc(b & z)

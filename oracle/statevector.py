@@ -40,15 +40,22 @@ def apply_terms(t: PauliTable, psi: np.ndarray) -> np.ndarray:
     return out
 
 
-def apply_terms_at(t: PauliTable, psi: np.ndarray, rows) -> np.ndarray:
-    """Selected entries (H psi)[k] = sum_t c_t i**ph_t (-1)**popc((k^x_t) & z_t) psi[k ^ x_t]."""
+def apply_terms_at(t: PauliTable, psi: np.ndarray, rows, block: int = 1) -> np.ndarray:
+    """Selected entries (H psi)[k] = sum_t c_t i**ph_t (-1)**popc((k^x_t) & z_t) psi[k ^ x_t]
+    (`block` rows at a time; each row is still one sum over all terms)."""
     rows = np.asarray(rows, dtype=np.int64)
     w = t.weights()
     out = np.zeros(rows.shape[0], dtype=np.complex128)
-    for r, k in enumerate(rows.tolist()):
-        src = k ^ t.x
-        sign = 1 - 2 * parity(src & t.z)
-        out[r] = np.sum(w * sign * psi[src])
+    if block <= 1:
+        for r, k in enumerate(rows.tolist()):
+            src = k ^ t.x
+            sign = 1 - 2 * parity(src & t.z)
+            out[r] = np.sum(w * sign * psi[src])
+        return out
+    for r0 in range(0, rows.shape[0], block):
+        src = rows[r0:r0 + block, None] ^ t.x[None, :]
+        sign = 1 - 2 * parity(src & t.z[None, :])
+        out[r0:r0 + block] = np.sum(w[None, :] * sign * psi[src], axis=1)
     return out
 
 
@@ -125,7 +132,11 @@ def energy_grad(h: PauliTable, ref: np.ndarray, pool: list[PauliTable], ops, the
 #
 # The same per-term formula restricted to the nonzero entries of a state held
 # as (indices, values).  It lets full-size (24-qubit) cases with a sparse
-# input (a basis state evolved by a few operators) be checked exactly.
+# input (a basis state evolved by operators of the pool) be checked exactly.
+# Entries whose sum is exactly zero (strings of one generator cancelling at a
+# basis state the excitation cannot act on) are dropped: a zero amplitude
+# contributes nothing to any later product or sum, so every result is the
+# same as with the zeros kept, and the held support stays that of the state.
 
 def apply_terms_sparse(t: PauliTable, idx: np.ndarray, vals: np.ndarray, chunk: int = 512):
     idx = np.asarray(idx, dtype=np.int64)
@@ -144,28 +155,82 @@ def apply_terms_sparse(t: PauliTable, idx: np.ndarray, vals: np.ndarray, chunk: 
     keys, inv = np.unique(ai, return_inverse=True)
     acc = np.zeros(keys.shape[0], dtype=np.complex128)
     np.add.at(acc, inv, av)
-    return keys, acc
+    keep = acc != 0
+    return keys[keep], acc[keep]
+
+
+def apply_group_sparse(a: PauliTable, idx: np.ndarray, vals: np.ndarray):
+    """A psi for a generator whose strings share one x mask (every pool
+    operator): (A psi)[b ^ x] = D(b) psi[b] with D(b) = sum_t w_t
+    (-1)**popc(b & z_t) -- Eq. (3) with the terms of one x-group summed per
+    basis state before the product.  A fermionic excitation's string weights
+    are multiples of 1/8, so D(b) is exact and is exactly zero where the
+    excitation cannot act (there the term-by-term products leave rounding
+    residue of order 1e-16 |psi[b]|)."""
+    x = int(a.x[0])
+    assert np.all(a.x == x), "strings of one generator share their x mask"
+    idx = np.asarray(idx, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.complex128)
+    w = a.weights()
+    d = np.zeros(idx.shape[0], dtype=np.complex128)
+    for zt, wt in zip(a.z.tolist(), w.tolist()):
+        d += wt * (1 - 2 * parity(idx & zt))
+    keep = d != 0
+    oi = idx[keep] ^ x
+    ov = d[keep] * vals[keep]
+    order = np.argsort(oi)
+    return oi[order], ov[order]
 
 
 def _sparse_axpy(ai, av, bi, bv, scale):
     keys, inv = np.unique(np.concatenate([ai, bi]), return_inverse=True)
     acc = np.zeros(keys.shape[0], dtype=np.complex128)
     np.add.at(acc, inv, np.concatenate([av, scale * bv]))
-    return keys, acc
+    keep = acc != 0
+    return keys[keep], acc[keep]
 
 
 def taylor5_sparse(a: PauliTable, theta: float, idx, vals):
+    """taylor5 on a sparse state (the chain v_m = A v_{m-1} of Eq. 6)."""
     oi, ov = np.asarray(idx, np.int64), np.asarray(vals, np.complex128)
     vi, vv = oi, ov
     for m in range(1, 6):
-        vi, vv = apply_terms_sparse(a, vi, vv)
+        vi, vv = apply_group_sparse(a, vi, vv)
         oi, ov = _sparse_axpy(oi, ov, vi, vv, theta ** m / math.factorial(m))
     return oi, ov
 
 
-def prepare_state_sparse(ref_index: int, pool: list[PauliTable], ops, thetas):
+def taylor5_derivative_sparse(a: PauliTable, theta: float, idx, vals):
+    """taylor5_derivative on a sparse state."""
+    oi, ov = np.zeros(0, np.int64), np.zeros(0, np.complex128)
+    vi, vv = np.asarray(idx, np.int64), np.asarray(vals, np.complex128)
+    for m in range(1, 6):
+        vi, vv = apply_group_sparse(a, vi, vv)
+        oi, ov = _sparse_axpy(oi, ov, vi, vv, theta ** (m - 1) / math.factorial(m - 1))
+    return oi, ov
+
+
+def prepare_state_sparse(ref_index: int, pool: list[PauliTable], ops, thetas, keep_at=None):
+    """psi_P = T_P ... T_1 |ref> on a sparse state.  With keep_at (operator
+    positions j) also returns {j: psi_j}, psi_j the state before operator j
+    acts, for forward-mode derivatives (derivative_state_sparse)."""
     idx, vals = np.array([ref_index], np.int64), np.array([1.0 + 0j])
-    for k, th in zip(list(ops), list(thetas)):
+    want = set() if keep_at is None else {int(j) for j in keep_at}
+    kept = {}
+    for j, (k, th) in enumerate(zip(list(ops), list(thetas))):
+        if j in want:
+            kept[j] = (idx, vals)
+        idx, vals = taylor5_sparse(pool[int(k)], float(th), idx, vals)
+    if keep_at is None:
+        return idx, vals
+    return idx, vals, kept
+
+
+def derivative_state_sparse(pool: list[PauliTable], ops, thetas, j: int, psi_j):
+    """d psi_P / d theta_j (forward mode, as in energy_grad) from psi_j, the
+    state before operator j acts: T'_j, then T_{j+1} .. T_P."""
+    idx, vals = taylor5_derivative_sparse(pool[int(ops[j])], float(thetas[j]), *psi_j)
+    for k, th in zip(list(ops)[j + 1:], list(thetas)[j + 1:]):
         idx, vals = taylor5_sparse(pool[int(k)], float(th), idx, vals)
     return idx, vals
 

@@ -90,12 +90,17 @@ def test_autograd_adjoint_20q_vs_finite_differences_and_c64():
     assert 1.0 - sv.fidelity(a, b) < 1e-6
 
 
-def test_adapt_14q_mapping_invariant_first_iterations():
+def test_adapt_14q_mapping_invariant_30_operators():
+    """The 14-qubit workload (7 orbitals, 6 electrons, 204-operator pool)
+    grown to 30 operators under JW and BK, complex128: the same operator at
+    every iteration and the same energies (Sec. IV.B; BK is a basis
+    permutation of JW, so the method is exactly mapping invariant)."""
     ints, c = config_integrals("c2_14q")
     runs = {}
     for mp in ("jw", "bk"):
         p = gb.Problem.build(ints, 6, mapping=mp, precision="c128", device=0)
-        runs[mp] = gpu_adapt(p, max_ops=4, gtol=1e-4)
+        runs[mp] = gpu_adapt(p, max_ops=30, gtol=1e-4)
+    assert len(runs["jw"].ops) == 30
     assert runs["jw"].ops == runs["bk"].ops
     assert np.max(np.abs(np.array(runs["jw"].energies) - np.array(runs["bk"].energies))) < 1e-9
     assert all(b <= a + 1e-12 for a, b in zip(runs["jw"].energies, runs["jw"].energies[1:]))

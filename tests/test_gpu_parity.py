@@ -1,10 +1,19 @@
 """CUDA path vs the oracle, element by element, through the C ABI.
 
-Tolerances (written here, derived in the design doc):
-  complex128: relative 1e-10 on states and energies.
-  complex64 : |E - E_oracle| <= 1e-6 Ha, fidelity >= 1 - 1e-6, H psi entries
-              within 2e-5 of max|H psi| (FP32 amplitudes), gradients within
-              2e-6 absolute.
+Tolerances, the same in every test, with no per-test multipliers:
+  complex128: 1e-10 relative on every quantity (states and H psi relative to
+              their largest entry, E to max(1, |E|), gradients and
+              dE/dtheta to max(1, their largest magnitude)).
+  complex64 : |E - E_oracle| <= 1e-6 Ha relative to max(1, |E|) and
+              fidelity >= 1 - 1e-6 (the precision targets); states and H psi
+              within 2e-5 of their largest entry; gradients and dE/dtheta
+              within 2e-6 of max(1, their largest magnitude).  The last two
+              follow from FP32 rounding: an entry of H psi sums about G
+              products of |D| <= 5 in FP32 (relative error 6e-8 each), so its
+              error is about sqrt(G) 6e-8 5 ~ 1e-5 |psi| at G ~ 4000 groups;
+              a gradient is a sum of such entries times amplitudes of a
+              normalised state, so its error stays below ~1e-6.
+Each comparison prints its error over its tolerance (`pytest -s`).
 """
 
 import numpy as np
@@ -30,6 +39,12 @@ def _lib():
     from paper_2607_15906_gb300 import build
     build.build()
     gb.load()
+
+
+def _within(what, err, tol):
+    """err <= tol, with the ratio printed for the record."""
+    print(f"TOLCHECK {what}: err {err:.3e} tol {tol:.3e} ratio {err / tol if tol else float('inf'):.3f}")
+    assert err <= tol, (what, err, tol)
 
 
 def _to_dev(p, psi):
@@ -66,9 +81,9 @@ def test_apply_h_and_energy(prec, n_orb, n_elec, mp, seed):
     ref = sv.apply_terms(h, psi_in)
     got = _host(hd)
     scale = np.max(np.abs(ref))
-    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale
+    _within(f"apply_h {prec} {n_orb}o hpsi", np.max(np.abs(got - ref)), TOL[prec]["state"] * scale)
     e_ref = sv.energy(h, psi_in)
-    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    _within(f"apply_h {prec} {n_orb}o E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
     assert abs(nrm - np.vdot(psi_in, psi_in).real) <= 1e-12
     # apply without the energy epilogue gives the same vector
     h2 = torch.empty_like(d)
@@ -87,8 +102,8 @@ def test_prepare_state_and_fidelity(prec, n_orb, n_elec, mp, seed):
     d = p.new_states(1)[0]
     p.prepare_state(ops, th, d)
     got = _host(d)
-    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 4
-    assert 1.0 - sv.fidelity(got, ref) <= (1e-12 if prec == "c128" else 1e-6)
+    _within(f"prepare {prec} {n_orb}o psi", np.max(np.abs(got - ref)), TOL[prec]["state"] * np.max(np.abs(ref)))
+    _within(f"prepare {prec} {n_orb}o 1-F", 1.0 - sv.fidelity(got, ref), 1e-12 if prec == "c128" else 1e-6)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -101,7 +116,7 @@ def test_single_taylor_step_on_random_state(prec):
         psi_in = _host(d)
         p.taylor_step(k, 0.37, d)
         ref = sv.taylor5(tabs[k], 0.37, psi_in)
-        assert np.max(np.abs(_host(d) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref))
+        _within(f"taylor_step {prec} op {k}", np.max(np.abs(_host(d) - ref)), TOL[prec]["state"] * np.max(np.abs(ref)))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -117,7 +132,8 @@ def test_pool_gradients(prec, n_orb, n_elec, mp, seed):
     g = p.pool_gradients(ws[0], ws[1])
     psi_in = _host(ws[0])
     g_ref = sv.pool_gradients(h, tabs, psi_in)
-    assert np.max(np.abs(g - g_ref)) <= TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref)))
+    _within(f"pool_gradients {prec} {n_orb}o", np.max(np.abs(g - g_ref)),
+            TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref))))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -130,8 +146,9 @@ def test_energy_grad_adjoint(prec, n_orb, n_elec, mp, seed):
     e, de = p.energy_grad(ops, th)
     ref = sv.basis_state(n, p.info["ref_index"])
     e_ref, de_ref = sv.energy_grad(h, ref, tabs, ops, th)
-    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
-    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 10
+    _within(f"energy_grad {prec} {n_orb}o E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"energy_grad {prec} {n_orb}o dE", np.max(np.abs(de - de_ref)),
+            TOL[prec]["grad"] * max(1.0, np.max(np.abs(de_ref))))
     if prec == "c128":
         hs = 1e-5
         for j in range(len(ops)):
@@ -154,7 +171,8 @@ def test_adapt_step_selection(prec):
     mag = np.abs(g_ref)
     allowed = np.flatnonzero(mag >= mag.max() * (1 - 1e-3))
     assert sel == allowed.min()
-    assert abs(e - sv.energy(h, psi)) <= TOL[prec]["energy"] * 10
+    e_ref = sv.energy(h, psi)
+    _within(f"adapt_step {prec} E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
 
 
 def _hermitian_random_table(n, t, rng, anti=False):
@@ -190,7 +208,7 @@ def test_random_tables_with_phases(prec, n):
     hd = torch.empty_like(d)
     e, _ = p.energy(d, hd)
     ref = sv.apply_terms(H, psi_in)
-    assert np.max(np.abs(_host(hd) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 2
+    _within(f"random table {prec} {n}q hpsi", np.max(np.abs(_host(hd) - ref)), TOL[prec]["state"] * np.max(np.abs(ref)))
     # generator tables as the library canonicalised them
     off, gx, gz, gph, gc, fam = p.pool()
     tabs = [PauliTable(n, gx[off[k]:off[k + 1]].astype(np.int64), gz[off[k]:off[k + 1]].astype(np.int64),
@@ -199,11 +217,12 @@ def test_random_tables_with_phases(prec, n):
     d2 = p.new_states(1)[0]
     p.prepare_state(ops, th, d2)
     sref = sv.prepare_state(sv.basis_state(n, 0), tabs, ops, th)
-    assert np.max(np.abs(_host(d2) - sref)) <= TOL[prec]["state"] * np.max(np.abs(sref)) * 4
+    _within(f"random table {prec} {n}q psi", np.max(np.abs(_host(d2) - sref)), TOL[prec]["state"] * np.max(np.abs(sref)))
     e2, de = p.energy_grad(ops, th)
     e_ref, de_ref = sv.energy_grad(H, sv.basis_state(n, 0), tabs, ops, th)
-    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
-    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
+    _within(f"random table {prec} {n}q E", abs(e2 - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"random table {prec} {n}q dE", np.max(np.abs(de - de_ref)),
+            TOL[prec]["grad"] * max(1.0, np.max(np.abs(de_ref))))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -237,11 +256,12 @@ def test_chain_list_overflow_falls_back(prec, n):
     p.prepare_state(ops, th, d)
     sref = sv.prepare_state(sv.basis_state(n, 0), tabs, ops, th)
     assert np.count_nonzero(sref) > (1 << n) // 4
-    assert np.max(np.abs(_host(d) - sref)) <= TOL[prec]["state"] * np.max(np.abs(sref)) * 4
+    _within(f"overflow {prec} {n}q psi", np.max(np.abs(_host(d) - sref)), TOL[prec]["state"] * np.max(np.abs(sref)))
     e2, de = p.energy_grad(ops, th)
     e_ref, de_ref = sv.energy_grad(H, sv.basis_state(n, 0), tabs, ops, th)
-    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
-    assert np.max(np.abs(de - de_ref)) <= TOL[prec]["grad"] * 20 * max(1.0, np.max(np.abs(de_ref)))
+    _within(f"overflow {prec} {n}q E", abs(e2 - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"overflow {prec} {n}q dE", np.max(np.abs(de - de_ref)),
+            TOL[prec]["grad"] * max(1.0, np.max(np.abs(de_ref))))
 
 
 def _grouped_random_table(n, rng):
@@ -321,9 +341,10 @@ def test_tiled_h_random_grouped_tables(prec, n, hpsi_path):
         hd = torch.empty_like(d)
         e, nrm = p.energy(d, hd)
         ref = sv.apply_terms(H, psi_in)
-        assert np.max(np.abs(_host(hd) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref)) * 4
+        _within(f"grouped {prec} {n}q {kind} {hpsi_path} hpsi", np.max(np.abs(_host(hd) - ref)),
+                TOL[prec]["state"] * np.max(np.abs(ref)))
         e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
-        assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)) * 10
+        _within(f"grouped {prec} {n}q {kind} {hpsi_path} E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -344,13 +365,14 @@ def test_tiled_h_on_sector_states(prec, path, monkeypatch):
     assert 0 < live <= 0.25
     e, nrm = p.energy(ws[0], ws[1])
     ref = sv.apply_terms(h, psi_in)
-    assert np.max(np.abs(_host(ws[1]) - ref)) <= TOL[prec]["state"] * np.max(np.abs(ref))
+    _within(f"sector state {prec} {path} hpsi", np.max(np.abs(_host(ws[1]) - ref)), TOL[prec]["state"] * np.max(np.abs(ref)))
     e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
-    assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
+    _within(f"sector state {prec} {path} E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
     e2, _, g, sel = p.adapt_step(ops, th, ws=ws, tie_rel=1e-4)
     g_ref = sv.pool_gradients(h, tabs, psi_in)
-    assert abs(e2 - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref))
-    assert np.max(np.abs(g - g_ref)) <= TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref)))
+    _within(f"sector state {prec} {path} E2", abs(e2 - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"sector state {prec} {path} grads", np.max(np.abs(g - g_ref)),
+            TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref))))
 
 
 def test_empty_ansatz_gives_reference_energy():
@@ -392,7 +414,7 @@ def test_full_size_20q_sampled_rows(prec):
     ref = sv.apply_terms_at(h, psi_in, rows)
     got = _host(hd)[rows]
     scale = np.max(np.abs(ref))
-    assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale * 5
+    _within(f"20q rows {prec}", np.max(np.abs(got - ref)), TOL[prec]["state"] * scale)
 
 
 @pytest.mark.parametrize("path", ["auto", "staged"])
@@ -414,16 +436,18 @@ def test_full_size_24q_sparse_prepare_energy_gradients(path, monkeypatch):
     got = _host(ws[0])
     ref = np.zeros(1 << 24, np.complex128)
     ref[si] = svals
-    assert np.max(np.abs(got - ref)) <= 1e-6
-    assert 1.0 - sv.fidelity(got, ref) <= 1e-6
+    _within(f"24q 6-op {path} psi", np.max(np.abs(got - ref)), TOL["c64"]["state"] * np.max(np.abs(ref)))
+    _within(f"24q 6-op {path} 1-F", 1.0 - sv.fidelity(got, ref), 1e-6)
     hi, hv = sv.apply_terms_sparse(h, si, svals)
     nn = sv.sparse_dot(si, svals, si, svals).real
     e_ref = sv.sparse_dot(si, svals, hi, hv).real / nn
-    assert abs(e2 - e_ref) <= 1e-6
+    _within(f"24q 6-op {path} E", abs(e2 - e_ref), TOL["c64"]["energy"] * max(1.0, abs(e_ref)))
+    gs = {}
     for k in list(range(0, len(tabs), 97)) + [int(np.argmax(np.abs(g)))]:
         ai, av = sv.apply_terms_sparse(tabs[k], si, svals)
-        g_ref = 2 * sv.sparse_dot(hi, hv, ai, av).real / nn
-        assert abs(g[k] - g_ref) <= 2e-6, (k, g[k], g_ref)
+        gs[k] = 2 * sv.sparse_dot(hi, hv, ai, av).real / nn
+    gscale = max(1.0, max(abs(v) for v in gs.values()))
+    _within(f"24q 6-op {path} grads", max(abs(g[k] - v) for k, v in gs.items()), TOL["c64"]["grad"] * gscale)
 
 
 def test_larger_n_26q_c64():
@@ -443,7 +467,7 @@ def test_larger_n_26q_c64():
     rows = np.concatenate([np.random.default_rng(1).integers(0, 1 << 26, size=24), [0, (1 << 26) - 1]])
     ref = sv.apply_terms_at(h, psi_in, rows)
     got = _host(hd)[rows]
-    assert np.max(np.abs(got - ref)) <= TOL["c64"]["state"] * np.max(np.abs(ref)) * 5
+    _within("26q rows", np.max(np.abs(got - ref)), TOL["c64"]["state"] * np.max(np.abs(ref)))
     del d, hd, psi_in
     torch.cuda.empty_cache()
     tabs = opool.pool_tables(26, 12, "jw")
@@ -454,4 +478,79 @@ def test_larger_n_26q_c64():
     si, svals = sv.prepare_state_sparse(p.info["ref_index"], tabs, ops, th)
     hi, hv = sv.apply_terms_sparse(h, si, svals)
     nn = sv.sparse_dot(si, svals, si, svals).real
-    assert abs(e - sv.sparse_dot(si, svals, hi, hv).real / nn) <= 1e-6
+    e_ref = sv.sparse_dot(si, svals, hi, hv).real / nn
+    _within("26q E", abs(e - e_ref), TOL["c64"]["energy"] * max(1.0, abs(e_ref)))
+
+
+def _sparse_prepared_check(n_orb, n_elec, label, n_ops=6, seed=3, grads=8):
+    """A full-layout (2^n) complex64 problem at n = 2 n_orb: a prepared sparse
+    state compared with the oracle on the oracle's support (and no other
+    amplitude nonzero), E, and a sample of pool gradients."""
+    ints = molecular_integrals(n_orb, seed=0, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw", 1e-3, 0.0)
+    tabs = opool.pool_tables(2 * n_orb, n_elec, "jw")
+    p = gb.Problem.build(ints, n_elec, precision="c64", int_drop=1e-3, device=0, colour=False)
+    assert p.n_qubits == 2 * n_orb and p.dim == 1 << (2 * n_orb) and p.info["n_terms"] == len(h)
+    ops, th = draw_ansatz(len(tabs), n_ops, seed=seed, theta_sigma=0.3)
+    ws = p.workspace()
+    e, nrm, g, sel = p.adapt_step(ops, th, ws=ws, tie_rel=1e-4)
+    si, svals = sv.prepare_state_sparse(p.info["ref_index"], tabs, ops, th)
+    at = torch.from_numpy(si).to("cuda:0")
+    got = ws[0][at].cpu().numpy().astype(np.complex128)
+    assert int(torch.view_as_real(ws[0]).ne(0).any(-1).sum().item()) == len(si)
+    _within(f"{label} psi", np.max(np.abs(got - svals)), TOL["c64"]["state"] * np.max(np.abs(svals)))
+    hi, hv = sv.apply_terms_sparse(h, si, svals)
+    nn = sv.sparse_dot(si, svals, si, svals).real
+    e_ref = sv.sparse_dot(si, svals, hi, hv).real / nn
+    _within(f"{label} E", abs(e - e_ref), TOL["c64"]["energy"] * max(1.0, abs(e_ref)))
+    ks = sorted(set(np.linspace(0, len(tabs) - 1, grads).astype(int).tolist() + [sel]))
+    gs = {}
+    for k in ks:
+        ai, av = sv.apply_group_sparse(tabs[k], si, svals)
+        gs[k] = 2 * sv.sparse_dot(hi, hv, ai, av).real / nn
+    gscale = max(1.0, max(abs(v) for v in gs.values()))
+    _within(f"{label} grads", max(abs(g[k] - v) for k, v in gs.items()), TOL["c64"]["grad"] * gscale)
+    assert p.device_errors() == 0
+    del ws
+    p.close()
+    torch.cuda.empty_cache()
+
+
+def test_larger_n_28q_c64():
+    """28 qubits in the full layout (14 orbitals, 8 electrons; a 2 GiB
+    complex64 state): sampled H psi rows of a dense random state (the
+    staged kernel), then a prepared sparse state (the scatter kernel,
+    list-driven chains and gradients) against the oracle."""
+    ints = molecular_integrals(14, seed=0, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw", 1e-3, 0.0)
+    p = gb.Problem.build(ints, 8, precision="c64", int_drop=1e-3, device=0, colour=False)
+    rng = np.random.default_rng(28)
+    gen = torch.Generator(device="cuda:0").manual_seed(28)
+    d = torch.randn(1 << 28, dtype=torch.complex64, device="cuda:0", generator=gen)
+    d /= torch.linalg.vector_norm(d)
+    hd = torch.empty_like(d)
+    e, nrm = p.energy(d, hd)
+    rows = np.concatenate([rng.integers(0, 1 << 28, size=12), [0, (1 << 28) - 1]]).astype(np.int64)
+    # only the source amplitudes the sampled rows need (rows ^ x of every
+    # term) come back to the host; the oracle indexes them through a lookup
+    src = np.unique((rows[:, None] ^ h.x[None, :]).ravel())
+    vals = d[torch.from_numpy(src).to("cuda:0")].cpu().numpy().astype(np.complex128)
+
+    class _Gathered:
+        def __getitem__(self, idx):
+            return vals[np.searchsorted(src, idx)]
+
+    ref = sv.apply_terms_at(h, _Gathered(), rows)
+    got = hd[torch.from_numpy(rows).to("cuda:0")].cpu().numpy().astype(np.complex128)
+    _within("28q dense rows", np.max(np.abs(got - ref)), TOL["c64"]["state"] * np.max(np.abs(ref)))
+    del d, hd
+    p.close()
+    torch.cuda.empty_cache()
+    _sparse_prepared_check(14, 8, "28q sparse")
+
+
+def test_larger_n_30q_c64():
+    """30 qubits in the full layout (15 orbitals, 8 electrons; an 8 GiB
+    complex64 state, the uint32 index limit of this build): a prepared
+    sparse state, E and sampled pool gradients against the oracle."""
+    _sparse_prepared_check(15, 8, "30q sparse", n_ops=5)

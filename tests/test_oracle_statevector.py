@@ -153,3 +153,57 @@ def test_sparse_paths_equal_dense():
     hd[hi] = hv
     assert np.max(np.abs(hd - sv.apply_terms(h, dense))) < 1e-13
     assert abs(sv.sparse_dot(si, svals, hi, hv) - np.vdot(dense, hd)) < 1e-13
+
+
+def test_sparse_group_apply_derivative_and_intermediates_equal_dense():
+    """apply_group_sparse (a generator's strings summed per basis state
+    before the product) equals the term-by-term dense apply; the sparse
+    derivative state and the kept intermediate states equal their dense
+    forward-mode counterparts; exact zeros are not held."""
+    nq, ne = 8, 4
+    tabs = pool.pool_tables(nq, ne, "bk")
+    hf = mapping.hf_index("bk", nq, ne)
+    rng = np.random.default_rng(5)
+    ops, th = rng.integers(0, len(tabs), 7), rng.normal(0, 0.3, 7)
+    ref = sv.basis_state(nq, hf)
+    si, svals, kept = sv.prepare_state_sparse(hf, tabs, ops, th, keep_at=[0, 3, 6])
+    assert np.all(svals != 0)
+    dense = sv.prepare_state(ref, tabs, ops, th)
+    for k in (0, len(tabs) // 2, len(tabs) - 1):
+        ai, av = sv.apply_group_sparse(tabs[k], si, svals)
+        assert np.all(av != 0) and np.all(np.diff(ai) > 0)
+        back = np.zeros(1 << nq, np.complex128)
+        back[ai] = av
+        assert np.max(np.abs(back - sv.apply_terms(tabs[k], dense))) < 1e-14
+    for j in (0, 3, 6):
+        pre = np.zeros(1 << nq, np.complex128)
+        pre[kept[j][0]] = kept[j][1]
+        assert np.max(np.abs(pre - sv.prepare_state(ref, tabs, ops[:j], th[:j]))) < 1e-14
+        di, dv = sv.derivative_state_sparse(tabs, ops, th, j, kept[j])
+        d = ref.copy()
+        for i, (k, t) in enumerate(zip(ops, th)):
+            d = sv.taylor5_derivative(tabs[k], t, d) if i == j else sv.taylor5(tabs[k], t, d)
+        got = np.zeros(1 << nq, np.complex128)
+        got[di] = dv
+        assert np.max(np.abs(got - d)) < 1e-14
+
+
+def test_parallel_oracle_equals_serial():
+    """oracle.parallel (spawned workers over slices) gives the serial oracle's
+    H psi rows and pool gradients."""
+    from oracle import parallel
+    ints = molecular_integrals(4, seed=3, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw")
+    tabs = pool.pool_tables(8, 4, "jw")
+    hf = mapping.hf_index("jw", 8, 4)
+    rng = np.random.default_rng(2)
+    ops, th = rng.integers(0, len(tabs), 6), rng.normal(0, 0.3, 6)
+    si, svals = sv.prepare_state_sparse(hf, tabs, ops, th)
+    dense = np.zeros(256, np.complex128)
+    dense[si] = svals
+    rows = np.flatnonzero(parallel.generator_support(tabs, si, svals, n_procs=2) | (dense != 0))
+    hrows = parallel.hpsi_rows(h, si, svals, rows, n_procs=2)
+    assert np.max(np.abs(hrows - sv.apply_terms(h, dense)[rows])) < 1e-13
+    nrm = float(np.vdot(dense, dense).real)
+    g = parallel.pool_gradients(tabs, si, svals, rows, hrows, nrm, n_procs=2)
+    assert np.max(np.abs(g - sv.pool_gradients(h, tabs, dense))) < 1e-13
