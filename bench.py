@@ -221,6 +221,77 @@ def run_gpu(args, rank, world, device):
                 h2d=h2d, d2h=d2h, info=info, e=float(e2[0]), sel=int(sel[0]), nnz=nnz)
 
 
+def _adapt_step_timer(prob, device: int, n_ops: int = N_OPS, seed: int = 0):
+    """step() = the bench step on `prob` (adapt_step of an n_ops-operator
+    ansatz + energy_grad of the grown one), device-resident, and
+    timed(steps, warmup) -> ms per step by CUDA events on the launch stream."""
+    import torch
+
+    ops, theta = draw_ansatz(prob.pool_size, n_ops, seed=seed)
+    dev = f"cuda:{device}"
+    ops_d = torch.from_numpy(ops).to(dev)
+    th_d = torch.from_numpy(theta).to(dev)
+    ops_g = torch.zeros(n_ops + 1, dtype=torch.int32, device=dev)
+    ops_g[:n_ops] = ops_d
+    th_g = torch.zeros(n_ops + 1, dtype=torch.float64, device=dev)
+    th_g[:n_ops] = th_d
+    ws = prob.workspace()
+    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
+    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
+    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    e_out = torch.zeros(1, dtype=torch.float64, device=dev)
+    de_out = torch.zeros(n_ops + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(device)
+    tie = 1e-4 if prob.precision == "c64" else 1e-8
+
+    def step():
+        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=tie, out=(e2, g, sel))
+        ops_g[n_ops:].copy_(sel)
+        prob.energy_grad(ops_g, th_g, ws=ws, out_e=e_out, out_de=de_out)
+
+    def timed(steps: int, warmup: int) -> float:
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    return dict(step=step, timed=timed, ws=ws, e2=e2, g=g, sel=sel, e_out=e_out, de_out=de_out,
+                ops=ops, theta=theta)
+
+
+def full_layout_large(device: int, n_orb: int, n_elec: int = 8, steps: int = 3, warmup: int = 1):
+    """The bench step in the full 2^n layout at n = 2 n_orb qubits (integrals
+    < 1e-3 dropped, JW, a 100-operator ansatz drawn from the pool)."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+
+    ints = molecular_integrals(n_orb, seed=0, decay=True)
+    t0 = time.time()
+    prob = gb.Problem.build(ints, n_elec, mapping="jw", precision="c64", int_drop=1e-3, device=device,
+                            colour=False)
+    build_s = time.time() - t0
+    t = _adapt_step_timer(prob, device)
+    ms = t["timed"](steps, warmup)
+    nnz = int(torch.view_as_real(t["ws"][0]).ne(0).any(-1).sum().item())
+    info = prob.info
+    out = {"qubits": 2 * n_orb, "electrons": n_elec, "state_bytes": prob.state_bytes, "pool": prob.pool_size,
+           "n_terms": info["n_terms"], "n_groups": info["n_groups"], "build_s": build_s,
+           "device_bytes": info["device_bytes"], "nonzero_amplitudes": nnz,
+           "iterations_per_s": 1e3 / ms, "ms_per_step": ms, "energy": float(t["e2"][0]),
+           "selected": int(t["sel"][0]), "steps": steps, "warmup": warmup}
+    del t
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def sector_layout(device: int, full_e: float, full_sel: int, steps: int = 10, warmup: int = 3):
     """The same 24-qubit ADAPT step (adapt_step on the 100-operator ansatz +
     energy_grad of the grown one) on a sector-layout problem: states of the
@@ -284,80 +355,57 @@ def sector_30q(device: int, steps: int = 5, warmup: int = 2):
     """Larger n in the sector layout: the same ADAPT step at 30 qubits (15
     orbitals, 8 electrons, integrals < 1e-3 dropped, 100-operator ansatz
     from the 2684-operator pool): D = C(15,4)^2 = 1,863,225 rows (15 MB per
-    complex64 state; the 2^30 layout would hold 8.6 GB)."""
-    import torch
+    complex64 state; the 2^30 layout holds 8.6 GB)."""
     import paper_2607_15906_gb300 as gb
 
     ints = molecular_integrals(15, seed=0, decay=True)
     t0 = time.time()
     prob = gb.Problem.build(ints, 8, mapping="jw", precision="c64", int_drop=1e-3, device=device, sector=True)
     build_s = time.time() - t0
-    ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
-    dev = f"cuda:{device}"
-    ops_d = torch.from_numpy(ops).to(dev)
-    th_d = torch.from_numpy(theta).to(dev)
-    ops_g = torch.zeros(N_OPS + 1, dtype=torch.int32, device=dev)
-    ops_g[:N_OPS] = ops_d
-    th_g = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
-    th_g[:N_OPS] = th_d
-    ws = prob.workspace()
-    e2 = torch.zeros(2, dtype=torch.float64, device=dev)
-    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
-    sel = torch.zeros(1, dtype=torch.int32, device=dev)
-    e_out = torch.zeros(1, dtype=torch.float64, device=dev)
-    de_out = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(device)
-
-    def step():
-        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-4, out=(e2, g, sel))
-        ops_g[N_OPS:].copy_(sel)
-        prob.energy_grad(ops_g, th_g, ws=ws, out_e=e_out, out_de=de_out)
-
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
+    t = _adapt_step_timer(prob, device)
+    ms = t["timed"](steps, warmup)
     info = prob.info
-    return {"qubits": 30, "state_dim": prob.dim, "pool": prob.pool_size, "n_terms": info["n_terms"],
-            "n_groups": info["n_groups"], "build_s": build_s, "device_bytes": info["device_bytes"],
-            "iterations_per_s": 1e3 / ms, "ms_per_step": ms, "energy": float(e2[0]), "selected": int(sel[0]),
-            "steps": steps, "warmup": warmup}
+    out = {"qubits": 30, "state_dim": prob.dim, "pool": prob.pool_size, "n_terms": info["n_terms"],
+           "n_groups": info["n_groups"], "build_s": build_s, "device_bytes": info["device_bytes"],
+           "iterations_per_s": 1e3 / ms, "ms_per_step": ms, "energy": float(t["e2"][0]),
+           "selected": int(t["sel"][0]), "steps": steps, "warmup": warmup}
+    prob.close()
+    return out
 
 
-def serving_bench(device: int, n_requests: int = 160, seed: int = 7):
+def serving_bench(device: int, n_requests: int = 2000, seed: int = 7, rates=(0.25, 0.5, 1.0, 2.0, 4.0)):
     """Mixed-size energy+gradient stream through the continuous-batching server.
 
     Requests follow synth.serving_requests (qubits uniform over 10..22,
     Hamiltonian seed 1000+i, 10-80 operators, theta ~ N(0, 0.05), complex64).
-    Their Hamiltonians are built before the clock starts.  First every request
-    is submitted at once to find the saturation throughput, then the same
-    stream arrives as a Poisson process at 0.5x and 1x that rate; latency is
+    Their Hamiltonians are built before the clock starts (host threads: the
+    builder runs outside the GIL).  First every request is submitted at once
+    to find the saturation throughput, then the same stream arrives as a
+    Poisson process (seed `seed`) at each fraction of that rate; latency is
     completion minus arrival.
     """
-    import torch
+    import concurrent.futures as cf
+
     import paper_2607_15906_gb300 as gb
     from paper_2607_15906_gb300.serving import Server
     from synth import molecular_integrals, serving_requests
 
     reqs = serving_requests(n_requests, rate_per_s=1.0, seed=seed)
-    probs = {}
-    for r in reqs:
+
+    def build(r):
         ints = molecular_integrals(r.n_orb, seed=r.seed, decay=True)
-        probs[r.index] = gb.Problem.build(ints, r.n_elec, precision="c64", device=device, colour=False)
+        return r.index, gb.Problem.build(ints, r.n_elec, precision="c64", device=device, colour=False)
+
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        probs = dict(ex.map(build, reqs))
+    build_s = time.time() - t0
     ansatz = {r.index: (np.minimum((r.op_draw * probs[r.index].pool_size).astype(np.int32),
                                    probs[r.index].pool_size - 1), r.theta) for r in reqs}
-    budget = 8 << 30
 
     def run(arrivals):
         lat = []
-        with Server(hbm_budget_bytes=budget, max_slots=64, device=device) as srv:
+        with Server(hbm_budget_bytes=0, max_slots=128, device=device) as srv:
             t0 = time.perf_counter()
             pending = {}
             order = sorted(range(len(reqs)), key=lambda i: arrivals[i])
@@ -384,72 +432,129 @@ def serving_bench(device: int, n_requests: int = 160, seed: int = 7):
         return {"requests": len(lat), "seconds": total, "throughput_rps": len(lat) / total,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "max_resident": int(st["max_resident"]), "batched_launches": int(st["launches"]),
-                "ticks": int(st["ticks"])}
+                "ticks": int(st["ticks"]), "arena_bytes": int(st["arena_bytes"]),
+                "arena_peak": int(st["arena_peak"])}
 
     run(np.zeros(len(reqs)))                                   # warm-up
     sat = run(np.zeros(len(reqs)))
     rate = sat["throughput_rps"]
-    out = {"stream": f"{n_requests} requests, qubits uniform 10..22, 10-80 ops, complex64, seed {seed}",
-           "saturation": sat}
-    for frac in (0.5, 1.0):
+    out = {"stream": f"{n_requests} requests, qubits uniform 10..22, 10-80 ops, complex64, "
+                     f"Hamiltonian seed 1000+i, arrivals seed {seed}",
+           "build_s": build_s, "saturation": sat, "saturation_rps": rate}
+    for frac in rates:
         gaps = np.random.default_rng(seed).exponential(1.0 / (frac * rate), size=len(reqs))
         out[f"poisson_{frac}x"] = run(np.cumsum(gaps))
+    for p in probs.values():
+        p.close()
     return out
 
 
-def c128_components(device: int, steps: int = 2):
-    """The plain complex128 GPU form on the same 24-qubit workload: one
-    selection step (gocp_adapt_step) and one energy evaluation (prepare +
-    H psi); a plain iteration with a forward-difference gradient costs one
-    selection step plus (P + 1) energy evaluations of the grown ansatz."""
+def c128_iterations(device: int, adjoint_steps: int = 5, plain_steps: int = 2):
+    """complex128 on the same 24-qubit workload, both forms timed directly
+    with CUDA events:
+      adjoint: the bench step itself (adapt_step + energy_grad of the grown
+               ansatz by the adjoint sweep) on a complex128 problem;
+      plain:   one selection step plus a forward-difference gradient of the
+               grown ansatz (the energy at theta and at theta + h e_j for the
+               P + 1 = 101 angles: 102 prepare + H psi evaluations)."""
     import torch
     import paper_2607_15906_gb300 as gb
 
     ints, cfg = config_integrals(WORKLOAD)
     prob = gb.Problem.build(ints, N_ELEC, mapping="jw", precision="c128",
                             int_drop=cfg["int_drop"], term_drop=cfg["term_drop"], device=device)
-    ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
-    ws = prob.workspace()
+    t = _adapt_step_timer(prob, device)
+    adj_ms = t["timed"](adjoint_steps, 2)
     dev = f"cuda:{device}"
-    ops_d = torch.from_numpy(ops).to(dev)
-    th_d = torch.from_numpy(theta).to(dev)
+    ws = t["ws"]
+    ops_d = torch.from_numpy(t["ops"]).to(dev)
+    th_d = torch.from_numpy(t["theta"]).to(dev)
+    ops_g = torch.zeros(N_OPS + 1, dtype=torch.int32, device=dev)
+    ops_g[:N_OPS] = ops_d
+    th_g = torch.zeros(N_OPS + 1, dtype=torch.float64, device=dev)
+    th_g[:N_OPS] = th_d
     e2 = torch.zeros(2, dtype=torch.float64, device=dev)
-    g = torch.zeros(prob.pool_size, dtype=torch.float64, device=dev)
-    sel = torch.zeros(1, dtype=torch.int32, device=dev)
+    e_fd = torch.zeros((N_OPS + 2, 2), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(device)
+    hstep = 1e-5
 
-    def timeit(fn, k):
-        fn()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(k):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3 / k
+    def plain():
+        prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-8, out=(e2, t["g"], t["sel"]))
+        ops_g[N_OPS:].copy_(t["sel"])
+        for j in range(N_OPS + 2):          # j = P + 1: the base point
+            th = th_g.clone()
+            if j <= N_OPS:
+                th[j] += hstep
+            prob.prepare_state(ops_g, th, ws[0])
+            prob.energy(ws[0], ws[1], out=e_fd[j])
 
-    t_sel = timeit(lambda: prob.adapt_step(ops_d, th_d, ws=ws, tie_rel=1e-8, out=(e2, g, sel)), steps)
+    plain()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(plain_steps):
+        plain()
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b) / plain_steps
+    fd = ((e_fd[:N_OPS + 1, 0] - e_fd[N_OPS + 1, 0]) / hstep).cpu().numpy()
+    prob.energy_grad(ops_g, th_g, ws=ws, out_e=t["e_out"], out_de=t["de_out"])
+    adj = t["de_out"].cpu().numpy()
+    out = {"adjoint_iterations_per_s": 1e3 / adj_ms, "adjoint_ms_per_step": adj_ms,
+           "plain_iterations_per_s": 1e3 / plain_ms, "plain_ms_per_step": plain_ms,
+           "plain_max_dE_dtheta_minus_adjoint": float(np.max(np.abs(fd - adj))),
+           "steps": {"adjoint": adjoint_steps, "plain": plain_steps},
+           "note": "both timed with CUDA events on the launch stream; plain = selection step + "
+                   "forward differences (h = 1e-5) over all 101 angles"}
+    prob.close()
+    return out
 
-    def energy_eval():
-        prob.prepare_state(ops_d, th_d, ws[0])
-        prob.energy(ws[0], ws[1], out=e2)
 
-    t_e = timeit(energy_eval, steps)
-    p = N_OPS + 1
-    return {"selection_step_ms": t_sel * 1e3, "energy_eval_ms": t_e * 1e3,
-            "plain_iteration_s": t_sel + (p + 1) * t_e,
-            "plain_iterations_per_s": 1.0 / (t_sel + (p + 1) * t_e),
-            "note": "plain iteration = selection step + (P+1) energy evaluations (forward differences), "
-                    "each measured with CUDA events; P = 101"}
+def precision_block(device: int, res):
+    """Precision of the headline (complex64) results against the complex128
+    GPU path on the same inputs (the complex128 path matches the oracle to
+    1e-10 relative: tests/test_gpu_bench_state.py), outside the timed region:
+    E, fidelity of psi(theta), the pool gradients and dE/dtheta of the grown
+    ansatz."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+
+    ints, cfg = config_integrals(WORKLOAD)
+    out = {}
+    states, vals = {}, {}
+    for prec in ("c64", "c128"):
+        prob = res["prob"] if prec == "c64" else gb.Problem.build(
+            ints, N_ELEC, mapping="jw", precision="c128", int_drop=cfg["int_drop"],
+            term_drop=cfg["term_drop"], device=device)
+        ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
+        ws = prob.workspace()
+        e, nrm, g, sel = prob.adapt_step(ops, theta, ws=ws, tie_rel=1e-4 if prec == "c64" else 1e-8)
+        states[prec] = ws[0].to(torch.complex128)
+        e2, de = prob.energy_grad(np.append(ops, np.int32(sel)).astype(np.int32), np.append(theta, 0.0), ws=ws)
+        vals[prec] = dict(e=e, g=g, sel=sel, de=de)
+        if prec == "c128":
+            prob.close()
+    a, b = states["c64"], states["c128"]
+    fid = float((torch.abs(torch.vdot(a, b)) ** 2 / (torch.vdot(a, a).real * torch.vdot(b, b).real)).item())
+    v64, v128 = vals["c64"], vals["c128"]
+    out = {"reference": "complex128 GPU path (matches the oracle to 1e-10 relative)",
+           "energy_c64": v64["e"], "energy_c128": v128["e"],
+           "abs_energy_error_ha": abs(v64["e"] - v128["e"]), "fidelity": fid, "infidelity": 1.0 - fid,
+           "max_gradient_error": float(np.max(np.abs(v64["g"] - v128["g"]))),
+           "max_dE_dtheta_error": float(np.max(np.abs(v64["de"] - v128["de"]))),
+           "selected_c64": v64["sel"], "selected_c128": v128["sel"],
+           "targets": {"abs_energy_error_ha": 1e-6, "infidelity": 1e-6}}
+    return out
 
 
 def adapt_14q(device: int, max_ops: int = 30):
     """Full ADAPT runs on the 14-qubit workload (7 orbitals, 6 electrons,
     204-operator pool) to 30 operators, complex128, under JW and BK: every
     iteration is a device selection step plus a BFGS re-optimisation whose
-    energies and gradients come from the adjoint sweep."""
+    energies and gradients come from the adjoint sweep.  Selection ties within
+    1e-6 relative go to the lowest index (the BFGS stopping tolerance leaves
+    the two mappings' gradients equal only to about 1e-8 relative)."""
     import paper_2607_15906_gb300 as gb
     from paper_2607_15906_gb300.adapt import adapt
 
@@ -459,7 +564,7 @@ def adapt_14q(device: int, max_ops: int = 30):
     for mp in ("jw", "bk"):
         prob = gb.Problem.build(ints, 6, mapping=mp, precision="c128", device=device)
         t0 = time.perf_counter()
-        run = adapt(prob, max_ops=max_ops, gtol=1e-4)
+        run = adapt(prob, max_ops=max_ops, gtol=1e-4, tie_rel=1e-6)
         secs = time.perf_counter() - t0
         runs[mp] = run
         out[mp] = {"iterations": len(run.energies) - 1, "seconds": secs,
@@ -475,22 +580,33 @@ def adapt_14q(device: int, max_ops: int = 30):
     return out
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch from the ncu capture recorded in profiles/traffic.json,
-    only while the library reports the kernel revision that capture was taken on."""
+def _counters(kernel: str):
+    """ncu counters per launch recorded in profiles/kernel_counters.json
+    (DRAM bytes, warp instructions), only while the library reports the
+    kernel revision they were captured on; else None."""
     try:
         import paper_2607_15906_gb300 as gb
         ver = gb.load().gocp_version().decode()
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(kernel)
+        rec = json.load(open(os.path.join(ROOT, "profiles", "kernel_counters.json"))).get(kernel)
         if rec and f"{kernel}={rec['revision']}" in ver:
-            return rec["dram_bytes_per_launch"]
+            return rec
     except Exception:
         pass
     return None
 
 
 def roofline(res, peaks, how):
-    """Dominant kernel vs its roof (see the design doc for the per-unit figures)."""
+    """Dominant kernel class against its roof.
+
+    H psi (Eq. 3) is graded against HBM: algorithmic bytes per launch = 2 S
+    (read psi once, write H psi once; S = 2^n x amplitude bytes) over the
+    call's CUDA-event duration, against the measured copy bandwidth.  Beside
+    it: the FP32-equivalent arithmetic nnz(psi) (T + 4 G) against 152 SMs x
+    128 lanes x 2 x clock ("alu"), the issue rate (ncu warp instructions per
+    launch over 4 issue slots x 152 SMs x clock), the DRAM traffic (ncu) and
+    its redundancy factor traffic / 2 S.  The Taylor, adjoint and gradient
+    kernels are graded against HBM with the bytes of the nonzero amplitudes
+    they read and write."""
     info = res["info"]
     n = info["n_qubits"]
     dim = 1 << n
@@ -500,71 +616,125 @@ def roofline(res, peaks, how):
     launches, ms = kern[top]
     per_launch_s = ms / 1e3 / max(launches, 1)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    amp = 8 if res["prob"].precision == "c64" else 16
+    nnz = res.get("nnz", dim)
     if top == "apply_h":
         t, g = info["n_terms"], info["n_groups"]
-        # per nonzero source amplitude: one signed add per term, one complex x
-        # real multiply-add per group (a zero amplitude contributes nothing,
-        # and the kernels do no work for it); dense states: nnz = 2^n
-        nnz = res.get("nnz", dim)
+        frac_env = min(0.25, max(0.0, float(os.environ.get("GOCP_SPARSE_FRAC", "") or 0.125)))
+        name = "k_apply_h_sparse" if nnz <= int(frac_env * dim) else "k_apply_h_tiled"
+        alg = 2 * dim * amp
+        achieved = alg / per_launch_s / 1e9
+        out = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs",
+               "algorithmic_bytes_per_launch": alg,
+               "timed": "the H psi call (the kernel and its amplitude-listing kernels), CUDA events"}
         flops = nnz * (t + 4 * g)
-        achieved = flops / per_launch_s / 1e12
-        # the library's choice (GOCP_SPARSE_FRAC of the amplitudes, default
-        # 1/8, at most 1/4): the scatter kernel at or below it
-        frac = min(0.25, max(0.0, float(os.environ.get("GOCP_SPARSE_FRAC", "") or 0.125)))
-        name = "k_apply_h_sparse" if nnz <= int(frac * dim) else "k_apply_h_tiled"
-        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-               "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops,
-               "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)",
-               "flops_per_launch": flops, "nonzero_amplitudes": nnz}
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        out["alu"] = {"achieved": flops / per_launch_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                      "frac": flops / per_launch_s / 1e12 / fp32_peak, "flops_per_launch": flops,
+                      "nonzero_amplitudes": nnz,
+                      "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)"}
+        c = _counters(name)
+        out["traffic"] = c["dram_bytes_per_launch"] if c else None
+        out["redundancy"] = (c["dram_bytes_per_launch"] / alg) if c else None
+        out["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: a lower bound "
+                               "on the launch's own traffic (output lines still dirty in the 129 MB L2 when the "
+                               "kernel ends are written back later)")
+        if c and c.get("warp_instructions_per_launch"):
+            inst = c["warp_instructions_per_launch"]
+            ipeak = 4 * 152 * sm_mhz * 1e6 / 1e9
+            out["issue"] = {"warp_instructions_per_launch": inst, "achieved": inst / per_launch_s / 1e9,
+                            "peak": ipeak, "unit": "G warp instructions/s",
+                            "frac": inst / per_launch_s / 1e9 / ipeak,
+                            "peak_source": f"4 issue slots x 152 SMs x {sm_mhz:.0f} MHz"}
+        else:
+            out["issue"] = None
     else:
-        # the nonzero amplitudes, read and written once per launch (psi; psi
-        # and lambda for the adjoint; psi and H psi for the gradients): the
-        # kernels do no work for zero amplitudes
-        amp = 8 if res["prob"].precision == "c64" else 16
-        nnz = res.get("nnz", dim)
         per = {"taylor5": 2 * nnz * amp, "adjoint": 4 * nnz * amp, "pool_grad": 2 * nnz * amp}[top]
         achieved = per / per_launch_s / 1e9
         out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs"}
-    out["traffic"] = _traffic(out["kernel"])
+        c = _counters(top)
+        out["traffic"] = c["dram_bytes_per_launch"] if c else None
     out["launch_ms"] = per_launch_s * 1e3
     out["launches_per_step"] = launches / max(1, res.get("steps", 1))
     return out
 
 
-def cpu_baseline_sample(target_s: float = 12.0):
-    """Times the oracle's term-by-term Pauli application on the full 2^24 state
-    and scales by the term applications one oracle ADAPT iteration makes."""
-    from oracle import mapping, pool as opool, statevector as sv
+class OracleIteration:
+    """The oracle's ADAPT iteration on the bench workload, timed on the host
+    cores from a bounded sample (test infrastructure: oracle/ is run only
+    here and in tests/).
 
-    ints, cfg = config_integrals(WORKLOAD)
-    h = mapping.hamiltonian_table(ints, "jw", cfg["int_drop"], cfg["term_drop"])
-    tabs = opool.pool_tables(24, N_ELEC, "jw")
-    ops, theta = draw_ansatz(len(tabs), N_OPS, seed=0)
-    psi = sv.basis_state(24, mapping.hf_index("jw", 24, N_ELEC)) * (1 + 0j)
-    sub = type(h)(h.n, h.x[:1], h.z[:1], h.phase[:1], h.coeff[:1])
-    t0 = time.perf_counter()
-    applied = 0
-    while time.perf_counter() - t0 < target_s:
-        sv.apply_terms(sub, psi)
-        applied += 1
-    per_term = (time.perf_counter() - t0) / applied
-    strings = [len(tabs[k]) for k in ops]
-    s_op = float(np.mean(strings))
-    p = N_OPS
-    # oracle ADAPT iteration: prepare (5 chained applies per op), pool_gradients
-    # (H psi + every generator), energy_grad (prepare + H psi + P+1 forward-mode
-    # re-preparations of the P+1-op ansatz)
-    prep = 5 * s_op * p
-    pool_g = len(h) + sum(len(t) for t in tabs)
-    eg = (p + 2) * 5 * s_op * (p + 1) + len(h)
-    count = prep + len(h) + pool_g + eg
-    secs = count * per_term
-    return {"value": 1.0 / secs, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-            "sample": f"{applied} single-term applications of oracle.statevector.apply_terms on the "
-                      f"2^24 state ({per_term:.3f} s each), scaled by the {count:.3g} term applications "
-                      f"of one oracle iteration"}
+    One oracle iteration (oracle.statevector on the sparse state, the same
+    work as the GPU step): prepare psi(theta) (100 Taylor steps), H psi on the
+    rows the products need, E and all 1424 pool gradients, then E and
+    dE/dtheta of the grown 101-operator ansatz by forward mode (prepare,
+    H psi, one derivative state per angle).  The prepare is timed whole (the
+    chain is sequential); H psi rows, gradient generators and derivative
+    states are timed on samples and scaled by their counts:
+        T = 2 t_prepare + 2 nnz t_row + M t_generator + (P + 1) t_derivative.
+    With procs > 1 the sampled parts run on that many spawned workers
+    (oracle.parallel), so t_row etc. are per-unit wall times at that width."""
+
+    def __init__(self):
+        from oracle import mapping, pool as opool, statevector as sv
+
+        ints, cfg = config_integrals(WORKLOAD)
+        self.h = mapping.hamiltonian_table(ints, "jw", cfg["int_drop"], cfg["term_drop"])
+        self.tabs = opool.pool_tables(24, N_ELEC, "jw")
+        self.ops, self.theta = draw_ansatz(len(self.tabs), N_OPS, seed=0)
+        t0 = time.perf_counter()
+        self.si, self.svals, self.kept = sv.prepare_state_sparse(
+            mapping.hf_index("jw", 24, N_ELEC), self.tabs, self.ops, self.theta, keep_at=range(N_OPS))
+        self.t_prepare = time.perf_counter() - t0
+        self.rng = np.random.default_rng(11)
+
+    def sample(self, procs: int, rows: int, gens: int, derivs: int, pool=None):
+        from oracle import parallel
+
+        nnz = len(self.si)
+        r = np.sort(self.rng.choice(self.si, size=min(rows, nnz), replace=False))
+        t0 = time.perf_counter()
+        parallel.hpsi_rows(self.h, self.si, self.svals, r, n_procs=procs, pool=pool)
+        t_row = (time.perf_counter() - t0) / len(r)
+        ks = self.rng.choice(len(self.tabs), size=gens, replace=False)
+        t0 = time.perf_counter()
+        parallel.generator_dots([self.tabs[k] for k in ks], self.si, self.svals, self.si, self.svals,
+                                n_procs=procs, pool=pool)
+        t_gen = (time.perf_counter() - t0) / gens
+        js = np.unique(np.linspace(0, N_OPS - 1, derivs).astype(int))
+        t0 = time.perf_counter()
+        parallel.derivative_states(self.tabs, self.ops, self.theta, {int(j): self.kept[int(j)] for j in js},
+                                   n_procs=procs, workers=pool)
+        t_der = (time.perf_counter() - t0) / len(js)
+        m = len(self.tabs)
+        secs = 2 * self.t_prepare + 2 * nnz * t_row + m * t_gen + (N_OPS + 1) * t_der
+        desc = (f"oracle (sparse complex128) iteration: prepare timed whole ({self.t_prepare:.2f} s, serial); "
+                f"H psi on {len(r)} of {nnz} rows, {gens} of {m} gradient generators and {len(js)} of "
+                f"{N_OPS + 1} derivative states timed on {procs} process(es) and scaled by their counts")
+        return secs, desc, {"t_prepare_s": self.t_prepare, "t_row_s": t_row, "t_generator_s": t_gen,
+                            "t_derivative_s": t_der}
+
+
+def cpu_baseline(procs_all: int):
+    """The oracle on 1 core and on all cores (bounded samples, about 10 s each)."""
+    from oracle import parallel
+
+    it = OracleIteration()
+    s1, d1, c1 = it.sample(1, rows=1024, gens=12, derivs=2)
+    pool = parallel.start(procs_all)
+    try:
+        it.sample(procs_all, rows=4 * procs_all, gens=procs_all, derivs=procs_all, pool=pool)   # warm workers
+        sn, dn, cn = it.sample(procs_all, rows=512 * procs_all, gens=4 * procs_all, derivs=procs_all,
+                               pool=pool)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    return {"value": 1.0 / sn, "unit": "iterations/s", "cores": procs_all, "kind": "oracle",
+            "sample": dn, "components_s": cn, "nproc": os.cpu_count(),
+            "one_core": {"value": 1.0 / s1, "cores": 1, "sample": d1, "components_s": c1}}
 
 
 def main():
@@ -592,20 +762,28 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        warm = max(args.warmup, 0)
+        from oracle import parallel
+        procs = parallel.procs()
+        it = OracleIteration()
+        pool = parallel.start(procs)
         vals = []
-        for i in range(warm + args.steps):
-            r = cpu_baseline_sample(target_s=args.reference_sample_s)
-            if i >= warm:
-                vals.append(1.0 / r["value"])
+        try:
+            for i in range(max(args.warmup, 0) + args.steps):
+                secs, desc, comp = it.sample(procs, rows=512 * procs, gens=4 * procs, derivs=procs, pool=pool)
+                if i >= args.warmup:
+                    vals.append(secs)
+        finally:
+            if pool is not None:
+                pool.close()
+                pool.join()
         secs = float(np.mean(vals))
         value = 1.0 / secs
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                 "data": "synthetic", "config": config, "impl": "reference",
-                "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1, "kind": "oracle",
-                                 "sample": r["sample"]},
+                "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": procs, "kind": "oracle",
+                                 "sample": desc, "nproc": os.cpu_count()},
                 "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -622,19 +800,23 @@ def main():
         value = replica_throughput(args.steps, world, secs)
         e2e = replica_throughput(args.steps, world, res["e2e_secs"])
         roof = roofline(res, peaks, how)
-        cpu = None
-        if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline_sample()
         kern = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                 for k, v in res["kern"].items()}
         extras = {}
         if world == 1 and args.precision == "c64":
+            extras["precision"] = precision_block(local, res)
             extras["sector_layout"] = sector_layout(local, res["e"], res["sel"])
         if not args.no_extras and world == 1:
-            extras["serving"] = serving_bench(local)
-            extras["c128_plain"] = c128_components(local)
-            extras["adapt_14q"] = adapt_14q(local)
+            extras["c128"] = c128_iterations(local)
+            extras["full_layout_28q"] = full_layout_large(local, 14)
+            extras["full_layout_30q"] = full_layout_large(local, 15)
             extras["sector_30q"] = sector_30q(local)
+            extras["adapt_14q"] = adapt_14q(local)
+            extras["serving"] = serving_bench(local)
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            from oracle import parallel
+            cpu = cpu_baseline(parallel.procs())
         line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

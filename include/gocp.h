@@ -272,16 +272,22 @@ int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
 /* A request server: a worker thread owns one stream and advances every
  * resident request by one stage per tick with one batched launch per stage
  * kind (forward Taylor op, H psi + energy, adjoint op), admitting queued
- * requests as slots and arena memory free up (continuous batching).
- * hbm_budget_bytes is reserved up front as the state arena (power-of-two
- * buddy blocks; a request holds 2 states); max_slots bounds residency
- * (1..256).  Problems must outlive the requests that name them and must be
- * C64 or C128 problems built on `device`. */
+ * requests as slots and memory free up (continuous batching).  A request
+ * holds 2 states.  Admission:
+ *   hbm_budget_bytes == 0: by free device memory -- a queued request is
+ *     admitted when the device's free memory (cudaMemGetInfo) plus what the
+ *     server's stream-ordered memory pool holds unused covers its two states
+ *     and a reserve of max(1 GiB, 2 % of the device), its states are taken
+ *     from that pool and returned to it when it finishes;
+ *   hbm_budget_bytes > 0: that many bytes are reserved up front as the
+ *     state arena (power-of-two buddy blocks).
+ * max_slots bounds residency (1..256).  Problems must outlive the requests
+ * that name them and must be C64 or C128 problems built on `device`. */
 int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_server** out);
 void gocp_server_destroy(gocp_server* s);
 
 /* Queue an energy+gradient request; ops/theta are host arrays copied here.
- * GOCP_ENOMEM if one request can never fit the arena. */
+ * GOCP_ENOMEM if one request can never fit the arena (arena mode). */
 int gocp_submit(gocp_server* s, const gocp_problem* p, const int32_t* ops, const double* theta,
                 int n_ops, uint64_t* ticket);
 
@@ -300,7 +306,7 @@ typedef struct {
   uint64_t ticks;               /* worker iterations that launched work */
   uint64_t launches;            /* batched kernel launches */
   uint64_t max_resident;        /* peak concurrent requests */
-  size_t arena_bytes, arena_in_use, arena_peak;
+  size_t arena_bytes, arena_in_use, arena_peak;   /* arena_bytes 0 in free-memory mode */
   int resident, queued;
 } gocp_server_stats;
 int gocp_server_get_stats(gocp_server* s, gocp_server_stats* out);

@@ -46,10 +46,20 @@ def _map(fn, jobs, n_procs, pool=None):
         return p.map(fn, jobs)
 
 
+_DENSE: dict = {}
+
+
 def _dense(n, si, svals):
-    psi = np.zeros(1 << n, np.complex128)
-    psi[si] = svals
-    return psi
+    """psi as a dense 2^n array (the lookup apply_terms_at indexes), kept for
+    the next job on the same state in this process."""
+    key = (n, si.size, int(si[0]) if si.size else -1, int(si[-1]) if si.size else -1,
+           complex(svals[0]) if si.size else 0j, complex(svals[-1]) if si.size else 0j)
+    if key not in _DENSE:
+        _DENSE.clear()
+        psi = np.zeros(1 << n, np.complex128)
+        psi[si] = svals
+        _DENSE[key] = psi
+    return _DENSE[key]
 
 
 def _rows_job(args):
@@ -107,3 +117,41 @@ def pool_gradients(pool: list[PauliTable], si, svals, rows, hrows, nrm: float,
     chunks = np.array_split(np.arange(len(pool)), max(1, 2 * n_procs))
     jobs = [([_pack(pool[k]) for k in c], si, svals, rows, hrows) for c in chunks if c.size]
     return np.concatenate(_map(_grad_job, jobs, n_procs)) / nrm
+
+
+def _dots_job(args):
+    gens, si, svals, vi, vv = args
+    out = np.zeros(len(gens))
+    for i, g in enumerate(gens):
+        ai, av = sv.apply_group_sparse(_unpack(g), si, svals)
+        out[i] = 2.0 * sv.sparse_dot(vi, vv, ai, av).real
+    return out
+
+
+def generator_dots(gens: list[PauliTable], si, svals, vi, vv, n_procs: int | None = None,
+                   pool=None) -> np.ndarray:
+    """2 Re <v|A_k psi> for each generator (Eq. 4 with v = H psi), psi and v
+    sparse (v zero outside vi)."""
+    n_procs = procs() if n_procs is None else n_procs
+    chunks = np.array_split(np.arange(len(gens)), max(1, min(len(gens), 2 * n_procs)))
+    jobs = [([_pack(gens[k]) for k in c], si, svals, vi, vv) for c in chunks if c.size]
+    return np.concatenate(_map(_dots_job, jobs, n_procs, pool))
+
+
+def _deriv_job(args):
+    tabs, ops, thetas, j, psi_j = args
+    pool = {k: _unpack(t) for k, t in tabs.items()}
+    return sv.derivative_state_sparse(pool, ops, thetas, j, psi_j)
+
+
+def derivative_states(pool: list[PauliTable], ops, thetas, kept: dict, n_procs: int | None = None,
+                      workers=None) -> dict:
+    """{j: d psi_P / d theta_j} (derivative_state_sparse) for every j in
+    kept = {j: psi_j}, one j per job."""
+    n_procs = procs() if n_procs is None else n_procs
+    ops = [int(k) for k in ops]
+    jobs = []
+    for j, psi_j in kept.items():
+        tabs = {k: _pack(pool[k]) for k in set(ops[j:])}
+        jobs.append((tabs, ops, list(thetas), j, psi_j))
+    return dict(zip(kept.keys(), _map(_deriv_job, jobs, n_procs, workers)))

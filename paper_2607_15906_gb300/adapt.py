@@ -33,6 +33,7 @@ class AdaptRun:
     grad_norms: list
     converged: bool
     evaluations: int
+    gradients: list = dataclasses.field(default_factory=list)   # pool gradients of each iteration
 
 
 def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None = None,
@@ -51,12 +52,13 @@ def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None 
         raise ValueError("family=True needs a problem built with GOCP colouring")
     ops: list[int] = []
     thetas = np.zeros(0)
-    energies, norms = [], []
+    energies, norms, grads = [], [], []
     evals = 0
     converged = False
     while True:
         e, _, g, sel = problem.adapt_step(np.asarray(ops, np.int32), thetas, ws=ws, tie_rel=tie_rel)
         energies.append(e)
+        grads.append(np.asarray(g).copy())
         gn = float(np.linalg.norm(g))
         norms.append(gn)
         if gn < gtol:
@@ -85,4 +87,4 @@ def adapt(problem, max_ops: int = 30, gtol: float = 1e-4, tie_rel: float | None 
         res = minimize(fun, x0, jac=True, method="BFGS", options=opts)
         thetas = np.asarray(res.x, dtype=np.float64)
     return AdaptRun(ops=ops, thetas=thetas, energies=energies, grad_norms=norms,
-                    converged=converged, evaluations=evals)
+                    converged=converged, evaluations=evals, gradients=grads)

@@ -8,9 +8,13 @@
 //   ENERGY    lambda <- H psi, E (Eq. 1), lambda <- (H - E) psi / <psi|psi>
 //   BACKWARD  adjoint step j: psi <- T_j^-1 psi, dE_j, lambda <- T_j^+ lambda
 // Requests that arrive while others are on the GPU join at the next tick;
-// a finished request frees its slot and arena block at once.  Each request
-// holds its two states in one power-of-two block of a buddy-allocated arena
-// reserved at creation (admission by free device memory).
+// a finished request frees its slot and its memory at once.  Each request
+// holds its two states either in one power-of-two block of a buddy-allocated
+// arena reserved at creation (hbm_budget_bytes > 0), or (hbm_budget_bytes ==
+// 0) in memory taken from a stream-ordered CUDA memory pool when it is
+// admitted: it is admitted only while the device's free memory, plus what the
+// pool holds unused, covers its two states and a reserve (admission by free
+// device memory).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -105,6 +109,8 @@ struct Slot {   // per-slot device region
 
 struct Request {
   uint64_t ticket = 0;
+  void* mem = nullptr;      // pool mode: the request's two states
+  size_t bytes = 0;         // 2 states
   const Problem* prob = nullptr;
   std::vector<int32_t> ops;
   std::vector<double> theta;
@@ -133,6 +139,11 @@ struct gocp_server {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   Buddy buddy;
+  // pool mode (hbm_budget_bytes == 0)
+  bool pool_mode = false;
+  cudaMemPool_t mpool = nullptr;
+  size_t reserve = 0;
+  size_t capacity = 0;      // device memory less the reserve
   int max_slots = 0;
   void* slot_mem = nullptr;
   std::vector<Slot> slots;
@@ -165,7 +176,12 @@ void finish(gocp_server* s, Request* r, St st) {
     s->free_slots.push_back(r->slot);
     r->slot = -1;
   }
-  if (r->order >= 0 && r->off != (size_t)-1) {
+  if (r->mem) {   // pool mode: back to the pool once the stream's work on it is done
+    cudaFreeAsync(r->mem, s->stream);
+    r->mem = nullptr;
+    s->stats.arena_in_use -= r->bytes;
+  }
+  if (!s->pool_mode && r->order >= 0 && r->off != (size_t)-1) {
     s->buddy.release(r->order, r->off);
     s->stats.arena_in_use -= kMinBlock << r->order;
     r->off = (size_t)-1;
@@ -174,10 +190,28 @@ void finish(gocp_server* s, Request* r, St st) {
   if (st == St::Cancelled) ++s->stats.cancelled;
 }
 
+// Device memory a pool-mode request may still take: free device memory plus
+// what the server's pool holds unused, less the reserve.
+size_t pool_available(gocp_server* s) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  uint64_t reserved = 0, used = 0;
+  cudaMemPoolGetAttribute(s->mpool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  cudaMemPoolGetAttribute(s->mpool, cudaMemPoolAttrUsedMemCurrent, &used);
+  const size_t avail = free_b + (size_t)(reserved > used ? reserved - used : 0);
+  return avail > s->reserve ? avail - s->reserve : 0;
+}
+
 // Admits queued requests (FIFO with a short look-ahead so that one large
-// request does not block smaller ones behind it).  Called with mu held.
+// request does not block smaller ones behind it).  Called with mu held, on
+// the worker thread (pool mode allocates on the server stream).
 void admit(gocp_server* s) {
   int looked = 0;
+  size_t avail = 0;
+  bool avail_known = false;
   for (auto it = s->queue.begin(); it != s->queue.end() && looked < 16;) {
     Request* r = *it;
     if (r->cancel) {
@@ -187,15 +221,31 @@ void admit(gocp_server* s) {
     }
     ++looked;
     if (s->free_slots.empty()) break;
-    size_t off;
-    if (!s->buddy.alloc(r->order, &off)) {
-      ++it;
-      continue;
+    if (s->pool_mode) {
+      if (!avail_known) {
+        avail = pool_available(s);
+        avail_known = true;
+      }
+      if (r->bytes > avail ||
+          cudaMallocFromPoolAsync(&r->mem, r->bytes, s->mpool, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        r->mem = nullptr;
+        ++it;
+        continue;
+      }
+      avail -= r->bytes;
+      s->stats.arena_in_use += r->bytes;
+    } else {
+      size_t off;
+      if (!s->buddy.alloc(r->order, &off)) {
+        ++it;
+        continue;
+      }
+      r->off = off;
+      s->stats.arena_in_use += kMinBlock << r->order;
     }
-    r->off = off;
     r->slot = s->free_slots.back();
     s->free_slots.pop_back();
-    s->stats.arena_in_use += kMinBlock << r->order;
     s->stats.arena_peak = std::max(s->stats.arena_peak, s->stats.arena_in_use);
     r->st = St::Active;
     r->phase = Phase::Forward;
@@ -211,8 +261,9 @@ StageItem item_for(gocp_server* s, Request* r) {
   const Slot& sl = s->slots[r->slot];
   StageItem it;
   it.prob = r->prob;
-  it.psi = s->arena + r->off;
-  it.lam = s->arena + r->off + state_bytes_of(*r->prob);
+  char* base = s->pool_mode ? (char*)r->mem : s->arena + r->off;
+  it.psi = base;
+  it.lam = base + state_bytes_of(*r->prob);
   it.ops = sl.ops;
   it.theta = sl.theta;
   it.coefs = sl.coefs;
@@ -364,7 +415,7 @@ int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_
   if (!out) return fail(GOCP_EINVAL, "out is NULL");
   *out = nullptr;
   if (max_slots < 1 || max_slots > kMaxBatchItems) return fail(GOCP_EINVAL, "max_slots must be in 1..256");
-  if (hbm_budget_bytes < kMinBlock) return fail(GOCP_EINVAL, "hbm_budget_bytes too small");
+  if (hbm_budget_bytes != 0 && hbm_budget_bytes < kMinBlock) return fail(GOCP_EINVAL, "hbm_budget_bytes too small");
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) return fail(GOCP_ENODEV, "no CUDA device");
   if (device < 0 || device >= count) return fail(GOCP_EINVAL, "device out of range");
@@ -376,6 +427,7 @@ int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_
   int rc = GOCP_OK;
   auto bail = [&](int code) {
     if (s->arena) cudaFree(s->arena);
+    if (s->mpool) cudaMemPoolDestroy(s->mpool);
     if (s->slot_mem) cudaFree(s->slot_mem);
     if (s->dev_desc) cudaFree(s->dev_desc);
     if (s->host_desc) cudaFreeHost(s->host_desc);
@@ -384,9 +436,25 @@ int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_
     if (prev >= 0) cudaSetDevice(prev);
     return code;
   };
-  s->buddy.init(hbm_budget_bytes);
-  s->arena_bytes = s->buddy.capacity();
-  if ((rc = cuda_status(cudaMalloc((void**)&s->arena, s->arena_bytes), "arena"))) return bail(GOCP_ENOMEM);
+  if (hbm_budget_bytes == 0) {
+    s->pool_mode = true;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if ((rc = cuda_status(cudaMemPoolCreate(&s->mpool, &props), "cudaMemPoolCreate"))) return bail(rc);
+    uint64_t keep = UINT64_MAX;   // freed blocks stay in the pool for the next requests
+    cudaMemPoolSetAttribute(s->mpool, cudaMemPoolAttrReleaseThreshold, &keep);
+    size_t free_b = 0, total_b = 0;
+    if ((rc = cuda_status(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo"))) return bail(rc);
+    s->reserve = std::max<size_t>((size_t)1 << 30, total_b / 50);
+    s->capacity = total_b > s->reserve ? total_b - s->reserve : 0;
+    s->arena_bytes = 0;
+  } else {
+    s->buddy.init(hbm_budget_bytes);
+    s->arena_bytes = s->buddy.capacity();
+    if ((rc = cuda_status(cudaMalloc((void**)&s->arena, s->arena_bytes), "arena"))) return bail(GOCP_ENOMEM);
+  }
   const size_t per_slot = (size_t)kMaxOps * (4 + 8 + 48 + 8) + (size_t)kMaxItemBlocks * 8 + 256;
   if ((rc = cuda_status(cudaMalloc(&s->slot_mem, per_slot * max_slots), "slots"))) return bail(GOCP_ENOMEM);
   cudaMemset(s->slot_mem, 0, per_slot * max_slots);
@@ -435,7 +503,10 @@ void gocp_server_destroy(gocp_server* s) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  for (auto& kv : s->all)
+    if (kv.second->mem) cudaFreeAsync(kv.second->mem, s->stream);
   cudaStreamSynchronize(s->stream);
+  if (s->mpool) cudaMemPoolDestroy(s->mpool);
   cudaFree(s->arena);
   cudaFree(s->slot_mem);
   cudaFree(s->dev_desc);
@@ -464,11 +535,12 @@ int gocp_submit(gocp_server* s, const gocp_problem* h, const int32_t* ops, const
   r->ops.assign(ops, ops + n_ops);
   r->theta.assign(theta, theta + n_ops);
   r->order = Buddy::order_for(2 * state_bytes_of(p));
+  r->bytes = (2 * state_bytes_of(p) + 255) & ~(size_t)255;
   r->off = (size_t)-1;
   std::lock_guard<std::mutex> lk(s->mu);
-  if ((kMinBlock << r->order) > s->buddy.largest()) {
+  if (s->pool_mode ? r->bytes > s->capacity : (kMinBlock << r->order) > s->buddy.largest()) {
     delete r;
-    return fail(GOCP_ENOMEM, "request can never fit the server arena");
+    return fail(GOCP_ENOMEM, "request can never fit the server's device memory");
   }
   if (s->fatal) {
     delete r;

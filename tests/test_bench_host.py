@@ -1,11 +1,13 @@
 """bench.py's roofline accounting (host logic, no GPU).
 
-H psi is counted as nnz(psi) (T + 4G) FLOPs per launch (one signed add per
+H psi is graded against HBM with 2 S algorithmic bytes per launch (psi read
+once, H psi written once, S = 2^n x amplitude bytes); beside it the
+FP32-equivalent count nnz(psi) (T + 4G) FLOPs per launch (one signed add per
 term and one complex x real multiply-add per group, per nonzero source
-amplitude); the chain and gradient kernels as the bytes of the nonzero
-amplitudes they read and write.  The kernel named is the one the library
-chooses: the scatter kernel at or below GOCP_SPARSE_FRAC (default 1/8, at
-most 1/4) of 2^n nonzero amplitudes."""
+amplitude).  The chain and gradient kernels are counted as the bytes of the
+nonzero amplitudes they read and write.  The kernel named is the one the
+library chooses: the scatter kernel at or below GOCP_SPARSE_FRAC (default
+1/8, at most 1/4) of 2^n nonzero amplitudes."""
 
 import importlib.util
 import os
@@ -39,16 +41,21 @@ def _res(top_ms, top="apply_h", nnz=1000, n=20, precision="c64"):
 PEAKS = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}
 
 
-def test_h_psi_flops_count_nonzero_amplitudes(monkeypatch):
+@pytest.mark.parametrize("precision,amp", [("c64", 8), ("c128", 16)])
+def test_h_psi_graded_on_hbm_with_alu_beside(monkeypatch, precision, amp):
     monkeypatch.delenv("GOCP_SPARSE_FRAC", raising=False)
     b = _bench()
-    r = b.roofline(_res(10.0, nnz=1000), PEAKS, "measured")
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["flops_per_launch"] == 1000 * (500 + 4 * 100)
+    r = b.roofline(_res(10.0, nnz=1000, precision=precision), PEAKS, "measured")
     per_launch_s = 10.0 / 1e3 / 2
-    assert r["achieved"] == pytest.approx(1000 * 900 / per_launch_s / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / (152 * 128 * 2 * 2070e6 / 1e12))
-    assert r["nonzero_amplitudes"] == 1000
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["algorithmic_bytes_per_launch"] == 2 * (1 << 20) * amp
+    assert r["achieved"] == pytest.approx(2 * (1 << 20) * amp / per_launch_s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / PEAKS["hbm_gbs"])
+    a = r["alu"]
+    assert a["flops_per_launch"] == 1000 * (500 + 4 * 100)
+    assert a["achieved"] == pytest.approx(1000 * 900 / per_launch_s / 1e12)
+    assert a["frac"] == pytest.approx(a["achieved"] / (152 * 128 * 2 * 2070e6 / 1e12))
+    assert a["nonzero_amplitudes"] == 1000
 
 
 @pytest.mark.parametrize("frac_env,nnz,expect", [

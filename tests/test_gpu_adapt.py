@@ -94,14 +94,26 @@ def test_adapt_14q_mapping_invariant_30_operators():
     """The 14-qubit workload (7 orbitals, 6 electrons, 204-operator pool)
     grown to 30 operators under JW and BK, complex128: the same operator at
     every iteration and the same energies (Sec. IV.B; BK is a basis
-    permutation of JW, so the method is exactly mapping invariant)."""
+    permutation of JW, so the method is exactly mapping invariant).
+
+    The selection window is 1e-6 relative: the BFGS re-optimisation stops at
+    a gradient norm of 1e-8, so the angles -- and with them the pool
+    gradients -- of the two mappings agree only to about 1e-8 relative, and
+    two operators whose |g| lie closer than that (alpha/beta mirror
+    excitations of a nearly symmetric state) may otherwise be ordered
+    differently."""
     ints, c = config_integrals("c2_14q")
     runs = {}
     for mp in ("jw", "bk"):
         p = gb.Problem.build(ints, 6, mapping=mp, precision="c128", device=0)
-        runs[mp] = gpu_adapt(p, max_ops=30, gtol=1e-4)
+        runs[mp] = gpu_adapt(p, max_ops=30, gtol=1e-4, tie_rel=1e-6)
     assert len(runs["jw"].ops) == 30
-    assert runs["jw"].ops == runs["bk"].ops
+    a, b = runs["jw"], runs["bk"]
+    for i, (x, y) in enumerate(zip(a.ops, b.ops)):
+        if x != y:
+            ga, gb_ = np.abs(a.gradients[i]), np.abs(b.gradients[i])
+            pytest.fail(f"iteration {i}: JW chose {x}, BK {y}; |g| JW {ga[x]:.15g} {ga[y]:.15g}, "
+                        f"BK {gb_[x]:.15g} {gb_[y]:.15g}, max {ga.max():.15g}")
     assert np.max(np.abs(np.array(runs["jw"].energies) - np.array(runs["bk"].energies))) < 1e-9
     assert all(b <= a + 1e-12 for a, b in zip(runs["jw"].energies, runs["jw"].energies[1:]))
 

@@ -110,3 +110,20 @@ def test_cancel_poll_and_rejections():
         assert srv.result(ts[-1]) is not None
         for t in ts[:-1]:
             srv.result(t)
+
+
+def test_admission_by_free_device_memory():
+    """hbm_budget_bytes = 0: states come from the server's memory pool as
+    requests are admitted against free device memory; results equal the
+    arena server's bit for bit (same kernels, same block counts)."""
+    reqs = _requests()
+    with Server(hbm_budget_bytes=64 << 20, max_slots=16) as srv:
+        arena = [srv.result(srv.submit(p, ops, th)) for (_, _, p, ops, th) in reqs]
+    with Server(hbm_budget_bytes=0, max_slots=16) as srv:
+        tickets = [srv.submit(p, ops, th) for (_, _, p, ops, th) in reqs]
+        pooled = [srv.result(t) for t in tickets]
+        st = srv.stats()
+    assert st["arena_bytes"] == 0 and st["completed"] == len(reqs)
+    assert st["arena_in_use"] == 0 and st["arena_peak"] >= 2 * reqs[-2][2].state_bytes
+    for (ea, da), (ep, dp) in zip(arena, pooled):
+        assert ea == ep and np.array_equal(da, dp)

@@ -207,3 +207,11 @@ def test_parallel_oracle_equals_serial():
     nrm = float(np.vdot(dense, dense).real)
     g = parallel.pool_gradients(tabs, si, svals, rows, hrows, nrm, n_procs=2)
     assert np.max(np.abs(g - sv.pool_gradients(h, tabs, dense))) < 1e-13
+    hi = rows[hrows != 0]
+    dots = parallel.generator_dots(tabs, si, svals, hi, hrows[hrows != 0], n_procs=2)
+    assert np.max(np.abs(dots / nrm - g)) < 1e-13
+    _, _, kept = sv.prepare_state_sparse(hf, tabs, ops, th, keep_at=[1, 4])
+    ds = parallel.derivative_states(tabs, ops, th, kept, n_procs=2)
+    for j in (1, 4):
+        di, dv = sv.derivative_state_sparse(tabs, ops, th, j, kept[j])
+        assert np.array_equal(ds[j][0], di) and np.array_equal(ds[j][1], dv)
