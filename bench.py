@@ -281,7 +281,7 @@ def full_layout_large(device: int, n_orb: int, n_elec: int = 8, steps: int = 3, 
     ms = t["timed"](steps, warmup)
     nnz = int(torch.view_as_real(t["ws"][0]).ne(0).any(-1).sum().item())
     info = prob.info
-    out = {"qubits": 2 * n_orb, "electrons": n_elec, "state_bytes": prob.state_bytes, "pool": prob.pool_size,
+    out = {"qubits": 2 * n_orb, "electrons": n_elec, "state_bytes": prob.state_bytes(), "pool": prob.pool_size,
            "n_terms": info["n_terms"], "n_groups": info["n_groups"], "build_s": build_s,
            "device_bytes": info["device_bytes"], "nonzero_amplitudes": nnz,
            "iterations_per_s": 1e3 / ms, "ms_per_step": ms, "energy": float(t["e2"][0]),
@@ -530,7 +530,7 @@ def precision_block(device: int, res):
         ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
         ws = prob.workspace()
         e, nrm, g, sel = prob.adapt_step(ops, theta, ws=ws, tie_rel=1e-4 if prec == "c64" else 1e-8)
-        states[prec] = ws[0].to(torch.complex128)
+        states[prec] = ws[0].to(torch.complex128, copy=True)   # the adjoint below overwrites ws
         e2, de = prob.energy_grad(np.append(ops, np.int32(sel)).astype(np.int32), np.append(theta, 0.0), ws=ws)
         vals[prec] = dict(e=e, g=g, sel=sel, de=de)
         if prec == "c128":
@@ -746,8 +746,6 @@ def main():
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the serving and complex128 sub-measurements")
-    ap.add_argument("--reference-sample-s", type=float, default=4.0,
-                    help="seconds of oracle work per reference-arm step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -243,28 +243,37 @@ int gocp_adapt_step(const gocp_problem* p, const int32_t* ops, const double* the
                     int mem, void* ws, double tie_rel, double* out_e, double* grads,
                     int32_t* selected, void* stream);
 
-/* The same H psi and energy as gocp_energy (identical kernel and results),
- * allocating nothing: its reduction scratch is a fixed device array inside
- * this library rather than memory allocated with the problem.  It is meant
- * for callers that cannot call cudaMalloc where they compute -- a host loop
- * with real-time or no-blocking guarantees, or a caller whose device memory
- * is owned by another allocator -- and that pass every input and output
- * (tables built earlier, psi, hpsi, out) themselves.  The paper has no
- * counterpart; this is a deployment variant of Eq. (1) and Eq. (3).
+/* H psi and the energy (E, <psi|psi>) like gocp_energy, computed without
+ * allocating anything: the reduction scratch is a fixed device array inside
+ * this library rather than memory of the problem or of the call.  The paper
+ * has no counterpart.  It serves callers that cannot call cudaMalloc at the
+ * point where they compute -- a host loop with real-time or no-blocking
+ * guarantees (cudaMalloc can block and synchronise the device), or a caller
+ * whose device memory is owned by another allocator -- and that pass every
+ * input and output themselves (tables built earlier, psi, hpsi, out).
+ * It runs the untiled H psi kernel: below the tile size (13 qubits for
+ * complex64, 12 for complex128) that is gocp_energy's own kernel and block
+ * decomposition, so the results are bit-identical; from the tile size on
+ * gocp_energy runs the tiled kernels and the two agree within rounding (the
+ * parity tolerances), not bit for bit.
  * Limits: at most 24 qubits (the array holds 8192 block partials, one per
- * 2048-amplitude tile; larger states return GOCP_EINVAL with the numbers).
- * The first call on a device resolves the array's address on that device
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call shares the one array: calls that overlap on the GPU
- * race, so order them on one stream.  out: 2 doubles (E, <psi|psi>), host or
- * device per `mem`. */
+ * 2048-amplitude tile; larger states return GOCP_EINVAL with the numbers);
+ * full-layout problems only.  The array (about 128 KiB) is held on every GPU
+ * that loads the library until the process exits.  The first call on a
+ * device resolves the array's address there (cudaGetSymbolAddress) and keeps
+ * it, so make that first call before any stream capture, and make no call
+ * after a cudaDeviceReset in the same process.  Every call shares the one
+ * array: calls that overlap on the GPU race, so order them on one stream.
+ * out: 2 doubles (E, <psi|psi>), host or device per `mem`. */
 int gocp_energy_static(const gocp_problem* p, const void* psi, void* hpsi, double* out, int mem,
                        void* stream);
 
 /* Device-side errors flagged since the last call, and clear them.  Bit 0: an
  * op index out of range in a GOCP_MEM_DEVICE ansatz.  Bit 1: a shared-memory
- * staging wait of the tiled H psi kernel gave up after 2 s (the H psi and
- * energy of that call are then undefined).  Synchronises `stream`. */
+ * staging wait of the staged H psi kernel gave up (after 2 s, or after
+ * GOCP_STAGE_WAIT_NS nanoseconds when that environment variable is set; the
+ * H psi and energy of that call are then undefined, later calls are not
+ * affected).  Synchronises `stream`. */
 int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
 
 /* ---------------------------------------------------------------- serving */

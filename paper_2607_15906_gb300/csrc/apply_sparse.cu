@@ -10,26 +10,27 @@
 //  * a listing pass writes the nonzero amplitudes (index, value) in index
 //    order, and the first entry of every tile;
 //  * a block (one per SM) owns an output tile t of 2^LB amplitudes and
-//    accumulates it in shared memory.  Its work units are (piece, chunk): 32
-//    consecutive nonzero amplitudes of the piece's source tile
-//    u = t ^ (x >> LB), one per lane, against the piece's groups, which the
-//    warp walks together from its own shared-memory copy of the piece's
-//    blob.  Units are numbered piece by piece from a per-tile scan of chunk
-//    counts and claimed a few at a time.  For a group with mask x the lane's
+//    accumulates it in shared memory.  Its work units are (piece, chunk):
+//    32 kSpAmps consecutive nonzero amplitudes of the piece's source tile
+//    u = t ^ (x >> LB), kSpAmps per lane, against the piece's groups, which
+//    the warp walks together.  Units are numbered piece by piece from a
+//    per-tile scan of chunk counts and claimed a few at a time.  For a group with mask x the lane's
 //    amplitude psi(k') goes to output k = k' ^ x with weight D(k): a LUT
 //    group reads its entry at code(k) (the code is linear in k over GF(2)),
 //    a term-list group sums its terms' signs at k (times the factor 0 or 2
-//    of a paired group).  A nonzero product is added to the accumulator with
-//    a shared-memory atomic; a zero weight adds nothing and is left out;
+//    of a paired group).  A nonzero product is added to the accumulator, in
+//    64-bit fixed point, with shared-memory integer atomics; a zero weight
+//    adds nothing and is left out;
 //  * after the last unit, lanes over the nonzero amplitudes of the own tile
 //    add the diagonal group and the identity and take the energy partials;
 //    then the whole tile (zeros included) is streamed to H psi.
 //
 // Every lane does the same work for every group, whatever the sparsity
 // pattern, and a group's descriptor and LUT are read at one address per
-// warp.  The order in which products reach an accumulator element is not
-// fixed, so the result may differ from run to run in the last bits of a sum
-// (and from the staged kernel's order); every term is the same.
+// warp (from global memory through L1).  The order in which products reach
+// an accumulator element is not fixed, but integer addition does not depend
+// on it: H psi, E and everything computed from them are reproducible bit
+// for bit from run to run.
 //
 // The kernel is launched with the staged one; each returns at once unless
 // the count of nonzero amplitudes selects it, so the choice needs no host
@@ -47,11 +48,25 @@ namespace {
 
 constexpr int kAmpBlock = 256;   // listing passes: one amplitude word (4 octets) per thread
 constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
+#ifndef GOCP_SP_AMPS
+#define GOCP_SP_AMPS 1
+#endif
+constexpr int kSpAmps = GOCP_SP_AMPS;   // nonzero source amplitudes per lane per work unit
 
 // One block per SM: 1024 threads for complex64 (64 registers), 512 for
 // complex128 (128 registers).
+#ifdef GOCP_SP_SMEMBLOB
+// descriptors copied into per-warp shared-memory buffers (16 warps)
+template <typename R>
+__host__ __device__ constexpr int sp_threads() { return 512; }
+template <typename T>
+__device__ __forceinline__ T ldb(const T* p) { return *p; }
+#else
 template <typename R>
 __host__ __device__ constexpr int sp_threads() { return sizeof(R) == 4 ? 1024 : 512; }
+template <typename T>
+__device__ __forceinline__ T ldb(const T* p) { return __ldg(p); }
+#endif
 
 template <typename R>
 __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t octet, C_t<R> (&v)[kAmpsH]) {
@@ -129,9 +144,11 @@ k_amp_count(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, con
 
 // counts[0..nb) -> exclusive prefix sums in place; *total = the sum (when
 // set; and, when ring is set, the chain-list ring's base(slot) = the sum,
-// count(slot) = count(first) = 0).  One block of 1024 threads.
+// count(slot) = count(first) = 0); *amax = 0 when set.  One block of 1024
+// threads.
 __global__ void __launch_bounds__(1024)
-k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int slot, int first) {
+k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int slot, int first,
+           unsigned long long* amax) {
   __shared__ uint32_t s[1024];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -153,6 +170,7 @@ k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int s
   }
   if (threadIdx.x == 0) {
     if (total) *total = carry;
+    if (amax) *amax = 0ull;
     if (ring) {
       ring[kRingBase(slot)] = carry;
       ring[kRingAdd(slot)] = 0u;
@@ -164,12 +182,14 @@ k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int s
 // Writes the index (and, when aval is set, the psi value) of every amplitude
 // nonzero in psi or psi2, in index order, at the offsets of k_amp_scan;
 // entries at or beyond cap are not stored.  With amask set, also writes
-// amask[w] = amplitude word w (one bit per amplitude, zeros included).
+// amask[w] = amplitude word w (one bit per amplitude, zeros included).  With
+// amax set, raises *amax to the largest |Re| or |Im| of the listed psi values
+// (the bits of a non-negative double, which order as unsigned integers).
 template <typename R>
 __global__ void __launch_bounds__(kAmpBlock)
 k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, const uint32_t* __restrict__ mask,
            uint32_t words, const uint32_t* __restrict__ offs, uint32_t* aidx, C_t<R>* aval, uint32_t* amask,
-           uint32_t cap) {
+           uint32_t cap, unsigned long long* amax) {
   __shared__ uint32_t red[kAmpBlock / 32];
   const uint32_t w = blockIdx.x * kAmpBlock + threadIdx.x;
   const uint32_t word = w < words ? amp_word<R>(psi, psi2, mask, w) : 0u;
@@ -186,13 +206,22 @@ k_amp_list(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, cons
   uint32_t before = 0;
   for (int q = 0; q < warp; ++q) before += red[q];
   uint32_t at = offs[blockIdx.x] + before + incl - c;
+  R big = R(0);
   for (uint32_t m = word; m; m &= m - 1u, ++at) {
     if (at >= cap) break;
     const uint32_t k = 32u * w + (uint32_t)(__ffs(m) - 1);
     aidx[at] = k;
-    if (aval) aval[at] = psi[k];
+    if (aval) {
+      const C_t<R> v = psi[k];
+      aval[at] = v;
+      big = fmax(big, fmax(fabs(v.x), fabs(v.y)));
+    }
   }
   if (amask && w < words) amask[w] = word;
+  if (amax) {
+    for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, o));
+    if (lane == 0 && big > R(0)) atomicMax(amax, (unsigned long long)__double_as_longlong((double)big));
+  }
 }
 
 // off[u] = first stored entry with index >> shift >= u, u = 0 .. ntiles
@@ -222,27 +251,81 @@ __device__ __forceinline__ uint32_t acc_at(uint32_t k) {
   return (2u * i) * kOct + (o ^ (i << 2));
 }
 
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void acc_add(R* acc, uint32_t k, R re, R im) {
-  const uint32_t at = acc_at<kOct>(k);
-  atomicAdd(acc + at, re);
-  atomicAdd(acc + at + kOct, im);
+// Fixed-point accumulation.  A product p is added as the integer
+// round(p 2^F) (the amplitudes are scaled by 2^F once, see below), so the
+// sum is exact integer arithmetic: the same in any order of the atomics,
+// and the result is bit-for-bit reproducible.  F is chosen per call so that
+// the sum of the magnitudes of all contributions to one output component --
+// at most hbound x 2 max(|Re psi|, |Im psi|) -- stays below 2^62: no partial
+// sum can overflow.  For complex64, F also keeps every off-diagonal product
+// below 2^30, so that it converts with a 32-bit instruction; its rounding,
+// at most 2^-(F+1), is then about 1e-9 of the largest possible product, and
+// an entry of H psi collects it from at most a few thousand products.  For
+// complex128 the rounding is at most 2^-(F+1) with F near 62 - log2 of the
+// bound, far below the FP64 rounding of the products.
+__device__ __forceinline__ void fx_add(unsigned long long* p, long long v) {
+#ifdef GOCP_SP_ATOM32
+  // two 32-bit atomics, the carry out of the low word taken from the old
+  // value it returns (exact modulo 2^64 in any order)
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  const uint32_t lo = (uint32_t)(unsigned long long)v, hi = (uint32_t)((unsigned long long)v >> 32);
+  const uint32_t old = atomicAdd(w, lo);
+  atomicAdd(w + 1, hi + (uint32_t)(old + lo < old));
+#else
+  atomicAdd(p, (unsigned long long)v);
+#endif
 }
 
-// One LUT group against the lane's nonzero amplitude psi(ks) = v.  The
-// entry's magnitude depends on phi(k) alone (lut16[phi | 8] = -lut16[phi]),
-// so the sign parity is taken only for a nonzero entry.
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void sp_lut(const HLut<R>& L, uint32_t ks, C_t<R> v, bool valid, R* acc) {
-  const uint4 h0 = *reinterpret_cast<const uint4*>(&L.x);     // x, z0, v0, v1
-  const uint32_t v2 = L.v2;
-  const uint32_t k = ks ^ h0.x;
-  const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
-                       ((uint32_t)(__popc(k & v2) & 1) << 2);
-  const R d0 = L.lut16[phi];
-  if (valid && d0 != R(0)) {
-    const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
-    acc_add<R, kOct>(acc, k, d * v.x, d * v.y);
+// A scaled product as an integer.  complex64: every off-diagonal product is
+// below 2^30 by the choice of F, so a 32-bit conversion suffices (the 64-bit
+// conversions run on the FP64 pipe, narrow on this part); complex128: FP64
+// products, a 64-bit conversion.
+template <typename R>
+__device__ __forceinline__ long long fx_prod(R v) {
+  return sizeof(R) == 4 ? (long long)__float2int_rn((float)v) : __double2ll_rn((double)v);
+}
+
+// A scaled value up to 2^62 (the diagonal's products, once per amplitude).
+template <typename R>
+__device__ __forceinline__ long long fx_wide(R v) {
+  return sizeof(R) == 4 ? __float2ll_rn((float)v) : __double2ll_rn((double)v);
+}
+
+// An accumulator value back in R (zeros, most of a sector state's tile,
+// skip the conversion).
+template <typename R>
+__device__ __forceinline__ R fx_val(unsigned long long a) {
+  if (a == 0ull) return R(0);
+  return sizeof(R) == 4 ? (R)__ll2float_rn((long long)a) : (R)__ll2double_rn((long long)a);
+}
+
+template <uint32_t kOct>
+__device__ __forceinline__ void acc_add(unsigned long long* acc, uint32_t k, long long re, long long im) {
+  const uint32_t at = acc_at<kOct>(k);
+  fx_add(acc + at, re);
+  fx_add(acc + at + kOct, im);
+}
+
+// One LUT group (descriptor in global memory, read through L1 at one
+// address per warp) against the lane's nonzero amplitudes psi(ks[s]), whose
+// values vs[s] are pre-scaled by 2^F.  The entry's magnitude depends on
+// phi(k) alone (lut16[phi | 8] = -lut16[phi]), so the sign parity is taken
+// only for a nonzero entry.
+template <typename R, uint32_t kOct, int A>
+__device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint32_t (&ks)[A],
+                                       const C_t<R> (&vs)[A], const bool (&valid)[A], unsigned long long* acc) {
+  const uint4 h0 = ldb(reinterpret_cast<const uint4*>(&L->x));     // x, z0, v0, v1
+  const uint32_t v2 = ldb(&L->v2);
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    const uint32_t k = ks[s] ^ h0.x;
+    const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
+                         ((uint32_t)(__popc(k & v2) & 1) << 2);
+    const R d0 = ldb(L->lut16 + phi);
+    if (valid[s] && d0 != R(0)) {
+      const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
+      acc_add<kOct>(acc, k, fx_prod<R>(d * vs[s].x), fx_prod<R>(d * vs[s].y));
+    }
   }
 }
 
@@ -250,49 +333,104 @@ __device__ __forceinline__ void sp_lut(const HLut<R>& L, uint32_t ks, C_t<R> v, 
 // [tb, tm), imaginary [tm, te); a paired group keeps one term of each pair
 // and D = (1 + sigma (-1)^popc(k & delta)) E(k), the factor 0 or 2.  Called
 // by every lane of the warp (the group is warp-uniform).
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void sp_terms(const TiledGroup& G, const uint32_t* __restrict__ zs,
-                                         const R* __restrict__ ws, uint32_t ks, C_t<R> v, bool valid, R* acc) {
-  const uint32_t k = ks ^ G.x;
-  R f = R(1);
-  if (G.delta) {
-    const uint32_t p = __popc(k & G.delta) & 1u;
-    f = (G.neg ? p : p ^ 1u) ? R(2) : R(0);
+template <typename R, uint32_t kOct, int A>
+__device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const uint32_t* __restrict__ zs,
+                                         const R* __restrict__ ws, const uint32_t (&ks)[A],
+                                         const C_t<R> (&vs)[A], const bool (&valid)[A],
+                                         unsigned long long* acc) {
+  const uint4 g0 = ldb(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
+  const uint2 g1 = ldb(reinterpret_cast<const uint2*>(&G->delta)); // delta, neg
+  uint32_t k[A];
+  R f[A];
+  bool on = false;
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    k[s] = ks[s] ^ g0.x;
+    f[s] = R(1);
+    if (g1.x) {
+      const uint32_t p = __popc(k[s] & g1.x) & 1u;
+      f[s] = (g1.y ? p : p ^ 1u) ? R(2) : R(0);
+    }
+    on |= valid[s] && f[s] != R(0);
   }
-  const bool on = valid && f != R(0);
   if (!__any_sync(0xffffffffu, on)) return;
-  R dr = R(0), di = R(0);
-  for (uint32_t t = G.tb; t < G.tm; ++t) dr += (__popc(k & zs[t]) & 1) ? -ws[t] : ws[t];
-  for (uint32_t t = G.tm; t < G.te; ++t) di += (__popc(k & zs[t]) & 1) ? -ws[t] : ws[t];
-  dr *= f;
-  di *= f;
-  if (on && (dr != R(0) || di != R(0))) acc_add<R, kOct>(acc, k, dr * v.x - di * v.y, dr * v.y + di * v.x);
+  R dr[A], di[A];
+#pragma unroll
+  for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
+  for (uint32_t t = g0.y; t < g0.z; ++t) {
+    const uint32_t z = ldb(zs + t);
+    const R w = ldb(ws + t);
+#pragma unroll
+    for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
+  }
+  for (uint32_t t = g0.z; t < g0.w; ++t) {
+    const uint32_t z = ldb(zs + t);
+    const R w = ldb(ws + t);
+#pragma unroll
+    for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
+  }
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    const R a = dr[s] * f[s], b = di[s] * f[s];
+    if (valid[s] && f[s] != R(0) && (a != R(0) || b != R(0)))
+      acc_add<kOct>(acc, k[s], fx_prod<R>(a * vs[s].x - b * vs[s].y), fx_prod<R>(a * vs[s].y + b * vs[s].x));
+  }
+}
+
+// 2^e as R, for |e| beyond one float exponent split in two factors.
+template <typename R>
+__device__ __forceinline__ void pow2_split(int e, R* a, R* b) {
+  const int lim = sizeof(R) == 4 ? 120 : 1000;
+  const int e1 = e > lim ? lim : (e < -lim ? -lim : e);
+  int e2 = e - e1;
+  e2 = e2 > lim ? lim : (e2 < -lim ? -lim : e2);
+  *a = sizeof(R) == 4 ? (R)ldexpf(1.0f, e1) : (R)ldexp(1.0, e1);
+  *b = sizeof(R) == 4 ? (R)ldexpf(1.0f, e2) : (R)ldexp(1.0, e2);
 }
 
 template <typename R>
 __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const SparseArgs<R> a) {
   constexpr int LB = TiledBits<R>::LB;
   constexpr int NT = sp_threads<R>();
+  constexpr int A = kSpAmps;                  // amplitudes per lane per work unit
+  constexpr uint32_t kChunk = 32u * A;        // amplitudes per work unit
   constexpr uint32_t kOct = 1u << (LB - 3);   // octets per tile
   if (*a.alen > a.max_amps) return;           // the staged kernel takes this state
-  // dynamic shared memory: the tile's accumulator (16 components x kOct
-  // octets), then one piece blob per warp
+  // dynamic shared memory: the tile's fixed-point accumulator, 16 components
+  // x kOct octets of 8 bytes
   extern __shared__ __align__(16) uint8_t sp_raw[];
-  R* acc = reinterpret_cast<R*>(sp_raw);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(sp_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t* wblob = sp_raw + kOct * 16u * sizeof(R) + (size_t)warp * kTiledBlobBytes;
   __shared__ uint32_t s_tile, s_unext;
   __shared__ uint32_t s_pre[kSpMaxPieces + 1];   // first unit of each piece; s_pre[P] = units
   __shared__ uint32_t s_wsum[32];
-  __shared__ double tot[2];
+  __shared__ double s_red[2][NT / 32];
+  __shared__ bool s_last;
   const uint32_t ntiles = 1u << (a.n - LB);
   const uint32_t P = (uint32_t)a.n_pieces;
-  for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) acc[j] = R(0);
+  for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) acc[j] = 0ull;
+  // fixed-point scale 2^F: every sum below 2^62 (hbound x 2 max|component|
+  // x 2^F <= 2^62) and, for complex64, every off-diagonal product below 2^30
+  // (dmax x 2 max|component| x 2^F <= 2^30)
+  int F = 0;
+  {
+    const double m = __longlong_as_double((long long)*a.amax);
+    const double bnd = 2.0 * a.hbound * m, bnd1 = 2.0 * a.dmax * m;
+    if (bnd > 0.0) {
+      int e;
+      frexp(bnd, &e);   // bnd < 2^e
+      F = 62 - e;
+      if (sizeof(R) == 4 && bnd1 > 0.0) {
+        frexp(bnd1, &e);
+        F = min(F, 30 - e);
+      }
+    }
+  }
+  R up_a, up_b, dn_a, dn_b;          // 2^F and 2^-F, each as two factors
+  pow2_split<R>(F, &up_a, &up_b);
+  pow2_split<R>(-F, &dn_a, &dn_b);
+  const double dn = ldexp(1.0, -F);
   const R idr = (R)a.identity;
-  // this thread's |psi|^2 and <psi|H - identity|psi> partials (in shared
-  // memory: touched once per tile)
-  __shared__ double2 s_v[NT];
-  s_v[threadIdx.x] = make_double2(0.0, 0.0);
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(a.tile_counter, 1u);
@@ -301,16 +439,16 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     __syncthreads();
     const uint32_t t = s_tile;
     if (t >= ntiles) break;
-    // Work units are (piece p, chunk c): the nonzero amplitudes 32c .. 32c + 31
-    // of p's source tile u = t ^ (x >> LB) against p's groups, numbered piece
-    // by piece (s_pre: a block scan of the chunk counts).
+    // Work units are (piece p, chunk c): the nonzero amplitudes kChunk c ..
+    // kChunk (c + 1) - 1 of p's source tile u = t ^ (x >> LB) against p's
+    // groups, numbered piece by piece (s_pre: a block scan of the chunk counts).
     {
       const uint32_t per = (P + NT - 1) / NT, p0 = threadIdx.x * per, p1 = min(P, p0 + per);
       uint32_t mine = 0;
       for (uint32_t p = p0; p < p1; ++p) {
         const TiledPiece pc = a.piece[p];
         const uint32_t u = t ^ pc.xhi;
-        const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + 31u) >> 5 : 0u;
+        const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + kChunk - 1u) / kChunk : 0u;
         s_pre[p] = nch;
         mine += nch;
       }
@@ -322,12 +460,12 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       if (lane == 31) s_wsum[warp] = incl;
       __syncthreads();
       if (warp == 0) {
-        uint32_t w = lane < NT / 32 ? s_wsum[lane] : 0u, wi = w;
+        uint32_t ws = lane < NT / 32 ? s_wsum[lane] : 0u, wi = ws;
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t q = __shfl_up_sync(0xffffffffu, wi, o);
           if (lane >= o) wi += q;
         }
-        if (lane < NT / 32) s_wsum[lane] = wi - w;   // exclusive
+        if (lane < NT / 32) s_wsum[lane] = wi - ws;   // exclusive
         if (lane == NT / 32 - 1) s_pre[P] = wi;
       }
       __syncthreads();
@@ -340,10 +478,13 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     }
     __syncthreads();
     const uint32_t n_units = s_pre[P];
+#ifdef GOCP_SP_SMEMBLOB
+    uint8_t* wblob = sp_raw + kOct * 16u * sizeof(unsigned long long) + (size_t)warp * kTiledBlobBytes;
     uint32_t cur = 0xFFFFFFFFu;   // piece whose blob this warp holds
+#endif
     for (;;) {
       // kUnitBatch consecutive units per claim: mostly chunks of one piece,
-      // whose blob is then copied once
+      // whose descriptors then stay in L1
       uint32_t j0 = 0;
       if (lane == 0) j0 = atomicAdd(&s_unext, kUnitBatch);
       j0 = __shfl_sync(0xffffffffu, j0, 0);
@@ -363,35 +504,45 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         p = lo;
       }
       for (uint32_t j = j0; j < j1; ++j) {
-      while (p + 1 < P && s_pre[p + 1] <= j) ++p;
-      const uint32_t c = j - s_pre[p];
-      const TiledPiece pc = a.piece[p];
-      if (p != cur) {
-        // the piece's blob into this warp's buffer, 16 bytes per lane
-        __syncwarp();
-        const uint4* src = reinterpret_cast<const uint4*>(a.blob + pc.off);
-        uint4* dst = reinterpret_cast<uint4*>(wblob);
-        for (uint32_t q = (uint32_t)lane; q < pc.bytes / 16u; q += 32u) dst[q] = __ldg(src + q);
-        __syncwarp();
-        cur = p;
-      }
-      const uint32_t u = t ^ pc.xhi;
-      const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
-      const TiledHead* hd = reinterpret_cast<const TiledHead*>(wblob);
-      const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(wblob + sizeof(TiledHead));
-      const TiledGroup* gs =
-          reinterpret_cast<const TiledGroup*>(wblob + sizeof(TiledHead) + hd->n_lut * sizeof(HLut<R>));
-      const uint32_t* zs = reinterpret_cast<const uint32_t*>(wblob + hd->z_off);
-      const R* ws = reinterpret_cast<const R*>(wblob + hd->w_off);
-      const uint32_t li = a0 + 32u * c + (uint32_t)lane;
-      const bool valid = li < a1;
-      const uint32_t ks = a.aidx[valid ? li : a0];
-      const C_t<R> v = a.aval[valid ? li : a0];
-      const int nl = (int)hd->n_lut;
-      for (int g = 0; g < nl; ++g) sp_lut<R, kOct>(ls[g], ks, v, valid, acc);
-      // the term-list groups fill the blob from the LUT groups to z_off
-      const int nt = (int)((hd->z_off - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
-      for (int g = 0; g < nt; ++g) sp_terms<R, kOct>(gs[g], zs, ws, ks, v, valid, acc);
+        while (p + 1 < P && s_pre[p + 1] <= j) ++p;
+        const uint32_t c = j - s_pre[p];
+        const TiledPiece pc = a.piece[p];
+        const uint32_t u = t ^ pc.xhi;
+        const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
+#ifdef GOCP_SP_SMEMBLOB
+        if (p != cur) {
+          __syncwarp();
+          const uint4* src = reinterpret_cast<const uint4*>(a.blob + pc.off);
+          uint4* dst = reinterpret_cast<uint4*>(wblob);
+          for (uint32_t q = (uint32_t)lane; q < pc.bytes / 16u; q += 32u) dst[q] = __ldg(src + q);
+          __syncwarp();
+          cur = p;
+        }
+        const uint8_t* blob = wblob;
+#else
+        const uint8_t* blob = a.blob + pc.off;
+#endif
+        const uint4 hd = ldb(reinterpret_cast<const uint4*>(blob));   // n_runs, n_lut, z_off, w_off
+        const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(blob + sizeof(TiledHead));
+        const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(blob + sizeof(TiledHead) + hd.y * sizeof(HLut<R>));
+        const uint32_t* zs = reinterpret_cast<const uint32_t*>(blob + hd.z);
+        const R* ws = reinterpret_cast<const R*>(blob + hd.w);
+        uint32_t ks[A];
+        C_t<R> vs[A];
+        bool valid[A];
+#pragma unroll
+        for (int s = 0; s < A; ++s) {
+          const uint32_t li = a0 + kChunk * c + 32u * s + (uint32_t)lane;
+          valid[s] = li < a1;
+          ks[s] = a.aidx[valid[s] ? li : a0];
+          const C_t<R> v = a.aval[valid[s] ? li : a0];
+          vs[s] = cmake<R>(v.x * up_a * up_b, v.y * up_a * up_b);
+        }
+        const int nl = (int)hd.y;
+        for (int g = 0; g < nl; ++g) sp_lut<R, kOct, A>(ls + g, ks, vs, valid, acc);
+        // the term-list groups fill the blob from the LUT groups to z_off
+        const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
+        for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, ks, vs, valid, acc);
       }
     }
     __syncthreads();
@@ -400,8 +551,8 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     // and the energy partials (zero amplitudes add to neither); each k is
     // one lane's, so its accumulator entry is updated without atomics
     {
+      double2 w = make_double2(0.0, 0.0);   // this thread's |psi|^2 and <psi|H - identity|psi> partials
       const uint32_t e0 = a.toff[t], e1 = a.toff[t + 1];
-      double2 w = s_v[threadIdx.x];
       for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
         const uint32_t k = a.aidx[e];
         const C_t<R> q = a.aval[e];
@@ -417,28 +568,44 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
           }
         }
         for (int m = a.nd_mid; m < a.nd; ++m) di += (__popc(k & a.dz[m]) & 1) ? -a.dw[m] : a.dw[m];
-        R* e2 = acc + acc_at<kOct>(k);
-        const C_t<R> off = cmake<R>(e2[0], e2[kOct]);
+        unsigned long long* e2 = acc + acc_at<kOct>(k);
+        const double ox = (double)(long long)e2[0] * dn, oy = (double)(long long)e2[kOct] * dn;
         const double pp = (double)q.x * q.x + (double)q.y * q.y;
         w.x += pp;
-        w.y += (double)q.x * off.x + (double)q.y * off.y + ((double)dr - (double)dc) * pp;
+        w.y += (double)q.x * ox + (double)q.y * oy + ((double)dr - (double)dc) * pp;
         const R d0 = dr - dc + idr;
-        e2[0] = off.x + d0 * q.x - di * q.y;
-        e2[kOct] = off.y + d0 * q.y + di * q.x;
+        const C_t<R> qs = cmake<R>(q.x * up_a * up_b, q.y * up_a * up_b);
+        e2[0] = (unsigned long long)((long long)e2[0] + fx_wide<R>(d0 * qs.x - di * qs.y));
+        e2[kOct] = (unsigned long long)((long long)e2[kOct] + fx_wide<R>(d0 * qs.y + di * qs.x));
       }
-      s_v[threadIdx.x] = w;
+      // the tile's energy partials, summed in a fixed order (warps that
+      // hold no amplitude of the tile skip the FP64 shuffles)
+      if (a.partials) {
+        const bool any = __any_sync(0xffffffffu, w.x != 0.0 || w.y != 0.0);
+        const double sx = any ? warp_sum(w.x) : 0.0, sy = any ? warp_sum(w.y) : 0.0;
+        if (lane == 0) {
+          s_red[0][warp] = sx;
+          s_red[1][warp] = sy;
+        }
+      }
     }
     __syncthreads();
+    if (a.partials && threadIdx.x < 2) {
+      double sum = 0.0;
+      for (int q = 0; q < NT / 32; ++q) sum += s_red[threadIdx.x][q];
+      a.partials[2u * t + threadIdx.x] = sum;
+    }
     // then the whole tile out (zeros included) and the accumulator cleared
     for (uint32_t o = threadIdx.x; o < kOct; o += NT) {
       const uint32_t k0 = ((t << (LB - 3)) | o) << 3;
       C_t<R> res[kAmpsH];
 #pragma unroll
       for (int i = 0; i < kAmpsH; ++i) {
-        R* e = acc + acc_at<kOct>(k0 | (uint32_t)i);
-        res[i] = cmake<R>(e[0], e[kOct]);
-        e[0] = R(0);
-        e[kOct] = R(0);
+        unsigned long long* e = acc + acc_at<kOct>(k0 | (uint32_t)i);
+        const R re = fx_val<R>(e[0]), im = fx_val<R>(e[kOct]);
+        res[i] = cmake<R>(re * dn_a * dn_b, im * dn_a * dn_b);
+        e[0] = 0ull;
+        e[kOct] = 0ull;
       }
       C_t<R>* dst = a.out + k0;
       if (sizeof(R) == 4) {
@@ -455,15 +622,48 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     }
     __syncthreads();
   }
-  const double v[2] = {s_v[threadIdx.x].x, s_v[threadIdx.x].y};
-  if (a.partials && block_grid_sum<2, NT>(v, a.partials, a.counter, gridDim.x, blockIdx.x, a.scal + 1, tot)) {
-    if (threadIdx.x == 0) a.scal[0] = a.identity + tot[1] / tot[0];
+  if (!a.partials) return;
+  // the last block to finish adds the per-tile partials in tile order, so E
+  // does not depend on which block took which tile
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc0 = 0.0, acc1 = 0.0;
+  for (uint32_t u = threadIdx.x; u < ntiles; u += NT) {
+    acc0 += ((volatile double*)a.partials)[2u * u];
+    acc1 += ((volatile double*)a.partials)[2u * u + 1u];
+  }
+  acc0 = warp_sum(acc0);
+  acc1 = warp_sum(acc1);
+  if (lane == 0) {
+    s_red[0][warp] = acc0;
+    s_red[1][warp] = acc1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double n2 = 0.0, eh = 0.0;
+    for (int q = 0; q < NT / 32; ++q) {
+      n2 += s_red[0][q];
+      eh += s_red[1][q];
+    }
+    a.scal[1] = n2;
+    a.scal[2] = eh;
+    a.scal[0] = a.identity + eh / n2;
+    *a.counter = 0u;
   }
 }
 
 template <typename R>
 constexpr uint32_t sparse_smem() {
-  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(R) + (sp_threads<R>() / 32) * kTiledBlobBytes;
+#ifdef GOCP_SP_SMEMBLOB
+  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(unsigned long long) +
+         (sp_threads<R>() / 32) * kTiledBlobBytes;
+#else
+  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(unsigned long long);
+#endif
 }
 
 }  // namespace
@@ -471,8 +671,9 @@ constexpr uint32_t sparse_smem() {
 template <typename R>
 int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStream_t st) {
   constexpr int LB = TiledBits<R>::LB;
-  if (a.n < LB || !lv.toff || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts || a.max_amps > lv.acap)
+  if (a.n < LB || !lv.toff || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts || !lv.amax || a.max_amps > lv.acap)
     return fail(GOCP_EINVAL, "scatter H psi needs the amplitude list");
+  a.amax = lv.amax;
   a.aidx = lv.aidx;
   a.aval = reinterpret_cast<const C_t<R>*>(lv.aval);
   a.alen = lv.alen;
@@ -510,15 +711,15 @@ int amp_list(int precision, const void* psi, const uint32_t* mask, int n, const 
   if (precision == GOCP_C64) {
     const float2* p = reinterpret_cast<const float2*>(psi);
     k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0, lv.amax);
     k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
-                                                reinterpret_cast<float2*>(lv.aval), nullptr, lv.acap);
+                                                reinterpret_cast<float2*>(lv.aval), nullptr, lv.acap, lv.amax);
   } else {
     const double2* p = reinterpret_cast<const double2*>(psi);
     k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts);
-    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0);
+    k_amp_scan<<<1, 1024, 0, st>>>(lv.acounts, nb, lv.alen, nullptr, 0, 0, lv.amax);
     k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, nullptr, mask, words, lv.acounts, lv.aidx,
-                                                 reinterpret_cast<double2*>(lv.aval), nullptr, lv.acap);
+                                                 reinterpret_cast<double2*>(lv.aval), nullptr, lv.acap, lv.amax);
   }
   count_launches(3);
   return cuda_status(cudaGetLastError(), "k_amp_list");
@@ -534,14 +735,16 @@ int chain_list(int precision, const void* psi, const void* lam, const uint32_t* 
     const float2* p = reinterpret_cast<const float2*>(psi);
     const float2* q = reinterpret_cast<const float2*>(lam);
     k_amp_count<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
-    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first);
-    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first, nullptr);
+    k_amp_list<float><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap,
+                                                nullptr);
   } else {
     const double2* p = reinterpret_cast<const double2*>(psi);
     const double2* q = reinterpret_cast<const double2*>(lam);
     k_amp_count<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts);
-    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first);
-    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap);
+    k_amp_scan<<<1, 1024, 0, st>>>(counts, nb, nullptr, cl.cnt, slot, first, nullptr);
+    k_amp_list<double><<<nb, kAmpBlock, 0, st>>>(p, q, mask, words, counts, cl.list, nullptr, cl.amask, cl.cap,
+                                                 nullptr);
   }
   count_launches(3);
   return cuda_status(cudaGetLastError(), "chain list");

@@ -20,10 +20,11 @@
 // exactly zero).  States confined to a particle-number sector, as the ADAPT
 // states are, leave most octets zero; a dense state skips nothing.
 //
-// Every wait on an mbarrier gives up after kWaitNs of %globaltimer: the block
-// then records bit 1 in the error flags, waits (bounded again) for its own
-// copies in flight, and leaves the tile loop; results are then undefined and
-// gocp_device_errors reports the flag.
+// Every staging wait on an mbarrier gives up after a limit of %globaltimer
+// (2 s, or GOCP_STAGE_WAIT_NS nanoseconds from the environment): the block
+// then records bit 1 in the error flags, waits -- always with the full 2 s
+// limit -- for its own copies in flight, and leaves the tile loop; results
+// are then undefined and gocp_device_errors reports the flag.
 #include <cuda.h>
 
 #include <cmath>
@@ -72,14 +73,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete; false after kWaitNs.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the phase with the given parity to complete; false after
+// limit_ns of %globaltimer.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 32; ++i)
       if (mbar_try(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -322,6 +324,7 @@ struct TiledArgs {
   // kernel of apply_sparse.cu takes the state)
   const uint32_t* gate;
   uint32_t gate_max;
+  uint64_t wait_ns;     // limit of a staging wait (stage_wait_ns)
 };
 
 template <typename R>
@@ -467,14 +470,14 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
       // out as soon as their stage is released
       bool ok = true;
       while (ok && !s_done && s_next <= it) {
-        ok = mbar_wait(empty_s + 8u * (s_next % S), (s_next / S - 1u) & 1u);
+        ok = mbar_wait(empty_s + 8u * (s_next % S), (s_next / S - 1u) & 1u, a.wait_ns);
         if (ok) issue_next();
       }
       while (ok && !s_done && mbar_try(empty_s + 8u * (s_next % S), (s_next / S - 1u) & 1u)) issue_next();
       if (!ok) s_abort = 1;
     }
     __syncwarp();
-    if (!__all_sync(0xffffffffu, mbar_wait(full_s + 8u * st, ph))) {
+    if (!__all_sync(0xffffffffu, mbar_wait(full_s + 8u * st, ph, a.wait_ns))) {
       s_abort = 1;
       break;
     }
@@ -572,7 +575,8 @@ __global__ void __launch_bounds__(tiled_threads<R>(), sizeof(R) == 4 ? GOCP_TILE
   if (threadIdx.x == 0 && s_abort) {
     atomicOr(a.err, kErrStageTimeout);
     // let the copies this block started land before its shared memory goes
-    for (uint32_t j = it; j < s_next; ++j) mbar_wait(full_s + 8u * (j % S), (j / S) & 1u);
+    // (always with the full limit, whatever a.wait_ns is)
+    for (uint32_t j = it; j < s_next; ++j) mbar_wait(full_s + 8u * (j % S), (j / S) & 1u, kWaitNs);
   }
   // (a normal exit consumed every issued item: nothing is in flight)
   const double v[2] = {s_v[threadIdx.x].x, s_v[threadIdx.x].y};
@@ -621,6 +625,16 @@ int smem_optin(int device) {
 // Fraction of nonzero amplitudes up to which the scatter kernel takes a
 // state (GOCP_SPARSE_FRAC; 0 keeps every state on the staged kernel; the
 // amplitude list holds a quarter of the state at most).
+// Limit of a staging wait in the staged kernel: GOCP_STAGE_WAIT_NS, default
+// kWaitNs.  A short limit makes the kernel give up (and flag it) instead of
+// waiting for a copy, which lets a test drive that path.
+uint64_t stage_wait_ns() {
+  const char* e = std::getenv("GOCP_STAGE_WAIT_NS");
+  if (!e || !*e) return kWaitNs;
+  const long long v = std::atoll(e);
+  return v < 0 ? kWaitNs : (uint64_t)v;
+}
+
 double sparse_frac() {
   const char* e = std::getenv("GOCP_SPARSE_FRAC");
   if (!e || !*e) return 0.125;
@@ -675,6 +689,8 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     s.out = reinterpret_cast<C_t<R>*>(hpsi);
     s.mask = t.octmask;
     s.max_amps = max_amps;
+    s.hbound = t.hbound;
+    s.dmax = t.dmax;
     s.dz = t.dz;
     s.dw = reinterpret_cast<const R*>(t.dw);
     s.nd = t.nd;
@@ -706,6 +722,7 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
   a.counter = counter;
   a.scal = scal;
   a.err = err;
+  a.wait_ns = stage_wait_ns();
   const uint64_t ntiles = 1ull << (t.n - LB);
   const int per_sm = sizeof(R) == 4 ? GOCP_TILED_MINB_C64 : 1;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1) * per_sm);

@@ -88,14 +88,16 @@ int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grad
 int dev_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE,
                 cudaStream_t st);
 int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out, cudaStream_t st);
+int dev_energy_static(Problem& p, const void* psi, void* hpsi, double* out, int mem, cudaStream_t st);
 
 namespace {
 
 struct DeviceGuard {
   int prev = -1;
+  cudaError_t err = cudaSuccess;   // of the switch to `dev`
   explicit DeviceGuard(int dev) {
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    if (dev >= 0 && dev != prev) err = cudaSetDevice(dev);
   }
   ~DeviceGuard() {
     if (prev >= 0) cudaSetDevice(prev);
@@ -484,6 +486,18 @@ int gocp_energy(const gocp_problem* h, const void* psi, void* hpsi, double* out,
   return deliver(scalars_ptr(p), out, 2, mem, st);
 }
 
+int gocp_energy_static(const gocp_problem* h, const void* psi, void* hpsi, double* out, int mem,
+                       void* stream) {
+  int rc = check_problem(h);
+  if (rc || (rc = check_mem(mem))) return rc;
+  Problem& p = const_cast<Problem&>(h->p);
+  if (p.sector) return fail(GOCP_EINVAL, "gocp_energy_static takes full-layout problems only");
+  if (!psi || !hpsi || psi == hpsi || !out) return fail(GOCP_EINVAL, "psi/hpsi/out NULL or aliased");
+  DeviceGuard g(p.device);
+  if (g.err != cudaSuccess) return cuda_status(g.err, "cudaSetDevice");
+  return dev_energy_static(p, psi, hpsi, out, mem, (cudaStream_t)stream);
+}
+
 int gocp_pool_gradients(const gocp_problem* h, const void* psi, const void* hpsi, double* grads,
                         int mem, void* stream) {
   int rc = check_problem(h);
@@ -625,6 +639,6 @@ int gocp_profile_read(int kind, int64_t* launches, double* total_ms) {
 const char* gocp_last_error(void) { return t_last_error.c_str(); }
 int64_t gocp_launch_count(void) { return g_launches.load(); }
 // The k_apply_h revision names the kernel that profiles/traffic.json was measured on.
-const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h_tiled=tiled-tma-r12; k_apply_h_sparse=scatter-amp-r6; chain=amp-list-ring-2; sector=pair-lists-csr-1; chains=graphs-1; grads=nonzero-amps-1)"; }
+const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h_tiled=tiled-tma-r12; k_apply_h_sparse=scatter-fixed-r8; chain=amp-list-ring-2; onchip=smem-chain-1; sector=pair-lists-csr-1; chains=graphs-1; grads=nonzero-amps-1)"; }
 
 }  // extern "C"

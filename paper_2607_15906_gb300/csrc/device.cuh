@@ -273,6 +273,13 @@ struct DevTables {
   const void* sp_w = nullptr;
   // diagonal group (x = 0) without the identity: [0, nd_mid) real, [nd_mid, nd) imaginary
   int nd = 0, nd_mid = 0;
+  // bound on the magnitude of H's couplings at any basis state: the sum over
+  // the off-diagonal groups of max_k |D_g(k)|, plus the diagonal group's and
+  // the identity's sum of |w| (the scatter kernel's fixed-point scale)
+  double hbound = 0.0;
+  // the largest coupling of one off-diagonal group, max_g max_k |D_g(k)|
+  // (term-list groups: the sum of their |w|)
+  double dmax = 0.0;
   const uint32_t* dz = nullptr;
   const void* dw = nullptr;
   int M = 0;
@@ -476,6 +483,7 @@ struct LiveOctets {
   uint32_t acap = 0;
   uint32_t* alen = nullptr;     // one entry
   uint32_t* acounts = nullptr;  // one per block of 256 amplitude words (32 amplitudes each), + 1
+  unsigned long long* amax = nullptr;   // bits of max(|Re|, |Im|) over the listed amplitudes, as a double
 };
 
 // Lists the live octets of `mask` (2^(n-3) bits, n >= 8) into lv.list and
@@ -508,6 +516,9 @@ struct SparseArgs {
   const C_t<R>* aval;
   const uint32_t* alen;
   const uint32_t* toff;
+  const unsigned long long* amax;   // max(|Re|, |Im|) of the listed amplitudes (double bits)
+  double hbound;                // DevTables::hbound
+  double dmax;                  // DevTables::dmax
   uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
   const uint32_t* dz;
   const R* dw;

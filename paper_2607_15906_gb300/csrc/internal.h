@@ -182,7 +182,13 @@ struct StageItem {
 };
 constexpr int kMaxBatchItems = 256;
 constexpr int kMaxItemBlocks = 1216;
-enum StageKind { STAGE_SETUP = 0, STAGE_FORWARD = 1, STAGE_ENERGY = 2, STAGE_BACKWARD = 3 };
+enum StageKind { STAGE_SETUP = 0, STAGE_FORWARD = 1, STAGE_ENERGY = 2, STAGE_BACKWARD = 3,
+                 STAGE_FORWARD_ALL = 4,    // every forward step of the item, one block (on-chip chain)
+                 STAGE_BACKWARD_ALL = 5 }; // every backward step of the item, one block
+// Whether an item of this problem can take the on-chip stage `kind`
+// (STAGE_FORWARD_ALL: its state fits one block's shared memory;
+// STAGE_BACKWARD_ALL: its two states do).
+bool stage_onchip(const Problem& p, int kind);
 // Launches one batched stage over items[0..n) of one precision.  host_desc /
 // dev_desc: a pinned host and a device buffer of >= batch_desc_bytes(n)
 // bytes used to ship the item descriptors; they must stay untouched until

@@ -908,6 +908,141 @@ k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
                   dpart);
 }
 
+// ------------------------------------------------------------ on-chip chains
+//
+// A state that fits one block's shared memory (kSmemStateBytes: 2^14
+// complex64 or 2^13 complex128 amplitudes for the forward chain; the
+// backward sweep holds psi and lambda, so 2^13 / 2^12) runs its whole chain
+// in one launch: the block loads the state, applies every step of the
+// ansatz in order with a barrier between steps, and stores it back.  Each
+// step visits the operator's enumerated touched pairs with the same per-pair
+// arithmetic as the one-launch-per-step kernels (taylor_pair, adjoint_pair),
+// so the forward chain gives the same state bit for bit; the backward sweep
+// sums each dE_j over the block in a fixed order.  A step costs one pass of
+// the block over shared memory instead of a grid launch.
+constexpr int kSmemThreads = 1024;
+constexpr uint32_t kSmemStateBytes = 128u << 10;
+
+template <typename R>
+__device__ __forceinline__ void smem_copy_in(C_t<R>* dst, const C_t<R>* src, uint32_t dim) {
+  const uint32_t n16 = dim * (uint32_t)sizeof(C_t<R>) / 16u;
+  for (uint32_t i = threadIdx.x; i < n16; i += kSmemThreads)
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+}
+
+template <typename R>
+__device__ __forceinline__ void smem_copy_out(C_t<R>* dst, const C_t<R>* src, uint32_t dim) {
+  const uint32_t n16 = dim * (uint32_t)sizeof(C_t<R>) / 16u;
+  for (uint32_t i = threadIdx.x; i < n16; i += kSmemThreads)
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+}
+
+// psi <- T(theta_{P-1} A_{ops[P-1]}) ... T(theta_0 A_{ops[0]}) psi, LUT pools
+// only, by one block of kSmemThreads threads with the state in sp (shared
+// memory).  With mask set, also writes the exact nonzero-octet mask of the
+// result (see octet_mask).
+template <typename R>
+__device__ void taylor_chain_smem_body(const DevTables& tb, const int32_t* ops, const double* coefs, int n_ops,
+                                       C_t<R>* psi, int32_t* err, uint32_t* mask, C_t<R>* sp) {
+  const uint32_t dim = 1u << tb.n;
+  smem_copy_in<R>(sp, psi, dim);
+  __syncthreads();
+  for (int j = 0; j < n_ops; ++j) {
+    const int op = ops[j];
+    if (op < 0 || op >= tb.M) {   // acts as the identity, flagged
+      if (threadIdx.x == 0) atomicOr(err, 1);
+      continue;
+    }
+    const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];
+    const PairEnum& E = tb.penum[op];
+    R c[6];
+    step_coefs<R>(coefs, j, c);
+    const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
+    for (uint32_t q = threadIdx.x; q < count; q += kSmemThreads) {
+      uint32_t ph;
+      const uint32_t b = enum_pair(E, q, &ph);
+      C_t<R> o1, o2;
+      taylor_pair<R>(L, c, b, ph, sp, o1, o2);
+    }
+    __syncthreads();
+  }
+  smem_copy_out<R>(psi, sp, dim);
+  if (mask) {
+    // one octet per thread; a warp's 32 octets make one mask word
+    for (uint32_t o0 = 0; o0 < ((dim + 7u) >> 3); o0 += kSmemThreads) {
+      const uint32_t o = o0 + threadIdx.x;
+      bool nz = false;
+      if (o < (dim >> 3))
+        for (int i = 0; i < 8; ++i) nz |= sp[8u * o + i].x != R(0) || sp[8u * o + i].y != R(0);
+      const uint32_t word = __ballot_sync(0xffffffffu, nz);
+      if ((threadIdx.x & 31) == 0 && o < (dim >> 3)) mask[o >> 5] = word;
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1)
+k_taylor_chain_smem(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi,
+                    int32_t* err, uint32_t* mask) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  taylor_chain_smem_body<R>(tb, ops, coefs, n_ops, psi, err, mask, reinterpret_cast<C_t<R>*>(cs_raw));
+}
+
+// The backward sweep of the adjoint (see adjoint_pair) for j = P-1 .. 0 over
+// psi and lambda, by one block with both in shared memory (sp: 2 states);
+// dtheta[j] = the block's fixed-order sum.
+template <typename R>
+__device__ void adjoint_chain_smem_body(const DevTables& tb, const int32_t* ops, const double* coefs, int n_ops,
+                                        C_t<R>* psi, C_t<R>* lam, double* dtheta, int32_t* err, C_t<R>* sp) {
+  __shared__ double s_red[kSmemThreads / 32];
+  const uint32_t dim = 1u << tb.n;
+  C_t<R>* sl = sp + dim;
+  smem_copy_in<R>(sp, psi, dim);
+  smem_copy_in<R>(sl, lam, dim);
+  __syncthreads();
+  for (int j = n_ops - 1; j >= 0; --j) {
+    const int op = ops[j];
+    if (op < 0 || op >= tb.M) {
+      if (threadIdx.x == 0) {
+        atomicOr(err, 1);
+        dtheta[j] = 0.0;
+      }
+      continue;
+    }
+    const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];
+    const PairEnum& E = tb.penum[op];
+    R c[6];
+    step_coefs<R>(coefs, j, c);
+    const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
+    double v = 0.0;
+    for (uint32_t q = threadIdx.x; q < count; q += kSmemThreads) {
+      uint32_t ph;
+      const uint32_t b = enum_pair(E, q, &ph);
+      C_t<R> o[4];
+      v += adjoint_pair<R>(L, c, b, ph, sp, sl, o);
+    }
+    const double w = __any_sync(0xffffffffu, v != 0.0) ? warp_sum(v) : 0.0;
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < kSmemThreads / 32; ++q) t += s_red[q];
+      dtheta[j] = t;
+    }
+    __syncthreads();
+  }
+  smem_copy_out<R>(psi, sp, dim);
+  smem_copy_out<R>(lam, sl, dim);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1)
+k_adjoint_chain_smem(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi,
+                     C_t<R>* lam, double* dtheta, int32_t* err) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  adjoint_chain_smem_body<R>(tb, ops, coefs, n_ops, psi, lam, dtheta, err, reinterpret_cast<C_t<R>*>(cs_raw));
+}
+
 // ------------------------------------------------------------ pool gradients
 
 // blockIdx.y selects kOpsPerBlock operators in GOCP family order; the
@@ -1345,6 +1480,25 @@ __global__ void __launch_bounds__(kThreads) k_stage_backward(const BatchItemDev*
                   it.counter, it.dtheta, it.err, bid, it.nb);
 }
 
+// The whole forward chain / backward sweep of one small item per block
+// (on-chip chains; the items' states fit kSmemStateBytes, two states for the
+// backward sweep).
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_stage_forward_all(const BatchItemDev* items) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  const BatchItemDev& it = items[blockIdx.x];
+  taylor_chain_smem_body<R>(it.t, it.ops, it.coefs, it.n_ops, (C_t<R>*)it.psi, it.err, nullptr,
+                            reinterpret_cast<C_t<R>*>(cs_raw));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_stage_backward_all(const BatchItemDev* items) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  const BatchItemDev& it = items[blockIdx.x];
+  adjoint_chain_smem_body<R>(it.t, it.ops, it.coefs, it.n_ops, (C_t<R>*)it.psi, (C_t<R>*)it.lam, it.dtheta,
+                             it.err, reinterpret_cast<C_t<R>*>(cs_raw));
+}
+
 // ------------------------------------------------------------ upload
 
 namespace {
@@ -1704,7 +1858,8 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)) ||
       (rc = dalloc(d, &d.live.aidx, (size_t)1 << (n - 2), bytes)) ||
       (rc = dalloc(d, reinterpret_cast<C_t<R>**>(&d.live.aval), (size_t)1 << (n - 2), bytes)) ||
-      (rc = dalloc(d, &d.live.alen, 1, bytes)) || (rc = dalloc(d, &d.live.acounts, ((((size_t)1 << (n - 5)) + 255) / 256) + 1, bytes)))
+      (rc = dalloc(d, &d.live.alen, 1, bytes)) || (rc = dalloc(d, &d.live.acounts, ((((size_t)1 << (n - 5)) + 255) / 256) + 1, bytes)) ||
+      (rc = dalloc(d, &d.live.amax, 1, bytes)))
     return rc;
   d.live.acap = 1u << (n - 2);
   d.t.tblob = dblob;
@@ -1868,6 +2023,25 @@ int upload_typed(Problem& p, DeviceTables& d, size_t& bytes, double* identity) {
   d.t.n_lchunks = (int)lchunk.size() - 1;
   d.t.lchunk = dlchunk;
   d.t.lchunk_xl = dlchunk_xl;
+  {
+    // coupling bound for the scatter kernel's fixed-point scale
+    double hb = std::fabs(ident), dm = 0.0;
+    for (const HLut<R>& L : hl) {
+      double m = 0.0;
+      for (int c = 0; c < 16; ++c) m = std::max(m, std::fabs((double)L.lut16[c]));
+      hb += m;
+      dm = std::max(dm, m);
+    }
+    for (size_t g = 0; g + 1 < goff.size(); ++g) {
+      double m = 0.0;
+      for (int32_t t = goff[g]; t < goff[g + 1]; ++t) m += std::fabs((double)tw[t]);
+      hb += m;
+      dm = std::max(dm, m);
+    }
+    for (const R& w : dw) hb += std::fabs((double)w);
+    d.t.hbound = hb;
+    d.t.dmax = dm;
+  }
   if ((rc = build_tiled<R>(p.n_qubits, hl, gx, goff, gmid, gbk, tz, tw, d, bytes))) return rc;
   // ---- pool
   const Pool& P = p.pool;
@@ -2090,6 +2264,41 @@ void free_device(Problem& p) {
   p.dev = nullptr;
 }
 
+// Whether the on-chip forward chain / backward sweep takes this problem.
+template <typename R>
+bool smem_chain_fits(const DeviceTables& d, int states) {
+  return d.t.pool_lut && ((uint64_t)states << d.t.n) * sizeof(C_t<R>) <= kSmemStateBytes;
+}
+
+// Opts the on-chip chain kernels into kSmemStateBytes of dynamic shared
+// memory on the current device (once per device).
+template <typename R>
+int smem_chain_optin() {
+  static std::mutex mu;
+  static std::vector<bool> done;
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(mu);
+  if (device >= (int)done.size()) done.resize(device + 1, false);
+  if (!done[device]) {
+    e = cudaFuncSetAttribute(k_taylor_chain_smem<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemStateBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adjoint_chain_smem<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemStateBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage_forward_all<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemStateBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_stage_backward_all<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemStateBytes);
+    if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(on-chip chains)");
+    done[device] = true;
+  }
+  return GOCP_OK;
+}
+
 // ------------------------------------------------------------ launchers
 
 // Blocks of an adjoint step (k_adjoint).
@@ -2263,6 +2472,15 @@ template <typename R>
 static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked,
                                cudaStream_t st) {
   DeviceTables& d = *p.dev;
+  if (n_ops > 0 && smem_chain_fits<R>(d, 1)) {   // the whole chain in one block
+    int rc = smem_chain_optin<R>();
+    if (rc) return rc;
+    ProfScope ps(GOCP_KERNEL_TAYLOR, st, 1);
+    k_taylor_chain_smem<R><<<1, kSmemThreads, (size_t)sizeof(C_t<R>) << p.n_qubits, st>>>(
+        d.t, d_ops, d.coefs, n_ops, (C_t<R>*)psi, d.err, tracked ? d.t.octmask : nullptr);
+    count_launches(1);
+    return cuda_status(cudaGetLastError(), "k_taylor_chain_smem");
+  }
   const int grid = d.t.pool_lut ? grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm)
                                 : grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
   uint32_t* mask = tracked && d.t.pool_lut ? d.t.octmask : nullptr;
@@ -2405,6 +2623,16 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
   const uint64_t dim = 1ull << p.n_qubits;
   const int g1 = grid_for(dim, d.sm_count, 8);
   k_residual<R><<<g1, kThreads, 0, st>>>((const C_t<R>*)psi, (C_t<R>*)lam, p.n_qubits, d.scalars);
+  if (smem_chain_fits<R>(d, 2)) {   // the whole sweep in one block
+    count_launches(1);   // k_residual
+    int rc = smem_chain_optin<R>();
+    if (rc) return rc;
+    ProfScope ps(GOCP_KERNEL_ADJOINT, st, 1);
+    k_adjoint_chain_smem<R><<<1, kSmemThreads, (size_t)(2 * sizeof(C_t<R>)) << p.n_qubits, st>>>(
+        d.t, d_ops, d.coefs, n_ops, (C_t<R>*)psi, (C_t<R>*)lam, d_dE, d.err);
+    count_launches(1);
+    return cuda_status(cudaGetLastError(), "k_adjoint_chain_smem");
+  }
   const int grid = adjoint_grid(d);
   // nonzero octets of psi or lambda, kept valid by the sweep
   uint32_t* mask = d.t.pool_lut ? d.t.octmask2 : nullptr;
@@ -2465,7 +2693,15 @@ int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out
 //
 // The array is shared by every call in the process: calls that overlap on
 // the GPU race on it.  Every GPU that loads this library holds it (128 KiB
-// of partials plus a few scalars) until the process exits.
+// of partials plus a few scalars) until the process exits.  Its device
+// address is resolved once per device and kept; a cudaDeviceReset (or
+// anything else that destroys the device's primary context) leaves that
+// address stale, so no call may follow one in the same process.
+//
+// The H psi kernel is the untiled k_apply_h, the one gocp_energy runs below
+// the tile size (13 qubits for complex64, 12 for complex128), with the same
+// block decomposition there; from the tile size on gocp_energy runs the
+// tiled kernels, which sum in another order.
 
 constexpr int kStaticEnergyBlocks = 8192;   // one block per 2048-amplitude tile: n <= 24
 
@@ -2507,26 +2743,14 @@ int launch_energy_static(Problem& p, const void* psi, void* hpsi, StaticEnergySc
 
 }  // namespace
 
-}  // namespace gocp
-
-extern "C" int gocp_energy_static(const gocp_problem* h, const void* psi, void* hpsi, double* out,
-                                  int mem, void* stream) {
-  using namespace gocp;
-  if (!h) return fail(GOCP_EINVAL, "problem is NULL");
-  Problem& p = const_cast<Problem&>(h->p);
-  if (!p.dev) return fail(GOCP_ENODEV, "problem has no device tables (built with device = -1)");
-  if (p.sector) return fail(GOCP_EINVAL, "gocp_energy_static takes full-layout problems only");
-  if (mem != GOCP_MEM_HOST && mem != GOCP_MEM_DEVICE) return fail(GOCP_EINVAL, "mem must be GOCP_MEM_HOST or GOCP_MEM_DEVICE");
-  if (!psi || !hpsi || psi == hpsi || !out) return fail(GOCP_EINVAL, "psi/hpsi/out NULL or aliased");
+// gocp_energy_static's work, on the problem's device (current): the untiled
+// H psi kernel with the reduction scratch in g_static_energy.
+int dev_energy_static(Problem& p, const void* psi, void* hpsi, double* out, int mem, cudaStream_t st) {
   const int blocks = apply_grid(p.n_qubits);
   if (blocks > kStaticEnergyBlocks)
     return fail(GOCP_EINVAL, "gocp_energy_static: a state of 2^" + std::to_string(p.n_qubits) +
                                  " amplitudes needs " + std::to_string(blocks) +
                                  " reduction blocks; the static scratch holds 8192 (at most 24 qubits)");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != p.device) cudaSetDevice(p.device);
-  cudaStream_t st = (cudaStream_t)stream;
   StaticEnergyScratch* sc = nullptr;
   int rc = static_scratch(p.device, &sc);
   // the block counter must start at zero (the kernel also leaves it at zero)
@@ -2538,15 +2762,23 @@ extern "C" int gocp_energy_static(const gocp_problem* h, const void* psi, void* 
                                                                  : cudaMemcpyDeviceToDevice, st),
                             "copy energy");
   if (!rc && mem == GOCP_MEM_HOST) rc = cuda_status(cudaStreamSynchronize(st), "synchronise");
-  if (prev >= 0 && prev != p.device) cudaSetDevice(prev);
   return rc;
 }
+
+}  // namespace gocp
 
 namespace gocp {
 
 // ------------------------------------------------------------ batched launch
 
 size_t batch_desc_bytes(int n) { return (size_t)n * sizeof(BatchItemDev); }
+
+bool stage_onchip(const Problem& p, int kind) {
+  if (!p.dev || p.sector) return false;
+  const int states = kind == STAGE_BACKWARD_ALL ? 2 : 1;
+  return p.precision == GOCP_C64 ? smem_chain_fits<float>(*p.dev, states)
+                                 : smem_chain_fits<double>(*p.dev, states);
+}
 
 namespace {
 
@@ -2616,6 +2848,16 @@ int launch_stage_typed(int kind, const StageItem* items, int n, void* host_desc,
       k_stage_backward<R><<<total, kThreads, 0, st>>>(dd, ix);
       *launches += 1;
       break;
+    case STAGE_FORWARD_ALL:
+    case STAGE_BACKWARD_ALL: {
+      if ((rc = smem_chain_optin<R>())) return rc;
+      if (kind == STAGE_FORWARD_ALL)
+        k_stage_forward_all<R><<<n, kSmemThreads, kSmemStateBytes, st>>>(dd);
+      else
+        k_stage_backward_all<R><<<n, kSmemThreads, kSmemStateBytes, st>>>(dd);
+      *launches += 1;
+      break;
+    }
     default:
       return fail(GOCP_EINVAL, "unknown stage kind");
   }

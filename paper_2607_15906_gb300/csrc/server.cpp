@@ -1,12 +1,17 @@
 // Continuous-batching request server for energy + dE/dtheta solves.
 //
 // A worker thread owns one CUDA stream.  Each tick it admits queued requests
-// while slots and arena memory allow, then advances every resident request
-// by one stage with one batched launch per stage kind and precision:
+// while slots and memory allow, then advances every resident request with
+// one batched launch per stage kind and precision:
 //   SETUP     |psi> = |ref>, Taylor coefficients of the ansatz
-//   FORWARD   psi <- T(theta_j A_j) psi                        (Eq. 5, 6)
+//   FORWARD   psi <- T(theta_j A_j) psi, up to 8 steps a tick     (Eq. 5, 6)
 //   ENERGY    lambda <- H psi, E (Eq. 1), lambda <- (H - E) psi / <psi|psi>
-//   BACKWARD  adjoint step j: psi <- T_j^-1 psi, dE_j, lambda <- T_j^+ lambda
+//   BACKWARD  adjoint step j: psi <- T_j^-1 psi, dE_j, lambda <- T_j^+ lambda,
+//             up to 8 steps a tick
+// A request whose state fits one block's shared memory (up to 14 qubits
+// complex64, 13 complex128) takes its whole forward chain in one block
+// (FORWARD_ALL), and, when its two states fit, its whole backward sweep
+// (BACKWARD_ALL): such a request can finish within the tick that admits it.
 // Requests that arrive while others are on the GPU join at the next tick;
 // a finished request frees its slot and its memory at once.  Each request
 // holds its two states either in one power-of-two block of a buddy-allocated
@@ -277,7 +282,7 @@ StageItem item_for(gocp_server* s, Request* r) {
   return it;
 }
 
-constexpr int kDescSlotsPerTick = 4 * (2 * kOpsPerTick + 2);
+constexpr int kDescSlotsPerTick = 4 * (2 * kOpsPerTick + 4);
 
 int run_stage(gocp_server* s, int kind, std::vector<StageItem>& items, int* desc_slot,
               int64_t* launches) {
@@ -337,6 +342,18 @@ void worker_loop(gocp_server* s) {
         r->needs_setup = false;
       }
     if (!items.empty()) rc = run_stage(s, STAGE_SETUP, items, &desc_slot, &launches);
+    // FORWARD_ALL: requests whose state fits one block's shared memory run
+    // their whole forward chain in one block
+    if (rc == GOCP_OK) {
+      items.clear();
+      for (Request* r : work)
+        if (r->phase == Phase::Forward && r->j == 0 && !r->ops.empty() &&
+            stage_onchip(*r->prob, STAGE_FORWARD_ALL)) {
+          items.push_back(item_for(s, r));
+          r->j = (int)r->ops.size();
+        }
+      if (!items.empty()) rc = run_stage(s, STAGE_FORWARD_ALL, items, &desc_slot, &launches);
+    }
     // FORWARD: up to kOpsPerTick operators per request
     for (int round = 0; round < kOpsPerTick && rc == GOCP_OK; ++round) {
       items.clear();
@@ -358,6 +375,18 @@ void worker_loop(gocp_server* s) {
           r->j = (int)r->ops.size() - 1;
         }
       if (!items.empty()) rc = run_stage(s, STAGE_ENERGY, items, &desc_slot, &launches);
+    }
+    // BACKWARD_ALL: requests whose two states fit one block's shared memory
+    // run their whole backward sweep in one block
+    if (rc == GOCP_OK) {
+      items.clear();
+      for (Request* r : work)
+        if (r->phase == Phase::Backward && !r->ops.empty() && r->j == (int)r->ops.size() - 1 &&
+            stage_onchip(*r->prob, STAGE_BACKWARD_ALL)) {
+          items.push_back(item_for(s, r));
+          r->j = -1;
+        }
+      if (!items.empty()) rc = run_stage(s, STAGE_BACKWARD_ALL, items, &desc_slot, &launches);
     }
     // BACKWARD: up to kOpsPerTick adjoint steps
     for (int round = 0; round < kOpsPerTick && rc == GOCP_OK; ++round) {

@@ -123,3 +123,28 @@ def test_bench_state_24q(prec, oracle24):
     assert de_err <= tol["grad"]
     assert p.device_errors() == 0
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_bench_state_h_psi_reproducible(prec, oracle24):
+    """H psi and E of the timed state are the same bit for bit from call to
+    call (the scatter kernel sums in fixed point, the energy partials in tile
+    order), and so are the pool gradients built on them."""
+    o = oracle24
+    p = gb.Problem.build(o["ints"], 8, precision=prec, int_drop=o["cfg"]["int_drop"],
+                         term_drop=o["cfg"]["term_drop"], device=0)
+    ws = p.workspace()
+    p.prepare_state(o["ops"], o["th"], ws[0])
+    first = None
+    for _ in range(3):
+        e, nrm = p.energy(ws[0], ws[1])
+        g = p.pool_gradients(ws[0], ws[1])
+        cur = (ws[1].clone(), e, nrm, g)
+        if first is None:
+            first = cur
+        else:
+            assert torch.equal(first[0], cur[0])
+            assert first[1] == cur[1] and first[2] == cur[2]
+            assert np.array_equal(first[3], cur[3])
+    assert abs(first[1] - o["e"]) <= TOL[prec]["energy"] * max(1.0, abs(o["e"]))
+    p.close()

@@ -554,3 +554,32 @@ def test_larger_n_30q_c64():
     complex64 state, the uint32 index limit of this build): a prepared
     sparse state, E and sampled pool gradients against the oracle."""
     _sparse_prepared_check(15, 8, "30q sparse", n_ops=5)
+
+
+@pytest.mark.parametrize("n_orb,n_elec,prec", [(5, 4, "c128"), (6, 6, "c64"), (6, 6, "c128"), (7, 6, "c64"),
+                                               (7, 6, "c128")])
+def test_onchip_chains_match_oracle(n_orb, n_elec, prec):
+    """Forward chains of states up to 128 KiB (14 qubits complex64, 13
+    complex128) and backward sweeps whose psi and lambda together fit 128 KiB
+    (13 / 12 qubits) run as one block over shared memory; the larger cases
+    here take the grid kernels.  States, E and dE/dtheta against the oracle
+    (Eq. 5, 6; the adjoint of Eq. 1)."""
+    ints, h, tabs = _case(n_orb, n_elec, "jw", n_orb)
+    p = gb.Problem.build(ints, n_elec, precision=prec, device=0)
+    n = 2 * n_orb
+    ops, th = draw_ansatz(len(tabs), 16, seed=n_orb, theta_sigma=0.3)
+    ref = sv.basis_state(n, p.info["ref_index"])
+    d = p.new_states(1)[0]
+    p.prepare_state(ops, th, d)
+    want = sv.prepare_state(ref, tabs, ops, th)
+    _within(f"onchip {prec} {n}q psi", np.max(np.abs(_host(d) - want)), TOL[prec]["state"] * np.max(np.abs(want)))
+    e, de = p.energy_grad(ops, th)
+    e_ref, de_ref = sv.energy_grad(h, ref, tabs, ops, th)
+    _within(f"onchip {prec} {n}q E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"onchip {prec} {n}q dE", np.max(np.abs(de - de_ref)), TOL[prec]["grad"] * max(1.0, np.max(np.abs(de_ref))))
+    bad = np.array([0, 10 ** 6, 1], np.int32)      # an out-of-range operator acts as the identity, flagged
+    p.prepare_state(torch.from_numpy(bad).cuda(), torch.tensor([0.2, 0.3, -0.1], dtype=torch.float64).cuda(), d)
+    assert p.device_errors() == 1
+    _within(f"onchip {prec} {n}q flagged", np.max(np.abs(_host(d) - sv.prepare_state(ref, tabs, [0, 1], [0.2, -0.1]))),
+            TOL[prec]["state"])
+    p.close()

@@ -124,6 +124,6 @@ def test_admission_by_free_device_memory():
         pooled = [srv.result(t) for t in tickets]
         st = srv.stats()
     assert st["arena_bytes"] == 0 and st["completed"] == len(reqs)
-    assert st["arena_in_use"] == 0 and st["arena_peak"] >= 2 * reqs[-2][2].state_bytes
+    assert st["arena_in_use"] == 0 and st["arena_peak"] >= 2 * reqs[-2][2].state_bytes()
     for (ea, da), (ep, dp) in zip(arena, pooled):
         assert ea == ep and np.array_equal(da, dp)

@@ -4,9 +4,11 @@ It exists for callers that cannot call cudaMalloc where they compute (a host
 loop with real-time or no-blocking guarantees, or a caller whose device
 memory belongs to another allocator): its reduction scratch is a fixed
 device array inside the library.  Through the C ABI, two calls in a row must
-give the same H psi and energy as gocp_energy within the tolerances of the
-parity tests, and states beyond the array's 24-qubit limit must be refused.
-The file name keeps this module last in collection order.
+give the same H psi and energy as gocp_energy: bit for bit below the tile
+size (where both run the untiled kernel), within the tolerances of the
+parity tests above it (where gocp_energy runs the tiled kernels); states
+beyond the array's 24-qubit limit must be refused.  The file name keeps
+this module last in collection order.
 """
 
 import ctypes as C
@@ -67,6 +69,8 @@ def test_static_energy_matches_gocp_energy_twice(prec, n_orb, n_elec):
         h = torch.full_like(psi, float("nan"))
         e, nrm = _energy_static(p, psi, h, mem)
         got = h.cpu().numpy().astype(np.complex128)
+        if n < (13 if prec == "c64" else 12):      # the same kernel as gocp_energy
+            assert np.array_equal(got, ref) and e == e_ref and nrm == nrm_ref, call
         assert np.max(np.abs(got - ref)) <= TOL[prec]["state"] * scale, call
         assert abs(e - e_ref) <= TOL[prec]["energy"] * max(1.0, abs(e_ref)), call
         assert abs(nrm - nrm_ref) <= 1e-12 * max(1.0, nrm_ref), call
