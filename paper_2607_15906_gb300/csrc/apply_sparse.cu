@@ -47,7 +47,10 @@ namespace gocp {
 namespace {
 
 constexpr int kAmpBlock = 256;   // listing passes: one amplitude word (4 octets) per thread
-constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
+#ifndef GOCP_SP_BATCH
+#define GOCP_SP_BATCH 2
+#endif
+constexpr uint32_t kUnitBatch = GOCP_SP_BATCH;   // scatter work units per claim
 #ifndef GOCP_SP_AMPS
 #define GOCP_SP_AMPS 1
 #endif
@@ -312,16 +315,27 @@ __device__ __forceinline__ void acc_add(unsigned long long* acc, uint32_t k, lon
 // phi(k) alone (lut16[phi | 8] = -lut16[phi]), so the sign parity is taken
 // only for a nonzero entry.
 template <typename R, uint32_t kOct, int A>
-__device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint32_t (&ks)[A],
+__device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint4 h0, const uint32_t v2,
+                                       const uint4 m0, const uint4 m1, const uint32_t (&ks)[A],
                                        const C_t<R> (&vs)[A], const bool (&valid)[A], unsigned long long* acc) {
-  const uint4 h0 = ldb(reinterpret_cast<const uint4*>(&L->x));     // x, z0, v0, v1
-  const uint32_t v2 = ldb(&L->v2);
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     const uint32_t k = ks[s] ^ h0.x;
     const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
                          ((uint32_t)(__popc(k & v2) & 1) << 2);
+#ifdef GOCP_SP_LUTREG
+    // the 8 magnitudes lut16[0..7] were loaded with the descriptor (complex64)
+    R d0;
+    if (sizeof(R) == 4) {
+      const uint4 q = (phi & 4u) ? m1 : m0;
+      const uint32_t lo = (phi & 1u) ? q.y : q.x, hi = (phi & 1u) ? q.w : q.z;
+      d0 = (R)__uint_as_float((phi & 2u) ? hi : lo);
+    } else {
+      d0 = ldb(L->lut16 + phi);
+    }
+#else
     const R d0 = ldb(L->lut16 + phi);
+#endif
     if (valid[s] && d0 != R(0)) {
       const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
       acc_add<kOct>(acc, k, fx_prod<R>(d * vs[s].x), fx_prod<R>(d * vs[s].y));
@@ -446,7 +460,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       const uint32_t per = (P + NT - 1) / NT, p0 = threadIdx.x * per, p1 = min(P, p0 + per);
       uint32_t mine = 0;
       for (uint32_t p = p0; p < p1; ++p) {
-        const TiledPiece pc = a.piece[p];
+        const TiledPiece pc = a.piece[a.porder[p]];
         const uint32_t u = t ^ pc.xhi;
         const uint32_t nch = pc.bytes ? (a.toff[u + 1] - a.toff[u] + kChunk - 1u) / kChunk : 0u;
         s_pre[p] = nch;
@@ -506,17 +520,18 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       for (uint32_t j = j0; j < j1; ++j) {
         while (p + 1 < P && s_pre[p + 1] <= j) ++p;
         const uint32_t c = j - s_pre[p];
-        const TiledPiece pc = a.piece[p];
+        const uint32_t pid = a.porder[p];
+        const TiledPiece pc = a.piece[pid];
         const uint32_t u = t ^ pc.xhi;
         const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
 #ifdef GOCP_SP_SMEMBLOB
-        if (p != cur) {
+        if (pid != cur) {
           __syncwarp();
           const uint4* src = reinterpret_cast<const uint4*>(a.blob + pc.off);
           uint4* dst = reinterpret_cast<uint4*>(wblob);
           for (uint32_t q = (uint32_t)lane; q < pc.bytes / 16u; q += 32u) dst[q] = __ldg(src + q);
           __syncwarp();
-          cur = p;
+          cur = pid;
         }
         const uint8_t* blob = wblob;
 #else
@@ -539,7 +554,27 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
           vs[s] = cmake<R>(v.x * up_a * up_b, v.y * up_a * up_b);
         }
         const int nl = (int)hd.y;
-        for (int g = 0; g < nl; ++g) sp_lut<R, kOct, A>(ls + g, ks, vs, valid, acc);
+        // each group's descriptor (x, z0, v0, v1 and v2) is loaded while the
+        // group before it is computed
+        uint4 h0n = make_uint4(0u, 0u, 0u, 0u), m0n = h0n, m1n = h0n;
+        uint32_t v2n = 0u;
+        auto fetch = [&](int g) {
+          h0n = ldb(reinterpret_cast<const uint4*>(&ls[g].x));
+          v2n = ldb(&ls[g].v2);
+#ifdef GOCP_SP_LUTREG
+          if (sizeof(R) == 4) {
+            m0n = ldb(reinterpret_cast<const uint4*>(ls[g].lut16));
+            m1n = ldb(reinterpret_cast<const uint4*>(ls[g].lut16) + 1);
+          }
+#endif
+        };
+        if (nl > 0) fetch(0);
+        for (int g = 0; g < nl; ++g) {
+          const uint4 h0 = h0n, m0 = m0n, m1 = m1n;
+          const uint32_t v2 = v2n;
+          if (g + 1 < nl) fetch(g + 1);
+          sp_lut<R, kOct, A>(ls + g, h0, v2, m0, m1, ks, vs, valid, acc);
+        }
         // the term-list groups fill the blob from the LUT groups to z_off
         const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
         for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, ks, vs, valid, acc);

@@ -683,6 +683,7 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     SparseArgs<R> s;
     s.blob = t.tblob;
     s.piece = t.tpiece;
+    s.porder = t.tporder;
     s.n_pieces = t.n_pieces;
     s.n = t.n;
     s.psi = reinterpret_cast<const C_t<R>*>(psi);

@@ -252,6 +252,7 @@ struct DevTables {
   int n_pieces = 0;
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
+  const uint32_t* tporder = nullptr;   // piece indices by descending blob size
   uint32_t* octmask = nullptr;
   uint32_t* tflags = nullptr;   // tiled form: one bit per tile (scratch)
   // second mask of the same size, for the adjoint sweep (psi and lambda)
@@ -508,6 +509,7 @@ template <typename R>
 struct SparseArgs {
   const uint8_t* blob;
   const TiledPiece* piece;
+  const uint32_t* porder;       // pieces by descending blob size (work units are numbered in this order)
   int n_pieces, n;
   const C_t<R>* psi;
   C_t<R>* out;

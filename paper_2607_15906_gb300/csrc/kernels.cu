@@ -1850,10 +1850,19 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       pieces.push_back(pc);
     } while (li < ls.size() || ti < ts.size());
   }
+  // the scatter kernel numbers a tile's work units piece by piece in this
+  // order (costliest first), so that the units left at the end of a tile are
+  // short ones
+  std::vector<uint32_t> porder(pieces.size());
+  for (size_t i = 0; i < porder.size(); ++i) porder[i] = (uint32_t)i;
+  std::stable_sort(porder.begin(), porder.end(),
+                   [&](uint32_t a, uint32_t b) { return pieces[a].bytes > pieces[b].bytes; });
   uint8_t* dblob;
   TiledPiece* dpiece;
+  uint32_t* dporder;
   int rc;
   if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
+      (rc = upload(d, &dporder, porder, bytes)) ||
       (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)) ||
       (rc = dalloc(d, &d.live.toff, ((size_t)1 << (n - LB)) + 1, bytes)) ||
       (rc = dalloc(d, &d.live.aidx, (size_t)1 << (n - 2), bytes)) ||
@@ -1864,6 +1873,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   d.live.acap = 1u << (n - 2);
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
+  d.t.tporder = dporder;
   d.t.n_pieces = (int)pieces.size();
   return GOCP_OK;
 }
