@@ -271,9 +271,11 @@ int gocp_energy_static(const gocp_problem* p, const void* psi, void* hpsi, doubl
 /* Device-side errors flagged since the last call, and clear them.  Bit 0: an
  * op index out of range in a GOCP_MEM_DEVICE ansatz.  Bit 1: a shared-memory
  * staging wait of the staged H psi kernel gave up (after 2 s, or after
- * GOCP_STAGE_WAIT_NS nanoseconds when that environment variable is set; the
- * H psi and energy of that call are then undefined, later calls are not
- * affected).  Synchronises `stream`. */
+ * GOCP_STAGE_WAIT_NS nanoseconds when that environment variable is set, at
+ * once when it is 0; the H psi and energy of that call are then undefined,
+ * later calls are not affected).  Bit 2: a grid-wide barrier between the steps of a persistent
+ * Taylor or adjoint chain gave up after 2 s (that chain's results are then
+ * undefined).  Synchronises `stream`. */
 int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
 
 /* ---------------------------------------------------------------- serving */
@@ -291,7 +293,10 @@ int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
  *   hbm_budget_bytes > 0: that many bytes are reserved up front as the
  *     state arena (power-of-two buddy blocks).
  * max_slots bounds residency (1..256).  Problems must outlive the requests
- * that name them and must be C64 or C128 problems built on `device`. */
+ * that name them and must be C64 or C128 problems built on `device`.  The
+ * server computes H psi of requests of 13 qubits or more (12 for C128) with
+ * the problem's own scratch, so while such requests are queued or running no
+ * other call may compute on their problem. */
 int gocp_server_create(size_t hbm_budget_bytes, int max_slots, int device, gocp_server** out);
 void gocp_server_destroy(gocp_server* s);
 

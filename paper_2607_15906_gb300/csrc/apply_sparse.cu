@@ -47,29 +47,14 @@ namespace gocp {
 namespace {
 
 constexpr int kAmpBlock = 256;   // listing passes: one amplitude word (4 octets) per thread
-#ifndef GOCP_SP_BATCH
-#define GOCP_SP_BATCH 2
-#endif
-constexpr uint32_t kUnitBatch = GOCP_SP_BATCH;   // scatter work units per claim
-#ifndef GOCP_SP_AMPS
-#define GOCP_SP_AMPS 1
-#endif
-constexpr int kSpAmps = GOCP_SP_AMPS;   // nonzero source amplitudes per lane per work unit
+constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
+constexpr int kSpAmps = 2;           // nonzero source amplitudes per lane per work unit
 
 // One block per SM: 1024 threads for complex64 (64 registers), 512 for
 // complex128 (128 registers).
-#ifdef GOCP_SP_SMEMBLOB
-// descriptors copied into per-warp shared-memory buffers (16 warps)
-template <typename R>
-__host__ __device__ constexpr int sp_threads() { return 512; }
-template <typename T>
-__device__ __forceinline__ T ldb(const T* p) { return *p; }
-#else
 template <typename R>
 __host__ __device__ constexpr int sp_threads() { return sizeof(R) == 4 ? 1024 : 512; }
-template <typename T>
-__device__ __forceinline__ T ldb(const T* p) { return __ldg(p); }
-#endif
+
 
 template <typename R>
 __device__ __forceinline__ void load_octet(const C_t<R>* __restrict__ psi, uint32_t octet, C_t<R> (&v)[kAmpsH]) {
@@ -266,17 +251,16 @@ __device__ __forceinline__ uint32_t acc_at(uint32_t k) {
 // an entry of H psi collects it from at most a few thousand products.  For
 // complex128 the rounding is at most 2^-(F+1) with F near 62 - log2 of the
 // bound, far below the FP64 rounding of the products.
+
+// Adds v to the 64-bit accumulator word p as two 32-bit atomics: the low
+// word's, and the high word's plus the carry out of the low word, taken from
+// the old value that atomic returns.  The pair is exact modulo 2^64 in any
+// order of the atomics (measured faster than one 64-bit atomic).
 __device__ __forceinline__ void fx_add(unsigned long long* p, long long v) {
-#ifdef GOCP_SP_ATOM32
-  // two 32-bit atomics, the carry out of the low word taken from the old
-  // value it returns (exact modulo 2^64 in any order)
   uint32_t* w = reinterpret_cast<uint32_t*>(p);
   const uint32_t lo = (uint32_t)(unsigned long long)v, hi = (uint32_t)((unsigned long long)v >> 32);
   const uint32_t old = atomicAdd(w, lo);
   atomicAdd(w + 1, hi + (uint32_t)(old + lo < old));
-#else
-  atomicAdd(p, (unsigned long long)v);
-#endif
 }
 
 // A scaled product as an integer.  complex64: every off-diagonal product is
@@ -316,26 +300,14 @@ __device__ __forceinline__ void acc_add(unsigned long long* acc, uint32_t k, lon
 // only for a nonzero entry.
 template <typename R, uint32_t kOct, int A>
 __device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint4 h0, const uint32_t v2,
-                                       const uint4 m0, const uint4 m1, const uint32_t (&ks)[A],
-                                       const C_t<R> (&vs)[A], const bool (&valid)[A], unsigned long long* acc) {
+                                       const uint32_t (&ks)[A], const C_t<R> (&vs)[A], const bool (&valid)[A],
+                                       unsigned long long* acc) {
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     const uint32_t k = ks[s] ^ h0.x;
     const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
                          ((uint32_t)(__popc(k & v2) & 1) << 2);
-#ifdef GOCP_SP_LUTREG
-    // the 8 magnitudes lut16[0..7] were loaded with the descriptor (complex64)
-    R d0;
-    if (sizeof(R) == 4) {
-      const uint4 q = (phi & 4u) ? m1 : m0;
-      const uint32_t lo = (phi & 1u) ? q.y : q.x, hi = (phi & 1u) ? q.w : q.z;
-      d0 = (R)__uint_as_float((phi & 2u) ? hi : lo);
-    } else {
-      d0 = ldb(L->lut16 + phi);
-    }
-#else
-    const R d0 = ldb(L->lut16 + phi);
-#endif
+    const R d0 = __ldg(L->lut16 + phi);
     if (valid[s] && d0 != R(0)) {
       const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
       acc_add<kOct>(acc, k, fx_prod<R>(d * vs[s].x), fx_prod<R>(d * vs[s].y));
@@ -352,8 +324,8 @@ __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const
                                          const R* __restrict__ ws, const uint32_t (&ks)[A],
                                          const C_t<R> (&vs)[A], const bool (&valid)[A],
                                          unsigned long long* acc) {
-  const uint4 g0 = ldb(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
-  const uint2 g1 = ldb(reinterpret_cast<const uint2*>(&G->delta)); // delta, neg
+  const uint4 g0 = __ldg(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
+  const uint2 g1 = __ldg(reinterpret_cast<const uint2*>(&G->delta)); // delta, neg
   uint32_t k[A];
   R f[A];
   bool on = false;
@@ -372,14 +344,14 @@ __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const
 #pragma unroll
   for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
   for (uint32_t t = g0.y; t < g0.z; ++t) {
-    const uint32_t z = ldb(zs + t);
-    const R w = ldb(ws + t);
+    const uint32_t z = __ldg(zs + t);
+    const R w = __ldg(ws + t);
 #pragma unroll
     for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
   }
   for (uint32_t t = g0.z; t < g0.w; ++t) {
-    const uint32_t z = ldb(zs + t);
-    const R w = ldb(ws + t);
+    const uint32_t z = __ldg(zs + t);
+    const R w = __ldg(ws + t);
 #pragma unroll
     for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
   }
@@ -492,10 +464,6 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     }
     __syncthreads();
     const uint32_t n_units = s_pre[P];
-#ifdef GOCP_SP_SMEMBLOB
-    uint8_t* wblob = sp_raw + kOct * 16u * sizeof(unsigned long long) + (size_t)warp * kTiledBlobBytes;
-    uint32_t cur = 0xFFFFFFFFu;   // piece whose blob this warp holds
-#endif
     for (;;) {
       // kUnitBatch consecutive units per claim: mostly chunks of one piece,
       // whose descriptors then stay in L1
@@ -524,20 +492,8 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         const TiledPiece pc = a.piece[pid];
         const uint32_t u = t ^ pc.xhi;
         const uint32_t a0 = a.toff[u], a1 = a.toff[u + 1];
-#ifdef GOCP_SP_SMEMBLOB
-        if (pid != cur) {
-          __syncwarp();
-          const uint4* src = reinterpret_cast<const uint4*>(a.blob + pc.off);
-          uint4* dst = reinterpret_cast<uint4*>(wblob);
-          for (uint32_t q = (uint32_t)lane; q < pc.bytes / 16u; q += 32u) dst[q] = __ldg(src + q);
-          __syncwarp();
-          cur = pid;
-        }
-        const uint8_t* blob = wblob;
-#else
         const uint8_t* blob = a.blob + pc.off;
-#endif
-        const uint4 hd = ldb(reinterpret_cast<const uint4*>(blob));   // n_runs, n_lut, z_off, w_off
+        const uint4 hd = __ldg(reinterpret_cast<const uint4*>(blob));   // n_runs, n_lut, z_off, w_off
         const HLut<R>* ls = reinterpret_cast<const HLut<R>*>(blob + sizeof(TiledHead));
         const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(blob + sizeof(TiledHead) + hd.y * sizeof(HLut<R>));
         const uint32_t* zs = reinterpret_cast<const uint32_t*>(blob + hd.z);
@@ -556,24 +512,20 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         const int nl = (int)hd.y;
         // each group's descriptor (x, z0, v0, v1 and v2) is loaded while the
         // group before it is computed
-        uint4 h0n = make_uint4(0u, 0u, 0u, 0u), m0n = h0n, m1n = h0n;
+        uint4 h0n = make_uint4(0u, 0u, 0u, 0u);
         uint32_t v2n = 0u;
-        auto fetch = [&](int g) {
-          h0n = ldb(reinterpret_cast<const uint4*>(&ls[g].x));
-          v2n = ldb(&ls[g].v2);
-#ifdef GOCP_SP_LUTREG
-          if (sizeof(R) == 4) {
-            m0n = ldb(reinterpret_cast<const uint4*>(ls[g].lut16));
-            m1n = ldb(reinterpret_cast<const uint4*>(ls[g].lut16) + 1);
-          }
-#endif
-        };
-        if (nl > 0) fetch(0);
+        if (nl > 0) {
+          h0n = __ldg(reinterpret_cast<const uint4*>(&ls[0].x));
+          v2n = __ldg(&ls[0].v2);
+        }
         for (int g = 0; g < nl; ++g) {
-          const uint4 h0 = h0n, m0 = m0n, m1 = m1n;
+          const uint4 h0 = h0n;
           const uint32_t v2 = v2n;
-          if (g + 1 < nl) fetch(g + 1);
-          sp_lut<R, kOct, A>(ls + g, h0, v2, m0, m1, ks, vs, valid, acc);
+          if (g + 1 < nl) {
+            h0n = __ldg(reinterpret_cast<const uint4*>(&ls[g + 1].x));
+            v2n = __ldg(&ls[g + 1].v2);
+          }
+          sp_lut<R, kOct, A>(ls + g, h0, v2, ks, vs, valid, acc);
         }
         // the term-list groups fill the blob from the LUT groups to z_off
         const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
@@ -693,12 +645,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
 
 template <typename R>
 constexpr uint32_t sparse_smem() {
-#ifdef GOCP_SP_SMEMBLOB
-  return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(unsigned long long) +
-         (sp_threads<R>() / 32) * kTiledBlobBytes;
-#else
   return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(unsigned long long);
-#endif
 }
 
 }  // namespace

@@ -74,8 +74,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Waits for the phase with the given parity to complete; false after
-// limit_ns of %globaltimer.
+// limit_ns of %globaltimer.  A limit of 0 gives up without looking (the
+// abort path on every call, for a test).
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
@@ -626,8 +628,8 @@ int smem_optin(int device) {
 // state (GOCP_SPARSE_FRAC; 0 keeps every state on the staged kernel; the
 // amplitude list holds a quarter of the state at most).
 // Limit of a staging wait in the staged kernel: GOCP_STAGE_WAIT_NS, default
-// kWaitNs.  A short limit makes the kernel give up (and flag it) instead of
-// waiting for a copy, which lets a test drive that path.
+// kWaitNs.  0 makes every staging wait give up at once (the kernel flags it
+// and returns), which lets a test drive that path.
 uint64_t stage_wait_ns() {
   const char* e = std::getenv("GOCP_STAGE_WAIT_NS");
   if (!e || !*e) return kWaitNs;

@@ -9,6 +9,8 @@
 
 #include "gocp.h"
 
+typedef struct CUstream_st* cudaStream_t;
+
 namespace gocp {
 
 // ------------------------------------------------------------ errors
@@ -184,7 +186,16 @@ constexpr int kMaxBatchItems = 256;
 constexpr int kMaxItemBlocks = 1216;
 enum StageKind { STAGE_SETUP = 0, STAGE_FORWARD = 1, STAGE_ENERGY = 2, STAGE_BACKWARD = 3,
                  STAGE_FORWARD_ALL = 4,    // every forward step of the item, one block (on-chip chain)
-                 STAGE_BACKWARD_ALL = 5 }; // every backward step of the item, one block
+                 STAGE_BACKWARD_ALL = 5,   // every backward step of the item, one block
+                 STAGE_RESIDUAL = 6 };     // lambda <- (H psi - E psi) / <psi|psi> only (E, <psi|psi> in scal)
+// Whether H psi of this problem runs the tiled kernels (full layout from 13
+// qubits complex64 / 12 complex128): the server then computes a request's
+// H psi and energy with dev_apply_h on the problem's own scratch.
+bool has_tiled_form(const Problem& p);
+// H psi (+ the energy into scalars_ptr(p): E, <psi|psi>, Re<psi|H'psi>) of a
+// full-layout problem on `st` (kernels.cu).
+int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st);
+double* scalars_ptr(Problem& p);
 // Whether an item of this problem can take the on-chip stage `kind`
 // (STAGE_FORWARD_ALL: its state fits one block's shared memory;
 // STAGE_BACKWARD_ALL: its two states do).

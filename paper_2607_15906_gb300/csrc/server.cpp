@@ -6,6 +6,7 @@
 //   SETUP     |psi> = |ref>, Taylor coefficients of the ansatz
 //   FORWARD   psi <- T(theta_j A_j) psi, up to 8 steps a tick     (Eq. 5, 6)
 //   ENERGY    lambda <- H psi, E (Eq. 1), lambda <- (H - E) psi / <psi|psi>
+//             (from the tile size on: the problem's tiled H psi, per request)
 //   BACKWARD  adjoint step j: psi <- T_j^-1 psi, dE_j, lambda <- T_j^+ lambda,
 //             up to 8 steps a tick
 // A request whose state fits one block's shared memory (up to 14 qubits
@@ -282,7 +283,7 @@ StageItem item_for(gocp_server* s, Request* r) {
   return it;
 }
 
-constexpr int kDescSlotsPerTick = 4 * (2 * kOpsPerTick + 4);
+constexpr int kDescSlotsPerTick = 4 * (2 * kOpsPerTick + 5);
 
 int run_stage(gocp_server* s, int kind, std::vector<StageItem>& items, int* desc_slot,
               int64_t* launches) {
@@ -365,16 +366,31 @@ void worker_loop(gocp_server* s) {
       if (items.empty()) break;
       rc = run_stage(s, STAGE_FORWARD, items, &desc_slot, &launches);
     }
-    // ENERGY for requests whose forward sweep is complete
+    // ENERGY for requests whose forward sweep is complete: the batched
+    // octet kernel below the tile size; from it on, the problem's own tiled
+    // H psi (the scatter kernel for a sector-confined state), one request
+    // after the other on this stream, with E and <psi|psi> copied to the
+    // request's slot before the next request on the same problem runs
     if (rc == GOCP_OK) {
       items.clear();
+      std::vector<StageItem> tiled;
       for (Request* r : work)
         if (r->phase == Phase::Forward && r->j >= (int)r->ops.size()) {
-          items.push_back(item_for(s, r));
+          (has_tiled_form(*r->prob) ? tiled : items).push_back(item_for(s, r));
           r->phase = Phase::Backward;
           r->j = (int)r->ops.size() - 1;
         }
       if (!items.empty()) rc = run_stage(s, STAGE_ENERGY, items, &desc_slot, &launches);
+      for (const StageItem& it : tiled) {
+        if (rc != GOCP_OK) break;
+        Problem& p = const_cast<Problem&>(*it.prob);
+        rc = dev_apply_h(p, it.psi, it.lam, true, s->stream);
+        if (rc == GOCP_OK)
+          rc = cuda_status(cudaMemcpyAsync(it.scal, scalars_ptr(p), 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                           s->stream),
+                           "request energy");
+      }
+      if (rc == GOCP_OK && !tiled.empty()) rc = run_stage(s, STAGE_RESIDUAL, tiled, &desc_slot, &launches);
     }
     // BACKWARD_ALL: requests whose two states fit one block's shared memory
     // run their whole backward sweep in one block

@@ -2,9 +2,9 @@
 
 The staged H psi kernel bounds every wait on its shared-memory staging
 barriers (2 s, or GOCP_STAGE_WAIT_NS nanoseconds from the environment).  A
-limit of 0 ns makes the blocks give up at their first wait that is not
-already complete: they record bit 1 of the device error flags, let the
-copies they started land (always with the full limit), and return.  The
+limit of 0 ns makes every staging wait give up at once, as a wait that ran
+out: the blocks record bit 1 of the device error flags, let the copies they
+started land (always with the full limit), and return.  The
 test checks that the call returns, that gocp_device_errors reports the flag,
 and that the next call, at the default limit, is correct again -- the
 context stays usable.

@@ -583,3 +583,26 @@ def test_onchip_chains_match_oracle(n_orb, n_elec, prec):
     _within(f"onchip {prec} {n}q flagged", np.max(np.abs(_host(d) - sv.prepare_state(ref, tabs, [0, 1], [0.2, -0.1]))),
             TOL[prec]["state"])
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_persistent_chain_matches_step_by_step(prec):
+    """Above the on-chip sizes a prepared state's chain runs as one persistent
+    launch with a grid barrier between steps; applying the same operators
+    one gocp_taylor_step at a time (one launch each) gives the same state bit
+    for bit (the per-pair arithmetic is the same), and both match the oracle."""
+    ints, h, tabs = _case(8, 8, "jw", 3)                  # 16 qubits
+    p = gb.Problem.build(ints, 8, precision=prec, device=0)
+    ops, th = draw_ansatz(len(tabs), 20, seed=4, theta_sigma=0.3)
+    a = p.new_states(1)[0]
+    p.prepare_state(ops, th, a)
+    b = p.new_states(1)[0]
+    p.reference_state(b)
+    for k, t in zip(ops, th):
+        p.taylor_step(int(k), float(t), b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    want = sv.prepare_state(sv.basis_state(16, p.info["ref_index"]), tabs, ops, th)
+    _within(f"persistent {prec} psi", np.max(np.abs(_host(a) - want)), TOL[prec]["state"] * np.max(np.abs(want)))
+    assert p.device_errors() == 0
+    p.close()
