@@ -273,9 +273,7 @@ int gocp_energy_static(const gocp_problem* p, const void* psi, void* hpsi, doubl
  * staging wait of the staged H psi kernel gave up (after 2 s, or after
  * GOCP_STAGE_WAIT_NS nanoseconds when that environment variable is set, at
  * once when it is 0; the H psi and energy of that call are then undefined,
- * later calls are not affected).  Bit 2: a grid-wide barrier between the steps of a persistent
- * Taylor or adjoint chain gave up after 2 s (that chain's results are then
- * undefined).  Synchronises `stream`. */
+ * later calls are not affected).  Synchronises `stream`. */
 int gocp_device_errors(const gocp_problem* p, int* flags, void* stream);
 
 /* ---------------------------------------------------------------- serving */

@@ -48,7 +48,7 @@ struct DeviceTables {
   std::vector<void*> allocs;
   double* scratch = nullptr;
   size_t scratch_doubles = 0;
-  unsigned int* counters = nullptr;  // kMaxChunks + 16 (the last 8: kMaxChunks + 8, + 9 the chain barrier)
+  unsigned int* counters = nullptr;  // kMaxChunks + 8
   double* scalars = nullptr;         // [0] E  [1] <psi|psi>  [2] Re<psi|H'psi>
   int32_t* stage_ops = nullptr;
   double* stage_theta = nullptr;
@@ -906,89 +906,6 @@ k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
           double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask, double* dpart) {
   adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask,
                   dpart);
-}
-
-// ------------------------------------------------------------ persistent chains
-//
-// Above the on-chip sizes a chain of P steps runs as one cooperative launch
-// (every block resident at once, which cudaLaunchCooperativeKernel checks)
-// that loops over the steps with a grid-wide barrier between them, instead
-// of P launches: the per-step body is the same (taylor_body, adjoint_body),
-// so the results are the same bit for bit.
-constexpr uint64_t kBarrierNs = 2000000000ull;   // 2 s
-constexpr int32_t kErrBarrierTimeout = 4;
-
-__device__ __forceinline__ uint64_t chain_now_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier: the last block to arrive resets the count and advances
-// the generation; the others wait for the generation to change, each wait
-// bounded by kBarrierNs, after which the block records bit 2 in err and the
-// chain stops (its results are then undefined).  Returns false then.
-// bar[0]: arrival count (zero at rest), bar[1]: generation.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int32_t* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    s_ok = 1;
-    volatile unsigned int* gen = bar + 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == nblocks - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const uint64_t t0 = chain_now_ns();
-      while (*gen == g) {
-        __nanosleep(64);
-        if (chain_now_ns() - t0 > kBarrierNs) {
-          atomicOr(err, kErrBarrierTimeout);
-          s_ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_taylor_chain_coop(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi, int32_t* err,
-                    uint32_t* mask, unsigned int* bar) {
-  for (int j = 0; j < n_ops; ++j) {
-    taylor_body<R>(tb, ops, coefs, j, psi, err, blockIdx.x, gridDim.x, mask);
-    if (j + 1 < n_ops && !grid_barrier(bar, gridDim.x, err)) return;
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kThreads)
-k_adjoint_chain_coop(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi, C_t<R>* lam,
-                     double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask,
-                     double* dpart, unsigned int* bar) {
-  for (int j = n_ops - 1; j >= 0; --j) {
-    adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask,
-                    dpart);
-    if (j > 0 && !grid_barrier(bar, gridDim.x, err)) return;
-  }
-}
-
-// The largest grid of `kernel` (kThreads threads) whose blocks are all
-// resident at once on the current device, or 0.
-int coop_grid_limit(const void* kernel, int sm_count) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return per_sm * sm_count;
 }
 
 // ------------------------------------------------------------ on-chip chains
@@ -2333,13 +2250,13 @@ int upload_problem(Problem& p) {
     need = std::max(need, (size_t)std::max(nchunks, 1) * kOpsPerBlock * (size_t)pool_lut_nbx(d->t.penum_max));
   d->scratch_doubles = need;
   if ((rc = dalloc(*d, &d->scratch, need, bytes))) return rc;
-  if ((rc = dalloc(*d, &d->counters, kMaxChunks + 16, bytes))) return rc;
+  if ((rc = dalloc(*d, &d->counters, kMaxChunks + 8, bytes))) return rc;
   if ((rc = dalloc(*d, &d->scalars, 16, bytes))) return rc;
   if ((rc = dalloc(*d, &d->err, 1, bytes))) return rc;
   if ((rc = dalloc(*d, &d->selected, 1, bytes))) return rc;
   if ((rc = dalloc(*d, &d->grads, std::max(M, 1), bytes))) return rc;
   if ((rc = dalloc(*d, &d->graw, std::max(nchunks * kOpsPerBlock, 1), bytes))) return rc;
-  cudaMemset(d->counters, 0, (kMaxChunks + 16) * sizeof(unsigned int));
+  cudaMemset(d->counters, 0, (kMaxChunks + 8) * sizeof(unsigned int));
   cudaMemset(d->err, 0, sizeof(int32_t));
   cudaMemset(d->scalars, 0, 16 * sizeof(double));
   p.device_bytes = bytes;
@@ -2574,27 +2491,9 @@ static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void
     count_launches(1);
     return cuda_status(cudaGetLastError(), "k_taylor_chain_smem");
   }
-  int grid = d.t.pool_lut ? grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm)
-                          : grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
+  const int grid = d.t.pool_lut ? grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm)
+                                : grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
   uint32_t* mask = tracked && d.t.pool_lut ? d.t.octmask : nullptr;
-  if (d.t.pool_lut && n_ops > 1) {   // one persistent launch for the whole chain
-    const int lim = coop_grid_limit((const void*)k_taylor_chain_coop<R>, d.sm_count);
-    if (lim > 0) {
-      grid = std::min(grid, lim);
-      DevTables tb = d.t;
-      const int32_t* ops_ = d_ops;
-      const double* coefs = d.coefs;
-      int n = n_ops;
-      C_t<R>* ps_ = (C_t<R>*)psi;
-      int32_t* err = d.err;
-      unsigned int* bar = d.counters + kMaxChunks + 8;
-      void* args[] = {&tb, &ops_, &coefs, &n, &ps_, &err, &mask, &bar};
-      ProfScope ps(GOCP_KERNEL_TAYLOR, st, 1);
-      cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_taylor_chain_coop<R>, grid, kThreads, args, 0, st);
-      count_launches(1);
-      return cuda_status(e, "k_taylor_chain_coop");
-    }
-  }
   DevTables tb = d.t;
   const double* coefs = d.coefs;
   int j = 0;
@@ -2758,29 +2657,6 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
     return rc;
   double* dpart = d.t.pool_lut ? d.dpart : nullptr;
   count_launches(1);   // k_residual (and k_octet_mask counts itself)
-  if (dpart && n_ops > 1) {   // one persistent launch for the whole sweep
-    const int lim = coop_grid_limit((const void*)k_adjoint_chain_coop<R>, d.sm_count);
-    if (lim >= grid) {   // the partials are laid out for `grid` blocks
-      DevTables tb = d.t;
-      const double* coefs = d.coefs;
-      int n = n_ops;
-      C_t<R>* ps_ = (C_t<R>*)psi;
-      C_t<R>* ls_ = (C_t<R>*)lam;
-      double* partials = d.scratch;
-      unsigned int* counter = d.counters + kMaxChunks + 2;
-      int32_t* err = d.err;
-      unsigned int* bar = d.counters + kMaxChunks + 8;
-      void* args[] = {&tb, &d_ops, &coefs, &n, &ps_, &ls_, &partials, &counter, &d_dE, &err, &mask, &dpart, &bar};
-      {
-        ProfScope ps(GOCP_KERNEL_ADJOINT, st, 2);
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_adjoint_chain_coop<R>, grid, kThreads, args, 0, st);
-        if (e != cudaSuccess) return cuda_status(e, "k_adjoint_chain_coop");
-        k_dtheta_reduce<<<n_ops, kThreads, 0, st>>>(dpart, grid, d_dE);
-      }
-      count_launches(2);
-      return cuda_status(cudaGetLastError(), "k_adjoint_chain_coop");
-    }
-  }
   DevTables tb = d.t;
   const double* coefs = d.coefs;
   int j = 0;

@@ -586,11 +586,12 @@ def test_onchip_chains_match_oracle(n_orb, n_elec, prec):
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
-def test_persistent_chain_matches_step_by_step(prec):
-    """Above the on-chip sizes a prepared state's chain runs as one persistent
-    launch with a grid barrier between steps; applying the same operators
-    one gocp_taylor_step at a time (one launch each) gives the same state bit
-    for bit (the per-pair arithmetic is the same), and both match the oracle."""
+def test_tracked_chain_matches_step_by_step(prec):
+    """Above the on-chip sizes a prepared state's chain walks the list of its
+    nonzero amplitudes (one launch per step, replayed as a graph); applying
+    the same operators one gocp_taylor_step at a time to the reference state
+    (each step enumerating the operator's pairs) gives the same state bit for
+    bit (the per-pair arithmetic is the same), and both match the oracle."""
     ints, h, tabs = _case(8, 8, "jw", 3)                  # 16 qubits
     p = gb.Problem.build(ints, 8, precision=prec, device=0)
     ops, th = draw_ansatz(len(tabs), 20, seed=4, theta_sigma=0.3)
@@ -603,6 +604,6 @@ def test_persistent_chain_matches_step_by_step(prec):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     want = sv.prepare_state(sv.basis_state(16, p.info["ref_index"]), tabs, ops, th)
-    _within(f"persistent {prec} psi", np.max(np.abs(_host(a) - want)), TOL[prec]["state"] * np.max(np.abs(want)))
+    _within(f"tracked chain {prec} psi", np.max(np.abs(_host(a) - want)), TOL[prec]["state"] * np.max(np.abs(want)))
     assert p.device_errors() == 0
     p.close()
