@@ -196,7 +196,12 @@ int gocp_reference_state(const gocp_problem* p, void* psi, void* stream);
  * psi' = sum_{m=0..5} theta^m/m! v_m (Eq. 5).  ops/theta are host or device
  * arrays per `mem`; ops must lie in [0, pool_size) (GOCP_EINVAL for host
  * arrays; device arrays are clamped and flagged, see gocp_device_errors).
- * n_ops may be 0. */
+ * n_ops may be 0.  A chain of several steps on a full-layout state of at
+ * most 128 KiB runs in one thread block over shared memory (complex64 by
+ * default); the environment variable GOCP_ONCHIP_CHAINS = "off" | "block" |
+ * "all" selects the grid kernels only, the one-block form, or that and a
+ * thread-block cluster's shared memory for states up to 2 MiB.  Every form
+ * gives the same state bit for bit. */
 int gocp_prepare_state(const gocp_problem* p, const int32_t* ops, const double* theta, int n_ops,
                        int mem, void* psi, void* stream);
 

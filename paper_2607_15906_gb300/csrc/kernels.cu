@@ -16,15 +16,20 @@
 // order, so a result does not depend on scheduling or on the batch.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "device.cuh"
 #include "internal.h"
 
 namespace gocp {
+
+namespace cg = cooperative_groups;
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -591,15 +596,15 @@ __device__ __forceinline__ uint32_t chain_begin(const ChainList& cl, int j, bool
 // computed once, by its base's entry if the base is listed, else by its
 // partner's; a pair with neither end listed is zero and stays zero; the
 // unlisted end of a computed pair joins the list when it becomes nonzero.
+// p1, p2: the amplitudes of b and b ^ x (wherever they are held).
 template <typename R>
-__device__ __forceinline__ void taylor_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph, C_t<R>* psi,
-                                            C_t<R>& o1, C_t<R>& o2) {
+__device__ __forceinline__ void taylor_pair_at(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph,
+                                               C_t<R>* p1, C_t<R>* p2, C_t<R>& o1, C_t<R>& o2) {
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  const uint32_t b2 = b ^ L.x;
   const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
   const uint32_t sg = __popc(b & L.z0) & 1u;
   const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-  C_t<R> v1 = psi[b], v2 = psi[b2];
+  C_t<R> v1 = *p1, v2 = *p2;
   C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
 #pragma unroll
   for (int m = 1; m <= 5; ++m) {
@@ -611,8 +616,14 @@ __device__ __forceinline__ void taylor_pair(const LutDev<R>& L, const R (&c)[6],
   }
   o1 = csub<R>(s1, e1);
   o2 = csub<R>(s2, e2);
-  psi[b] = o1;
-  psi[b2] = o2;
+  *p1 = o1;
+  *p2 = o2;
+}
+
+template <typename R>
+__device__ __forceinline__ void taylor_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph, C_t<R>* psi,
+                                            C_t<R>& o1, C_t<R>& o2) {
+  taylor_pair_at<R>(L, c, b, ph, psi + b, psi + (b ^ L.x), o1, o2);
 }
 
 template <typename R>
@@ -724,11 +735,12 @@ k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 // With `mask` set (nonzero octets of psi or lambda) a pair on which both are
 // zero is skipped -- it adds nothing to dE and stays zero -- and a computed
 // pair marks both of its octets.
+// p1, p2 / q1, q2: the psi / lambda amplitudes of b and b ^ x.
 template <typename R>
-__device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph,
-                                               C_t<R>* psi, C_t<R>* lam, C_t<R> (&out)[4]) {
+__device__ __forceinline__ double adjoint_pair_at(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph,
+                                                  C_t<R>* p1, C_t<R>* p2, C_t<R>* q1p, C_t<R>* q2p,
+                                                  C_t<R> (&out)[4]) {
   const uint32_t phx = L.fx & 7u, sgx = (L.fx >> 3) & 1u;
-  const uint32_t b2 = b ^ L.x;
   const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
   const uint32_t sg = __popc(b & L.z0) & 1u;
   const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
@@ -738,23 +750,30 @@ __device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[
   const R cd = c[1] * mu + c[3] * mu2;
   const R inv = R(1) / (cc * cc - sc * sc * mu);
   const R sd1 = sc * d1, sd2 = sc * d2;
-  const C_t<R> u1 = psi[b], u2 = psi[b2];
+  const C_t<R> u1 = *p1, u2 = *p2;
   const C_t<R> q1 = cscale<R>(csub<R>(cscale<R>(u1, cc), cscale<R>(u2, sd1)), inv);
   const C_t<R> q2 = cscale<R>(csub<R>(cscale<R>(u2, cc), cscale<R>(u1, sd2)), inv);
   const C_t<R> t1 = cadd<R>(cscale<R>(q1, cd), cscale<R>(q2, cc * d1));
   const C_t<R> t2 = cadd<R>(cscale<R>(q2, cd), cscale<R>(q1, cc * d2));
-  const C_t<R> l1v = lam[b], l2v = lam[b2];
+  const C_t<R> l1v = *q1p, l2v = *q2p;
   // the pair's term of 2 Re<lambda|T' psi>, formed in R (one conversion)
   const double v = 2.0 * (double)(l1v.x * t1.x + l1v.y * t1.y + l2v.x * t2.x + l2v.y * t2.y);
   out[0] = q1;
   out[1] = q2;
   out[2] = cadd<R>(cscale<R>(l1v, cc), cscale<R>(l2v, sd2));
   out[3] = cadd<R>(cscale<R>(l1v, sd1), cscale<R>(l2v, cc));
-  psi[b] = out[0];
-  psi[b2] = out[1];
-  lam[b] = out[2];
-  lam[b2] = out[3];
+  *p1 = out[0];
+  *p2 = out[1];
+  *q1p = out[2];
+  *q2p = out[3];
   return v;
+}
+
+template <typename R>
+__device__ __forceinline__ double adjoint_pair(const LutDev<R>& L, const R (&c)[6], uint32_t b, uint32_t ph,
+                                               C_t<R>* psi, C_t<R>* lam, C_t<R> (&out)[4]) {
+  const uint32_t b2 = b ^ L.x;
+  return adjoint_pair_at<R>(L, c, b, ph, psi + b, psi + b2, lam + b, lam + b2, out);
 }
 
 // dpart set: each block writes its partial of dE_j to dpart[j nb + bid]
@@ -922,6 +941,7 @@ k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* 
 // the block over shared memory instead of a grid launch.
 constexpr int kSmemThreads = 1024;
 constexpr uint32_t kSmemStateBytes = 128u << 10;
+constexpr uint32_t kSmemDescBytes = 16u << 10;   // staged step descriptors (kStepChunk StepDesc)
 
 template <typename R>
 __device__ __forceinline__ void smem_copy_in(C_t<R>* dst, const C_t<R>* src, uint32_t dim) {
@@ -937,6 +957,50 @@ __device__ __forceinline__ void smem_copy_out(C_t<R>* dst, const C_t<R>* src, ui
     reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
 }
 
+template <typename R>
+__device__ __forceinline__ bool cz(const C_t<R>& v) { return v.x == R(0) && v.y == R(0); }
+
+// One step's operator, staged in shared memory ahead of the steps that use
+// it, so that a step reads no descriptor from global memory.
+template <typename R>
+struct StepDesc {
+  LutDev<R> L;
+  PairEnum E;
+  R c[6];     // theta^m / m!, m = 0..5
+  int valid;  // 0: the operator index was out of range (the step is the identity)
+};
+constexpr int kStepChunk = 64;   // steps staged at a time
+static_assert(kStepChunk * sizeof(StepDesc<double>) <= (16u << 10), "staged steps fit kSmemDescBytes");
+
+template <typename T>
+__device__ __forceinline__ void copy_words(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "word copy");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int w = (int)(threadIdx.x & 31); w < (int)(sizeof(T) / 4); w += 32) d[w] = s[w];
+}
+
+// sd[i] = step j0 + i for i < j1 - j0 (one warp per step); flags an
+// out-of-range operator in err when `flag`.  Ends with a block barrier.
+template <typename R>
+__device__ void stage_steps(const DevTables& tb, const int32_t* ops, const double* coefs, int j0, int j1,
+                            StepDesc<R>* sd, int32_t* err, bool flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < j1 - j0; i += kSmemThreads / 32) {
+    const int j = j0 + i, op = ops[j];
+    const bool ok = op >= 0 && op < tb.M;
+    if (lane == 0) sd[i].valid = ok ? 1 : 0;
+    if (!ok) {
+      if (flag && lane == 0) atomicOr(err, 1);
+      continue;
+    }
+    copy_words(&sd[i].L, ((const LutDev<R>*)tb.plut) + op);
+    copy_words(&sd[i].E, tb.penum + op);
+    if (lane < 6) sd[i].c[lane] = (R)coefs[6 * j + lane];
+  }
+  __syncthreads();
+}
+
 // psi <- T(theta_{P-1} A_{ops[P-1]}) ... T(theta_0 A_{ops[0]}) psi, LUT pools
 // only, by one block of kSmemThreads threads with the state in sp (shared
 // memory).  With mask set, also writes the exact nonzero-octet mask of the
@@ -945,22 +1009,22 @@ template <typename R>
 __device__ void taylor_chain_smem_body(const DevTables& tb, const int32_t* ops, const double* coefs, int n_ops,
                                        C_t<R>* psi, int32_t* err, uint32_t* mask, C_t<R>* sp) {
   const uint32_t dim = 1u << tb.n;
+  StepDesc<R>* sd = reinterpret_cast<StepDesc<R>*>(sp + dim);
   smem_copy_in<R>(sp, psi, dim);
-  __syncthreads();
   for (int j = 0; j < n_ops; ++j) {
-    const int op = ops[j];
-    if (op < 0 || op >= tb.M) {   // acts as the identity, flagged
-      if (threadIdx.x == 0) atomicOr(err, 1);
-      continue;
-    }
-    const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];
-    const PairEnum& E = tb.penum[op];
+    if (j % kStepChunk == 0) stage_steps<R>(tb, ops, coefs, j, min(n_ops, j + kStepChunk), sd, err, true);
+    const StepDesc<R>& D = sd[j % kStepChunk];
+    if (!D.valid) continue;   // acts as the identity, flagged
+    const LutDev<R>& L = D.L;
+    const PairEnum& E = D.E;
     R c[6];
-    step_coefs<R>(coefs, j, c);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) c[m] = D.c[m];
     const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
     for (uint32_t q = threadIdx.x; q < count; q += kSmemThreads) {
       uint32_t ph;
       const uint32_t b = enum_pair(E, q, &ph);
+      if (cz<R>(sp[b]) && cz<R>(sp[b ^ L.x])) continue;   // T maps (0, 0) to (0, 0)
       C_t<R> o1, o2;
       taylor_pair<R>(L, c, b, ph, sp, o1, o2);
     }
@@ -997,27 +1061,30 @@ __device__ void adjoint_chain_smem_body(const DevTables& tb, const int32_t* ops,
   __shared__ double s_red[kSmemThreads / 32];
   const uint32_t dim = 1u << tb.n;
   C_t<R>* sl = sp + dim;
+  StepDesc<R>* sd = reinterpret_cast<StepDesc<R>*>(sl + dim);
   smem_copy_in<R>(sp, psi, dim);
   smem_copy_in<R>(sl, lam, dim);
-  __syncthreads();
   for (int j = n_ops - 1; j >= 0; --j) {
-    const int op = ops[j];
-    if (op < 0 || op >= tb.M) {
-      if (threadIdx.x == 0) {
-        atomicOr(err, 1);
-        dtheta[j] = 0.0;
-      }
+    const int jc = j - j % kStepChunk;   // first step of j's chunk
+    if (j == n_ops - 1 || j % kStepChunk == kStepChunk - 1)
+      stage_steps<R>(tb, ops, coefs, jc, min(n_ops, jc + kStepChunk), sd, err, true);
+    const StepDesc<R>& D = sd[j - jc];
+    if (!D.valid) {
+      if (threadIdx.x == 0) dtheta[j] = 0.0;
       continue;
     }
-    const LutDev<R>& L = ((const LutDev<R>*)tb.plut)[op];
-    const PairEnum& E = tb.penum[op];
+    const LutDev<R>& L = D.L;
+    const PairEnum& E = D.E;
     R c[6];
-    step_coefs<R>(coefs, j, c);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) c[m] = D.c[m];
     const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
     double v = 0.0;
     for (uint32_t q = threadIdx.x; q < count; q += kSmemThreads) {
       uint32_t ph;
-      const uint32_t b = enum_pair(E, q, &ph);
+      const uint32_t b = enum_pair(E, q, &ph), b2 = b ^ L.x;
+      // psi and lambda zero at both ends: nothing to add, and they stay zero
+      if (cz<R>(sp[b]) && cz<R>(sp[b2]) && cz<R>(sl[b]) && cz<R>(sl[b2])) continue;
       C_t<R> o[4];
       v += adjoint_pair<R>(L, c, b, ph, sp, sl, o);
     }
@@ -2274,10 +2341,264 @@ void free_device(Problem& p) {
   p.dev = nullptr;
 }
 
+// Which on-chip chain forms may run: GOCP_ONCHIP_CHAINS = "all" (one block
+// and clusters), "block" (one block only), "off" (the grid kernels only);
+// default "block" for complex64 and "off" for complex128, whose FP64
+// arithmetic is better spread over every SM than held in a few.
+enum { kOnchipOff = 0, kOnchipBlock = 1, kOnchipAll = 2 };
+int onchip_mode(int precision) {
+  const char* e = std::getenv("GOCP_ONCHIP_CHAINS");
+  if (e && *e) {
+    if (!std::strcmp(e, "all")) return kOnchipAll;
+    if (!std::strcmp(e, "block")) return kOnchipBlock;
+    if (!std::strcmp(e, "off")) return kOnchipOff;
+  }
+  return precision == GOCP_C64 ? kOnchipBlock : kOnchipOff;
+}
+
+// ---- chains in cluster shared memory (DSMEM)
+//
+// A state too large for one block's shared memory but not for a cluster's
+// (kClusterMax blocks x kSmemStateBytes: 2 MiB) is spread over the blocks of
+// one thread-block cluster: block r holds amplitudes [r S, (r + 1) S), S =
+// 2^n / C.  Each step splits the operator's enumerated touched pairs over
+// the whole cluster; a thread reaches the two ends of its pair in whichever
+// block holds them (distributed shared memory, through map_shared_rank) and
+// computes them with the same per-pair arithmetic (taylor_pair_at,
+// adjoint_pair_at), so the forward chain gives the same state bit for bit.
+// A cluster barrier separates the steps.  The backward sweep keeps psi and
+// lambda (two slices per block); each dE_j is the fixed-order sum of the
+// blocks' partials, gathered in block 0.
+constexpr int kClusterMax = 16;
+
+template <typename R>
+__device__ void taylor_chain_cluster_body(const DevTables& tb, const int32_t* ops, const double* coefs, int n_ops,
+                                          C_t<R>* psi, int32_t* err, uint32_t* mask, uint8_t* cs_raw) {
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t C = cl.num_blocks(), rank = cl.block_rank();
+  const uint32_t dim = 1u << tb.n, slice = dim / C;
+  const int shift = __ffs((int)slice) - 1;
+  C_t<R>* mine = reinterpret_cast<C_t<R>*>(cs_raw);
+  StepDesc<R>* sd = reinterpret_cast<StepDesc<R>*>(mine + slice);
+  smem_copy_in<R>(mine, psi + (size_t)rank * slice, slice);
+  cl.sync();
+  for (int j = 0; j < n_ops; ++j) {
+    if (j % kStepChunk == 0) stage_steps<R>(tb, ops, coefs, j, min(n_ops, j + kStepChunk), sd, err, rank == 0);
+    const StepDesc<R>& D = sd[j % kStepChunk];
+    if (!D.valid) continue;   // acts as the identity, flagged
+    const LutDev<R>& L = D.L;
+    const PairEnum& E = D.E;
+    R c[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) c[m] = D.c[m];
+    const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
+    for (uint32_t q = rank * kSmemThreads + threadIdx.x; q < count; q += C * kSmemThreads) {
+      uint32_t ph;
+      const uint32_t b = enum_pair(E, q, &ph), b2 = b ^ L.x;
+      C_t<R>* p1 = cl.map_shared_rank(mine + (b & (slice - 1u)), b >> shift);
+      C_t<R>* p2 = cl.map_shared_rank(mine + (b2 & (slice - 1u)), b2 >> shift);
+      if (cz<R>(*p1) && cz<R>(*p2)) continue;   // T maps (0, 0) to (0, 0)
+      C_t<R> o1, o2;
+      taylor_pair_at<R>(L, c, b, ph, p1, p2, o1, o2);
+    }
+    cl.sync();
+  }
+  smem_copy_out<R>(psi + (size_t)rank * slice, mine, slice);
+  if (mask) {   // the exact nonzero-octet mask of this block's slice
+    const uint32_t o_base = rank * (slice >> 3);
+    for (uint32_t o0 = 0; o0 < ((slice + 7u) >> 3); o0 += kSmemThreads) {
+      const uint32_t o = o0 + threadIdx.x;
+      bool nz = false;
+      if (o < (slice >> 3))
+        for (int i = 0; i < 8; ++i) nz |= mine[8u * o + i].x != R(0) || mine[8u * o + i].y != R(0);
+      const uint32_t word = __ballot_sync(0xffffffffu, nz);
+      if ((threadIdx.x & 31) == 0 && o < (slice >> 3)) mask[(o_base + o) >> 5] = word;
+    }
+  }
+  cl.sync();   // no block leaves while another may still read its shared memory
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1)
+k_taylor_chain_cluster(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi,
+                       int32_t* err, uint32_t* mask) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  taylor_chain_cluster_body<R>(tb, ops, coefs, n_ops, psi, err, mask, cs_raw);
+}
+
+template <typename R>
+__device__ void adjoint_chain_cluster_body(const DevTables& tb, const int32_t* ops, const double* coefs, int n_ops,
+                                           C_t<R>* psi, C_t<R>* lam, double* dtheta, int32_t* err,
+                                           uint8_t* cs_raw) {
+  __shared__ double s_red[kSmemThreads / 32];
+  __shared__ double s_part[kClusterMax];   // block 0's: the blocks' partials of dE_j
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t C = cl.num_blocks(), rank = cl.block_rank();
+  const uint32_t dim = 1u << tb.n, slice = dim / C;
+  const int shift = __ffs((int)slice) - 1;
+  C_t<R>* mp = reinterpret_cast<C_t<R>*>(cs_raw);
+  C_t<R>* ml = mp + slice;
+  StepDesc<R>* sd = reinterpret_cast<StepDesc<R>*>(ml + slice);
+  smem_copy_in<R>(mp, psi + (size_t)rank * slice, slice);
+  smem_copy_in<R>(ml, lam + (size_t)rank * slice, slice);
+  double* part0 = cl.map_shared_rank(s_part, 0u);
+  cl.sync();
+  for (int j = n_ops - 1; j >= 0; --j) {
+    const int jc = j - j % kStepChunk;
+    if (j == n_ops - 1 || j % kStepChunk == kStepChunk - 1)
+      stage_steps<R>(tb, ops, coefs, jc, min(n_ops, jc + kStepChunk), sd, err, rank == 0);
+    const StepDesc<R>& D = sd[j - jc];
+    if (!D.valid) {
+      if (rank == 0 && threadIdx.x == 0) dtheta[j] = 0.0;
+      continue;
+    }
+    const LutDev<R>& L = D.L;
+    const PairEnum& E = D.E;
+    R c[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) c[m] = D.c[m];
+    const uint32_t count = (uint32_t)E.ncodes << E.log2cnt;
+    double v = 0.0;
+    for (uint32_t q = rank * kSmemThreads + threadIdx.x; q < count; q += C * kSmemThreads) {
+      uint32_t ph;
+      const uint32_t b = enum_pair(E, q, &ph), b2 = b ^ L.x;
+      const uint32_t r1 = b >> shift, r2 = b2 >> shift, o1 = b & (slice - 1u), o2 = b2 & (slice - 1u);
+      C_t<R>* a1 = cl.map_shared_rank(mp + o1, r1);
+      C_t<R>* a2 = cl.map_shared_rank(mp + o2, r2);
+      C_t<R>* l1 = cl.map_shared_rank(ml + o1, r1);
+      C_t<R>* l2 = cl.map_shared_rank(ml + o2, r2);
+      if (cz<R>(*a1) && cz<R>(*a2) && cz<R>(*l1) && cz<R>(*l2)) continue;   // nothing to add, stays zero
+      C_t<R> o[4];
+      v += adjoint_pair_at<R>(L, c, b, ph, a1, a2, l1, l2, o);
+    }
+    const double w = __any_sync(0xffffffffu, v != 0.0) ? warp_sum(v) : 0.0;
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < kSmemThreads / 32; ++q) t += s_red[q];
+      part0[rank] = t;
+    }
+    cl.sync();   // every pair of step j done, every partial in block 0
+    if (rank == 0 && threadIdx.x == 0) {
+      double t = 0.0;
+      for (uint32_t r = 0; r < C; ++r) t += s_part[r];
+      dtheta[j] = t;
+    }
+    cl.sync();   // block 0 has read the partials before the next step writes them
+  }
+  smem_copy_out<R>(psi + (size_t)rank * slice, mp, slice);
+  smem_copy_out<R>(lam + (size_t)rank * slice, ml, slice);
+  cl.sync();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1)
+k_adjoint_chain_cluster(DevTables tb, const int32_t* ops, const double* coefs, int n_ops, C_t<R>* psi,
+                        C_t<R>* lam, double* dtheta, int32_t* err) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  adjoint_chain_cluster_body<R>(tb, ops, coefs, n_ops, psi, lam, dtheta, err, cs_raw);
+}
+
+// The same for items whose state(s) need a cluster: one cluster per item,
+// items[first + blockIdx.x / cluster size].
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_stage_forward_cluster(const BatchItemDev* items, int first) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  const BatchItemDev& it = items[first + blockIdx.x / cg::this_cluster().num_blocks()];
+  taylor_chain_cluster_body<R>(it.t, it.ops, it.coefs, it.n_ops, (C_t<R>*)it.psi, it.err, nullptr, cs_raw);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_stage_backward_cluster(const BatchItemDev* items, int first) {
+  extern __shared__ __align__(16) uint8_t cs_raw[];
+  const BatchItemDev& it = items[first + blockIdx.x / cg::this_cluster().num_blocks()];
+  adjoint_chain_cluster_body<R>(it.t, it.ops, it.coefs, it.n_ops, (C_t<R>*)it.psi, (C_t<R>*)it.lam, it.dtheta,
+                                it.err, cs_raw);
+}
+
+// Blocks of the cluster that holds `states` states of this problem in
+// shared memory (a power of two, 2 .. kClusterMax), or 0 when one block
+// does or none fits.
+template <typename R>
+int chain_cluster_blocks(const DeviceTables& d, int states) {
+  if (!d.t.pool_lut || onchip_mode(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128) < kOnchipAll) return 0;
+  const uint64_t bytes = ((uint64_t)states << d.t.n) * sizeof(C_t<R>);
+  if (bytes <= kSmemStateBytes) return 0;
+  for (int c = 2; c <= kClusterMax; c *= 2)
+    if (bytes <= (uint64_t)c * kSmemStateBytes && (1ull << d.t.n) % (uint64_t)c == 0) return c;
+  return 0;
+}
+
+// Whether one cluster of `blocks` blocks of `kernel` (kSmemThreads threads,
+// bytes of dynamic shared memory each) can be resident on this device.
+bool cluster_fits_query(const void* kernel, int blocks, size_t bytes) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+  cfg.blockDim = dim3(kSmemThreads, 1, 1);
+  cfg.dynamicSmemBytes = bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)blocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters > 0;
+}
+
+// cluster_fits_query, remembered per (device, kernel, blocks, bytes).
+bool cluster_fits(const void* kernel, int blocks, size_t bytes) {
+  struct Key {
+    int device;
+    const void* kernel;
+    int blocks;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<std::pair<Key, bool>> seen;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  for (const auto& e : seen)
+    if (e.first.device == device && e.first.kernel == kernel && e.first.blocks == blocks && e.first.bytes == bytes)
+      return e.second;
+  const bool ok = cluster_fits_query(kernel, blocks, bytes);
+  seen.push_back({Key{device, kernel, blocks, bytes}, ok});
+  return ok;
+}
+
+// Launches `kernel` as `clusters` clusters of `blocks` blocks (kSmemThreads
+// each, bytes of dynamic shared memory each).
+int launch_cluster(const void* kernel, int blocks, size_t bytes, void** args, cudaStream_t st, int clusters = 1) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(blocks * clusters), 1, 1);
+  cfg.blockDim = dim3(kSmemThreads, 1, 1);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)blocks;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cuda_status(cudaLaunchKernelExC(&cfg, kernel, args), "cluster chain launch");
+}
+
 // Whether the on-chip forward chain / backward sweep takes this problem.
 template <typename R>
 bool smem_chain_fits(const DeviceTables& d, int states) {
-  return d.t.pool_lut && ((uint64_t)states << d.t.n) * sizeof(C_t<R>) <= kSmemStateBytes;
+  return d.t.pool_lut && onchip_mode(sizeof(R) == 4 ? GOCP_C64 : GOCP_C128) >= kOnchipBlock &&
+         ((uint64_t)states << d.t.n) * sizeof(C_t<R>) <= kSmemStateBytes;
 }
 
 // Opts the on-chip chain kernels into kSmemStateBytes of dynamic shared
@@ -2293,16 +2614,23 @@ int smem_chain_optin() {
   if (device >= (int)done.size()) done.resize(device + 1, false);
   if (!done[device]) {
     e = cudaFuncSetAttribute(k_taylor_chain_smem<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemStateBytes);
+                             (int)(kSmemStateBytes + kSmemDescBytes));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_adjoint_chain_smem<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemStateBytes);
+                               (int)(kSmemStateBytes + kSmemDescBytes));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_stage_forward_all<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemStateBytes);
+                               (int)(kSmemStateBytes + kSmemDescBytes));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_stage_backward_all<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemStateBytes);
+                               (int)(kSmemStateBytes + kSmemDescBytes));
+    for (const void* k : {(const void*)k_taylor_chain_cluster<R>, (const void*)k_adjoint_chain_cluster<R>,
+                          (const void*)k_stage_forward_cluster<R>, (const void*)k_stage_backward_cluster<R>}) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSmemStateBytes + kSmemDescBytes));
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
     if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(on-chip chains)");
     done[device] = true;
   }
@@ -2482,14 +2810,36 @@ template <typename R>
 static int launch_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, bool tracked,
                                cudaStream_t st) {
   DeviceTables& d = *p.dev;
-  if (n_ops > 0 && smem_chain_fits<R>(d, 1)) {   // the whole chain in one block
+  // chains of several steps on chip (a single step gains nothing from
+  // loading and storing the whole state, and stays on the grid kernels)
+  if (n_ops > 1 && smem_chain_fits<R>(d, 1)) {   // the whole chain in one block
     int rc = smem_chain_optin<R>();
     if (rc) return rc;
     ProfScope ps(GOCP_KERNEL_TAYLOR, st, 1);
-    k_taylor_chain_smem<R><<<1, kSmemThreads, (size_t)sizeof(C_t<R>) << p.n_qubits, st>>>(
+    k_taylor_chain_smem<R><<<1, kSmemThreads, ((size_t)sizeof(C_t<R>) << p.n_qubits) + kSmemDescBytes, st>>>(
         d.t, d_ops, d.coefs, n_ops, (C_t<R>*)psi, d.err, tracked ? d.t.octmask : nullptr);
     count_launches(1);
     return cuda_status(cudaGetLastError(), "k_taylor_chain_smem");
+  }
+  if (n_ops > 1) {   // the whole chain in one cluster's shared memory
+    const int cb = chain_cluster_blocks<R>(d, 1);
+    int rc = cb > 0 ? smem_chain_optin<R>() : GOCP_OK;
+    if (rc) return rc;
+    const size_t bytes = cb > 0 ? ((sizeof(C_t<R>) << p.n_qubits) / cb + kSmemDescBytes) : 0;
+    if (cb > 0 && cluster_fits((const void*)k_taylor_chain_cluster<R>, cb, bytes)) {
+      DevTables tb = d.t;
+      const int32_t* ops_ = d_ops;
+      const double* coefs = d.coefs;
+      int n = n_ops;
+      C_t<R>* ps_ = (C_t<R>*)psi;
+      int32_t* err = d.err;
+      uint32_t* mk = tracked ? d.t.octmask : nullptr;
+      void* args[] = {&tb, &ops_, &coefs, &n, &ps_, &err, &mk};
+      ProfScope ps(GOCP_KERNEL_TAYLOR, st, 1);
+      rc = launch_cluster((const void*)k_taylor_chain_cluster<R>, cb, bytes, args, st);
+      count_launches(1);
+      return rc;
+    }
   }
   const int grid = d.t.pool_lut ? grid_for((uint64_t)d.t.penum_max, d.sm_count, kChainBlocksPerSm)
                                 : grid_for(1ull << (p.n_qubits - 1), d.sm_count, 8);
@@ -2638,10 +2988,31 @@ static int launch_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi
     int rc = smem_chain_optin<R>();
     if (rc) return rc;
     ProfScope ps(GOCP_KERNEL_ADJOINT, st, 1);
-    k_adjoint_chain_smem<R><<<1, kSmemThreads, (size_t)(2 * sizeof(C_t<R>)) << p.n_qubits, st>>>(
+    k_adjoint_chain_smem<R><<<1, kSmemThreads, ((size_t)(2 * sizeof(C_t<R>)) << p.n_qubits) + kSmemDescBytes,
+                              st>>>(
         d.t, d_ops, d.coefs, n_ops, (C_t<R>*)psi, (C_t<R>*)lam, d_dE, d.err);
     count_launches(1);
     return cuda_status(cudaGetLastError(), "k_adjoint_chain_smem");
+  }
+  {
+    const int cb = chain_cluster_blocks<R>(d, 2);
+    int rc = cb > 0 ? smem_chain_optin<R>() : GOCP_OK;
+    if (rc) return rc;
+    const size_t bytes = cb > 0 ? ((2 * sizeof(C_t<R>) << p.n_qubits) / cb + kSmemDescBytes) : 0;
+    if (cb > 0 && cluster_fits((const void*)k_adjoint_chain_cluster<R>, cb, bytes)) {   // the whole sweep in one cluster
+      count_launches(1);   // k_residual
+      DevTables tb = d.t;
+      const double* coefs = d.coefs;
+      int n = n_ops;
+      C_t<R>* ps_ = (C_t<R>*)psi;
+      C_t<R>* ls_ = (C_t<R>*)lam;
+      int32_t* err = d.err;
+      void* args[] = {&tb, &d_ops, &coefs, &n, &ps_, &ls_, &d_dE, &err};
+      ProfScope ps(GOCP_KERNEL_ADJOINT, st, 1);
+      rc = launch_cluster((const void*)k_adjoint_chain_cluster<R>, cb, bytes, args, st);
+      count_launches(1);
+      return rc;
+    }
   }
   const int grid = adjoint_grid(d);
   // nonzero octets of psi or lambda, kept valid by the sweep
@@ -2785,11 +3156,26 @@ size_t batch_desc_bytes(int n) { return (size_t)n * sizeof(BatchItemDev); }
 
 bool has_tiled_form(const Problem& p) { return p.dev && !p.sector && p.dev->t.n_pieces > 0; }
 
+namespace {
+
+// Blocks one on-chip stage item of this problem takes: 1 (one block's shared
+// memory), 2..16 (one cluster), or 0 (the per-step stages).
+template <typename R>
+int stage_blocks(const Problem& p, int kind) {
+  const int states = kind == STAGE_BACKWARD_ALL ? 2 : 1;
+  if (smem_chain_fits<R>(*p.dev, states)) return 1;
+  const int cb = chain_cluster_blocks<R>(*p.dev, states);
+  if (cb <= 0 || smem_chain_optin<R>() != GOCP_OK) return 0;
+  const void* k = kind == STAGE_BACKWARD_ALL ? (const void*)k_stage_backward_cluster<R>
+                                             : (const void*)k_stage_forward_cluster<R>;
+  return cluster_fits(k, cb, ((size_t)states * sizeof(C_t<R>) << p.n_qubits) / cb + kSmemDescBytes) ? cb : 0;
+}
+
+}  // namespace
+
 bool stage_onchip(const Problem& p, int kind) {
   if (!p.dev || p.sector) return false;
-  const int states = kind == STAGE_BACKWARD_ALL ? 2 : 1;
-  return p.precision == GOCP_C64 ? smem_chain_fits<float>(*p.dev, states)
-                                 : smem_chain_fits<double>(*p.dev, states);
+  return (p.precision == GOCP_C64 ? stage_blocks<float>(p, kind) : stage_blocks<double>(p, kind)) > 0;
 }
 
 namespace {
@@ -2807,8 +3193,18 @@ int item_blocks(const Problem& p, int kind) {
 }
 
 template <typename R>
-int launch_stage_typed(int kind, const StageItem* items, int n, void* host_desc, void* dev_desc,
+int launch_stage_typed(int kind, const StageItem* items_in, int n, void* host_desc, void* dev_desc,
                        cudaStream_t st, int64_t* launches) {
+  // on-chip stages: items ordered by the blocks each takes (one launch per size)
+  std::vector<StageItem> sorted;
+  const StageItem* items = items_in;
+  if (kind == STAGE_FORWARD_ALL || kind == STAGE_BACKWARD_ALL) {
+    sorted.assign(items_in, items_in + n);
+    std::stable_sort(sorted.begin(), sorted.end(), [&](const StageItem& a, const StageItem& b) {
+      return stage_blocks<R>(*a.prob, kind) < stage_blocks<R>(*b.prob, kind);
+    });
+    items = sorted.data();
+  }
   BatchItemDev* hd = (BatchItemDev*)host_desc;
   BatchIndex ix;
   ix.n = n;
@@ -2866,12 +3262,33 @@ int launch_stage_typed(int kind, const StageItem* items, int n, void* host_desc,
       break;
     case STAGE_FORWARD_ALL:
     case STAGE_BACKWARD_ALL: {
+      // items ordered by blocks (1 first, then clusters of 2, 4, 8, 16):
+      // one launch per size
       if ((rc = smem_chain_optin<R>())) return rc;
-      if (kind == STAGE_FORWARD_ALL)
-        k_stage_forward_all<R><<<n, kSmemThreads, kSmemStateBytes, st>>>(dd);
-      else
-        k_stage_backward_all<R><<<n, kSmemThreads, kSmemStateBytes, st>>>(dd);
-      *launches += 1;
+      int i = 0;
+      while (i < n) {
+        const int nb = stage_blocks<R>(*items[i].prob, kind);
+        int e = i;
+        while (e < n && stage_blocks<R>(*items[e].prob, kind) == nb) ++e;
+        if (nb <= 0) return fail(GOCP_EINVAL, "on-chip stage item does not fit");
+        if (nb == 1) {
+          if (kind == STAGE_FORWARD_ALL)
+            k_stage_forward_all<R><<<e - i, kSmemThreads, kSmemStateBytes + kSmemDescBytes, st>>>(dd + i);
+          else
+            k_stage_backward_all<R><<<e - i, kSmemThreads, kSmemStateBytes + kSmemDescBytes, st>>>(dd + i);
+          if ((rc = cuda_status(cudaGetLastError(), "on-chip stage"))) return rc;
+        } else {
+          const BatchItemDev* base = dd;
+          int first = i;
+          void* args[] = {&base, &first};
+          if ((rc = launch_cluster(kind == STAGE_FORWARD_ALL ? (const void*)k_stage_forward_cluster<R>
+                                                             : (const void*)k_stage_backward_cluster<R>,
+                                   nb, kSmemStateBytes + kSmemDescBytes, args, st, e - i)))
+            return rc;
+        }
+        *launches += 1;
+        i = e;
+      }
       break;
     }
     default:

@@ -557,13 +557,18 @@ def test_larger_n_30q_c64():
 
 
 @pytest.mark.parametrize("n_orb,n_elec,prec", [(5, 4, "c128"), (6, 6, "c64"), (6, 6, "c128"), (7, 6, "c64"),
-                                               (7, 6, "c128")])
-def test_onchip_chains_match_oracle(n_orb, n_elec, prec):
+                                               (7, 6, "c128"), (8, 8, "c64"), (8, 8, "c128")])
+def test_onchip_chains_match_oracle(n_orb, n_elec, prec, monkeypatch):
     """Forward chains of states up to 128 KiB (14 qubits complex64, 13
     complex128) and backward sweeps whose psi and lambda together fit 128 KiB
-    (13 / 12 qubits) run as one block over shared memory; the larger cases
-    here take the grid kernels.  States, E and dE/dtheta against the oracle
-    (Eq. 5, 6; the adjoint of Eq. 1)."""
+    (13 / 12 qubits) run as one block over shared memory; larger ones, up to
+    2 MiB, in the distributed shared memory of one cluster of 2..16 blocks
+    (here: 14 qubits complex64 backward on 2 blocks, 14 complex128 forward /
+    backward on 2 / 4, 16 complex64 on 4 / 8, 16 complex128 on 8 / 16).
+    States, E and dE/dtheta against the oracle (Eq. 5, 6; the adjoint of
+    Eq. 1).  Every form is enabled here (GOCP_ONCHIP_CHAINS=all); by default
+    complex64 takes the one-block form and complex128 the grid kernels."""
+    monkeypatch.setenv("GOCP_ONCHIP_CHAINS", "all")
     ints, h, tabs = _case(n_orb, n_elec, "jw", n_orb)
     p = gb.Problem.build(ints, n_elec, precision=prec, device=0)
     n = 2 * n_orb
@@ -585,13 +590,20 @@ def test_onchip_chains_match_oracle(n_orb, n_elec, prec):
     p.close()
 
 
+@pytest.mark.parametrize("mode", ["default", "all"])
 @pytest.mark.parametrize("prec", ["c64", "c128"])
-def test_tracked_chain_matches_step_by_step(prec):
+def test_tracked_chain_matches_step_by_step(prec, mode, monkeypatch):
     """Above the on-chip sizes a prepared state's chain walks the list of its
     nonzero amplitudes (one launch per step, replayed as a graph); applying
     the same operators one gocp_taylor_step at a time to the reference state
     (each step enumerating the operator's pairs) gives the same state bit for
-    bit (the per-pair arithmetic is the same), and both match the oracle."""
+    bit (the per-pair arithmetic is the same), and both match the oracle.
+    mode "all": the prepared chain runs in one cluster (4 blocks complex64,
+    8 complex128)."""
+    if mode == "all":
+        monkeypatch.setenv("GOCP_ONCHIP_CHAINS", "all")
+    else:
+        monkeypatch.delenv("GOCP_ONCHIP_CHAINS", raising=False)
     ints, h, tabs = _case(8, 8, "jw", 3)                  # 16 qubits
     p = gb.Problem.build(ints, 8, precision=prec, device=0)
     ops, th = draw_ansatz(len(tabs), 20, seed=4, theta_sigma=0.3)
@@ -605,5 +617,29 @@ def test_tracked_chain_matches_step_by_step(prec):
     assert torch.equal(a, b)
     want = sv.prepare_state(sv.basis_state(16, p.info["ref_index"]), tabs, ops, th)
     _within(f"tracked chain {prec} psi", np.max(np.abs(_host(a) - want)), TOL[prec]["state"] * np.max(np.abs(want)))
+    assert p.device_errors() == 0
+    p.close()
+
+
+def test_cluster_chain_16_blocks_18q_c64(monkeypatch):
+    """An 18-qubit complex64 forward chain (2 MiB) runs in one cluster of 16
+    blocks: the prepared state against the oracle on its support (and no
+    other amplitude nonzero), and the same state as the step-by-step path."""
+    monkeypatch.setenv("GOCP_ONCHIP_CHAINS", "all")
+    ints, h, tabs = _case(9, 8, "jw", 2)
+    p = gb.Problem.build(ints, 8, precision="c64", device=0)
+    ops, th = draw_ansatz(len(tabs), 24, seed=6, theta_sigma=0.3)
+    a = p.new_states(1)[0]
+    p.prepare_state(ops, th, a)
+    b = p.new_states(1)[0]
+    p.reference_state(b)
+    for k, t in zip(ops, th):
+        p.taylor_step(int(k), float(t), b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    si, svals = sv.prepare_state_sparse(p.info["ref_index"], tabs, ops, th)
+    got = _host(a)
+    assert np.count_nonzero(got) == len(si)
+    _within("cluster 18q psi", np.max(np.abs(got[si] - svals)), TOL["c64"]["state"] * np.max(np.abs(svals)))
     assert p.device_errors() == 0
     p.close()

@@ -127,3 +127,39 @@ def test_admission_by_free_device_memory():
     assert st["arena_in_use"] == 0 and st["arena_peak"] >= 2 * reqs[-2][2].state_bytes()
     for (ea, da), (ep, dp) in zip(arena, pooled):
         assert ea == ep and np.array_equal(da, dp)
+
+
+@pytest.mark.parametrize("mode", ["default", "all"])
+def test_cluster_stage_requests(mode, monkeypatch):
+    """Requests of 16 and 18 qubits run their chains in one thread-block
+    cluster each (16 qubits complex64: 4 / 8 blocks, complex128: 8 / 16; 18
+    qubits complex64: a 16-block forward chain, per-step backward stages),
+    mixed with a small one-block request: the same results alone and in the
+    mix bit for bit, and the direct path's within the parity tolerances.
+    mode "default": the on-chip forms the library picks by default (one
+    block for complex64, none for complex128); "all": clusters too."""
+    if mode == "all":
+        monkeypatch.setenv("GOCP_ONCHIP_CHAINS", "all")
+    else:
+        monkeypatch.delenv("GOCP_ONCHIP_CHAINS", raising=False)
+    reqs = []
+    for i, (n, prec) in enumerate([(16, "c64"), (18, "c64"), (16, "c128"), (10, "c64")]):
+        ints = molecular_integrals(n // 2, seed=2000 + i, decay=True)
+        ne = 2 * (n // 4)
+        p = gb.Problem.build(ints, ne, precision=prec, device=0, colour=False)
+        ops, th = draw_ansatz(p.pool_size, 12 + 4 * i, seed=i, theta_sigma=0.2)
+        reqs.append((p, ops, th))
+    alone = []
+    with Server(hbm_budget_bytes=0, max_slots=16) as srv:
+        for (p, ops, th) in reqs:
+            alone.append(srv.result(srv.submit(p, ops, th)))
+    with Server(hbm_budget_bytes=0, max_slots=16) as srv:
+        tickets = [srv.submit(p, ops, th) for (p, ops, th) in reqs]
+        mixed = [srv.result(t) for t in tickets]
+    for (p, ops, th), (ea, da), (em, dm) in zip(reqs, alone, mixed):
+        assert ea == em and np.array_equal(da, dm)
+        e_d, de_d = p.energy_grad(ops, th)
+        tol = 1e-10 if p.precision == "c128" else 1e-6
+        assert abs(ea - e_d) <= tol * max(1.0, abs(e_d))
+        assert np.max(np.abs(da - de_d)) <= (1e-10 if p.precision == "c128" else 2e-6) * max(1.0, np.max(np.abs(de_d)))
+        assert p.device_errors() == 0
