@@ -33,6 +33,16 @@ __device__ __forceinline__ C_t<R> cscale(C_t<R> a, R s) { return cmake<R>(a.x * 
 template <typename R>
 __device__ __forceinline__ C_t<R> cconj(C_t<R> a) { return cmake<R>(a.x, -a.y); }
 
+// Start of one step of a chain launched with programmatic dependencies
+// (launch_chain): wait until the previous step's grid has finished and its
+// writes are visible, then let the next step's blocks be scheduled while this
+// one runs.  Both instructions do nothing in a kernel launched without such a
+// dependency.
+__device__ __forceinline__ void chain_step_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // An x-group (or generator) in LUT form, see LutForm:
 //   D(b) = (-1)^popc(b & z0) * lut[phi(b)],  phi(b) = sum_i (popc(b & v_i) & 1) << i,
 // with real weights only.  fx holds phi(x) (bits 0..2) and popc(x & z0) & 1

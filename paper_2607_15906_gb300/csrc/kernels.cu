@@ -718,6 +718,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_taylor5(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, int32_t* err,
           uint32_t* mask) {
+  chain_step_begin();
   taylor_body<R>(tb, ops, coefs, j, psi, err, blockIdx.x, gridDim.x, mask);
 }
 
@@ -923,6 +924,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_adjoint(DevTables tb, const int32_t* ops, const double* coefs, int j, C_t<R>* psi, C_t<R>* lam,
           double* partials, unsigned int* counter, double* dtheta, int32_t* err, uint32_t* mask, double* dpart) {
+  chain_step_begin();
   adjoint_body<R>(tb, ops, coefs, j, psi, lam, partials, counter, dtheta, err, blockIdx.x, gridDim.x, mask,
                   dpart);
 }
@@ -2708,13 +2710,24 @@ int launch_plain(const void* kernel, unsigned grid, unsigned block, int n, bool 
 
 }  // namespace
 
+// Whether consecutive steps of a chain graph are joined by programmatic
+// edges (GOCP_CHAIN_PDL=0 joins them by full completion instead).  Every
+// kernel passed to launch_chain starts with chain_step_begin(), so step j + 1
+// reads nothing before step j has finished either way; the programmatic edge
+// only lets its blocks be scheduled earlier.
+bool chain_pdl() {
+  const char* e = std::getenv("GOCP_CHAIN_PDL");
+  return !(e && !std::strcmp(e, "0"));
+}
+
 int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, int n, bool reverse, void** args,
                  const size_t* sizes, int nargs, int jidx, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (n <= 0) return GOCP_OK;
   count_launches(n);
+  const bool pdl = chain_pdl();
   std::string key((const char*)&kernel, sizeof(kernel));
-  const unsigned hdr[4] = {grid, block, (unsigned)n, reverse ? 1u : 0u};
+  const unsigned hdr[5] = {grid, block, (unsigned)n, reverse ? 1u : 0u, pdl ? 1u : 0u};
   key.append((const char*)hdr, sizeof(hdr));
   for (int i = 0; i < nargs; ++i)
     if (i != jidx) key.append((const char*)args[i], sizes[i]);
@@ -2726,7 +2739,8 @@ int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, 
       e.used = c.clock;
       return cuda_status(cudaGraphLaunch(e.exec, st), "chain graph launch");
     }
-  // build the graph: n kernel nodes in a line, node i with op index j(i)
+  // build the graph: n kernel nodes in a line, node i with op index j(i),
+  // each depending on the one before (programmatically where possible)
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) {
     cudaGetLastError();
@@ -2744,7 +2758,16 @@ int launch_chain(Problem& p, const void* kernel, unsigned grid, unsigned block, 
     kp.blockDim = dim3(block);
     kp.kernelParams = args;
     cudaGraphNode_t node;
-    ok = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp) == cudaSuccess;
+    ok = cudaGraphAddKernelNode(&node, g, nullptr, 0, &kp) == cudaSuccess;
+    if (ok && prev) {
+      cudaGraphEdgeData ed = {};
+      ed.from_port = cudaGraphKernelNodePortProgrammatic;
+      ed.type = cudaGraphDependencyTypeProgrammatic;
+      if (!pdl || cudaGraphAddDependencies(g, &prev, &node, &ed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        ok = cudaGraphAddDependencies(g, &prev, &node, nullptr, 1) == cudaSuccess;
+      }
+    }
     prev = node;
   }
   j = j_saved;

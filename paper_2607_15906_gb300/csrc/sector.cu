@@ -92,6 +92,7 @@ template <typename R>
 __global__ void __launch_bounds__(kSecThreads)
 k_sec_taylor(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, const int32_t* ops,
              const double* coefs, int j, C_t<R>* psi, int32_t* err) {
+  chain_step_begin();
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
@@ -367,6 +368,7 @@ k_sec_adjoint(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, co
               const double* coefs, int j, C_t<R>* psi, C_t<R>* lam, double* partials, unsigned int* counter,
               double* dtheta, int32_t* err) {
   __shared__ double tot[1];
+  chain_step_begin();
   const int op = ops[j];
   if (op < 0 || op >= tb.M) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
