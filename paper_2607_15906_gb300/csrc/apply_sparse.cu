@@ -329,6 +329,22 @@ __device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint
   }
 }
 
+// Zero test and sign flip of a weight.  For complex128 both work on the
+// bits with integer instructions: FP64 compares and negations run on the
+// FP64 pipe, narrow on this part, and there they would be executed for
+// every (amplitude, group) item.
+template <typename R>
+__device__ __forceinline__ bool is_nonzero(R v) {
+  if constexpr (sizeof(R) == 8) return (__double_as_longlong((double)v) << 1) != 0ll;
+  else return v != R(0);
+}
+template <typename R>
+__device__ __forceinline__ R flip_sign(R v, uint32_t neg) {
+  if constexpr (sizeof(R) == 8)
+    return (R)__longlong_as_double(__double_as_longlong((double)v) ^ ((long long)neg << 63));
+  else return neg ? -v : v;
+}
+
 // A compacted item: the output index k, the weight D(k) and the lane's
 // scaled amplitude.  A warp's buffer holds up to 32 (A + 1) items: at most
 // 31 wait after a flush and a group adds at most 32 A.
@@ -365,12 +381,12 @@ __device__ __forceinline__ void sp_lut_pack(const HLut<R>* __restrict__ L, const
     const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
                          ((uint32_t)(__popc(k & v2) & 1) << 2);
     const R d0 = __ldg(L->lut16 + phi);
-    const bool nz = valid[s] && d0 != R(0);
+    const bool nz = valid[s] && is_nonzero<R>(d0);
     const uint32_t m = __ballot_sync(0xffffffffu, nz);
     if (nz) {
       SpItem<R> e;
       e.k = k;
-      e.d = (__popc(k & h0.y) & 1) ? -d0 : d0;
+      e.d = flip_sign<R>(d0, (uint32_t)__popc(k & h0.y) & 1u);
       e.vx = vs[s].x;
       e.vy = vs[s].y;
       wb[cnt + (uint32_t)__popc(m & lt)] = e;
@@ -382,47 +398,78 @@ __device__ __forceinline__ void sp_lut_pack(const HLut<R>* __restrict__ L, const
 // One term-list group: D(k) = sum_t w_t (-1)^popc(k & z_t), real terms
 // [tb, tm), imaginary [tm, te); a paired group keeps one term of each pair
 // and D = (1 + sigma (-1)^popc(k & delta)) E(k), the factor 0 or 2.  Called
-// by every lane of the warp (the group is warp-uniform).
+// by every lane of the warp (the group is warp-uniform).  complex64 sums the
+// weights ws in FP32; complex128 sums their fixed-point copies wq exactly
+// with integer adds (D = (sum of all w) - 2 (sum of the w with odd parity))
+// and converts once, times wscale.
 template <typename R, uint32_t kOct, int A>
 __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const uint32_t* __restrict__ zs,
-                                         const R* __restrict__ ws, const uint32_t (&ks)[A],
+                                         const R* __restrict__ ws, const long long* __restrict__ wq,
+                                         const double wscale, const uint32_t (&ks)[A],
                                          const C_t<R> (&vs)[A], const bool (&valid)[A],
                                          unsigned long long* acc) {
   const uint4 g0 = __ldg(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
   const uint2 g1 = __ldg(reinterpret_cast<const uint2*>(&G->delta)); // delta, neg
-  uint32_t k[A];
-  R f[A];
+  uint32_t k[A], fz[A];   // fz: the factor 0, 1 or 2
   bool on = false;
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     k[s] = ks[s] ^ g0.x;
-    f[s] = R(1);
+    fz[s] = 1u;
     if (g1.x) {
       const uint32_t p = __popc(k[s] & g1.x) & 1u;
-      f[s] = (g1.y ? p : p ^ 1u) ? R(2) : R(0);
+      fz[s] = (g1.y ? p : p ^ 1u) ? 2u : 0u;
     }
-    on |= valid[s] && f[s] != R(0);
+    on |= valid[s] && fz[s] != 0u;
   }
   if (!__any_sync(0xffffffffu, on)) return;
   R dr[A], di[A];
+  if constexpr (sizeof(R) == 8) {
+    unsigned long long ar = 0ull, ai = 0ull, odr[A], odi[A];   // modulo 2^64; the results fit
 #pragma unroll
-  for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
-  for (uint32_t t = g0.y; t < g0.z; ++t) {
-    const uint32_t z = __ldg(zs + t);
-    const R w = __ldg(ws + t);
+    for (int s = 0; s < A; ++s) odr[s] = odi[s] = 0ull;
+    for (uint32_t t = g0.y; t < g0.z; ++t) {
+      const uint32_t z = __ldg(zs + t);
+      const unsigned long long w = (unsigned long long)__ldg(wq + t);
+      ar += w;
 #pragma unroll
-    for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
-  }
-  for (uint32_t t = g0.z; t < g0.w; ++t) {
-    const uint32_t z = __ldg(zs + t);
-    const R w = __ldg(ws + t);
+      for (int s = 0; s < A; ++s)
+        if (__popc(k[s] & z) & 1) odr[s] += w;
+    }
+    for (uint32_t t = g0.z; t < g0.w; ++t) {
+      const uint32_t z = __ldg(zs + t);
+      const unsigned long long w = (unsigned long long)__ldg(wq + t);
+      ai += w;
 #pragma unroll
-    for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
+      for (int s = 0; s < A; ++s)
+        if (__popc(k[s] & z) & 1) odi[s] += w;
+    }
+#pragma unroll
+    for (int s = 0; s < A; ++s) {
+      dr[s] = (R)(__ll2double_rn((long long)(ar - 2ull * odr[s])) * wscale);
+      di[s] = (R)(__ll2double_rn((long long)(ai - 2ull * odi[s])) * wscale);
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
+    for (uint32_t t = g0.y; t < g0.z; ++t) {
+      const uint32_t z = __ldg(zs + t);
+      const R w = __ldg(ws + t);
+#pragma unroll
+      for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
+    }
+    for (uint32_t t = g0.z; t < g0.w; ++t) {
+      const uint32_t z = __ldg(zs + t);
+      const R w = __ldg(ws + t);
+#pragma unroll
+      for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
+    }
   }
 #pragma unroll
   for (int s = 0; s < A; ++s) {
-    const R a = dr[s] * f[s], b = di[s] * f[s];
-    if (valid[s] && f[s] != R(0) && (a != R(0) || b != R(0)))
+    const R f = fz[s] == 2u ? R(2) : R(1);
+    const R a = dr[s] * f, b = di[s] * f;
+    if (valid[s] && fz[s] != 0u && (is_nonzero<R>(a) || is_nonzero<R>(b)))
       acc_add<kOct>(acc, k[s], fx_prod<R>(a * vs[s].x - b * vs[s].y), fx_prod<R>(a * vs[s].y + b * vs[s].x));
   }
 }
@@ -567,6 +614,8 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(blob + sizeof(TiledHead) + hd.y * sizeof(HLut<R>));
         const uint32_t* zs = reinterpret_cast<const uint32_t*>(blob + hd.z);
         const R* ws = reinterpret_cast<const R*>(blob + hd.w);
+        const long long* wq =
+            sizeof(R) == 8 ? reinterpret_cast<const long long*>(a.wfix + pc.off + hd.w) : nullptr;
         uint32_t ks[A];
         C_t<R> vs[A];
         bool valid[A];
@@ -606,7 +655,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         }
         // the term-list groups fill the blob from the LUT groups to z_off
         const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
-        for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, ks, vs, valid, acc);
+        for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, wq, a.wscale, ks, vs, valid, acc);
       }
     }
     if (cnt) sp_flush<R, kOct>(wb, (uint32_t)lane, (uint32_t)lane < cnt, acc);   // the rest, fewer than 32
@@ -735,6 +784,7 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
   constexpr int LB = TiledBits<R>::LB;
   if (a.n < LB || !lv.toff || !lv.aidx || !lv.aval || !lv.alen || !lv.acounts || !lv.amax || a.max_amps > lv.acap)
     return fail(GOCP_EINVAL, "scatter H psi needs the amplitude list");
+  if (sizeof(R) == 8 && !a.wfix) return fail(GOCP_EINVAL, "scatter H psi (complex128) needs the fixed-point weights");
   a.amax = lv.amax;
   a.aidx = lv.aidx;
   a.aval = reinterpret_cast<const C_t<R>*>(lv.aval);

@@ -694,6 +694,8 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     s.max_amps = max_amps;
     s.hbound = t.hbound;
     s.dmax = t.dmax;
+    s.wfix = t.twfix;
+    s.wscale = t.twscale;
     s.dz = t.dz;
     s.dw = reinterpret_cast<const R*>(t.dw);
     s.nd = t.nd;

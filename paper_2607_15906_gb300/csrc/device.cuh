@@ -263,6 +263,11 @@ struct DevTables {
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
   const uint32_t* tporder = nullptr;   // piece indices by descending blob size
+  // complex128: the blobs' term-list weights as 64-bit fixed-point integers
+  // round(w 2^F_w), each at its weight's offset in tblob (elsewhere zero),
+  // and twscale = 2^-F_w; F_w keeps every group's sum of |w| below 2^61
+  const uint8_t* twfix = nullptr;
+  double twscale = 0.0;
   uint32_t* octmask = nullptr;
   uint32_t* tflags = nullptr;   // tiled form: one bit per tile (scratch)
   // second mask of the same size, for the adjoint sweep (psi and lambda)
@@ -531,6 +536,8 @@ struct SparseArgs {
   const unsigned long long* amax;   // max(|Re|, |Im|) of the listed amplitudes (double bits)
   double hbound;                // DevTables::hbound
   double dmax;                  // DevTables::dmax
+  const uint8_t* wfix;          // DevTables::twfix (complex128)
+  double wscale;                // DevTables::twscale
   uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
   const uint32_t* dz;
   const R* dw;

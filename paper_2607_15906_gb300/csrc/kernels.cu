@@ -1926,10 +1926,53 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   for (size_t i = 0; i < porder.size(); ++i) porder[i] = (uint32_t)i;
   std::stable_sort(porder.begin(), porder.end(),
                    [&](uint32_t a, uint32_t b) { return pieces[a].bytes > pieces[b].bytes; });
+  // complex128: the term weights again, as fixed-point integers at their
+  // own offsets (the scatter kernel sums them exactly with integer adds)
+  std::vector<uint8_t> wfix;
+  int fw = 0;
+  if constexpr (sizeof(R) == 8) {
+    double wmax = 0.0;   // largest sum of |w| over a group's real or imaginary stored terms
+    for (const TiledPiece& pc : pieces) {
+      TiledHead h;
+      std::memcpy(&h, blob.data() + pc.off, sizeof(h));
+      const TiledGroup* tg = reinterpret_cast<const TiledGroup*>(blob.data() + pc.off + sizeof(TiledHead) +
+                                                                 h.n_lut * sizeof(HLut<R>));
+      const int ntg = (int)((h.z_off - sizeof(TiledHead) - h.n_lut * sizeof(HLut<R>)) / sizeof(TiledGroup));
+      const R* w = reinterpret_cast<const R*>(blob.data() + pc.off + h.w_off);
+      for (int g = 0; g < ntg; ++g) {
+        double sr = 0.0, si = 0.0;
+        for (uint32_t t = tg[g].tb; t < tg[g].tm; ++t) sr += std::fabs((double)w[t]);
+        for (uint32_t t = tg[g].tm; t < tg[g].te; ++t) si += std::fabs((double)w[t]);
+        wmax = std::max(wmax, std::max(sr, si));
+      }
+    }
+    if (wmax > 0.0) {
+      int e;
+      std::frexp(wmax, &e);   // wmax < 2^e
+      fw = 61 - e;
+    }
+    wfix.assign(blob.size(), 0);
+    for (const TiledPiece& pc : pieces) {
+      TiledHead h;
+      std::memcpy(&h, blob.data() + pc.off, sizeof(h));
+      for (uint32_t o = h.w_off; o + sizeof(R) <= pc.bytes; o += sizeof(R)) {
+        double v;
+        std::memcpy(&v, blob.data() + pc.off + o, sizeof(v));
+        const long long q = std::llround(std::ldexp(v, fw));
+        std::memcpy(wfix.data() + pc.off + o, &q, sizeof(q));
+      }
+    }
+  }
   uint8_t* dblob;
   TiledPiece* dpiece;
   uint32_t* dporder;
   int rc;
+  if (!wfix.empty()) {
+    uint8_t* dw;
+    if ((rc = upload(d, &dw, wfix, bytes))) return rc;
+    d.t.twfix = dw;
+    d.t.twscale = std::ldexp(1.0, -fw);
+  }
   if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
       (rc = upload(d, &dporder, porder, bytes)) ||
       (rc = dalloc(d, &d.t.tflags, ((size_t)1 << (n - LB)) / 32 + 1, bytes)) ||
