@@ -53,16 +53,12 @@ namespace {
 constexpr int kAmpBlock = 256;   // listing passes: one amplitude word (4 octets) per thread
 constexpr uint32_t kUnitBatch = 4;   // scatter work units per claim
 
-// Nonzero source amplitudes per lane per work unit, and whether LUT-group
-// items go through the per-warp compaction buffer: complex64 two amplitudes,
-// direct atomics (its integer work, not the products, bounds it); complex128
-// one amplitude, compacted (measured on the 24-qubit ADAPT state: 2.61 ms
-// and 11.6 ms per call, against 15.4 ms with two amplitudes and direct
-// atomics).
+// Nonzero source amplitudes per lane per work unit: complex64 two, with
+// FP32 products added at once; complex128 one, with integer products of the
+// fixed-point weights and amplitudes, its LUT-group items compacted per warp
+// (see sp_lut_q).
 template <typename R>
 __host__ __device__ constexpr int sp_amps() { return sizeof(R) == 4 ? 2 : 1; }
-template <typename R>
-__host__ __device__ constexpr bool sp_compact() { return sizeof(R) == 8; }
 
 // One block per SM: 1024 threads for complex64 (64 registers), 512 for
 // complex128 (128 registers).
@@ -329,83 +325,131 @@ __device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint
   }
 }
 
-// Zero test and sign flip of a weight.  For complex128 both work on the
-// bits with integer instructions: FP64 compares and negations run on the
-// FP64 pipe, narrow on this part, and there they would be executed for
-// every (amplitude, group) item.
-template <typename R>
-__device__ __forceinline__ bool is_nonzero(R v) {
-  if constexpr (sizeof(R) == 8) return (__double_as_longlong((double)v) << 1) != 0ll;
-  else return v != R(0);
-}
-template <typename R>
-__device__ __forceinline__ R flip_sign(R v, uint32_t neg) {
-  if constexpr (sizeof(R) == 8)
-    return (R)__longlong_as_double(__double_as_longlong((double)v) ^ ((long long)neg << 63));
-  else return neg ? -v : v;
+// complex128 products in integers.  The weights (LUT entries and term-list
+// weights) are stored as d_q = round(d 2^Fd) (DevTables::twfix, |d_q| < 2^62)
+// and the lane's amplitude components as v_q = round(v 2^(F + 63 - Fd))
+// (|v_q| < 2^63: |v| 2^F < 2^61 / hbound and hbound >= dmax >= 2^(61 - Fd));
+// their product shifted right by 63 is round(d v 2^F), the fixed-point
+// product, formed exactly and rounded once.  FP64 instructions run on a pipe
+// about 1/64 the width of FP32 here; these are integer instructions.
+__device__ __forceinline__ long long q_mul(long long a, long long b) {
+  const unsigned long long hi = (unsigned long long)__mul64hi(a, b);
+  const unsigned long long lo = (unsigned long long)a * (unsigned long long)b;
+  return (long long)((hi << 1) + (lo >> 63) + ((lo >> 62) & 1ull));
 }
 
-// A compacted item: the output index k, the weight D(k) and the lane's
-// scaled amplitude.  A warp's buffer holds up to 32 (A + 1) items: at most
-// 31 wait after a flush and a group adds at most 32 A.
-template <typename R> struct SpItem;
-template <> struct __align__(16) SpItem<float> { uint32_t k; float d, vx, vy; };
-template <> struct __align__(16) SpItem<double> { uint32_t k, pad; double d, vx, vy; };
-template <typename R>
-__host__ __device__ constexpr uint32_t sp_cap() { return 32u * (uint32_t)(sp_amps<R>() + 1); }
+// A compacted complex128 item: the output index k, the weight d_q and the
+// lane's amplitude v_q.  A warp's buffer holds up to 32 (A + 1) items: at
+// most 31 wait after a flush and a group adds at most 32 A.
+struct __align__(16) SpItemQ {
+  uint32_t k, pad;
+  long long d, vx, vy;
+};
+constexpr uint32_t kSpCapQ = 32u * (uint32_t)(sp_amps<double>() + 1);
 
 // Adds buffered item `at` (if `on`) to the accumulator; the warp
 // synchronises before (the items are other lanes' stores) and after (the
 // slots are then reused).
-template <typename R, uint32_t kOct>
-__device__ __forceinline__ void sp_flush(const SpItem<R>* wb, uint32_t at, bool on, unsigned long long* acc) {
+template <uint32_t kOct>
+__device__ __forceinline__ void sp_flush_q(const SpItemQ* wb, uint32_t at, bool on, unsigned long long* acc) {
   __syncwarp();
   if (on) {
-    const SpItem<R> e = wb[at];
-    acc_add<kOct>(acc, e.k, fx_prod<R>(e.d * e.vx), fx_prod<R>(e.d * e.vy));
+    const SpItemQ e = wb[at];
+    acc_add<kOct>(acc, e.k, q_mul(e.d, e.vx), q_mul(e.d, e.vy));
   }
   __syncwarp();
 }
 
-// sp_lut with the nonzero items appended to the warp's buffer (cnt items,
-// warp-uniform) in lane order instead of added at once; lt = the lanes
-// below this one.
-template <typename R, uint32_t kOct, int A>
-__device__ __forceinline__ void sp_lut_pack(const HLut<R>* __restrict__ L, const uint4 h0, const uint32_t v2,
-                                            const uint32_t (&ks)[A], const C_t<R> (&vs)[A],
-                                            const bool (&valid)[A], SpItem<R>* wb, uint32_t& cnt,
-                                            const uint32_t lt) {
+// complex128 LUT group: the integer LUT entry lq[phi] (the group's lut16 in
+// the fixed-point copy of the blob), nonzero items appended to the warp's
+// buffer (cnt items, warp-uniform) in lane order; lt = the lanes below this
+// one.  About two thirds of a sector-confined state's items have a zero
+// weight, so the products run 32 at a time with every lane busy.
+template <uint32_t kOct, int A>
+__device__ __forceinline__ void sp_lut_q(const long long* __restrict__ lq, const uint4 h0, const uint32_t v2,
+                                         const uint32_t (&ks)[A], const long long (&vx)[A],
+                                         const long long (&vy)[A], const bool (&valid)[A], SpItemQ* wb,
+                                         uint32_t& cnt, const uint32_t lt) {
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     const uint32_t k = ks[s] ^ h0.x;
     const uint32_t phi = (uint32_t)(__popc(k & h0.z) & 1) | ((uint32_t)(__popc(k & h0.w) & 1) << 1) |
                          ((uint32_t)(__popc(k & v2) & 1) << 2);
-    const R d0 = __ldg(L->lut16 + phi);
-    const bool nz = valid[s] && is_nonzero<R>(d0);
+    const long long d0 = __ldg(lq + phi);
+    const bool nz = valid[s] && d0 != 0ll;
     const uint32_t m = __ballot_sync(0xffffffffu, nz);
     if (nz) {
-      SpItem<R> e;
+      SpItemQ e;
       e.k = k;
-      e.d = flip_sign<R>(d0, (uint32_t)__popc(k & h0.y) & 1u);
-      e.vx = vs[s].x;
-      e.vy = vs[s].y;
+      e.pad = 0u;
+      e.d = (__popc(k & h0.y) & 1) ? -d0 : d0;
+      e.vx = vx[s];
+      e.vy = vy[s];
       wb[cnt + (uint32_t)__popc(m & lt)] = e;
     }
     cnt += (uint32_t)__popc(m);
   }
 }
 
+// complex128 term-list group (see sp_terms): the fixed-point weights wq
+// summed exactly, D_q = (sum of all w_q) - 2 (sum of the w_q with odd
+// parity), times the factor 0, 1 or 2, and the complex product in integers.
+template <uint32_t kOct, int A>
+__device__ __forceinline__ void sp_terms_q(const TiledGroup* __restrict__ G, const uint32_t* __restrict__ zs,
+                                           const long long* __restrict__ wq, const uint32_t (&ks)[A],
+                                           const long long (&vx)[A], const long long (&vy)[A],
+                                           const bool (&valid)[A], unsigned long long* acc) {
+  const uint4 g0 = __ldg(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
+  const uint2 g1 = __ldg(reinterpret_cast<const uint2*>(&G->delta)); // delta, neg
+  uint32_t k[A], fz[A];   // fz: the factor 0, 1 or 2
+  bool on = false;
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    k[s] = ks[s] ^ g0.x;
+    fz[s] = 1u;
+    if (g1.x) {
+      const uint32_t p = __popc(k[s] & g1.x) & 1u;
+      fz[s] = (g1.y ? p : p ^ 1u) ? 2u : 0u;
+    }
+    on |= valid[s] && fz[s] != 0u;
+  }
+  if (!__any_sync(0xffffffffu, on)) return;
+  unsigned long long ar = 0ull, ai = 0ull, odr[A], odi[A];   // modulo 2^64; the results fit
+#pragma unroll
+  for (int s = 0; s < A; ++s) odr[s] = odi[s] = 0ull;
+  for (uint32_t t = g0.y; t < g0.z; ++t) {
+    const uint32_t z = __ldg(zs + t);
+    const unsigned long long w = (unsigned long long)__ldg(wq + t);
+    ar += w;
+#pragma unroll
+    for (int s = 0; s < A; ++s)
+      if (__popc(k[s] & z) & 1) odr[s] += w;
+  }
+  for (uint32_t t = g0.z; t < g0.w; ++t) {
+    const uint32_t z = __ldg(zs + t);
+    const unsigned long long w = (unsigned long long)__ldg(wq + t);
+    ai += w;
+#pragma unroll
+    for (int s = 0; s < A; ++s)
+      if (__popc(k[s] & z) & 1) odi[s] += w;
+  }
+#pragma unroll
+  for (int s = 0; s < A; ++s) {
+    const int sh = fz[s] == 2u ? 1 : 0;
+    const long long a = (long long)((ar - 2ull * odr[s]) << sh), b = (long long)((ai - 2ull * odi[s]) << sh);
+    if (valid[s] && fz[s] != 0u && (a | b) != 0ll)
+      acc_add<kOct>(acc, k[s], q_mul(a, vx[s]) - q_mul(b, vy[s]), q_mul(a, vy[s]) + q_mul(b, vx[s]));
+  }
+}
+
 // One term-list group: D(k) = sum_t w_t (-1)^popc(k & z_t), real terms
 // [tb, tm), imaginary [tm, te); a paired group keeps one term of each pair
 // and D = (1 + sigma (-1)^popc(k & delta)) E(k), the factor 0 or 2.  Called
-// by every lane of the warp (the group is warp-uniform).  complex64 sums the
-// weights ws in FP32; complex128 sums their fixed-point copies wq exactly
-// with integer adds (D = (sum of all w) - 2 (sum of the w with odd parity))
-// and converts once, times wscale.
+// by every lane of the warp (the group is warp-uniform).  complex64 (complex128
+// uses sp_terms_q).
 template <typename R, uint32_t kOct, int A>
 __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const uint32_t* __restrict__ zs,
-                                         const R* __restrict__ ws, const long long* __restrict__ wq,
-                                         const double wscale, const uint32_t (&ks)[A],
+                                         const R* __restrict__ ws, const uint32_t (&ks)[A],
                                          const C_t<R> (&vs)[A], const bool (&valid)[A],
                                          unsigned long long* acc) {
   const uint4 g0 = __ldg(reinterpret_cast<const uint4*>(&G->x));     // x, tb, tm, te
@@ -424,52 +468,25 @@ __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const
   }
   if (!__any_sync(0xffffffffu, on)) return;
   R dr[A], di[A];
-  if constexpr (sizeof(R) == 8) {
-    unsigned long long ar = 0ull, ai = 0ull, odr[A], odi[A];   // modulo 2^64; the results fit
 #pragma unroll
-    for (int s = 0; s < A; ++s) odr[s] = odi[s] = 0ull;
-    for (uint32_t t = g0.y; t < g0.z; ++t) {
-      const uint32_t z = __ldg(zs + t);
-      const unsigned long long w = (unsigned long long)__ldg(wq + t);
-      ar += w;
+  for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
+  for (uint32_t t = g0.y; t < g0.z; ++t) {
+    const uint32_t z = __ldg(zs + t);
+    const R w = __ldg(ws + t);
 #pragma unroll
-      for (int s = 0; s < A; ++s)
-        if (__popc(k[s] & z) & 1) odr[s] += w;
-    }
-    for (uint32_t t = g0.z; t < g0.w; ++t) {
-      const uint32_t z = __ldg(zs + t);
-      const unsigned long long w = (unsigned long long)__ldg(wq + t);
-      ai += w;
+    for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
+  }
+  for (uint32_t t = g0.z; t < g0.w; ++t) {
+    const uint32_t z = __ldg(zs + t);
+    const R w = __ldg(ws + t);
 #pragma unroll
-      for (int s = 0; s < A; ++s)
-        if (__popc(k[s] & z) & 1) odi[s] += w;
-    }
-#pragma unroll
-    for (int s = 0; s < A; ++s) {
-      dr[s] = (R)(__ll2double_rn((long long)(ar - 2ull * odr[s])) * wscale);
-      di[s] = (R)(__ll2double_rn((long long)(ai - 2ull * odi[s])) * wscale);
-    }
-  } else {
-#pragma unroll
-    for (int s = 0; s < A; ++s) dr[s] = di[s] = R(0);
-    for (uint32_t t = g0.y; t < g0.z; ++t) {
-      const uint32_t z = __ldg(zs + t);
-      const R w = __ldg(ws + t);
-#pragma unroll
-      for (int s = 0; s < A; ++s) dr[s] += (__popc(k[s] & z) & 1) ? -w : w;
-    }
-    for (uint32_t t = g0.z; t < g0.w; ++t) {
-      const uint32_t z = __ldg(zs + t);
-      const R w = __ldg(ws + t);
-#pragma unroll
-      for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
-    }
+    for (int s = 0; s < A; ++s) di[s] += (__popc(k[s] & z) & 1) ? -w : w;
   }
 #pragma unroll
   for (int s = 0; s < A; ++s) {
     const R f = fz[s] == 2u ? R(2) : R(1);
     const R a = dr[s] * f, b = di[s] * f;
-    if (valid[s] && fz[s] != 0u && (is_nonzero<R>(a) || is_nonzero<R>(b)))
+    if (valid[s] && fz[s] != 0u && (a != R(0) || b != R(0)))
       acc_add<kOct>(acc, k[s], fx_prod<R>(a * vs[s].x - b * vs[s].y), fx_prod<R>(a * vs[s].y + b * vs[s].x));
   }
 }
@@ -499,10 +516,13 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(sp_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // complex128: the warp's item buffer after the accumulator
-  SpItem<R>* wb = reinterpret_cast<SpItem<R>*>(sp_raw + kOct * 16u * sizeof(unsigned long long)) +
-                  (sp_compact<R>() ? warp * sp_cap<R>() : 0u);
+  SpItemQ* wb = reinterpret_cast<SpItemQ*>(sp_raw + kOct * 16u * sizeof(unsigned long long)) +
+                (sizeof(R) == 8 ? warp * kSpCapQ : 0u);
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t cnt = 0;   // items in wb (warp-uniform)
+  // complex128: the fixed-point copy of a blob byte is at the same offset
+  // from a.wfix as the byte from a.blob
+  const ptrdiff_t wdelta = a.wfix - a.blob;
   __shared__ uint32_t s_tile, s_unext;
   __shared__ uint32_t s_pre[kSpMaxPieces + 1];   // first unit of each piece; s_pre[P] = units
   __shared__ uint32_t s_wsum[32];
@@ -614,10 +634,9 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         const TiledGroup* gs = reinterpret_cast<const TiledGroup*>(blob + sizeof(TiledHead) + hd.y * sizeof(HLut<R>));
         const uint32_t* zs = reinterpret_cast<const uint32_t*>(blob + hd.z);
         const R* ws = reinterpret_cast<const R*>(blob + hd.w);
-        const long long* wq =
-            sizeof(R) == 8 ? reinterpret_cast<const long long*>(a.wfix + pc.off + hd.w) : nullptr;
         uint32_t ks[A];
         C_t<R> vs[A];
+        long long vqx[A], vqy[A];   // complex128: the amplitudes as v_q (see q_mul)
         bool valid[A];
 #pragma unroll
         for (int s = 0; s < A; ++s) {
@@ -626,6 +645,10 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
           ks[s] = a.aidx[valid[s] ? li : a0];
           const C_t<R> v = a.aval[valid[s] ? li : a0];
           vs[s] = cmake<R>(v.x * up_a * up_b, v.y * up_a * up_b);
+          if constexpr (sizeof(R) == 8) {
+            vqx[s] = __double2ll_rn((double)vs[s].x * a.wscale);
+            vqy[s] = __double2ll_rn((double)vs[s].y * a.wscale);
+          }
         }
         const int nl = (int)hd.y;
         // each group's descriptor (x, z0, v0, v1 and v2) is loaded while the
@@ -643,11 +666,13 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
             h0n = __ldg(reinterpret_cast<const uint4*>(&ls[g + 1].x));
             v2n = __ldg(&ls[g + 1].v2);
           }
-          if constexpr (sp_compact<R>()) {
-            sp_lut_pack<R, kOct, A>(ls + g, h0, v2, ks, vs, valid, wb, cnt, lt);
+          if constexpr (sizeof(R) == 8) {
+            const long long* lq = reinterpret_cast<const long long*>(
+                reinterpret_cast<const uint8_t*>(ls[g].lut16) + wdelta);
+            sp_lut_q<kOct, A>(lq, h0, v2, ks, vqx, vqy, valid, wb, cnt, lt);
             while (cnt >= 32u) {
               cnt -= 32u;
-              sp_flush<R, kOct>(wb, cnt + (uint32_t)lane, true, acc);
+              sp_flush_q<kOct>(wb, cnt + (uint32_t)lane, true, acc);
             }
           } else {
             sp_lut<R, kOct, A>(ls + g, h0, v2, ks, vs, valid, acc);
@@ -655,10 +680,15 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
         }
         // the term-list groups fill the blob from the LUT groups to z_off
         const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
-        for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, wq, a.wscale, ks, vs, valid, acc);
+        if constexpr (sizeof(R) == 8) {
+          const long long* wq = reinterpret_cast<const long long*>(reinterpret_cast<const uint8_t*>(ws) + wdelta);
+          for (int g = 0; g < nt; ++g) sp_terms_q<kOct, A>(gs + g, zs, wq, ks, vqx, vqy, valid, acc);
+        } else {
+          for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, ks, vs, valid, acc);
+        }
       }
     }
-    if (cnt) sp_flush<R, kOct>(wb, (uint32_t)lane, (uint32_t)lane < cnt, acc);   // the rest, fewer than 32
+    if (cnt) sp_flush_q<kOct>(wb, (uint32_t)lane, (uint32_t)lane < cnt, acc);   // the rest, fewer than 32
     cnt = 0;
     __syncthreads();
     // epilogue, first the nonzero amplitudes of the own tile (one lane
@@ -774,7 +804,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
 template <typename R>
 constexpr uint32_t sparse_smem() {
   return (1u << (TiledBits<R>::LB - 3)) * 16u * (uint32_t)sizeof(unsigned long long) +
-         (sp_compact<R>() ? (uint32_t)(sp_threads<R>() / 32) * sp_cap<R>() * (uint32_t)sizeof(SpItem<R>) : 0u);
+         (sizeof(R) == 8 ? (uint32_t)(sp_threads<R>() / 32) * kSpCapQ * (uint32_t)sizeof(SpItemQ) : 0u);
 }
 
 }  // namespace

@@ -263,9 +263,11 @@ struct DevTables {
   const uint8_t* tblob = nullptr;
   const TiledPiece* tpiece = nullptr;
   const uint32_t* tporder = nullptr;   // piece indices by descending blob size
-  // complex128: the blobs' term-list weights as 64-bit fixed-point integers
-  // round(w 2^F_w), each at its weight's offset in tblob (elsewhere zero),
-  // and twscale = 2^-F_w; F_w keeps every group's sum of |w| below 2^61
+  // complex128: the blobs' LUT entries and term-list weights as 64-bit
+  // fixed-point integers round(w 2^Fd), each at its value's offset in tblob
+  // (elsewhere zero), Fd = 62 - e with dmax < 2^e; and twscale = 2^(63 - Fd),
+  // the factor that takes an amplitude scaled by 2^F to the integer whose
+  // product with a weight, shifted right by 63, is the product at 2^F
   const uint8_t* twfix = nullptr;
   double twscale = 0.0;
   uint32_t* octmask = nullptr;
@@ -537,7 +539,7 @@ struct SparseArgs {
   double hbound;                // DevTables::hbound
   double dmax;                  // DevTables::dmax
   const uint8_t* wfix;          // DevTables::twfix (complex128)
-  double wscale;                // DevTables::twscale
+  double wscale;                // DevTables::twscale (complex128)
   uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
   const uint32_t* dz;
   const R* dw;

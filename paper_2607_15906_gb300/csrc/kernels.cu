@@ -1926,41 +1926,33 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
   for (size_t i = 0; i < porder.size(); ++i) porder[i] = (uint32_t)i;
   std::stable_sort(porder.begin(), porder.end(),
                    [&](uint32_t a, uint32_t b) { return pieces[a].bytes > pieces[b].bytes; });
-  // complex128: the term weights again, as fixed-point integers at their
-  // own offsets (the scatter kernel sums them exactly with integer adds)
+  // complex128: the LUT entries and term weights again, as fixed-point
+  // integers round(w 2^Fd) at their own offsets (the scatter kernel forms
+  // its products in integers, see q_mul there).  Fd = 62 - e with
+  // dmax < 2^e, so that every |w| 2^Fd, and every group's sum of |w| 2^Fd,
+  // stays below 2^62.
   std::vector<uint8_t> wfix;
-  int fw = 0;
+  int fd = 0;
   if constexpr (sizeof(R) == 8) {
-    double wmax = 0.0;   // largest sum of |w| over a group's real or imaginary stored terms
-    for (const TiledPiece& pc : pieces) {
-      TiledHead h;
-      std::memcpy(&h, blob.data() + pc.off, sizeof(h));
-      const TiledGroup* tg = reinterpret_cast<const TiledGroup*>(blob.data() + pc.off + sizeof(TiledHead) +
-                                                                 h.n_lut * sizeof(HLut<R>));
-      const int ntg = (int)((h.z_off - sizeof(TiledHead) - h.n_lut * sizeof(HLut<R>)) / sizeof(TiledGroup));
-      const R* w = reinterpret_cast<const R*>(blob.data() + pc.off + h.w_off);
-      for (int g = 0; g < ntg; ++g) {
-        double sr = 0.0, si = 0.0;
-        for (uint32_t t = tg[g].tb; t < tg[g].tm; ++t) sr += std::fabs((double)w[t]);
-        for (uint32_t t = tg[g].tm; t < tg[g].te; ++t) si += std::fabs((double)w[t]);
-        wmax = std::max(wmax, std::max(sr, si));
-      }
-    }
-    if (wmax > 0.0) {
+    if (d.t.dmax > 0.0) {
       int e;
-      std::frexp(wmax, &e);   // wmax < 2^e
-      fw = 61 - e;
+      std::frexp(d.t.dmax, &e);   // dmax < 2^e
+      fd = 62 - e;
     }
+    auto put = [&](size_t at) {
+      double v;
+      std::memcpy(&v, blob.data() + at, sizeof(v));
+      const long long q = std::llround(std::ldexp(v, fd));
+      std::memcpy(wfix.data() + at, &q, sizeof(q));
+    };
     wfix.assign(blob.size(), 0);
     for (const TiledPiece& pc : pieces) {
       TiledHead h;
       std::memcpy(&h, blob.data() + pc.off, sizeof(h));
-      for (uint32_t o = h.w_off; o + sizeof(R) <= pc.bytes; o += sizeof(R)) {
-        double v;
-        std::memcpy(&v, blob.data() + pc.off + o, sizeof(v));
-        const long long q = std::llround(std::ldexp(v, fw));
-        std::memcpy(wfix.data() + pc.off + o, &q, sizeof(q));
-      }
+      for (uint32_t g = 0; g < h.n_lut; ++g)
+        for (int c = 0; c < 16; ++c)
+          put(pc.off + sizeof(TiledHead) + g * sizeof(HLut<R>) + offsetof(HLut<R>, lut16) + c * sizeof(R));
+      for (uint32_t o = h.w_off; o + sizeof(R) <= pc.bytes; o += sizeof(R)) put(pc.off + o);
     }
   }
   uint8_t* dblob;
@@ -1971,7 +1963,7 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
     uint8_t* dw;
     if ((rc = upload(d, &dw, wfix, bytes))) return rc;
     d.t.twfix = dw;
-    d.t.twscale = std::ldexp(1.0, -fw);
+    d.t.twscale = std::ldexp(1.0, 63 - fd);
   }
   if ((rc = upload(d, &dblob, blob, bytes)) || (rc = upload(d, &dpiece, pieces, bytes)) ||
       (rc = upload(d, &dporder, porder, bytes)) ||
