@@ -33,6 +33,15 @@ __device__ __forceinline__ C_t<R> cscale(C_t<R> a, R s) { return cmake<R>(a.x * 
 template <typename R>
 __device__ __forceinline__ C_t<R> cconj(C_t<R> a) { return cmake<R>(a.x, -a.y); }
 
+// v == 0 (either sign of zero).  For double the test is on the bits, with
+// integer instructions: FP64 compares run on the FP64 pipe, about 1/64 the
+// width of FP32 on this part.
+template <typename R>
+__device__ __forceinline__ bool rzero(R v) {
+  if constexpr (sizeof(R) == 8) return (__double_as_longlong((double)v) << 1) == 0ll;
+  else return v == R(0);
+}
+
 // Start of one step of a chain launched with programmatic dependencies
 // (launch_chain): wait until the previous step's grid has finished and its
 // writes are visible, then let the next step's blocks be scheduled while this

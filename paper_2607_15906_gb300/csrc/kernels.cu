@@ -649,12 +649,12 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
         uint32_t b;
         if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
         const uint32_t ph = lut_phi(L, b);
-        if (L.lut[ph] == R(0) && L.lut[ph ^ phx] == R(0)) continue;   // T = I on the pair
+        if (rzero<R>(L.lut[ph]) && rzero<R>(L.lut[ph ^ phx])) continue;   // T = I on the pair
         C_t<R> o1, o2;
         taylor_pair<R>(L, c, b, ph, psi, o1, o2);
         const uint32_t other = b == k ? b ^ L.x : b;
         const C_t<R> ov = b == k ? o2 : o1;
-        if ((ov.x != R(0) || ov.y != R(0)) && !chain_listed(cl, other)) chain_append(cl, other, n0, cur, mask);
+        if (!(rzero<R>(ov.x) && rzero<R>(ov.y)) && !chain_listed(cl, other)) chain_append(cl, other, n0, cur, mask);
       }
       return;
     }
@@ -811,13 +811,13 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
       uint32_t b;
       if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
       const uint32_t ph = lut_phi(L, b);
-      if (L.lut[ph] == R(0) && L.lut[ph ^ phx] == R(0)) continue;   // T = I, T' = 0 on the pair
+      if (rzero<R>(L.lut[ph]) && rzero<R>(L.lut[ph ^ phx])) continue;   // T = I, T' = 0 on the pair
       C_t<R> o[4];
       v[0] += adjoint_pair<R>(L, c, b, ph, psi, lam, o);
       const bool base = b == k;
       const uint32_t other = base ? b ^ L.x : b;
       const C_t<R> op1 = base ? o[1] : o[0], ol1 = base ? o[3] : o[2];
-      if ((op1.x != R(0) || op1.y != R(0) || ol1.x != R(0) || ol1.y != R(0)) && !chain_listed(cl, other))
+      if (!(rzero<R>(op1.x) && rzero<R>(op1.y) && rzero<R>(ol1.x) && rzero<R>(ol1.y)) && !chain_listed(cl, other))
         chain_append(cl, other, n0, cur, mask);
     }
   } else {
@@ -1358,6 +1358,21 @@ int live_octets(const uint32_t* mask, int n, const LiveOctets& lv, cudaStream_t 
 // block in FP64; (H psi)_b is read only where
 // D_k(b) != 0.  Returns at once when the list is incomplete (more than acap
 // amplitudes): the live-octet kernel then runs.
+//
+// complex128: the FP64 pipe is about 1/64 the width of FP32 here, and most
+// (amplitude, generator) items have D_k(b) = 0.  The zero test and the sign
+// work on the bits of D with integer instructions, and a warp packs its
+// nonzero items (b, list index, signed D) into a shared-memory buffer and
+// computes them 32 at a time with every lane busy, instead of running the
+// FP64 products whenever any lane has a nonzero item.  A lane's items are
+// summed in the same order either way except for that grouping, so the
+// gradients differ only by the rounding of the per-thread sums.
+struct __align__(16) GradItem {
+  uint32_t b, l;
+  double d;
+};
+constexpr int kGradCap = 64;   // items a warp's buffer holds: < 32 left after a flush + 32 new
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
 k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* __restrict__ aidx,
@@ -1366,6 +1381,64 @@ k_pool_grad_amp(DevTables tb, const C_t<R>* __restrict__ hpsi, const uint32_t* _
   if (*alen > acap) return;
   __shared__ LutDev<R> s_op[kOpsPerBlock];
   __shared__ double s_red[kOpsPerBlock][kWarps];
+  if constexpr (sizeof(R) == 8) {
+    __shared__ GradItem s_items[kWarps][kGradCap];
+    const int first = blockIdx.y * kOpsPerBlock;
+    const int nops = min(kOpsPerBlock, tb.M - first);
+    if (threadIdx.x < nops) s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[tb.porder[first + threadIdx.x]];
+    __syncthreads();
+    const uint32_t n = *alen;
+    const uint32_t per = (n + nbx - 1) / nbx;
+    const uint32_t l0 = blockIdx.x * per, l1 = min(n, l0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    GradItem* wb = s_items[warp];
+    auto flush = [&](uint32_t at, bool on, double& acc) {
+      __syncwarp();
+      if (on) {
+        const GradItem e = wb[at];
+        const C_t<R> p = aval[e.l], h = hpsi[e.b];
+        acc += e.d * ((double)h.x * p.x + (double)h.y * p.y);
+      }
+      __syncwarp();
+    };
+    for (int o = 0; o < nops; ++o) {
+      const LutDev<R>& L = s_op[o];
+      double acc = 0.0;
+      uint32_t cnt = 0;   // items in wb (warp-uniform)
+      // the warp walks the slice together so that the ballots see every lane
+      for (uint32_t l = l0 + (uint32_t)threadIdx.x - (uint32_t)lane; l < l1; l += kThreads) {
+        const uint32_t li = l + (uint32_t)lane;
+        const bool in = li < l1;
+        const uint32_t b = (in ? aidx[li] : 0u) ^ L.x;
+        const long long db = __double_as_longlong((double)L.lut[lut_phi(L, b)]);
+        const bool nz = in && (db << 1) != 0ll;
+        const uint32_t m = __ballot_sync(0xffffffffu, nz);
+        if (nz) {
+          GradItem e;
+          e.b = b;
+          e.l = li;
+          e.d = __longlong_as_double(db ^ ((long long)(__popc(b & L.z0) & 1) << 63));
+          wb[cnt + (uint32_t)__popc(m & lt)] = e;
+        }
+        cnt += (uint32_t)__popc(m);
+        if (cnt >= 32u) {
+          cnt -= 32u;
+          flush(cnt + (uint32_t)lane, true, acc);
+        }
+      }
+      if (cnt) flush((uint32_t)lane, (uint32_t)lane < cnt, acc);
+      acc = warp_sum(acc);
+      if (lane == 0) s_red[o][warp] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < nops) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s_red[threadIdx.x][w];
+      part[(size_t)(first + threadIdx.x) * nbx + blockIdx.x] = t;
+    }
+    return;
+  }
   const int first = blockIdx.y * kOpsPerBlock;
   const int nops = min(kOpsPerBlock, tb.M - first);
   if (threadIdx.x < nops) s_op[threadIdx.x] = ((const LutDev<R>*)tb.plut)[tb.porder[first + threadIdx.x]];
