@@ -604,18 +604,34 @@ __device__ __forceinline__ void taylor_pair_at(const LutDev<R>& L, const R (&c)[
   const R l1 = L.lut[ph], l2 = L.lut[ph ^ phx];
   const uint32_t sg = __popc(b & L.z0) & 1u;
   const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
-  C_t<R> v1 = *p1, v2 = *p2;
-  C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
+  const C_t<R> v1 = *p1, v2 = *p2;
+  if constexpr (sizeof(R) == 8) {
+    // complex128: the same fifth-order polynomial evaluated through
+    // A^2 = mu I on the pair (mu = D1 D2): T = C I + S A with
+    // C = c0 + c2 mu + c4 mu^2, S = c1 + c3 mu + c5 mu^2 -- 16 FP64
+    // operations instead of the chain's 40, on a pipe about 1/64 the width
+    // of FP32 here
+    const R mu = d1 * d2, mu2 = mu * mu;
+    const R cc = c[0] + c[2] * mu + c[4] * mu2;
+    const R sc = c[1] + c[3] * mu + c[5] * mu2;
+    const R sd1 = sc * d1, sd2 = sc * d2;
+    o1 = cmake<R>(cc * v1.x + sd1 * v2.x, cc * v1.y + sd1 * v2.y);
+    o2 = cmake<R>(cc * v2.x + sd2 * v1.x, cc * v2.y + sd2 * v1.y);
+  } else {
+    // complex64: the literal chain v_m = A v_(m-1) with compensated sums
+    C_t<R> w1 = v1, w2 = v2;
+    C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
 #pragma unroll
-  for (int m = 1; m <= 5; ++m) {
-    C_t<R> n1 = cscale<R>(v2, d1), n2 = cscale<R>(v1, d2);   // (A v)[b] = D(b) v[b^x]
-    v1 = n1;
-    v2 = n2;
-    kahan_add<R>(s1, e1, cscale<R>(v1, c[m]));
-    kahan_add<R>(s2, e2, cscale<R>(v2, c[m]));
+    for (int m = 1; m <= 5; ++m) {
+      C_t<R> n1 = cscale<R>(w2, d1), n2 = cscale<R>(w1, d2);   // (A v)[b] = D(b) v[b^x]
+      w1 = n1;
+      w2 = n2;
+      kahan_add<R>(s1, e1, cscale<R>(w1, c[m]));
+      kahan_add<R>(s2, e2, cscale<R>(w2, c[m]));
+    }
+    o1 = csub<R>(s1, e1);
+    o2 = csub<R>(s2, e2);
   }
-  o1 = csub<R>(s1, e1);
-  o2 = csub<R>(s2, e2);
   *p1 = o1;
   *p2 = o2;
 }

@@ -111,6 +111,17 @@ k_sec_taylor(SecDev s, DevTables tb, const uint2* pairs, const int64_t* off, con
     const uint32_t sg = __popc(k & L.z0) & 1u;
     const R d1 = sg ? -l1 : l1, d2 = (sg ^ sgx) ? -l2 : l2;
     C_t<R> v1 = psi[pr.x], v2 = psi[pr.y];
+    if constexpr (sizeof(R) == 8) {
+      // complex128: the same polynomial through A^2 = mu I on the pair (see
+      // taylor_pair_at in kernels.cu)
+      const R mu = d1 * d2, mu2 = mu * mu;
+      const R cc = c[0] + c[2] * mu + c[4] * mu2;
+      const R sc = c[1] + c[3] * mu + c[5] * mu2;
+      const R sd1 = sc * d1, sd2 = sc * d2;
+      psi[pr.x] = cmake<R>(cc * v1.x + sd1 * v2.x, cc * v1.y + sd1 * v2.y);
+      psi[pr.y] = cmake<R>(cc * v2.x + sd2 * v1.x, cc * v2.y + sd2 * v1.y);
+      continue;
+    }
     C_t<R> s1 = v1, s2 = v2, e1 = cmake<R>(0, 0), e2 = cmake<R>(0, 0);
 #pragma unroll
     for (int m = 1; m <= 5; ++m) {

@@ -375,6 +375,33 @@ def test_tiled_h_on_sector_states(prec, path, monkeypatch):
             TOL[prec]["grad"] * max(1.0, np.max(np.abs(g_ref))))
 
 
+@pytest.mark.parametrize("prec,scale", [("c128", 1e-150), ("c128", 1e150), ("c64", 1e-30), ("c64", 1e30)])
+def test_scatter_h_at_extreme_scales(prec, scale, monkeypatch):
+    """The scatter kernel's fixed-point scale 2^F follows the largest
+    amplitude, and complex128 forms its products as integers (weights at
+    2^Fd, amplitudes at 2^(F + 63 - Fd)): a sector state with random phases
+    (complex amplitudes), scaled by 1e+-150 (complex128) or 1e+-30
+    (complex64), gives scale x the oracle's H psi entry by entry and the
+    same energy, with no device error."""
+    monkeypatch.setenv("GOCP_SPARSE_FRAC", "1")
+    ints, h, tabs = _case(8, 8, "jw", 5)
+    p = gb.Problem.build(ints, 8, precision=prec, device=0)
+    ops, th = draw_ansatz(len(tabs), 24, seed=5, theta_sigma=0.3)
+    ws = p.workspace()
+    p.prepare_state(ops, th, ws[0])
+    base = _host(ws[0])
+    phase = np.exp(2j * np.pi * np.random.default_rng(11).random(base.size))
+    psi_in = base * phase * scale
+    d = _to_dev(p, psi_in)
+    hd = torch.empty_like(d)
+    e, nrm = p.energy(d, hd)
+    assert p.device_errors() == 0
+    ref = sv.apply_terms(h, psi_in)
+    _within(f"scaled {prec} {scale:g} hpsi", np.max(np.abs(_host(hd) - ref)), TOL[prec]["state"] * np.max(np.abs(ref)))
+    e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
+    _within(f"scaled {prec} {scale:g} E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+
+
 def test_empty_ansatz_gives_reference_energy():
     ints, h, tabs = _case(4, 4, "bk", 1)
     p = gb.Problem.build(ints, 4, mapping="bk", precision="c128", device=0)
