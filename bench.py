@@ -580,14 +580,16 @@ def adapt_14q(device: int, max_ops: int = 30):
     return out
 
 
-def _counters(kernel: str):
+def _counters(kernel: str, precision: str = "c64"):
     """ncu counters per launch recorded in profiles/kernel_counters.json
-    (DRAM bytes, warp instructions), only while the library reports the
-    kernel revision they were captured on; else None."""
+    for the kernel's instance of this precision (key "name<float>" or
+    "name<double>"; DRAM bytes, warp instructions), only while the library
+    reports the kernel revision they were captured on; else None."""
     try:
         import paper_2607_15906_gb300 as gb
         ver = gb.load().gocp_version().decode()
-        rec = json.load(open(os.path.join(ROOT, "profiles", "kernel_counters.json"))).get(kernel)
+        key = f"{kernel}<{'float' if precision == 'c64' else 'double'}>"
+        rec = json.load(open(os.path.join(ROOT, "profiles", "kernel_counters.json"))).get(key)
         if rec and f"{kernel}={rec['revision']}" in ver:
             return rec
     except Exception:
@@ -634,7 +636,7 @@ def roofline(res, peaks, how):
                       "frac": flops / per_launch_s / 1e12 / fp32_peak, "flops_per_launch": flops,
                       "nonzero_amplitudes": nnz,
                       "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_mhz:.0f} MHz (recipe unit counts)"}
-        c = _counters(name)
+        c = _counters(name, res["prob"].precision)
         out["traffic"] = c["dram_bytes_per_launch"] if c else None
         out["redundancy"] = (c["dram_bytes_per_launch"] / alg) if c else None
         out["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: a lower bound "
@@ -654,7 +656,7 @@ def roofline(res, peaks, how):
         achieved = per / per_launch_s / 1e9
         out = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{how} hbm_gbs"}
-        c = _counters(top)
+        c = _counters(top, res["prob"].precision)
         out["traffic"] = c["dram_bytes_per_launch"] if c else None
     out["launch_ms"] = per_launch_s * 1e3
     out["launches_per_step"] = launches / max(1, res.get("steps", 1))
