@@ -810,6 +810,7 @@ def main():
             extras["c128"] = c128_iterations(local)
             extras["full_layout_28q"] = full_layout_large(local, 14)
             extras["full_layout_30q"] = full_layout_large(local, 15)
+            extras["full_layout_32q"] = full_layout_large(local, 16, steps=2)
             extras["sector_30q"] = sector_30q(local)
             extras["adapt_14q"] = adapt_14q(local)
             extras["serving"] = serving_bench(local)

@@ -18,7 +18,7 @@
  *
  * Conventions shared by every entry point
  *   Pauli term (x, z, phase, coeff) = coeff * i^phase * X^x Z^z, with x, z
- *     uint32 bit masks (bit j = qubit j, so n <= 30 here) and Z applied
+ *     uint32 bit masks (bit j = qubit j, so n <= 32) and Z applied
  *     first: it maps |b> to coeff * i^phase * (-1)^popcount(b & z) |b ^ x>.
  *   Spin-orbital i = 2p + sigma (sigma 0 alpha, 1 beta) sits on qubit i.
  *   A state is an interleaved complex array of 2^n amplitudes, index bit j =
@@ -95,7 +95,7 @@ typedef struct gocp_server gocp_server;
  * tables to that CUDA device; device = -1 builds host tables only (export
  * works, compute calls return GOCP_ENODEV). */
 typedef struct {
-  int n_orb;            /* spatial orbitals; qubits = 2*n_orb, 1..15 */
+  int n_orb;            /* spatial orbitals; qubits = 2*n_orb, 1..16 */
   int n_elec;           /* electrons, 0..2*n_orb */
   int mapping;          /* GOCP_JW | GOCP_BK */
   int precision;        /* GOCP_C64 | GOCP_C128 */
@@ -122,7 +122,7 @@ int gocp_build(const gocp_build_args* args, gocp_problem** out);
  * (the commutator test needs generator coefficients that are multiples of
  * 1/8; otherwise GOCP_EINVAL). */
 typedef struct {
-  int n_qubits;                 /* 1..30 */
+  int n_qubits;                 /* 1..32 */
   int precision;
   int device;
   int flags;

@@ -144,12 +144,15 @@ k_amp_count(const C_t<R>* __restrict__ psi, const C_t<R>* __restrict__ psi2, con
 // counts[0..nb) -> exclusive prefix sums in place; *total = the sum (when
 // set; and, when ring is set, the chain-list ring's base(slot) = the sum,
 // count(slot) = count(first) = 0); *amax = 0 when set.  One block of 1024
-// threads.
+// threads.  The sum reaches 2^32 only for a 32-qubit state with every
+// amplitude nonzero; it is stored saturated at 2^32 - 1 (above every list
+// capacity, so the list is not used), while every prefix, at most the sum
+// less the last block's count, fits 32 bits.
 __global__ void __launch_bounds__(1024)
 k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int slot, int first,
            unsigned long long* amax) {
   __shared__ uint32_t s[1024];
-  __shared__ uint32_t carry;
+  __shared__ unsigned long long carry;
   if (threadIdx.x == 0) carry = 0;
   for (uint32_t base = 0; base < nb; base += 1024u) {
     const uint32_t i = base + threadIdx.x;
@@ -162,16 +165,17 @@ k_amp_scan(uint32_t* counts, uint32_t nb, uint32_t* total, uint32_t* ring, int s
       s[threadIdx.x] += u;
       __syncthreads();
     }
-    if (i < nb) counts[i] = carry + s[threadIdx.x] - v;
+    if (i < nb) counts[i] = (uint32_t)(carry + s[threadIdx.x] - v);
     __syncthreads();
     if (threadIdx.x == 0) carry += s[1023];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (total) *total = carry;
+    const uint32_t sum = carry > 0xffffffffull ? 0xffffffffu : (uint32_t)carry;
+    if (total) *total = sum;
     if (amax) *amax = 0ull;
     if (ring) {
-      ring[kRingBase(slot)] = carry;
+      ring[kRingBase(slot)] = sum;
       ring[kRingAdd(slot)] = 0u;
       ring[kRingAdd(first)] = 0u;
     }

@@ -213,7 +213,7 @@ extern "C" {
 
 int gocp_build(const gocp_build_args* a, gocp_problem** out) {
   if (!a || !out) return fail(GOCP_EINVAL, "args/out is NULL");
-  if (a->n_orb < 1 || a->n_orb > 15) return fail(GOCP_EINVAL, "n_orb must be in 1..15");
+  if (a->n_orb < 1 || a->n_orb > 16) return fail(GOCP_EINVAL, "n_orb must be in 1..16");
   if (a->n_elec < 0 || a->n_elec > 2 * a->n_orb) return fail(GOCP_EINVAL, "n_elec must be in 0..2*n_orb");
   if (a->mapping != GOCP_JW && a->mapping != GOCP_BK) return fail(GOCP_EINVAL, "mapping must be GOCP_JW or GOCP_BK");
   if (a->precision != GOCP_C64 && a->precision != GOCP_C128) return fail(GOCP_EINVAL, "precision must be GOCP_C64 or GOCP_C128");
@@ -264,7 +264,7 @@ int gocp_build(const gocp_build_args* a, gocp_problem** out) {
 
 int gocp_build_from_tables(const gocp_table_args* a, gocp_problem** out) {
   if (!a || !out) return fail(GOCP_EINVAL, "args/out is NULL");
-  if (a->n_qubits < 1 || a->n_qubits > 30) return fail(GOCP_EINVAL, "n_qubits must be in 1..30");
+  if (a->n_qubits < 1 || a->n_qubits > 32) return fail(GOCP_EINVAL, "n_qubits must be in 1..32");
   if (a->precision != GOCP_C64 && a->precision != GOCP_C128) return fail(GOCP_EINVAL, "precision must be GOCP_C64 or GOCP_C128");
   if (a->n_terms < 0 || (a->n_terms > 0 && (!a->x || !a->z || !a->phase || !a->coeff)))
     return fail(GOCP_EINVAL, "bad term arrays");

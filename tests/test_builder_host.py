@@ -44,6 +44,27 @@ def test_hamiltonian_table_bit_exact(cfg, n_elec, mp):
     assert p.info["ref_index"] == mapping.hf_index(mp, ref.n, n_elec)
 
 
+@pytest.mark.parametrize("mp", ["jw", "bk"])
+def test_hamiltonian_table_bit_exact_32_qubits(mp):
+    """16 spatial orbitals, the largest problem: the top qubit (bit 31 of
+    the masks) is in use, and the tables still match the oracle bit for
+    bit; 17 orbitals and 33 table qubits are refused."""
+    ints = molecular_integrals(16, seed=0, decay=True)
+    ref = mapping.hamiltonian_table(ints, mp, 1e-3, 0.0)
+    p = _host(ints, 8, mp, 1e-3, 0.0, colour=False)
+    x, z, ph, co = p.terms()
+    assert p.info["n_qubits"] == 32 and (int(np.max(ref.x | ref.z)) >> 31) == 1
+    assert np.array_equal(x.astype(np.int64), ref.x)
+    assert np.array_equal(z.astype(np.int64), ref.z)
+    assert np.array_equal(ph.astype(np.int64), ref.phase)
+    assert np.array_equal(co.view(np.int64), ref.coeff.view(np.int64))
+    assert p.info["ref_index"] == mapping.hf_index(mp, 32, 8)
+    with pytest.raises(gb.GocpError):
+        _host(molecular_integrals(17, seed=0, decay=True), 8, mp, 1e-3, 0.0, colour=False)
+    with pytest.raises(gb.GocpError):
+        gb.Problem.from_tables(33, ([1], [0], [0], [1.0]), [], ref_index=0, device=-1)
+
+
 @pytest.mark.parametrize("nq,ne", [(4, 2), (12, 8), (14, 6)])
 @pytest.mark.parametrize("mp", ["jw", "bk"])
 def test_pool_and_gocp_bit_exact(nq, ne, mp):

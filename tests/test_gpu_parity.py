@@ -578,9 +578,17 @@ def test_larger_n_28q_c64():
 
 def test_larger_n_30q_c64():
     """30 qubits in the full layout (15 orbitals, 8 electrons; an 8 GiB
-    complex64 state, the uint32 index limit of this build): a prepared
-    sparse state, E and sampled pool gradients against the oracle."""
+    complex64 state): a prepared sparse state, E and sampled pool gradients
+    against the oracle."""
     _sparse_prepared_check(15, 8, "30q sparse", n_ops=5)
+
+
+def test_larger_n_32q_c64():
+    """32 qubits in the full layout (16 orbitals, 8 electrons; a 32 GiB
+    complex64 state, amplitude indices up to 2^32 - 1 in the uint32 index
+    types): a prepared sparse state, E and sampled pool gradients against
+    the oracle."""
+    _sparse_prepared_check(16, 8, "32q sparse", n_ops=4)
 
 
 @pytest.mark.parametrize("n_orb,n_elec,prec", [(5, 4, "c128"), (6, 6, "c64"), (6, 6, "c128"), (7, 6, "c64"),
