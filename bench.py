@@ -351,6 +351,61 @@ def sector_layout(device: int, full_e: float, full_sel: int, steps: int = 10, wa
             "note": "GOCP_BUILD_SECTOR: same ADAPT step on the N_a = N_b = 4 determinants only"}
 
 
+def h_psi_by_n(device: int, peaks, how: str, reps: int = 20):
+    """H psi (+E) at 14..24 qubits, complex64 and complex128: the call's
+    CUDA-event time and 2S over it against the measured HBM peak (S = the
+    state's bytes), for the prepared 100-operator ADAPT state (sector-confined;
+    the scatter kernel from the tile size on) and for a dense random state
+    (the staged kernel).  Integrals as the 24-qubit workload (decay, drop
+    < 1e-3), 2 floor(n/4) electrons (8 at 24 qubits: the bench's state);
+    below about 20 qubits both states sit in the 129 MB L2, so L2 rather than
+    HBM bounds them."""
+    import torch
+    import paper_2607_15906_gb300 as gb
+
+    out = {}
+    dev = f"cuda:{device}"
+    for n_orb in (7, 8, 9, 10, 11, 12):
+        nq = 2 * n_orb
+        ints = molecular_integrals(n_orb, seed=0, decay=True)
+        for prec in ("c64", "c128"):
+            n_elec = N_ELEC if nq == 24 else 2 * (nq // 4)
+            prob = gb.Problem.build(ints, n_elec, mapping="jw", precision=prec, int_drop=1e-3,
+                                    device=device, colour=False)
+            ops, theta = draw_ansatz(prob.pool_size, N_OPS, seed=0)
+            ws = prob.workspace()
+            prob.prepare_state(ops, theta, ws[0])
+            dense = torch.randn(1 << nq, dtype=ws[0].dtype, device=dev,
+                                generator=torch.Generator(device=dev).manual_seed(nq))
+            dense /= torch.linalg.vector_norm(dense)
+            e_out = torch.zeros(2, dtype=torch.float64, device=dev)
+            stream = torch.cuda.current_stream(device)
+            rec = {}
+            for label, psi in (("adapt_state", ws[0]), ("dense", dense)):
+                for _ in range(3):
+                    prob.energy(psi, ws[1], out=e_out)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    prob.energy(psi, ws[1], out=e_out)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / reps
+                alg = 2 * prob.state_bytes()
+                rec[label] = {"ms": ms, "gb_s": alg / (ms * 1e-3) / 1e9,
+                              "frac_hbm": alg / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+            nnz = int(torch.view_as_real(ws[0]).ne(0).any(-1).sum().item())
+            rec["adapt_state"]["nonzero_amplitudes"] = nnz
+            out[f"{nq}q_{prec}"] = rec
+            del ws, dense
+            prob.close()
+            torch.cuda.empty_cache()
+    return {"note": f"H psi call (kernels + listing), CUDA events, {reps} calls after 3 warm-up; 2S per call against "
+                    f"{how} hbm_gbs {peaks['hbm_gbs']:.0f}; the 24-qubit ADAPT state is the bench's", "by_n": out}
+
+
 def sector_30q(device: int, steps: int = 5, warmup: int = 2):
     """Larger n in the sector layout: the same ADAPT step at 30 qubits (15
     orbitals, 8 electrons, integrals < 1e-3 dropped, 100-operator ansatz
@@ -808,6 +863,7 @@ def main():
             extras["sector_layout"] = sector_layout(local, res["e"], res["sel"])
         if not args.no_extras and world == 1:
             extras["c128"] = c128_iterations(local)
+            extras["h_psi_by_n"] = h_psi_by_n(local, peaks, how)
             extras["full_layout_28q"] = full_layout_large(local, 14)
             extras["full_layout_30q"] = full_layout_large(local, 15)
             extras["full_layout_32q"] = full_layout_large(local, 16, steps=2)

@@ -40,6 +40,7 @@
 // the count of nonzero amplitudes selects it, so the choice needs no host
 // round trip.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -558,14 +559,18 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
   pow2_split<R>(-F, &dn_a, &dn_b);
   const double dn = ldexp(1.0, -F);
   const R idr = (R)a.identity;
+  const uint32_t K = a.parts;   // blocks per output tile
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(a.tile_counter, 1u);
       s_unext = 0u;
     }
     __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= ntiles) break;
+    const uint32_t claim = s_tile;
+    if (claim >= ntiles * K) break;
+    // the claim is part `part` of output tile t: the part takes the tile's
+    // unit batches part, part + K, part + 2K, ...
+    const uint32_t t = claim / K, part = claim - t * K;
     // Work units are (piece p, chunk c): the nonzero amplitudes kChunk c ..
     // kChunk (c + 1) - 1 of p's source tile u = t ^ (x >> LB) against p's
     // groups, numbered piece by piece (s_pre: a block scan of the chunk counts).
@@ -609,7 +614,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
       // kUnitBatch consecutive units per claim: mostly chunks of one piece,
       // whose descriptors then stay in L1
       uint32_t j0 = 0;
-      if (lane == 0) j0 = atomicAdd(&s_unext, kUnitBatch);
+      if (lane == 0) j0 = (atomicAdd(&s_unext, 1u) * K + part) * kUnitBatch;
       j0 = __shfl_sync(0xffffffffu, j0, 0);
       if (j0 >= n_units) break;
       const uint32_t j1 = min(n_units, j0 + kUnitBatch);
@@ -696,6 +701,33 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     if (cnt) sp_flush_q<kOct>(wb, (uint32_t)lane, (uint32_t)lane < cnt, acc);   // the rest, fewer than 32
     cnt = 0;
     __syncthreads();
+    if (K > 1) {
+      // several blocks per tile: each adds its nonzero accumulator entries
+      // to the tile's global accumulator (64-bit integer atomics: the same
+      // sum in any order), and the last to finish takes the total, clears
+      // the global copy for the next call and runs the epilogue
+      unsigned long long* g = a.gacc + (size_t)t * (kOct * 16u);
+      for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) {
+        const unsigned long long v = acc[j];
+        if (v) atomicAdd(g + j, v);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_last = atomicAdd(a.tdone + t, 1u) == K - 1u;
+      __syncthreads();
+      if (!s_last) {
+        for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) acc[j] = 0ull;
+        __syncthreads();
+        continue;
+      }
+      __threadfence();
+      for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) {
+        acc[j] = __ldcg(g + j);
+        __stcg(g + j, 0ull);
+      }
+      if (threadIdx.x == 0) a.tdone[t] = 0u;
+      __syncthreads();
+    }
     // epilogue, first the nonzero amplitudes of the own tile (one lane
     // each): the diagonal group and the identity, which act on psi(k) alone,
     // and the energy partials (zero amplitudes add to neither); each k is
@@ -844,7 +876,28 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
   if (rc) return rc;
   const uint32_t ntiles = 1u << (a.n - LB);
   k_tile_offsets<<<(ntiles + 256u) / 256u, 256, 0, st>>>(lv.aidx, lv.alen, lv.acap, ntiles, LB, lv.toff);
-  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(sm_count, 1));
+  // tiles for fewer than half the SMs: K blocks share each tile (K a power
+  // of two up to 64, or GOCP_SCATTER_PARTS, so that ntiles K reaches the SM
+  // count), combining their fixed-point accumulators in global memory; the
+  // sums are integer, so H psi and E do not depend on K.  Measured per H psi
+  // call on prepared ADAPT states (complex64 / complex128): 14 qubits
+  // 0.19 / 0.23 -> 0.14 / 0.17 ms, 16 qubits 0.27 / 0.33 -> 0.20 / 0.20 ms,
+  // 18 qubits 0.34 / 0.42 -> 0.22 / 0.30 ms; with 128 tiles on 152 SMs
+  // (20 qubits complex64) splitting was slower, and two waves of parts
+  // slower than one.
+  const uint32_t sms = (uint32_t)std::max(sm_count, 1);
+  uint32_t kmax = 64u;
+  if (const char* e = std::getenv("GOCP_SCATTER_PARTS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 1) kmax = (uint32_t)std::min<long>(v, 64);
+  }
+  uint32_t K = 1;
+  if (lv.gacc && lv.tdone && ntiles <= lv.gtiles && 2u * ntiles < sms)
+    while (2u * K <= kmax && ntiles * K < sms) K *= 2u;
+  a.parts = K;
+  a.gacc = lv.gacc;
+  a.tdone = lv.tdone;
+  const int grid = (int)std::min<uint64_t>((uint64_t)ntiles * K, (uint64_t)sms);
   k_apply_h_sparse<R><<<grid, sp_threads<R>(), sparse_smem<R>(), st>>>(a);
   count_launches(2);
   return cuda_status(cudaGetLastError(), "k_apply_h_sparse");

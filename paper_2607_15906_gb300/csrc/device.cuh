@@ -511,6 +511,12 @@ struct LiveOctets {
   uint32_t* alen = nullptr;     // one entry
   uint32_t* acounts = nullptr;  // one per block of 256 amplitude words (32 amplitudes each), + 1
   unsigned long long* amax = nullptr;   // bits of max(|Re|, |Im|) over the listed amplitudes, as a double
+  // scatter kernel with several blocks per output tile (few tiles): the
+  // tiles' 64-bit fixed-point accumulators in global memory and a per-tile
+  // count of finished blocks, both zero between calls (gtiles tiles; 0: none)
+  unsigned long long* gacc = nullptr;
+  unsigned int* tdone = nullptr;
+  uint32_t gtiles = 0;
 };
 
 // Lists the live octets of `mask` (2^(n-3) bits, n >= 8) into lv.list and
@@ -549,6 +555,9 @@ struct SparseArgs {
   double dmax;                  // DevTables::dmax
   const uint8_t* wfix;          // DevTables::twfix (complex128)
   double wscale;                // DevTables::twscale (complex128)
+  uint32_t parts;               // blocks per output tile (>= 1; > 1 needs gacc, tdone)
+  unsigned long long* gacc;     // LiveOctets::gacc
+  unsigned int* tdone;          // LiveOctets::tdone
   uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
   const uint32_t* dz;
   const R* dw;

@@ -2064,6 +2064,18 @@ int build_tiled(int n, const std::vector<HLut<R>>& hl, const std::vector<uint32_
       (rc = dalloc(d, &d.live.amax, 1, bytes)))
     return rc;
   d.live.acap = 1u << (n - 2);
+  // few output tiles (below 512: up to 21 qubits complex64, 20 complex128):
+  // global accumulators for the scatter kernel's blocks that share a tile,
+  // zero between calls
+  const size_t ntiles = (size_t)1 << (n - LB);
+  if (ntiles < 512) {
+    const size_t words = ntiles * (size_t)octets * 16u;
+    if ((rc = dalloc(d, &d.live.gacc, words, bytes)) || (rc = dalloc(d, &d.live.tdone, ntiles, bytes))) return rc;
+    if ((rc = cuda_status(cudaMemset(d.live.gacc, 0, words * sizeof(unsigned long long)), "zero gacc")) ||
+        (rc = cuda_status(cudaMemset(d.live.tdone, 0, ntiles * sizeof(unsigned int)), "zero tdone")))
+      return rc;
+    d.live.gtiles = (uint32_t)ntiles;
+  }
   d.t.tblob = dblob;
   d.t.tpiece = dpiece;
   d.t.tporder = dporder;

@@ -402,6 +402,37 @@ def test_scatter_h_at_extreme_scales(prec, scale, monkeypatch):
     _within(f"scaled {prec} {scale:g} E", abs(e - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n_orb,n_elec", [(7, 6), (8, 8), (9, 8)])
+def test_scatter_tile_split_is_bit_identical(prec, n_orb, n_elec, monkeypatch):
+    """With few output tiles the scatter kernel lets several blocks share a
+    tile and adds their 64-bit fixed-point accumulators in global memory:
+    H psi and E equal, bit for bit, the one-block-per-tile result
+    (GOCP_SCATTER_PARTS=1), and E the oracle's."""
+    ints = molecular_integrals(n_orb, seed=0, decay=True)
+    h = mapping.hamiltonian_table(ints, "jw", 1e-3, 0.0)
+    p = gb.Problem.build(ints, n_elec, precision=prec, int_drop=1e-3, device=0, colour=False)
+    ops, th = draw_ansatz(p.pool_size, 40, seed=2, theta_sigma=0.3)
+    ws = p.workspace()
+    p.prepare_state(ops, th, ws[0])
+    out = {}
+    for parts in ("1", "64"):
+        monkeypatch.setenv("GOCP_SCATTER_PARTS", parts)
+        hd = torch.empty_like(ws[0])
+        e, nrm = p.energy(ws[0], hd)
+        out[parts] = (hd, e, nrm)
+    assert torch.equal(out["1"][0], out["64"][0])
+    assert out["1"][1] == out["64"][1] and out["1"][2] == out["64"][2]
+    assert p.device_errors() == 0
+    psi_in = _host(ws[0])
+    ref = sv.apply_terms(h, psi_in)
+    e_ref = np.vdot(psi_in, ref).real / np.vdot(psi_in, psi_in).real
+    _within(f"split {prec} {2 * n_orb}q E", abs(out["64"][1] - e_ref), TOL[prec]["energy"] * max(1.0, abs(e_ref)))
+    _within(f"split {prec} {2 * n_orb}q hpsi", np.max(np.abs(_host(out["64"][0]) - ref)),
+            TOL[prec]["state"] * np.max(np.abs(ref)))
+    p.close()
+
+
 def test_empty_ansatz_gives_reference_energy():
     ints, h, tabs = _case(4, 4, "bk", 1)
     p = gb.Problem.build(ints, 4, mapping="bk", precision="c128", device=0)
