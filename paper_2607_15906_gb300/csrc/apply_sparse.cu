@@ -610,14 +610,17 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
     }
     __syncthreads();
     const uint32_t n_units = s_pre[P];
+    // kUnitBatch consecutive units per claim (mostly chunks of one piece,
+    // whose descriptors then stay in L1); one per claim when the tile has
+    // fewer than kUnitBatch units per warp of its K blocks, so that the few
+    // units of a small state do not queue behind each other on one warp
+    const uint32_t batch = n_units < kUnitBatch * (uint32_t)(NT / 32) * K ? 1u : kUnitBatch;
     for (;;) {
-      // kUnitBatch consecutive units per claim: mostly chunks of one piece,
-      // whose descriptors then stay in L1
       uint32_t j0 = 0;
-      if (lane == 0) j0 = (atomicAdd(&s_unext, 1u) * K + part) * kUnitBatch;
+      if (lane == 0) j0 = (atomicAdd(&s_unext, 1u) * K + part) * batch;
       j0 = __shfl_sync(0xffffffffu, j0, 0);
       if (j0 >= n_units) break;
-      const uint32_t j1 = min(n_units, j0 + kUnitBatch);
+      const uint32_t j1 = min(n_units, j0 + batch);
       // p = the last piece with s_pre[p] <= j0 (pieces without units share
       // their successor's start and are passed over), then advanced along
       // the batch
