@@ -557,13 +557,6 @@ __device__ __forceinline__ void chain_append(const ChainList& cl, uint32_t k, ui
   octet_set(mask, k);
 }
 
-// The pair of listed index k for mask x (lowest set bit s): its base b
-// (bit s clear) and whether k's entry computes it -- the base's entry when
-// the base is listed, else the partner's.
-__device__ __forceinline__ bool chain_pair(const ChainList& cl, uint32_t k, uint32_t x, int s, uint32_t* b) {
-  *b = ((k >> s) & 1u) ? k ^ x : k;
-  return *b == k || !chain_listed(cl, *b);
-}
 
 // Start of step j of a chain (forward: the previous step was j - 1, the
 // next is j + 1; reverse: j + 1 and j - 1): the list length at the start
@@ -662,10 +655,12 @@ __device__ void taylor_lut_body(const DevTables& tb, const int32_t* ops, const d
     if (n0 <= cl.cap) {
       for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
         const uint32_t k = cl.list[q];
-        uint32_t b;
-        if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
+        // the pair's base; untouched pairs (T = I) are passed over before
+        // the membership read, which only a touched pair needs
+        const uint32_t b = ((k >> L.s) & 1u) ? k ^ L.x : k;
         const uint32_t ph = lut_phi(L, b);
         if (rzero<R>(L.lut[ph]) && rzero<R>(L.lut[ph ^ phx])) continue;   // T = I on the pair
+        if (b != k && chain_listed(cl, b)) continue;   // the base's entry computes the pair
         C_t<R> o1, o2;
         taylor_pair<R>(L, c, b, ph, psi, o1, o2);
         const uint32_t other = b == k ? b ^ L.x : b;
@@ -824,10 +819,10 @@ __device__ void adjoint_lut_body(const DevTables& tb, const int32_t* ops, const 
     // the listed amplitudes, nonzero in psi or lambda (see taylor_lut_body)
     for (uint32_t q = bid * kThreads + threadIdx.x; q < n0; q += (uint32_t)nb * kThreads) {
       const uint32_t k = cl.list[q];
-      uint32_t b;
-      if (!chain_pair(cl, k, L.x, L.s, &b)) continue;
+      const uint32_t b = ((k >> L.s) & 1u) ? k ^ L.x : k;   // the pair's base
       const uint32_t ph = lut_phi(L, b);
       if (rzero<R>(L.lut[ph]) && rzero<R>(L.lut[ph ^ phx])) continue;   // T = I, T' = 0 on the pair
+      if (b != k && chain_listed(cl, b)) continue;   // the base's entry computes the pair
       C_t<R> o[4];
       v[0] += adjoint_pair<R>(L, c, b, ph, psi, lam, o);
       const bool base = b == k;
