@@ -84,7 +84,7 @@ int dev_taylor_chain(Problem& p, const int32_t* d_ops, int n_ops, void* psi, boo
 int dev_apply_h(Problem& p, const void* psi, void* hpsi, bool energy, cudaStream_t st);
 int dev_norm(Problem& p, const void* psi, cudaStream_t st);
 int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, bool mask_current,
-                   cudaStream_t st);
+                   bool norm_current, cudaStream_t st);
 int dev_adjoint(Problem& p, const int32_t* d_ops, int n_ops, void* psi, void* lam, double* d_dE,
                 cudaStream_t st);
 int dev_select(Problem& p, const double* d_grads, double tie_rel, int32_t* d_out, cudaStream_t st);
@@ -507,7 +507,7 @@ int gocp_pool_gradients(const gocp_problem* h, const void* psi, const void* hpsi
   DeviceGuard g(p.device);
   cudaStream_t st = (cudaStream_t)stream;
   double* dst = mem == GOCP_MEM_DEVICE ? grads : grads_ptr(p);
-  if ((rc = p.sector ? sec_pool_grads(p, psi, hpsi, dst, st) : dev_pool_grads(p, psi, hpsi, dst, false, st)))
+  if ((rc = p.sector ? sec_pool_grads(p, psi, hpsi, dst, st) : dev_pool_grads(p, psi, hpsi, dst, false, false, st)))
     return rc;
   return deliver(dst, grads, p.pool.size(), mem, st);
 }
@@ -571,7 +571,8 @@ int gocp_adapt_step(const gocp_problem* h, const int32_t* ops, const double* the
     if ((rc = dev_setup(p, psi, d_theta, n_ops, st))) return rc;
     if ((rc = dev_taylor_chain(p, d_ops, n_ops, psi, true, st))) return rc;
     if ((rc = dev_apply_h(p, psi, hpsi, true, st))) return rc;
-    if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, true, st))) return rc;   // the chain's mask
+    // the chain's octet mask, and <psi|psi> from the energy epilogue just run
+    if ((rc = dev_pool_grads(p, psi, hpsi, d_grads, true, true, st))) return rc;
   }
   int32_t* d_sel = mem == GOCP_MEM_DEVICE ? selected : selected_ptr(p);
   if ((rc = dev_select(p, d_grads, tie_rel, d_sel, st))) return rc;

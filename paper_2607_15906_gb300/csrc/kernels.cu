@@ -3122,10 +3122,14 @@ static int launch_pool_grads(Problem& p, const void* psi, const void* hpsi, doub
 
 // `mask_current`: the problem's octet mask already describes psi (a tracked
 // chain produced it); otherwise it is rebuilt from psi first.
+// `norm_current`: scalars[1] already holds <psi|psi> (the energy epilogue of
+// the H psi call just made on psi wrote it); otherwise k_norm computes it.
 int dev_pool_grads(Problem& p, const void* psi, const void* hpsi, double* d_grads, bool mask_current,
-                   cudaStream_t st) {
-  int rc = dev_norm(p, psi, st);   // <psi|psi> -> scalars[1]
-  if (rc) return rc;
+                   bool norm_current, cudaStream_t st) {
+  if (!norm_current) {
+    int rc = dev_norm(p, psi, st);   // <psi|psi> -> scalars[1]
+    if (rc) return rc;
+  }
   return p.precision == GOCP_C64 ? launch_pool_grads<float>(p, psi, hpsi, d_grads, mask_current, st)
                                  : launch_pool_grads<double>(p, psi, hpsi, d_grads, mask_current, st);
 }
