@@ -200,8 +200,10 @@ int gocp_reference_state(const gocp_problem* p, void* psi, void* stream);
  * most 128 KiB runs in one thread block over shared memory (complex64 by
  * default); the environment variable GOCP_ONCHIP_CHAINS = "off" | "block" |
  * "all" selects the grid kernels only, the one-block form, or that and a
- * thread-block cluster's shared memory for states up to 2 MiB.  Every form
- * gives the same state bit for bit. */
+ * thread-block cluster's shared memory for states up to 2 MiB.  Larger
+ * states run one launch per step, replayed as a CUDA graph whose steps are
+ * joined by programmatic dependencies (GOCP_CHAIN_PDL=0: by full
+ * completion).  Every form gives the same state bit for bit. */
 int gocp_prepare_state(const gocp_problem* p, const int32_t* ops, const double* theta, int n_ops,
                        int mem, void* psi, void* stream);
 
@@ -212,9 +214,12 @@ int gocp_taylor_step(const gocp_problem* p, int op, double theta, void* psi, voi
  * Full layout from 13 (complex64) / 12 (complex128) qubits: a state whose
  * nonzero amplitudes are at most GOCP_SPARSE_FRAC (environment, default
  * 0.125, at most 0.25; 0 = never) of 2^n goes through the scatter kernel,
- * which sums with shared-memory atomics (results reproducible to rounding,
- * not bit for bit); other states through the staged kernel (fixed order).
- * The choice is made on the device from the count of nonzero amplitudes. */
+ * which sums the products in 64-bit fixed point (integer adds: the result
+ * is the same bit for bit from run to run); other states through the
+ * staged kernel (fixed order).  The choice is made on the device from the
+ * count of nonzero amplitudes.  With few output tiles the scatter kernel
+ * lets up to 64 blocks share a tile (GOCP_SCATTER_PARTS, environment, caps
+ * that number; 1 = one block per tile); the result does not depend on it. */
 int gocp_apply_h(const gocp_problem* p, const void* psi, void* hpsi, void* stream);
 
 /* hpsi <- H psi, and out[0] = E = Re<psi|H psi>/<psi|psi> (Eq. 1),
