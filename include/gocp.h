@@ -219,7 +219,10 @@ int gocp_taylor_step(const gocp_problem* p, int op, double theta, void* psi, voi
  * staged kernel (fixed order).  The choice is made on the device from the
  * count of nonzero amplitudes.  With few output tiles the scatter kernel
  * lets up to 64 blocks share a tile (GOCP_SCATTER_PARTS, environment, caps
- * that number; 1 = one block per tile); the result does not depend on it. */
+ * that number; 1 = one block per tile); the result does not depend on it.
+ * complex64 adds each fixed-point product as two independent 32-bit
+ * counts when H has fewer than 65536 off-diagonal x-groups
+ * (GOCP_SCATTER_SPLIT=0: as one 64-bit add with a carry); same result. */
 int gocp_apply_h(const gocp_problem* p, const void* psi, void* hpsi, void* stream);
 
 /* hpsi <- H psi, and out[0] = E = Re<psi|H psi>/<psi|psi> (Eq. 1),

@@ -271,7 +271,8 @@ __device__ __forceinline__ uint32_t acc_at(uint32_t k) {
 // Adds v to the 64-bit accumulator word p as two 32-bit atomics: the low
 // word's, and the high word's plus the carry out of the low word, taken from
 // the old value that atomic returns.  The pair is exact modulo 2^64 in any
-// order of the atomics (measured faster than one 64-bit atomic).
+// order of the atomics (measured faster than one 64-bit atomic).  complex128
+// adds its products this way; complex64 uses the split form (fx_add_split).
 __device__ __forceinline__ void fx_add(unsigned long long* p, long long v) {
   uint32_t* w = reinterpret_cast<uint32_t*>(p);
   const uint32_t lo = (uint32_t)(unsigned long long)v, hi = (uint32_t)((unsigned long long)v >> 32);
@@ -302,11 +303,35 @@ __device__ __forceinline__ R fx_val(unsigned long long a) {
   return sizeof(R) == 4 ? (R)__ll2float_rn((long long)a) : (R)__ll2double_rn((long long)a);
 }
 
-template <uint32_t kOct>
+// Split form of the accumulator word (complex64, products below 2^30): its
+// low 32-bit half sums the low 16 bits of each product (0 .. 65535) and its
+// high half the product shifted right by 16 (arithmetic, |.| <= 2^14), two
+// independent atomics with no carry between them.  With fewer than 65536
+// products per word (one per off-diagonal group) neither half can wrap:
+// low < 2^16 * 65536 = 2^32, |high| < 2^30.  The word's value is
+// high * 2^16 + low, formed exactly by split_to_wide once every product has
+// been added.
+__device__ __forceinline__ void fx_add_split(unsigned long long* p, int v) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  atomicAdd(w, (uint32_t)v & 0xFFFFu);
+  atomicAdd(w + 1, (uint32_t)(v >> 16));
+}
+
+__device__ __forceinline__ unsigned long long split_to_wide(unsigned long long w) {
+  const long long high = (long long)(int)(uint32_t)(w >> 32);
+  return (unsigned long long)(high * 65536ll + (long long)(w & 0xffffffffull));
+}
+
+template <uint32_t kOct, bool SPLIT = false>
 __device__ __forceinline__ void acc_add(unsigned long long* acc, uint32_t k, long long re, long long im) {
   const uint32_t at = acc_at<kOct>(k);
-  fx_add(acc + at, re);
-  fx_add(acc + at + kOct, im);
+  if constexpr (SPLIT) {
+    fx_add_split(acc + at, (int)re);
+    fx_add_split(acc + at + kOct, (int)im);
+  } else {
+    fx_add(acc + at, re);
+    fx_add(acc + at + kOct, im);
+  }
 }
 
 // One LUT group (descriptor in global memory, read through L1 at one
@@ -314,7 +339,7 @@ __device__ __forceinline__ void acc_add(unsigned long long* acc, uint32_t k, lon
 // values vs[s] are pre-scaled by 2^F.  The entry's magnitude depends on
 // phi(k) alone (lut16[phi | 8] = -lut16[phi]), so the sign parity is taken
 // only for a nonzero entry.
-template <typename R, uint32_t kOct, int A>
+template <typename R, uint32_t kOct, int A, bool SPLIT>
 __device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint4 h0, const uint32_t v2,
                                        const uint32_t (&ks)[A], const C_t<R> (&vs)[A], const bool (&valid)[A],
                                        unsigned long long* acc) {
@@ -326,7 +351,7 @@ __device__ __forceinline__ void sp_lut(const HLut<R>* __restrict__ L, const uint
     const R d0 = __ldg(L->lut16 + phi);
     if (valid[s] && d0 != R(0)) {
       const R d = (__popc(k & h0.y) & 1) ? -d0 : d0;
-      acc_add<kOct>(acc, k, fx_prod<R>(d * vs[s].x), fx_prod<R>(d * vs[s].y));
+      acc_add<kOct, SPLIT>(acc, k, fx_prod<R>(d * vs[s].x), fx_prod<R>(d * vs[s].y));
     }
   }
 }
@@ -453,7 +478,7 @@ __device__ __forceinline__ void sp_terms_q(const TiledGroup* __restrict__ G, con
 // and D = (1 + sigma (-1)^popc(k & delta)) E(k), the factor 0 or 2.  Called
 // by every lane of the warp (the group is warp-uniform).  complex64 (complex128
 // uses sp_terms_q).
-template <typename R, uint32_t kOct, int A>
+template <typename R, uint32_t kOct, int A, bool SPLIT>
 __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const uint32_t* __restrict__ zs,
                                          const R* __restrict__ ws, const uint32_t (&ks)[A],
                                          const C_t<R> (&vs)[A], const bool (&valid)[A],
@@ -493,7 +518,8 @@ __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const
     const R f = fz[s] == 2u ? R(2) : R(1);
     const R a = dr[s] * f, b = di[s] * f;
     if (valid[s] && fz[s] != 0u && (a != R(0) || b != R(0)))
-      acc_add<kOct>(acc, k[s], fx_prod<R>(a * vs[s].x - b * vs[s].y), fx_prod<R>(a * vs[s].y + b * vs[s].x));
+      acc_add<kOct, SPLIT>(acc, k[s], fx_prod<R>(a * vs[s].x - b * vs[s].y),
+                           fx_prod<R>(a * vs[s].y + b * vs[s].x));
   }
 }
 
@@ -508,8 +534,11 @@ __device__ __forceinline__ void pow2_split(int e, R* a, R* b) {
   *b = sizeof(R) == 4 ? (R)ldexpf(1.0f, e2) : (R)ldexp(1.0, e2);
 }
 
-template <typename R>
+// SPLIT (complex64 only): products added to the accumulator in split form
+// (fx_add_split), converted to 64-bit values before the epilogue.
+template <typename R, bool SPLIT>
 __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const SparseArgs<R> a) {
+  static_assert(!SPLIT || sizeof(R) == 4, "the split accumulator takes 32-bit products");
   constexpr int LB = TiledBits<R>::LB;
   constexpr int NT = sp_threads<R>();
   constexpr int A = sp_amps<R>();             // amplitudes per lane per work unit
@@ -688,7 +717,7 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
               sp_flush_q<kOct>(wb, cnt + (uint32_t)lane, true, acc);
             }
           } else {
-            sp_lut<R, kOct, A>(ls + g, h0, v2, ks, vs, valid, acc);
+            sp_lut<R, kOct, A, SPLIT>(ls + g, h0, v2, ks, vs, valid, acc);
           }
         }
         // the term-list groups fill the blob from the LUT groups to z_off
@@ -697,13 +726,21 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
           const long long* wq = reinterpret_cast<const long long*>(reinterpret_cast<const uint8_t*>(ws) + wdelta);
           for (int g = 0; g < nt; ++g) sp_terms_q<kOct, A>(gs + g, zs, wq, ks, vqx, vqy, valid, acc);
         } else {
-          for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A>(gs + g, zs, ws, ks, vs, valid, acc);
+          for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A, SPLIT>(gs + g, zs, ws, ks, vs, valid, acc);
         }
       }
     }
     if (cnt) sp_flush_q<kOct>(wb, (uint32_t)lane, (uint32_t)lane < cnt, acc);   // the rest, fewer than 32
     cnt = 0;
     __syncthreads();
+    if constexpr (SPLIT) {
+      // every product is in: the split words become 64-bit values
+      for (uint32_t j = threadIdx.x; j < kOct * 16u; j += NT) {
+        const unsigned long long v = acc[j];
+        if (v) acc[j] = split_to_wide(v);
+      }
+      __syncthreads();
+    }
     if (K > 1) {
       // several blocks per tile: each adds its nonzero accumulator entries
       // to the tile's global accumulator (64-bit integer atomics: the same
@@ -860,6 +897,14 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
   a.aval = reinterpret_cast<const C_t<R>*>(lv.aval);
   a.alen = lv.alen;
   a.toff = lv.toff;
+  // complex64 adds its products in split form when every accumulator word
+  // takes fewer than 65536 of them (one per off-diagonal group); the two
+  // forms give the same integers, so H psi does not depend on the choice
+  // (GOCP_SCATTER_SPLIT=0 selects the carry form)
+  bool split = sizeof(R) == 4 && a.n_offdiag < 65536u;
+  if (const char* ev = std::getenv("GOCP_SCATTER_SPLIT"))
+    if (ev[0] == '0') split = false;
+  auto kern = split ? k_apply_h_sparse<R, sizeof(R) == 4> : k_apply_h_sparse<R, false>;
   static std::mutex mu;
   static std::vector<bool> done;
   int device = 0;
@@ -869,8 +914,11 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
     std::lock_guard<std::mutex> lk(mu);
     if (device >= (int)done.size()) done.resize(device + 1, false);
     if (!done[device]) {
-      e = cudaFuncSetAttribute(k_apply_h_sparse<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_apply_h_sparse<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sparse_smem<R>());
+      if (e == cudaSuccess && sizeof(R) == 4)
+        e = cudaFuncSetAttribute(k_apply_h_sparse<R, sizeof(R) == 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sparse_smem<R>());
       if (e != cudaSuccess) return cuda_status(e, "cudaFuncSetAttribute(k_apply_h_sparse)");
       done[device] = true;
     }
@@ -901,7 +949,7 @@ int sparse_apply_h(SparseArgs<R> a, const LiveOctets& lv, int sm_count, cudaStre
   a.gacc = lv.gacc;
   a.tdone = lv.tdone;
   const int grid = (int)std::min<uint64_t>((uint64_t)ntiles * K, (uint64_t)sms);
-  k_apply_h_sparse<R><<<grid, sp_threads<R>(), sparse_smem<R>(), st>>>(a);
+  kern<<<grid, sp_threads<R>(), sparse_smem<R>(), st>>>(a);
   count_launches(2);
   return cuda_status(cudaGetLastError(), "k_apply_h_sparse");
 }

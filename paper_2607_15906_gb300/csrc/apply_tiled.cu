@@ -692,6 +692,7 @@ int launch_tiled(const DevTables& t, const LiveOctets& lv, int sm_count, const v
     s.out = reinterpret_cast<C_t<R>*>(hpsi);
     s.mask = t.octmask;
     s.max_amps = max_amps;
+    s.n_offdiag = (uint32_t)(t.G + t.GL);
     s.hbound = t.hbound;
     s.dmax = t.dmax;
     s.wfix = t.twfix;

@@ -559,6 +559,7 @@ struct SparseArgs {
   unsigned long long* gacc;     // LiveOctets::gacc
   unsigned int* tdone;          // LiveOctets::tdone
   uint32_t max_amps;            // the kernel runs only when *alen <= max_amps (<= acap)
+  uint32_t n_offdiag;           // off-diagonal groups (LUT and term-list): products per accumulator word
   const uint32_t* dz;
   const R* dw;
   int nd, nd_mid;

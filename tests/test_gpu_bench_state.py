@@ -148,3 +148,28 @@ def test_bench_state_h_psi_reproducible(prec, oracle24):
             assert np.array_equal(first[3], cur[3])
     assert abs(first[1] - o["e"]) <= TOL[prec]["energy"] * max(1.0, abs(o["e"]))
     p.close()
+
+
+def test_bench_state_split_accumulator_is_bit_identical(oracle24, monkeypatch):
+    """complex64: the scatter kernel's split accumulator words (low 16 bits
+    of each product and the product shifted right by 16, summed by
+    independent atomics) give the same integers as the 64-bit words with a
+    carry between their halves (GOCP_SCATTER_SPLIT=0): H psi, E and the pool
+    gradients of the timed state are equal bit for bit."""
+    o = oracle24
+    p = gb.Problem.build(o["ints"], 8, precision="c64", int_drop=o["cfg"]["int_drop"],
+                         term_drop=o["cfg"]["term_drop"], device=0)
+    ws = p.workspace()
+    p.prepare_state(o["ops"], o["th"], ws[0])
+    out = {}
+    for split in ("1", "0"):
+        monkeypatch.setenv("GOCP_SCATTER_SPLIT", split)
+        hd = torch.empty_like(ws[0])
+        e, nrm = p.energy(ws[0], hd)
+        out[split] = (hd, e, nrm, p.pool_gradients(ws[0], hd))
+    assert torch.equal(out["1"][0], out["0"][0])
+    assert out["1"][1] == out["0"][1] and out["1"][2] == out["0"][2]
+    assert np.array_equal(out["1"][3], out["0"][3])
+    assert abs(out["1"][1] - o["e"]) <= TOL["c64"]["energy"] * max(1.0, abs(o["e"]))
+    assert p.device_errors() == 0
+    p.close()

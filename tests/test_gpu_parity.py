@@ -423,6 +423,14 @@ def test_scatter_tile_split_is_bit_identical(prec, n_orb, n_elec, monkeypatch):
         out[parts] = (hd, e, nrm)
     assert torch.equal(out["1"][0], out["64"][0])
     assert out["1"][1] == out["64"][1] and out["1"][2] == out["64"][2]
+    if prec == "c64":   # split accumulator words against the carry form, both tile splits
+        for parts in ("1", "64"):
+            monkeypatch.setenv("GOCP_SCATTER_PARTS", parts)
+            monkeypatch.setenv("GOCP_SCATTER_SPLIT", "0")
+            hd = torch.empty_like(ws[0])
+            e, nrm = p.energy(ws[0], hd)
+            monkeypatch.delenv("GOCP_SCATTER_SPLIT")
+            assert torch.equal(out["1"][0], hd) and out["1"][1] == e and out["1"][2] == nrm
     assert p.device_errors() == 0
     psi_in = _host(ws[0])
     ref = sv.apply_terms(h, psi_in)
