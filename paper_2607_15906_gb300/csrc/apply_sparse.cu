@@ -523,6 +523,32 @@ __device__ __forceinline__ void sp_terms(const TiledGroup* __restrict__ G, const
   }
 }
 
+// complex64: a work unit's walk over the piece's LUT groups, then its
+// term-list groups, for the lane's A amplitudes.  Each group's descriptor
+// (x, z0, v0, v1 and v2) is loaded while the group before it is computed.
+template <typename R, uint32_t kOct, int A, bool SPLIT>
+__device__ __forceinline__ void sp_walk(const HLut<R>* __restrict__ ls, int nl, const TiledGroup* __restrict__ gs,
+                                        int nt, const uint32_t* __restrict__ zs, const R* __restrict__ ws,
+                                        const uint32_t (&ks)[A], const C_t<R> (&vs)[A], const bool (&valid)[A],
+                                        unsigned long long* acc) {
+  uint4 h0n = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t v2n = 0u;
+  if (nl > 0) {
+    h0n = __ldg(reinterpret_cast<const uint4*>(&ls[0].x));
+    v2n = __ldg(&ls[0].v2);
+  }
+  for (int g = 0; g < nl; ++g) {
+    const uint4 h0 = h0n;
+    const uint32_t v2 = v2n;
+    if (g + 1 < nl) {
+      h0n = __ldg(reinterpret_cast<const uint4*>(&ls[g + 1].x));
+      v2n = __ldg(&ls[g + 1].v2);
+    }
+    sp_lut<R, kOct, A, SPLIT>(ls + g, h0, v2, ks, vs, valid, acc);
+  }
+  for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A, SPLIT>(gs + g, zs, ws, ks, vs, valid, acc);
+}
+
 // 2^e as R, for |e| beyond one float exponent split in two factors.
 template <typename R>
 __device__ __forceinline__ void pow2_split(int e, R* a, R* b) {
@@ -693,22 +719,24 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
           }
         }
         const int nl = (int)hd.y;
-        // each group's descriptor (x, z0, v0, v1 and v2) is loaded while the
-        // group before it is computed
-        uint4 h0n = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t v2n = 0u;
-        if (nl > 0) {
-          h0n = __ldg(reinterpret_cast<const uint4*>(&ls[0].x));
-          v2n = __ldg(&ls[0].v2);
-        }
-        for (int g = 0; g < nl; ++g) {
-          const uint4 h0 = h0n;
-          const uint32_t v2 = v2n;
-          if (g + 1 < nl) {
-            h0n = __ldg(reinterpret_cast<const uint4*>(&ls[g + 1].x));
-            v2n = __ldg(&ls[g + 1].v2);
+        // the term-list groups fill the blob from the LUT groups to z_off
+        const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
+        if constexpr (sizeof(R) == 8) {
+          // each group's descriptor (x, z0, v0, v1 and v2) is loaded while
+          // the group before it is computed
+          uint4 h0n = make_uint4(0u, 0u, 0u, 0u);
+          uint32_t v2n = 0u;
+          if (nl > 0) {
+            h0n = __ldg(reinterpret_cast<const uint4*>(&ls[0].x));
+            v2n = __ldg(&ls[0].v2);
           }
-          if constexpr (sizeof(R) == 8) {
+          for (int g = 0; g < nl; ++g) {
+            const uint4 h0 = h0n;
+            const uint32_t v2 = v2n;
+            if (g + 1 < nl) {
+              h0n = __ldg(reinterpret_cast<const uint4*>(&ls[g + 1].x));
+              v2n = __ldg(&ls[g + 1].v2);
+            }
             const long long* lq = reinterpret_cast<const long long*>(
                 reinterpret_cast<const uint8_t*>(ls[g].lut16) + wdelta);
             sp_lut_q<kOct, A>(lq, h0, v2, ks, vqx, vqy, valid, wb, cnt, lt);
@@ -716,17 +744,19 @@ __global__ void __launch_bounds__(sp_threads<R>(), 1) k_apply_h_sparse(const Spa
               cnt -= 32u;
               sp_flush_q<kOct>(wb, cnt + (uint32_t)lane, true, acc);
             }
-          } else {
-            sp_lut<R, kOct, A, SPLIT>(ls + g, h0, v2, ks, vs, valid, acc);
           }
-        }
-        // the term-list groups fill the blob from the LUT groups to z_off
-        const int nt = (int)((hd.z - sizeof(TiledHead) - nl * sizeof(HLut<R>)) / sizeof(TiledGroup));
-        if constexpr (sizeof(R) == 8) {
           const long long* wq = reinterpret_cast<const long long*>(reinterpret_cast<const uint8_t*>(ws) + wdelta);
           for (int g = 0; g < nt; ++g) sp_terms_q<kOct, A>(gs + g, zs, wq, ks, vqx, vqy, valid, acc);
+        } else if (A > 1 && a0 + kChunk * c + 32u >= a1) {
+          // the unit's amplitudes fill the first lane slot at most (the last
+          // chunk of a source tile): the groups are walked for that slot
+          // alone instead of issuing the empty slots with every lane idle
+          const uint32_t ks1[1] = {ks[0]};
+          const C_t<R> vs1[1] = {vs[0]};
+          const bool valid1[1] = {valid[0]};
+          sp_walk<R, kOct, 1, SPLIT>(ls, nl, gs, nt, zs, ws, ks1, vs1, valid1, acc);
         } else {
-          for (int g = 0; g < nt; ++g) sp_terms<R, kOct, A, SPLIT>(gs + g, zs, ws, ks, vs, valid, acc);
+          sp_walk<R, kOct, A, SPLIT>(ls, nl, gs, nt, zs, ws, ks, vs, valid, acc);
         }
       }
     }

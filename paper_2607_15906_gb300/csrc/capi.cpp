@@ -640,6 +640,6 @@ int gocp_profile_read(int kind, int64_t* launches, double* total_ms) {
 const char* gocp_last_error(void) { return t_last_error.c_str(); }
 int64_t gocp_launch_count(void) { return g_launches.load(); }
 // The k_apply_h revision names the kernel that profiles/traffic.json was measured on.
-const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h_tiled=tiled-tma-r12; k_apply_h_sparse=scatter-fixed-r17; chain=amp-list-ring-4; onchip=smem-chain-2; sector=pair-lists-csr-1; chains=graphs-pdl-2; grads=nonzero-amps-2)"; }
+const char* gocp_version(void) { return "gocp-gb300 0.2 (sm_103a; k_apply_h_tiled=tiled-tma-r12; k_apply_h_sparse=scatter-fixed-r18; chain=amp-list-ring-4; onchip=smem-chain-2; sector=pair-lists-csr-1; chains=graphs-pdl-2; grads=nonzero-amps-2)"; }
 
 }  // extern "C"
